@@ -1,0 +1,218 @@
+"""Seeded synthetic workloads: box hierarchies, initial-data parameters, noise.
+
+This module holds geometry and seeded random inputs only -- none of the
+method's arithmetic.  Both the CUDA path and the CPU oracle are fed from here.
+
+Workloads (cell-centred grids, refinement factor 2, 3 ghost cells):
+  * ``standing_wave_2level(n)``: periodic [0,1)^3, level 0 n^3, one fine box
+    over [0.25,0.75]^3; u = sin(2 pi x) sin(2 pi y) sin(2 pi z), Pi = 0.
+  * ``gaussian_3level(n, seed)``: periodic [0,1)^3, 3 levels; levels 1 and 2
+    are unions of 6-20 uneven seeded boxes (edges 8-24 cells at n = 64, scaled
+    with n); Gaussian pulse (amplitude 1, width 0.05, centre) plus smooth
+    seeded noise of total amplitude 1e-3 (8 Fourier modes, |k| <= 4).
+  * ``bl_7level()``: Z4c, [-32,32]^3, 7 nested levels, level 0 64^3 (h = 1),
+    finest h = 1/64; Brill-Lindquist punctures m = 0.5 at z = +-1.
+  * ``bl_3level(n, m1, m2, sep)``: small Z4c hierarchy for parity and serving.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Tuple
+
+import numpy as np
+
+Box = Tuple[Tuple[int, int, int], Tuple[int, int, int]]
+
+WAVE, Z4C = 0, 1
+BC_PERIODIC, BC_RADIATIVE = 0, 1
+ID_STANDING_WAVE, ID_GAUSSIAN, ID_BRILL_LINDQUIST, ID_MINKOWSKI, ID_SPHERICAL_GAUSSIAN = 0, 1, 2, 3, 4
+
+
+@dataclass
+class Hierarchy:
+    system: int
+    boxes: List[List[Box]]
+    ncells0: Tuple[int, int, int]
+    origin: Tuple[float, float, float]
+    h0: float
+    bc: int = BC_PERIODIC
+    cfl: float = 0.25
+    subcycle: bool = True
+    kappa1: float = 0.02
+    kappa2: float = 0.0
+    eta: float = 2.0
+    ko_sigma: float = 0.3
+    id_kind: int = ID_STANDING_WAVE
+    id_params: List[float] = field(default_factory=list)
+    name: str = ""
+
+    @property
+    def nlevels(self) -> int:
+        return len(self.boxes)
+
+    def interior_cells(self, level: int) -> int:
+        return sum((hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) for lo, hi in self.boxes[level])
+
+    def zone_updates_per_coarse_step(self) -> Tuple[float, float]:
+        """(finest-equivalent, actual) cell updates of one coarse step."""
+        L = self.nlevels
+        fin = float(2 ** (L - 1) * sum(self.interior_cells(l) for l in range(L)))
+        if self.subcycle:
+            act = float(sum(2 ** l * self.interior_cells(l) for l in range(L)))
+        else:
+            act = fin
+        return fin, act
+
+    def nfields(self) -> int:
+        return 2 if self.system == WAVE else 22
+
+    def cell_centres(self, level: int, box: int, ghosted: bool = False):
+        lo, hi = self.boxes[level][box]
+        h = self.h0 / 2 ** level
+        g = 3 if ghosted else 0
+        ax = [self.origin[d] + (np.arange(lo[d] - g, hi[d] + 1 + g) + 0.5) * h for d in range(3)]
+        Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        return X, Y, Z
+
+    def kwargs(self) -> dict:
+        return dict(bc=self.bc, cfl=self.cfl, subcycle=self.subcycle, kappa1=self.kappa1,
+                    kappa2=self.kappa2, eta=self.eta, ko_sigma=self.ko_sigma)
+
+
+def cube(lo: int, n: int) -> Box:
+    return ((lo, lo, lo), (lo + n - 1, lo + n - 1, lo + n - 1))
+
+
+def split_uniform(box: Box, parts: Tuple[int, int, int]) -> List[Box]:
+    """Split a box into parts[d] pieces per dimension (even-sized, for alignment)."""
+    (lo, hi) = box
+    cuts = []
+    for d in range(3):
+        n = hi[d] - lo[d] + 1
+        p = parts[d]
+        sizes = [2 * ((n // 2) // p + (1 if q < (n // 2) % p else 0)) for q in range(p)]
+        edges = [lo[d]]
+        for s in sizes:
+            edges.append(edges[-1] + s)
+        cuts.append(edges)
+    out = []
+    for k in range(parts[2]):
+        for j in range(parts[1]):
+            for i in range(parts[0]):
+                out.append(((cuts[0][i], cuts[1][j], cuts[2][k]),
+                            (cuts[0][i + 1] - 1, cuts[1][j + 1] - 1, cuts[2][k + 1] - 1)))
+    return out
+
+
+def random_split(box: Box, rng: np.random.Generator, min_edge: int, max_edge: int,
+                 scale: int = 1) -> List[Box]:
+    """Seeded split of a box into a tensor grid of uneven boxes: each dimension
+    is cut into 2 or 3 even-sized pieces with edges in [min_edge, max_edge]
+    (at the base resolution; every edge is then multiplied by scale).  The
+    number of boxes is 8, 12 or 18."""
+    (lo, hi) = box
+    n = [(hi[d] - lo[d] + 1) // scale for d in range(3)]
+    nparts = [(2, 2, 2), (2, 2, 3), (2, 3, 3)][rng.integers(3)]
+    nparts = tuple(np.array(nparts)[rng.permutation(3)])
+    edges = []
+    for d in range(3):
+        for _ in range(10000):
+            sizes = 2 * rng.integers(min_edge // 2, max_edge // 2 + 1, size=nparts[d] - 1)
+            last = n[d] - int(sizes.sum())
+            if min_edge <= last <= max_edge and last % 2 == 0:
+                sizes = list(sizes) + [last]
+                break
+        else:
+            raise RuntimeError("random_split: no admissible partition")
+        e = [lo[d]]
+        for sz in sizes:
+            e.append(int(e[-1] + int(sz) * scale))
+        edges.append(e)
+    out = []
+    for k in range(nparts[2]):
+        for j in range(nparts[1]):
+            for i in range(nparts[0]):
+                out.append(((edges[0][i], edges[1][j], edges[2][k]),
+                            (edges[0][i + 1] - 1, edges[1][j + 1] - 1, edges[2][k + 1] - 1)))
+    return out
+
+
+def standing_wave_2level(n: int = 32, subcycle: bool = True) -> Hierarchy:
+    """Periodic [0,1)^3, level 0 n^3, fine box over [0.25,0.75]^3."""
+    return Hierarchy(system=WAVE, boxes=[[cube(0, n)], [cube(n // 2, n)]], ncells0=(n, n, n),
+                     origin=(0.0, 0.0, 0.0), h0=1.0 / n, subcycle=subcycle,
+                     id_kind=ID_STANDING_WAVE, id_params=[1.0, 1.0, 1.0, 1.0],
+                     name=f"wave standing 2-level {n}^3 + fine {n}^3")
+
+
+def gaussian_3level(n: int = 64, seed: int = 0, subcycle: bool = True) -> Hierarchy:
+    """Periodic [0,1)^3, 3 levels; level 0 is a 3x3x3 uneven split of n^3."""
+    s = n // 64
+    assert s >= 1 and n % 64 == 0
+    rng = np.random.default_rng(seed)
+    l0 = split_uniform(cube(0, n), (3, 3, 3))
+    l1 = random_split(cube(40 * s, 48 * s), rng, 8, 24, scale=s)
+    l2 = random_split(cube(104 * s, 48 * s), rng, 8, 24, scale=s)
+    return Hierarchy(system=WAVE, boxes=[l0, l1, l2], ncells0=(n, n, n), origin=(0.0, 0.0, 0.0),
+                     h0=1.0 / n, subcycle=subcycle, id_kind=ID_GAUSSIAN,
+                     id_params=[1.0, 0.05, 0.5, 0.5, 0.5], name=f"wave gaussian 3-level {n}^3 seed {seed}")
+
+
+def noise_modes(seed: int, nmodes: int = 8, kmax: int = 4, total_amplitude: float = 1e-3):
+    """Seeded smooth noise: integer wave vectors with |k| <= kmax, phases,
+    amplitudes summing to total_amplitude."""
+    rng = np.random.default_rng(10_000 + seed)
+    ks = []
+    while len(ks) < nmodes:
+        k = rng.integers(-kmax, kmax + 1, size=3)
+        if 0 < np.linalg.norm(k) <= kmax:
+            ks.append(k)
+    amps = rng.random(nmodes)
+    amps *= total_amplitude / amps.sum()
+    phases = rng.random(nmodes) * 2 * np.pi
+    return np.array(ks), amps, phases
+
+
+def noise_field(X, Y, Z, seed: int) -> np.ndarray:
+    ks, amps, phases = noise_modes(seed)
+    out = np.zeros_like(X)
+    for k, a, p in zip(ks, amps, phases):
+        out += a * np.sin(2 * np.pi * (k[0] * X + k[1] * Y + k[2] * Z) + p)
+    return out
+
+
+def bl_7level(ko_sigma: float = 0.3) -> Hierarchy:
+    """Z4c 7-level box-in-box hierarchy over [-32,32]^3 (level 0: 64^3, h = 1)."""
+    def rng_cells(a, b, l):
+        h = 1.0 / 2 ** l
+        return int(round((a + 32) / h)), int(round((b + 32) / h)) - 1
+
+    def box(l, xr, yr, zr):
+        xs, ys, zs = rng_cells(*xr, l), rng_cells(*yr, l), rng_cells(*zr, l)
+        return ((xs[0], ys[0], zs[0]), (xs[1], ys[1], zs[1]))
+
+    levels = [
+        [box(0, (-32, 32), (-32, 32), (-32, 32))],
+        [box(1, (-16, 16), (-16, 16), (-16, 16))],
+        [box(2, (-8, 8), (-8, 8), (-8, 8))],
+        [box(3, (-4, 4), (-4, 4), (-4, 4))],
+        [box(4, (-2, 2), (-2, 2), (-3, 3))],
+        [box(5, (-1, 1), (-1, 1), (-2, 2))],
+        [box(6, (-0.5, 0.5), (-0.5, 0.5), (-1.5, -0.5)), box(6, (-0.5, 0.5), (-0.5, 0.5), (0.5, 1.5))],
+    ]
+    return Hierarchy(system=Z4C, boxes=levels, ncells0=(64, 64, 64), origin=(-32.0, -32.0, -32.0), h0=1.0,
+                     bc=BC_RADIATIVE, kappa1=0.02, kappa2=0.0, eta=2.0, ko_sigma=ko_sigma,
+                     id_kind=ID_BRILL_LINDQUIST, id_params=[0.5, 0.0, 0.0, 1.0, 0.5, 0.0, 0.0, -1.0],
+                     name="z4c BL 7-level 64^3 over [-32,32]^3, finest h=1/64")
+
+
+def bl_3level(n: int = 24, m1: float = 0.5, m2: float = 0.5, sep: float = 2.0, L: float = 8.0) -> Hierarchy:
+    """Small Z4c hierarchy: [-L,L]^3, level 0 n^3, levels 1/2 cubes of n cells
+    centred on the origin (n >= 20 for proper nesting); BL punctures on the z
+    axis."""
+    assert n % 4 == 0 and n >= 20
+    return Hierarchy(system=Z4C, boxes=[[cube(0, n)], [cube(n - n // 2, n)], [cube(2 * n - n // 2, n)]],
+                     ncells0=(n, n, n), origin=(-L, -L, -L), h0=2 * L / n, bc=BC_RADIATIVE,
+                     id_kind=ID_BRILL_LINDQUIST,
+                     id_params=[m1, 0.0, 0.0, sep / 2, m2, 0.0, 0.0, -sep / 2],
+                     name=f"z4c BL 3-level {n}^3 over [-{L},{L}]^3")

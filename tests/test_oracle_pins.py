@@ -1,0 +1,449 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+Each test names what it pins.  Nothing here compares the oracle with itself
+or retypes one of its formulas: the checks are closed forms (RK4 weights),
+exactness on polynomial/nilpotent cases, exact PDE solutions, measured
+convergence orders, and structural identities (split boxes, full coverage).
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from paper_2503_09629_gb300 import workloads as W
+
+
+def make(orc, h, **over):
+    kw = h.kwargs()
+    kw.update(over)
+    return orc.Oracle(h.system, h.boxes, h.ncells0, h.origin, h.h0, **kw)
+
+
+# ---------------------------------------------------------------- dense output
+def test_dense_output_weights_reduce_to_rk4(orc):
+    """Sec. II: at theta = 1 dense output must reproduce Eq. rk5 (1/6,1/3,1/3,1/6);
+    at theta = 0 it must vanish; sum_i b_i(theta) = theta (consistency)."""
+    np.testing.assert_allclose(orc.dense_b(1.0), [1 / 6, 1 / 3, 1 / 3, 1 / 6], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(orc.dense_b(0.0), [0, 0, 0, 0], atol=0)
+    for th in np.linspace(0, 1, 11):
+        assert abs(orc.dense_b(th).sum() - th) < 1e-15
+    # first derivative at theta = 0 is k1 (y' = f(y_n))
+    np.testing.assert_allclose(orc.dense_b(0.0, 1), [1, 0, 0, 0], atol=0)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_dense_output_derivatives_are_derivatives(orc, m):
+    """Eq. denseoutput2 uses d^m b_i / d theta^m: check against a centred
+    difference of the (m-1)-th derivative."""
+    eps = 1e-5
+    for th in (0.1, 0.37, 0.5, 0.8):
+        num = (orc.dense_b(th + eps, m - 1) - orc.dense_b(th - eps, m - 1)) / (2 * eps)
+        np.testing.assert_allclose(orc.dense_b(th, m), num, atol=1e-8)
+    np.testing.assert_allclose(orc.dense_b(0.3, 4), 0, atol=0)
+
+
+def _rk4_stages(L, y, H):
+    k1 = L @ y
+    k2 = L @ (y + H / 2 * k1)
+    k3 = L @ (y + H / 2 * k2)
+    k4 = L @ (y + H * k3)
+    return np.stack([k1, k2, k3, k4])
+
+
+def _fine_stages(L, y, h):
+    Y1 = y
+    Y2 = y + h / 2 * (L @ Y1)
+    Y3 = y + h / 2 * (L @ Y2)
+    Y4 = y + h * (L @ Y3)
+    return [Y1, Y2, Y3, Y4]
+
+
+def _recon(orc, yn, K, H, th0, which):
+    return np.array([orc.amr_value(yn[c], K[:, c], H, th0, which) for c in range(len(yn))])
+
+
+@pytest.mark.parametrize("theta0", [0.0, 0.5])
+def test_taylor_stages_exact_for_nilpotent_system(orc, theta0):
+    """Eqs. Y1-Y4 with dense output (Eqs. denseoutput1/2): for y' = L y with
+    L^4 = 0 the solution is a cubic in t, so dense output is exact and the
+    reconstructed stage states must equal the true fine RK4 stages exactly
+    (fine step h = H/2, f_y y'' = 4 (k3 - k2) / H^2 with the parent step H)."""
+    rng = np.random.default_rng(1)
+    L = np.diag(rng.uniform(0.5, 2.0, 3), 1)  # 4x4 Jordan-type, L^4 = 0
+    yn = rng.normal(size=4)
+    H = 0.37
+    K = _rk4_stages(L, yn, H)
+    y0 = scipy.linalg.expm(theta0 * H * L) @ yn
+    true = _fine_stages(L, y0, H / 2)
+    for i in range(4):
+        got = _recon(orc, yn, K, H, theta0, i + 1)
+        np.testing.assert_allclose(got, true[i], rtol=1e-13, atol=1e-13)
+    end = scipy.linalg.expm((theta0 + 0.5) * H * L) @ yn
+    np.testing.assert_allclose(_recon(orc, yn, K, H, theta0, 0), end, rtol=1e-13, atol=1e-13)
+
+
+def test_taylor_stages_fourth_order_for_general_system(orc):
+    """For a general linear system the reconstruction error of the stage
+    states is O(H^4) (the dense output is 4th order, Eq. denseoutput1)."""
+    rng = np.random.default_rng(2)
+    L = rng.normal(size=(5, 5))
+    yn = rng.normal(size=5)
+    errs = []
+    for H in (0.1, 0.05, 0.025):
+        e = 0.0
+        for th0 in (0.0, 0.5):
+            K = _rk4_stages(L, yn, H)
+            true = _fine_stages(L, scipy.linalg.expm(th0 * H * L) @ yn, H / 2)
+            for i in range(4):
+                e = max(e, np.abs(_recon(orc, yn, K, H, th0, i + 1) - true[i]).max())
+        errs.append(e)
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 3.7), orders
+
+
+# ------------------------------------------------------- prolongation/restriction
+def _poly(X, Y, Z, coef):
+    out = np.zeros_like(X)
+    for (a, b, c), v in coef.items():
+        out += v * X ** a * Y ** b * Z ** c
+    return out
+
+
+def _two_level_box():
+    # non-periodic cube, level 0 24^3, one fine box of 24^3 in the middle
+    return W.Hierarchy(system=W.WAVE, boxes=[[W.cube(0, 24)], [W.cube(12, 24)]], ncells0=(24, 24, 24),
+                       origin=(0.0, 0.0, 0.0), h0=1.0 / 24, bc=2)
+
+
+@pytest.mark.parametrize("deg_ok", [True, False])
+def test_prolongation_reproduces_quintics(orc, deg_ok):
+    """Prolongation (Sec. II step 2, Fig. 1), quintic Lagrange per dimension:
+    exact for every tensor polynomial of degree <= 5 per dimension, not for
+    degree 6."""
+    h = _two_level_box()
+    o = make(orc, h)
+    rng = np.random.default_rng(3)
+    if deg_ok:
+        coef = {(a, b, c): rng.normal() for a in range(6) for b in range(6) for c in range(6)}
+    else:
+        coef = {(6, 0, 0): 1.0, (0, 1, 2): 0.5}
+    X, Y, Z = h.cell_centres(0, 0, ghosted=True)
+    for f in range(2):
+        o.set_vector(0, 0, orc.V_YOLD, f, _poly(X, Y, Z, coef))
+        for j in range(4):
+            o.set_vector(0, 0, orc.V_K1 + j, f, np.zeros_like(X))
+    o.prolong(1)
+    o.fill_amr(1, orc.V_STAGE, 0.0, 1)
+    Xf, Yf, Zf = h.cell_centres(1, 0, ghosted=True)
+    exact = _poly(Xf, Yf, Zf, coef)
+    got = o.get_vector(1, 0, orc.V_STAGE, 0)
+    ghost = np.ones_like(got, dtype=bool)
+    ghost[3:-3, 3:-3, 3:-3] = False
+    err = np.abs(got - exact)[ghost].max() / np.abs(exact).max()
+    if deg_ok:
+        assert err < 1e-13, err
+    else:
+        assert err > 1e-10, err
+
+
+@pytest.mark.parametrize("deg_ok", [True, False])
+def test_restriction_reproduces_quintics(orc, deg_ok):
+    """Restriction (Sec. II step 7) onto the parent cells under the fine box,
+    quintic Lagrange per dimension: exact for tensor polynomials of degree
+    <= 5, not for degree 6; other parent cells untouched."""
+    h = _two_level_box()
+    o = make(orc, h)
+    rng = np.random.default_rng(4)
+    coef = ({(a, b, c): rng.normal() for a in range(6) for b in range(6) for c in range(6)}
+            if deg_ok else {(0, 6, 0): 1.0})
+    Xf, Yf, Zf = h.cell_centres(1, 0, ghosted=True)
+    o.set_field(1, 0, 0, _poly(Xf, Yf, Zf, coef), ghosted=True)
+    o.set_field(1, 0, 1, _poly(Xf, Yf, Zf, coef), ghosted=True)
+    o.restrict(1)
+    X, Y, Z = h.cell_centres(0, 0)
+    got = o.get_field(0, 0, 0)
+    exact = _poly(X, Y, Z, coef)
+    inner = np.zeros_like(got, dtype=bool)
+    inner[6:18, 6:18, 6:18] = True
+    err = np.abs(got - exact)[inner].max() / np.abs(exact[inner]).max()
+    assert np.all(got[~inner] == 0.0)
+    if deg_ok:
+        assert err < 1e-13, err
+    else:
+        assert err > 1e-10, err
+
+
+# ------------------------------------------------------------- finite differences
+def test_wave_rhs_exact_on_quintics(orc):
+    """Sec. IV.A with 4th-order centred differences: the discrete Laplacian
+    is exact on polynomials of degree <= 5 and not on degree 6."""
+    h = W.Hierarchy(system=W.WAVE, boxes=[[W.cube(0, 8)]], ncells0=(8, 8, 8), origin=(0.2, -0.1, 0.3),
+                    h0=0.1, bc=2)
+    o = make(orc, h)
+    X, Y, Z = h.cell_centres(0, 0, ghosted=True)
+    u = X ** 5 + 2 * X ** 2 * Y ** 3 - Y * Z ** 4 + 3 * Z ** 2
+    lap = 20 * X ** 3 + 4 * Y ** 3 + 12 * X ** 2 * Y - 12 * Y * Z ** 2 + 6
+    pi = np.sin(X) * Y
+    rhs = o.rhs_box(0, 0, np.stack([u, pi]))
+    s = (slice(3, -3),) * 3
+    np.testing.assert_allclose(rhs[0][s], pi[s], rtol=0, atol=0)
+    np.testing.assert_allclose(rhs[1][s], lap[s], rtol=1e-10, atol=1e-10)
+    u6 = X ** 6
+    rhs6 = o.rhs_box(0, 0, np.stack([u6, pi]))
+    assert np.abs(rhs6[1][s] - 30 * X[s] ** 4).max() > 1e-4
+
+
+# --------------------------------------------------------- end-to-end exactness
+def _cubic_wave_solution(rng):
+    """u0, Pi0 of total degree 3: Delta^2 = 0, so the semi-discrete system is
+    nilpotent (L^4 = 0) and RK4 is exact in time."""
+    mons = [(a, b, c) for a in range(4) for b in range(4) for c in range(4) if a + b + c <= 3]
+    cu = {m: rng.normal() for m in mons}
+    cp = {m: rng.normal() for m in mons}
+
+    def lap(coef):
+        out = {}
+        for (a, b, c), v in coef.items():
+            for d, e in enumerate((a, b, c)):
+                if e >= 2:
+                    m = [a, b, c]
+                    m[d] -= 2
+                    out[tuple(m)] = out.get(tuple(m), 0.0) + v * e * (e - 1)
+        return out
+
+    lu, lp = lap(cu), lap(cp)
+
+    def state(t, X, Y, Z):
+        u = _poly(X, Y, Z, cu) + t * _poly(X, Y, Z, cp) + t ** 2 / 2 * _poly(X, Y, Z, lu) + t ** 3 / 6 * _poly(X, Y, Z, lp)
+        p = _poly(X, Y, Z, cp) + t * _poly(X, Y, Z, lu) + t ** 2 / 2 * _poly(X, Y, Z, lp)
+        lapu = _poly(X, Y, Z, lu) + t * _poly(X, Y, Z, lp)
+        lapp = _poly(X, Y, Z, lp)
+        return u, p, lapu, lapp
+
+    return state
+
+
+@pytest.mark.parametrize("nlev", [2, 3])
+def test_subcycling_exact_for_cubic_wave(orc, nlev):
+    """Whole algorithm of Sec. II (dense output, Taylor stages, prolongation,
+    restriction, recursion) on a problem where every approximation is exact:
+    the subcycled run must reproduce the exact solution to roundoff."""
+    boxes = [[W.cube(0, 24)], [W.cube(12, 24)], [W.cube(36, 24)]][:nlev]
+    h = W.Hierarchy(system=W.WAVE, boxes=boxes, ncells0=(24, 24, 24), origin=(-0.75, -0.75, -0.75),
+                    h0=1.0 / 16, bc=2)
+    o = make(orc, h)
+    state = _cubic_wave_solution(np.random.default_rng(5))
+
+    def bc(which, t_n, dt, xyz):
+        X, Y, Z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+        if which == 0:
+            u, p, _, _ = state(t_n + dt, X, Y, Z)
+            return np.stack([u, p])
+        u, p, lu, lp = state(t_n, X, Y, Z)
+        # y, y' = L y, y'' = L^2 y, y''' = L^3 y for L(u, Pi) = (Pi, Lap u)
+        y0 = np.stack([u, p]); y1 = np.stack([p, lu]); y2 = np.stack([lu, lp]); y3 = np.stack([lp, 0 * lp])
+        return {1: y0, 2: y0 + dt / 2 * y1, 3: y0 + dt / 2 * y1 + dt ** 2 / 4 * y2,
+                4: y0 + dt * y1 + dt ** 2 / 2 * y2 + dt ** 3 / 4 * y3}[which]
+
+    o.set_bc_callback(bc)
+    for l in range(nlev):
+        X, Y, Z = h.cell_centres(l, 0, ghosted=True)
+        u, p, _, _ = state(0.0, X, Y, Z)
+        o.set_field(l, 0, 0, u, ghosted=True)
+        o.set_field(l, 0, 1, p, ghosted=True)
+    o.advance(3)
+    t = o.time
+    assert abs(t - 3 * 0.25 / 16) < 1e-15
+    for l in range(nlev):
+        X, Y, Z = h.cell_centres(l, 0)
+        u, p, _, _ = state(t, X, Y, Z)
+        for f, ex in enumerate((u, p)):
+            err = np.abs(o.get_field(l, 0, f) - ex).max() / np.abs(ex).max()
+            assert err < 1e-12, (l, f, err)
+
+
+# ------------------------------------------------------------------- convergence
+def _standing_wave_error(orc, n, subcycle=True, t_end=0.125):
+    h = W.standing_wave_2level(n, subcycle=subcycle)
+    o = make(orc, h)
+    o.set_initial_data(h.id_kind, h.id_params)
+    nsteps = int(round(t_end / (h.cfl * h.h0)))
+    o.advance(nsteps)
+    om = 2 * np.sqrt(3) * np.pi
+    err = 0.0
+    fields = []
+    for l in range(2):
+        X, Y, Z = h.cell_centres(l, 0)
+        s = np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y) * np.sin(2 * np.pi * Z)
+        u = o.get_field(l, 0, 0)
+        err = max(err, np.abs(u - s * np.cos(om * o.time)).max())
+        fields.append(u)
+    return err, fields
+
+
+@pytest.fixture(scope="module")
+def standing_runs(orc):
+    out = {}
+    for n in (12, 24, 48):
+        out[(n, True)] = _standing_wave_error(orc, n, True)
+        out[(n, False)] = _standing_wave_error(orc, n, False)
+    return out
+
+
+def test_standing_wave_fourth_order(standing_runs):
+    """Sec. IV.A (Fig. 2): errors against the exact standing wave
+    cos(2 sqrt(3) pi t) sin sin sin converge at 4th order (4 +- 0.2)."""
+    e = [standing_runs[(n, True)][0] for n in (12, 24, 48)]
+    order = np.log2(e[1] / e[2])
+    assert abs(order - 4.0) <= 0.2, (e, order)
+    assert e[2] < 1e-5
+
+
+def test_subcycled_matches_uniform_step(standing_runs):
+    """Sec. IV.A (Fig. 2): the uniform-time-step run also converges at 4th
+    order against the exact solution, and subcycled and uniform runs agree
+    to within truncation error: their difference shrinks with resolution and
+    stays below the error of either run against the exact solution."""
+    e = [standing_runs[(n, False)][0] for n in (12, 24, 48)]
+    order = np.log2(e[1] / e[2])
+    assert abs(order - 4.0) <= 0.2, (e, order)
+    d = []
+    for n in (12, 24, 48):
+        a = standing_runs[(n, True)][1]
+        b = standing_runs[(n, False)][1]
+        d.append(max(np.abs(x - y).max() for x, y in zip(a, b)))
+        assert d[-1] < standing_runs[(n, True)][0]
+        assert d[-1] < standing_runs[(n, False)][0]
+    assert d[0] > d[1] > d[2]
+    assert np.log2(d[1] / d[2]) > 2.8, d
+
+
+# ----------------------------------------------------------- structural identity
+def test_split_boxes_bitwise(orc):
+    """A level split into several boxes evolves bitwise like one box (ghost
+    exchange between siblings replaces the missing neighbours exactly)."""
+    one = W.standing_wave_2level(16)
+    many = W.Hierarchy(system=W.WAVE, boxes=[W.split_uniform(W.cube(0, 16), (2, 3, 2)),
+                                             W.split_uniform(W.cube(8, 16), (2, 2, 3))],
+                       ncells0=(16, 16, 16), origin=(0.0, 0.0, 0.0), h0=1.0 / 16)
+    a = make(orc, one)
+    b = make(orc, many)
+    for o in (a, b):
+        o.set_initial_data(W.ID_STANDING_WAVE, [1.0, 1.0, 2.0, 1.0])
+        o.advance(3)
+    for l in range(2):
+        full = a.get_field(l, 0, 0)
+        for bi, (lo, hi) in enumerate(many.boxes[l]):
+            blo = one.boxes[l][0][0]
+            sl = tuple(slice(lo[d] - blo[d], hi[d] - blo[d] + 1) for d in (2, 1, 0))
+            assert np.array_equal(b.get_field(l, bi, 0), full[sl])
+
+
+def test_full_cover_fine_level_equals_single_level(orc):
+    """A fine level covering the whole periodic domain has no refinement
+    boundary: it must evolve bitwise like a standalone run at its resolution."""
+    two = W.Hierarchy(system=W.WAVE, boxes=[[W.cube(0, 8)], [W.cube(0, 16)]], ncells0=(8, 8, 8),
+                      origin=(0.0, 0.0, 0.0), h0=1.0 / 8)
+    one = W.Hierarchy(system=W.WAVE, boxes=[[W.cube(0, 16)]], ncells0=(16, 16, 16), origin=(0.0, 0.0, 0.0),
+                      h0=1.0 / 16)
+    a = make(orc, two)
+    b = make(orc, one)
+    for o in (a, b):
+        o.set_initial_data(W.ID_STANDING_WAVE, [1.0, 1.0, 1.0, 1.0])
+    a.advance(3)
+    b.advance(6)
+    assert np.array_equal(a.get_field(1, 0, 0), b.get_field(0, 0, 0))
+    assert np.array_equal(a.get_field(1, 0, 1), b.get_field(0, 0, 1))
+
+
+# ------------------------------------------------------------------------- Z4c
+def test_minkowski_stays_flat(orc):
+    """Sec. III.A: flat space (W = alpha = 1, gt = delta, rest 0) is a static
+    solution of Z4c with the puncture gauge; it must stay flat to roundoff
+    through subcycled steps with the radiative boundary."""
+    h = W.bl_3level(20)
+    o = make(orc, h)
+    o.set_initial_data(W.ID_MINKOWSKI, [])
+    o.advance(2)
+    flat = np.zeros(22)
+    flat[[0, 1, 4, 6, 18]] = 1.0
+    for l in range(3):
+        for f in range(22):
+            assert np.abs(o.get_field(l, 0, f) - flat[f]).max() <= 1e-14
+
+
+def test_brill_lindquist_hamiltonian_converges(orc):
+    """Sec. III.B / Fig. 6: Brill-Lindquist data solve the Hamiltonian
+    constraint analytically, so the discrete H (which tests the conformal
+    Ricci terms R^W_ij) must vanish at 4th order away from the punctures."""
+    errs = []
+    for n in (16, 32, 64):
+        h = W.Hierarchy(system=W.Z4C, boxes=[[W.cube(0, n)]], ncells0=(n, n, n), origin=(-4.0, -4.0, -4.0),
+                        h0=8.0 / n, bc=W.BC_RADIATIVE)
+        o = make(orc, h)
+        o.set_initial_data(W.ID_BRILL_LINDQUIST, [0.5, 0.0, 0.0, 1.0, 0.5, 0.0, 0.0, -1.0])
+        c = o.constraints(0, 0)
+        X, Y, Z = h.cell_centres(0, 0)
+        r1 = np.sqrt(X ** 2 + Y ** 2 + (Z - 1) ** 2)
+        r2 = np.sqrt(X ** 2 + Y ** 2 + (Z + 1) ** 2)
+        mask = (np.minimum(r1, r2) > 1.5) & (np.abs(X) < 3) & (np.abs(Y) < 3) & (np.abs(Z) < 3)
+        errs.append(np.abs(c[0][mask]).max())
+        assert np.abs(c[1:4]).max() == 0.0  # K_ij = 0: momentum constraint identically zero
+    order = np.log2(errs[1] / errs[2])
+    assert abs(order - 4.0) < 0.3, (errs, order)
+
+
+def _gauge_wave_fields(n, A=0.1):
+    """Gauge wave along n = (1,1,0)/sqrt(2): flat spacetime with
+    gamma_ij = delta_ij + (H-1) n_i n_j, alpha = sqrt(H), beta = 0,
+    H = 1 - A sin(2 pi (x + y - sqrt(2) t)).  Returns the Z4c variables at
+    t = 0 and their exact time derivatives, as numpy callables."""
+    sp = pytest.importorskip("sympy")
+    t, x, y, z = sp.symbols("t x y z", real=True)
+    Hs = 1 - A * sp.sin(2 * sp.pi * (x + y - sp.sqrt(2) * t))
+    nv = sp.Matrix([1, 1, 0]) / sp.sqrt(2)
+    gam = sp.eye(3) + (Hs - 1) * nv * nv.T
+    al = sp.sqrt(Hs)
+    K = -sp.diff(gam, t) / (2 * al)
+    gu = sp.eye(3) + (1 / Hs - 1) * nv * nv.T  # inverse (n is a unit vector)
+    trK = sum(gu[i, j] * K[i, j] for i in range(3) for j in range(3))
+    Wf = Hs ** sp.Rational(-1, 6)  # det gamma = H
+    gt = Wf ** 2 * gam
+    At = Wf ** 2 * (K - gam * trK / 3)
+    gtu = gu / Wf ** 2
+    X = [x, y, z]
+    Gam = [-sum(sp.diff(gtu[i, j], X[j]) for j in range(3)) for i in range(3)]
+    sym = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    fields = [Wf] + [gt[i, j] for i, j in sym] + [trK] + [At[i, j] for i, j in sym] + Gam + [sp.Integer(0), al] + [sp.Integer(0)] * 3
+    vals = [sp.lambdify((x, y, z), f.subs(t, 0), "numpy") for f in fields]
+    dts = [sp.lambdify((x, y, z), sp.diff(f, t).subs(t, 0), "numpy") for f in fields]
+    return vals, dts
+
+
+def test_z4c_rhs_matches_gauge_wave_time_derivative(orc):
+    """Sec. III.A: for an exact vacuum solution the Z4c right-hand side of
+    the non-gauge variables (W, gt, Khat, At, Gamt, Theta) equals their true
+    time derivative up to the 4th-order truncation error of the stencils.
+    The gauge wave exercises the lapse terms, the extrinsic-curvature terms
+    and the full Ricci tensor with all index components."""
+    vals, dts = _gauge_wave_fields(0)
+    errs = []
+    for n in (12, 24, 48):
+        h = W.Hierarchy(system=W.Z4C, boxes=[[W.cube(0, n)]], ncells0=(n, n, n), origin=(0.0, 0.0, 0.0),
+                        h0=1.0 / n, bc=2, ko_sigma=0.0)
+        o = make(orc, h)
+        X, Y, Z = h.cell_centres(0, 0, ghosted=True)
+        st = np.stack([np.broadcast_to(np.asarray(f(X, Y, Z), dtype=float), X.shape) for f in vals])
+        rhs = o.rhs_box(0, 0, st)
+        s = (slice(3, -3),) * 3
+        e = 0.0
+        for f in range(18):
+            ex = np.broadcast_to(np.asarray(dts[f](X, Y, Z), dtype=float), X.shape)[s]
+            e = max(e, np.abs(rhs[f][s] - ex).max())
+        errs.append(e)
+    order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert order[-1] > 3.7, (errs, order)
+
+
+def test_flop_count_positive(orc):
+    c = orc.flop_counts()
+    assert c["total"] > 1000 and c["div"] > 0
