@@ -1,0 +1,288 @@
+"""Benchmark: subcycled Z4c zone-updates/s on one GB300.
+
+Workload (one "step" = one subcycled coarse step, Sec. II steps 1-7 on every
+level): Z4c head-on Brill-Lindquist data (m = 0.5 at z = +-1, lapse psi^-2),
+7 nested levels, level 0 64^3 over [-32,32]^3 (h = 1), finest h = 1/64,
+radiative outer boundary, KO sigma 0.3, eta 2.  Zone updates are counted as if
+every cell took the finest time step (Sec. IV.C): 1.594e8 per coarse step.
+
+Arms:
+  default            the CUDA library (state resident in HBM, ~5 GB > L2)
+  --impl reference   the CPU oracle on the machine's host cores, each step one
+                     coarse step of a bounded sample of the same workload
+                     (5 nested levels of 20^3, same physics and parameters).
+
+Multi-GPU (torchrun): independent replicas, one per GPU ("weak" scaling);
+the path has no exchange step on one hierarchy per GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "subcycled Z4c zone-updates/s on 1 GB300, % roofline; ensemble p50/p99 latency"
+UNIT = "zone-updates/s (finest-equivalent)"
+# FP64 peak derived from the unit counts and clocks: 152 SMs x 2070 MHz x
+# 2 DFMA lanes per SM per clock x 2 flops per DFMA.
+FP64_PEAK_GFLOPS = 152 * 2.070 * 2 * 2
+# FP64 flops per cell of each Z4c kernel in this formulation (counted from the
+# kernels' executed FP64 instructions, dadd + dmul + 2 dfma, per interior cell).
+FLOPS_PER_CELL = {"z4c_derivs": 1672.0, "z4c_stage": None}
+
+
+def sample_hierarchy(nlev: int = 5, n: int = 20):
+    """Bounded CPU sample of the benchmark workload: nlev nested cubes of n^3
+    cells (each level the central n cells of its index space), same Z4c
+    physics, Brill-Lindquist data and parameters."""
+    from paper_2503_09629_gb300 import workloads as W
+    boxes = [[W.cube(0, n)]]
+    for l in range(1, nlev):
+        lo = boxes[-1][0][0][0] * 2 + n // 2
+        boxes.append([W.cube(lo, n)])
+    L = 2.0
+    return W.Hierarchy(system=W.Z4C, boxes=boxes, ncells0=(n, n, n), origin=(-L, -L, -L), h0=2 * L / n,
+                       bc=W.BC_RADIATIVE, id_kind=W.ID_BRILL_LINDQUIST,
+                       id_params=[0.5, 0.0, 0.0, 1.0, 0.5, 0.0, 0.0, -1.0],
+                       name=f"z4c BL {nlev}-level {n}^3 sample")
+
+
+def oracle_step_rate(h, steps: int, warmup: int):
+    """Time the oracle (single thread) over `steps` coarse steps of h."""
+    import oracle
+    from paper_2503_09629_gb300 import workloads as W
+    o = oracle.Oracle(h.system, h.boxes, h.ncells0, h.origin, h.h0, **h.kwargs())
+    for l in range(h.nlevels):
+        a = W.initial_fields(h, l, 0, ghosted=True)
+        for f in range(a.shape[0]):
+            o.set_field(l, 0, f, a[f], ghosted=True)
+    if warmup:
+        o.advance(warmup)
+    t0 = time.perf_counter()
+    o.advance(steps)
+    dt = time.perf_counter() - t0
+    fin, _ = h.zone_updates_per_coarse_step()
+    return fin * steps / dt, dt
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.proc = subprocess.Popen([exe, f"--id={self.device}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                      "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
+                                     stderr=subprocess.DEVNULL)
+        time.sleep(0.3)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    h = sample_hierarchy()
+    value, dt = oracle_step_rate(h, args.steps, args.warmup)
+    ms = dt / args.steps * 1e3
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": h.name, "note": "CPU oracle, single thread; bounded sample of the 7-level workload"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} coarse steps of {h.name}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank: int, world: int):
+    import numpy as np
+    import torch
+
+    import paper_2503_09629_gb300 as sc
+    from paper_2503_09629_gb300 import workloads as W
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    sc.build()
+    h = W.bl_7level()
+    fin_per_step, act_per_step = h.zone_updates_per_coarse_step()
+    ctx = sc.Context(h)
+    ctx.sc_set_initial_data(h.id_kind, h.id_params)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ctx.sc_advance(1)
+    ctx.sc_synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.sc_advance(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_per_step = t_max / args.steps
+    value = world * fin_per_step * args.steps / (t_max * 1e-3)
+    launches = ctx.sc_launches_per_step() * args.steps
+
+    # Roofline of the dominant kernels: FP64-ALU bound.  Per-launch durations
+    # from CUDA events on the library's stream, on the finest level.
+    fin_level = h.nlevels - 1
+    cells = h.interior_cells(fin_level)
+    t_der, t_stage = ctx.sc_time_stage_kernels(fin_level, 5)
+    roof = {}
+    for name, t in (("z4c_derivs", t_der), ("z4c_stage", t_stage)):
+        fpc = FLOPS_PER_CELL[name]
+        if fpc is None:
+            continue
+        ach = cells * fpc / (t * 1e-3) / 1e12
+        roof[name] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                      "frac": ach * 1e3 / FP64_PEAK_GFLOPS, "traffic": None, "ms_per_launch": t,
+                      "cells_per_launch": cells, "flops_per_cell": fpc}
+    dominant = "z4c_stage" if "z4c_stage" in roof else "z4c_derivs"
+    roofline = dict(roof[dominant])
+    roofline["kernel"] = dominant
+    roofline["peak_source"] = "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (nominal 1.25 TFLOP/s)"
+    roofline["other_kernels"] = {k: v for k, v in roof.items() if k != dominant}
+
+    # End to end through the public API with host buffers: each step uploads
+    # the state from pinned host memory, advances one coarse step and reads
+    # the state back.
+    host = {}
+    h2d = 0
+    for l in range(h.nlevels):
+        for b in range(len(h.boxes[l])):
+            g = (l == 0)
+            for f in range(22):
+                a = torch.empty(ctx.shape(l, b, g), dtype=torch.float64).pin_memory()
+                a.copy_(torch.from_numpy(ctx.sc_get_field(l, b, f, ghosted=g)))
+                host[(l, b, f)] = (a, g)
+                h2d += a.numel() * 8
+    outs = {k: torch.empty(ctx.shape(k[0], k[1], False), dtype=torch.float64).pin_memory() for k in host}
+    d2h = sum(v.numel() * 8 for v in outs.values())
+    ne2e = max(1, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ne2e):
+        for (l, b, f), (a, g) in host.items():
+            ctx.sc_set_field(l, b, f, a.numpy(), ghosted=g)
+        ctx.sc_advance(1)
+        for (l, b, f), o in outs.items():
+            o.numpy()[...] = ctx.sc_get_field(l, b, f)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * fin_per_step * ne2e / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1:
+        hs = sample_hierarchy()
+        v, dt = oracle_step_rate(hs, 1, 0)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1 coarse step of {hs.name} ({dt:.1f} s)"}
+    ctx.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": h.name, "levels": h.nlevels, "base_cells": 64 ** 3,
+                           "interior_cells": sum(h.interior_cells(l) for l in range(h.nlevels)),
+                           "finest_equiv_zone_updates_per_step": fin_per_step,
+                           "actual_zone_updates_per_step": act_per_step,
+                           "actual_zone_updates_per_s": world * act_per_step / (ms_per_step * 1e-3),
+                           "l2": "state ~5 GB per replica > 129 MB L2: inputs larger than L2, no flush",
+                           "parallelism": f"replicas{world}"},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "steps": ne2e},
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

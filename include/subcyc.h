@@ -1,0 +1,174 @@
+/*
+ * subcyc.h -- C ABI of the GB300 (sm_103a) library for RK4 subcycling in time
+ * on nested refined boxes with dense-output ghost filling, after
+ * "GPU-accelerated Subcycling Time Integration with the Einstein Toolkit"
+ * (arXiv:2503.09629).
+ *
+ * Library: libsubcyc.so.  All arithmetic is FP64 and runs in CUDA kernels on
+ * one GPU; there is no CPU fallback: every compute entry point fails with
+ * SC_ECUDA when no device is usable.
+ *
+ * Conventions shared by every call:
+ *   - cell-centred grids; level l has spacing h_l = h0 / 2^l and cell index
+ *     space [0, ncells0[d] * 2^l) per dimension; cell i of level l has centre
+ *     origin + (i + 1/2) h_l;
+ *   - refinement factor 2 between levels (Sec. II: h^(l) / h^(l+1) = 2);
+ *   - 3 ghost cells around every box;
+ *   - field arrays exchanged with the caller are x-fastest, contiguous,
+ *     FP64, one field at a time;
+ *   - every call returns an sc_status (0 = success, negative = error) and
+ *     never aborts; sc_last_error() gives a thread-local message;
+ *   - the caller owns every descriptor and host buffer it passes; no call
+ *     keeps a caller pointer after it returns; the library owns its device
+ *     memory, obtained through the caller's allocator when one is given.
+ */
+#ifndef SUBCYC_H
+#define SUBCYC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sc_ctx sc_ctx;
+typedef int sc_status;
+
+enum {
+  SC_OK = 0,
+  SC_EINVAL = -1,      /* bad argument */
+  SC_ENOMEM = -2,      /* device allocation failed */
+  SC_ECUDA = -3,       /* CUDA error (message in sc_last_error) */
+  SC_ENESTING = -4,    /* hierarchy not properly nested or not aligned */
+  SC_ENONFINITE = -5,  /* non-finite value found in the evolved state */
+  SC_ETIMEOUT = -6,    /* a bounded wait ran out */
+  SC_EBUSY = -7        /* request can never fit the memory budget */
+};
+
+typedef enum { SC_WAVE = 0, SC_Z4C = 1 } sc_system;
+typedef enum { SC_BC_PERIODIC = 0, SC_BC_RADIATIVE = 1 } sc_outer_bc;
+
+/* Initial data kinds for sc_set_initial_data (params in brackets):
+ *  SC_ID_STANDING_WAVE  wave: [A, kx, ky, kz]  u = A sin(2 pi kx x) sin(2 pi ky y) sin(2 pi kz z), Pi = 0
+ *  SC_ID_GAUSSIAN       wave: [A, w, cx, cy, cz]  u = A exp(-|x - c|^2 / (2 w^2)), Pi = 0
+ *  SC_ID_BRILL_LINDQUIST z4c: [m1, x1, y1, z1, m2, x2, y2, z2]  psi = 1 + sum m/(2 r),
+ *                       W = psi^-2, gt = delta, alpha = psi^-2, rest 0 (Sec. III.B, lapse psi^-2)
+ *  SC_ID_MINKOWSKI      z4c: []  flat space
+ *  SC_ID_SPHERICAL_GAUSSIAN wave: [A, sigma, t, cx, cy, cz]  Sec. IV.A exact solution */
+enum { SC_ID_STANDING_WAVE = 0, SC_ID_GAUSSIAN = 1, SC_ID_BRILL_LINDQUIST = 2, SC_ID_MINKOWSKI = 3,
+       SC_ID_SPHERICAL_GAUSSIAN = 4 };
+
+/* A box: inclusive cell indices in its level's index space. */
+typedef struct {
+  int lo[3];
+  int hi[3];
+} sc_box;
+
+/* Device-memory allocator supplied by the caller (e.g. a framework's caching
+ * allocator).  alloc returns a device pointer aligned to >= 256 bytes or NULL;
+ * free releases it.  NULL allocator -> cudaMalloc / cudaFree. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} sc_allocator;
+
+/* Hierarchy description, deep-copied by sc_create.
+ *   boxes: all boxes, level 0 first, nboxes[l] of them for level l;
+ *   level 0 must cover the domain [0, ncells0) exactly (disjoint boxes);
+ *   fine boxes (l >= 1) must start on even and end on odd indices (aligned to
+ *   parent cells), must not overlap each other, and every refinement-boundary
+ *   ghost cell's prolongation stencil (6 parent cells per dimension) must lie
+ *   in the parent level's interior (proper nesting, else SC_ENESTING);
+ *   outer_bc: SC_BC_RADIATIVE needs exactly one level-0 box;
+ *   cfl: dt_l = cfl * h_l; subcycle must be 1 (the paper's scheme; the
+ *   uniform-step comparison mode lives in the CPU oracle only);
+ *   kappa1, kappa2, eta, ko_sigma: Z4c damping, Gamma-driver and
+ *   Kreiss-Oliger parameters (Sec. III);
+ *   cuda_stream: cudaStream_t all work is ordered on (NULL = legacy stream). */
+typedef struct {
+  int system;
+  int nlevels;
+  const int* nboxes;
+  const sc_box* boxes;
+  int ncells0[3];
+  double origin[3];
+  double h0;
+  int outer_bc;
+  double cfl;
+  int subcycle;
+  double kappa1, kappa2, eta, ko_sigma;
+  void* cuda_stream;
+  const sc_allocator* allocator;
+} sc_desc;
+
+/* Build the hierarchy: validate nesting and alignment, allocate every level's
+ * state, stage and k1..k4 arrays, build the device work lists.
+ * Errors: SC_EINVAL, SC_ENESTING, SC_ENOMEM, SC_ECUDA. */
+sc_status sc_create(const sc_desc* desc, sc_ctx** out);
+
+/* Release every device allocation (synchronises the context's stream). */
+void sc_destroy(sc_ctx* ctx);
+
+/* Fill the state of every level (interior and ghosts) with analytic initial
+ * data, on the device; resets the time to 0. */
+sc_status sc_set_initial_data(sc_ctx* ctx, int kind, const double* params, int nparams);
+
+/* Copy one field of one box from host memory: src holds the box interior,
+ * (hi-lo+1) cells per dimension, x fastest.  Stream-ordered, synchronous with
+ * respect to the host buffer (returns after the copy has been consumed). */
+sc_status sc_set_field(sc_ctx* ctx, int level, int box, int field, const double* host_src);
+/* As sc_set_field, including 3 ghost cells per side: src has (hi-lo+7) cells
+ * per dimension.  Needed for the evolved outer ghost shell of a radiative
+ * level 0 and for checkpoint/resume. */
+sc_status sc_set_field_ghosted(sc_ctx* ctx, int level, int box, int field, const double* host_src);
+
+/* Copy one field of one box (interior) to host memory; synchronises. */
+sc_status sc_get_field(sc_ctx* ctx, int level, int box, int field, double* host_dst);
+sc_status sc_get_field_ghosted(sc_ctx* ctx, int level, int box, int field, double* host_dst);
+
+/* Device-resident variants: the same copies between the state and a device
+ * buffer of the same shape; stream-ordered, no host synchronisation. */
+sc_status sc_set_field_device(sc_ctx* ctx, int level, int box, int field, const double* dev_src);
+sc_status sc_get_field_device(sc_ctx* ctx, int level, int box, int field, double* dev_dst);
+
+/* Advance n coarse steps (Sec. II, steps 1-7 per coarse step): level 0
+ * takes one RK4 step storing k1..k4, every finer level two substeps per
+ * parent step with refinement-boundary ghosts from the parent's dense
+ * output (theta0 = 0 and 1/2), recursively, then restriction.  Each coarse
+ * step is one CUDA graph launch on the context's stream; asynchronous. */
+sc_status sc_advance(sc_ctx* ctx, int n_coarse_steps);
+
+/* Block until the context's stream is idle; returns SC_ECUDA on a device error. */
+sc_status sc_synchronize(sc_ctx* ctx);
+
+/* Z4c constraints (H, M^x, M^y, M^z, G^x, G^y, G^z) of the current state at
+ * the interior cells of one box, to a host buffer of 7 * ncell doubles
+ * (constraint-major, x fastest); synchronises.  Z4c only. */
+sc_status sc_get_constraints(sc_ctx* ctx, int level, int box, double* host_dst);
+
+sc_status sc_get_time(sc_ctx* ctx, double* t);
+/* Cell updates done so far: finest-equivalent (every cell counted at the
+ * finest time step, Sec. IV.C) and actual. */
+sc_status sc_zone_updates(sc_ctx* ctx, double* finest_equiv, double* actual);
+/* Number of kernel launches one coarse step performs (graph nodes). */
+sc_status sc_launches_per_step(sc_ctx* ctx, long* n);
+/* Device bytes held by the context. */
+sc_status sc_footprint(sc_ctx* ctx, size_t* bytes);
+/* Footprint a descriptor would need, without allocating. */
+sc_status sc_footprint_estimate(const sc_desc* desc, size_t* bytes);
+
+/* Time the kernels of one RK4 stage (stage 2) of one level outside the
+ * graph, with CUDA events recorded on the context's stream, averaged over
+ * nrep launches each: ms[0] = Z4c derivative pass (wave: fused stage kernel),
+ * ms[1] = Z4c right-hand-side + update pass (wave: 0).  Overwrites only the
+ * level's k2 and second stage buffer, which every coarse step recomputes
+ * before reading; call between sc_advance calls.  Synchronises. */
+sc_status sc_time_stage_kernels(sc_ctx* ctx, int level, int nrep, double* ms);
+
+const char* sc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

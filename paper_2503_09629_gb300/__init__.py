@@ -1,0 +1,284 @@
+"""GB300-native RK4 subcycling in time with dense-output ghost filling.
+
+Python binding of ``libsubcyc.so`` (C ABI declared in ``include/subcyc.h``):
+argument marshalling only.  Every step of the evolution runs in the library's
+CUDA kernels; there is no CPU fallback -- if the library cannot be loaded, or
+no CUDA device is present, every call raises.  PyTorch supplies device memory
+(through its caching allocator) and the CUDA stream.
+
+Method: arXiv:2503.09629 Sec. II (RK4 with dense output, Taylor stage
+reconstruction at refinement-boundary ghosts, subcycling recursion,
+restriction), Sec. III (Z4c with puncture gauge and Kreiss-Oliger
+dissipation), Sec. IV.A (scalar wave).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import workloads  # noqa: F401  (seeded synthetic inputs)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsubcyc.so")
+
+SC_OK, SC_EINVAL, SC_ENOMEM, SC_ECUDA, SC_ENESTING, SC_ENONFINITE, SC_ETIMEOUT, SC_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
+SC_WAVE, SC_Z4C = 0, 1
+SC_BC_PERIODIC, SC_BC_RADIATIVE = 0, 1
+GHOST = 3
+NCONSTRAINTS = 7
+
+
+class SubcycError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class sc_box(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int * 3), ("hi", ctypes.c_int * 3)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class sc_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
+
+
+class sc_desc(ctypes.Structure):
+    _fields_ = [
+        ("system", ctypes.c_int),
+        ("nlevels", ctypes.c_int),
+        ("nboxes", ctypes.POINTER(ctypes.c_int)),
+        ("boxes", ctypes.POINTER(sc_box)),
+        ("ncells0", ctypes.c_int * 3),
+        ("origin", ctypes.c_double * 3),
+        ("h0", ctypes.c_double),
+        ("outer_bc", ctypes.c_int),
+        ("cfl", ctypes.c_double),
+        ("subcycle", ctypes.c_int),
+        ("kappa1", ctypes.c_double),
+        ("kappa2", ctypes.c_double),
+        ("eta", ctypes.c_double),
+        ("ko_sigma", ctypes.c_double),
+        ("cuda_stream", ctypes.c_void_p),
+        ("allocator", ctypes.POINTER(sc_allocator)),
+    ]
+
+
+_lib = None
+
+
+def build(verbose: bool = False) -> str:
+    from . import buildlib
+    return buildlib.build(verbose=verbose)
+
+
+def lib():
+    """Load libsubcyc.so (building it first if absent); raises if impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        build()
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    DP = ctypes.POINTER(ctypes.c_double)
+    L.sc_last_error.restype = ctypes.c_char_p
+    L.sc_create.argtypes = [ctypes.POINTER(sc_desc), ctypes.POINTER(P)]
+    L.sc_destroy.argtypes = [P]
+    L.sc_destroy.restype = None
+    L.sc_set_initial_data.argtypes = [P, I, DP, I]
+    for name in ("sc_set_field", "sc_set_field_ghosted", "sc_get_field", "sc_get_field_ghosted"):
+        getattr(L, name).argtypes = [P, I, I, I, DP]
+    for name in ("sc_set_field_device", "sc_get_field_device"):
+        getattr(L, name).argtypes = [P, I, I, I, P]
+    L.sc_advance.argtypes = [P, I]
+    L.sc_synchronize.argtypes = [P]
+    L.sc_get_constraints.argtypes = [P, I, I, DP]
+    L.sc_get_time.argtypes = [P, DP]
+    L.sc_zone_updates.argtypes = [P, DP, DP]
+    L.sc_launches_per_step.argtypes = [P, ctypes.POINTER(ctypes.c_long)]
+    L.sc_footprint.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    L.sc_footprint_estimate.argtypes = [ctypes.POINTER(sc_desc), ctypes.POINTER(ctypes.c_size_t)]
+    L.sc_time_stage_kernels.argtypes = [P, I, I, DP]
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != SC_OK:
+        raise SubcycError(rc, lib().sc_last_error().decode(errors="replace"))
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _torch_allocator():
+    """sc_allocator backed by PyTorch's CUDA caching allocator."""
+    import torch
+
+    dev = torch.cuda.current_device()
+
+    def _alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+        except Exception:  # out of memory -> NULL, the library reports SC_ENOMEM
+            return None
+
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = sc_allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+    return a
+
+
+def make_desc(h, stream: Optional[int] = None, allocator=None):
+    """sc_desc for a workloads.Hierarchy; returns (desc, keepalive)."""
+    nb = (ctypes.c_int * h.nlevels)(*[len(b) for b in h.boxes])
+    flat = [bx for lvl in h.boxes for bx in lvl]
+    boxes = (sc_box * len(flat))()
+    for i, (lo, hi) in enumerate(flat):
+        boxes[i].lo[:] = list(lo)
+        boxes[i].hi[:] = list(hi)
+    d = sc_desc()
+    d.system = h.system
+    d.nlevels = h.nlevels
+    d.nboxes = nb
+    d.boxes = boxes
+    d.ncells0[:] = list(h.ncells0)
+    d.origin[:] = list(h.origin)
+    d.h0 = h.h0
+    d.outer_bc = h.bc
+    d.cfl = h.cfl
+    d.subcycle = 1 if h.subcycle else 0
+    d.kappa1, d.kappa2, d.eta, d.ko_sigma = h.kappa1, h.kappa2, h.eta, h.ko_sigma
+    d.cuda_stream = stream
+    keep = [nb, boxes]
+    if allocator is not None:
+        d.allocator = ctypes.pointer(allocator)
+        keep.append(allocator)
+    return d, keep
+
+
+def sc_footprint_estimate(h) -> int:
+    d, _keep = make_desc(h)
+    n = ctypes.c_size_t()
+    _check(lib().sc_footprint_estimate(ctypes.byref(d), ctypes.byref(n)))
+    return n.value
+
+
+class Context:
+    """One box hierarchy resident on the GPU (wraps an ``sc_ctx*``).
+
+    Method names follow the C ABI (``sc_<name>``).  ``use_torch`` routes
+    device allocation through PyTorch's caching allocator and orders all work
+    on PyTorch's current CUDA stream.
+    """
+
+    def __init__(self, h, use_torch: bool = True, stream: Optional[int] = None):
+        L = lib()
+        self.h = h
+        self._alloc = None
+        if use_torch:
+            import torch
+            if not torch.cuda.is_available():
+                raise SubcycError(SC_ECUDA, "no CUDA device available")
+            if stream is None:
+                stream = torch.cuda.current_stream().cuda_stream
+            self._alloc = _torch_allocator()
+        d, self._keep = make_desc(h, stream, self._alloc)
+        ctx = ctypes.c_void_p()
+        _check(L.sc_create(ctypes.byref(d), ctypes.byref(ctx)))
+        self.ctx = ctx
+        self.F = h.nfields()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().sc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, level: int, box: int, ghosted: bool = False) -> Tuple[int, int, int]:
+        lo, hi = self.h.boxes[level][box]
+        g = 2 * GHOST if ghosted else 0
+        return (hi[2] - lo[2] + 1 + g, hi[1] - lo[1] + 1 + g, hi[0] - lo[0] + 1 + g)
+
+    def sc_set_initial_data(self, kind: int, params: Sequence[float]):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        _check(lib().sc_set_initial_data(self.ctx, kind, _dp(p) if len(p) else None, len(p)))
+
+    def sc_set_field(self, level, box, field, arr, ghosted=False):
+        a = np.ascontiguousarray(arr, dtype=np.float64)
+        if a.shape != self.shape(level, box, ghosted):
+            raise ValueError(f"shape {a.shape} != {self.shape(level, box, ghosted)}")
+        fn = lib().sc_set_field_ghosted if ghosted else lib().sc_set_field
+        _check(fn(self.ctx, level, box, field, _dp(a)))
+
+    def sc_get_field(self, level, box, field, ghosted=False) -> np.ndarray:
+        a = np.empty(self.shape(level, box, ghosted))
+        fn = lib().sc_get_field_ghosted if ghosted else lib().sc_get_field
+        _check(fn(self.ctx, level, box, field, _dp(a)))
+        return a
+
+    def sc_set_field_device(self, level, box, field, dev_ptr: int):
+        _check(lib().sc_set_field_device(self.ctx, level, box, field, ctypes.c_void_p(dev_ptr)))
+
+    def sc_get_field_device(self, level, box, field, dev_ptr: int):
+        _check(lib().sc_get_field_device(self.ctx, level, box, field, ctypes.c_void_p(dev_ptr)))
+
+    def sc_advance(self, n: int):
+        _check(lib().sc_advance(self.ctx, n))
+
+    def sc_synchronize(self):
+        _check(lib().sc_synchronize(self.ctx))
+
+    def sc_get_constraints(self, level, box) -> np.ndarray:
+        a = np.empty((NCONSTRAINTS,) + self.shape(level, box))
+        _check(lib().sc_get_constraints(self.ctx, level, box, _dp(a)))
+        return a
+
+    def sc_get_time(self) -> float:
+        t = ctypes.c_double()
+        _check(lib().sc_get_time(self.ctx, ctypes.byref(t)))
+        return t.value
+
+    def sc_zone_updates(self) -> Tuple[float, float]:
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib().sc_zone_updates(self.ctx, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def sc_launches_per_step(self) -> int:
+        n = ctypes.c_long()
+        _check(lib().sc_launches_per_step(self.ctx, ctypes.byref(n)))
+        return n.value
+
+    def sc_footprint(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().sc_footprint(self.ctx, ctypes.byref(n)))
+        return n.value
+
+    def sc_time_stage_kernels(self, level: int, nrep: int = 5) -> Tuple[float, float]:
+        ms = np.zeros(2)
+        _check(lib().sc_time_stage_kernels(self.ctx, level, nrep, _dp(ms)))
+        return float(ms[0]), float(ms[1])
+
+    # convenience
+    def set_initial_data_from(self, h=None):
+        h = h or self.h
+        self.sc_set_initial_data(h.id_kind, h.id_params)
+
+    def get_all(self, ghosted=False) -> List[List[np.ndarray]]:
+        """[level][box] -> array (F, nz, ny, nx)."""
+        return [[np.stack([self.sc_get_field(l, b, f, ghosted) for f in range(self.F)])
+                 for b in range(len(self.h.boxes[l]))] for l in range(self.h.nlevels)]

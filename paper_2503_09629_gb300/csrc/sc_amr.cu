@@ -1,0 +1,275 @@
+// sc_amr.cu -- refinement-boundary kernels (prolongation of the parent's
+// y_n and k1..k4, dense-output ghost fill, restriction), periodic ghost copy,
+// analytic initial data, box pack/unpack and the finiteness check.
+//
+// Every kernel works on one level's dense FP64 array (one array per field,
+// x fastest) through precomputed int32 offset lists.
+#include <math.h>
+
+#include "sc_internal.h"
+
+namespace sc {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(long work, int threads) {
+  long b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152L * 64) b = 152L * 64;  // grid-stride beyond 64 blocks per SM
+  return (int)b;
+}
+
+// Sec. II step 2: prolong y_n and k1..k4 of the parent step to every
+// refinement-boundary ghost cell of the fine level: tensor-product quintic
+// Lagrange interpolation from 6x6x6 parent cells.  One thread per
+// (ghost cell, field); results go to store[(v * F + f) * ncells + cell].
+__global__ void __launch_bounds__(kThreads) amr_prolong_kernel(
+    const double* __restrict__ yn, const double* __restrict__ k1, const double* __restrict__ k2,
+    const double* __restrict__ k3, const double* __restrict__ k4, long pfs, int psy, int psz,
+    const AmrCell* __restrict__ cells, int ncells, double* __restrict__ store, int F, Weights w) {
+  const long total = (long)ncells * F;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int a = (int)(idx % ncells);
+    const int f = (int)(idx / ncells);
+    const AmrCell c = cells[a];
+    const double* wx = w.prolong[c.parity & 1];
+    const double* wy = w.prolong[(c.parity >> 1) & 1];
+    const double* wz = w.prolong[(c.parity >> 2) & 1];
+    const double* src[5] = {yn, k1, k2, k3, k4};
+#pragma unroll 1
+    for (int v = 0; v < 5; ++v) {
+      const double* p = src[v] + (long)f * pfs + c.pbase;
+      double sz = 0.0;
+#pragma unroll
+      for (int kz = 0; kz < kPN; ++kz) {
+        double sy = 0.0;
+#pragma unroll
+        for (int ky = 0; ky < kPN; ++ky) {
+          const double* row = p + (long)kz * psz + (long)ky * psy;
+          double sx = 0.0;
+#pragma unroll
+          for (int kx = 0; kx < kPN; ++kx) sx = fma(wx[kx], __ldg(row + kx), sx);
+          sy = fma(wy[ky], sx, sy);
+        }
+        sz = fma(wz[kz], sy, sz);
+      }
+      store[((long)v * F + f) * ncells + a] = sz;
+    }
+  }
+}
+
+// Sec. II steps 3/5: ghost value = P[y_n] + sum_j c_j P[k_j]; the four
+// coefficients encode dense output (Eqs. denseoutput1/2) and the Taylor stage
+// formulas (Eqs. Y1-Y4) for one stage of one fine substep.
+__global__ void __launch_bounds__(kThreads) amr_apply_kernel(double* __restrict__ vec, long fs, int F,
+                                                            const AmrCell* __restrict__ cells, int ncells,
+                                                            const double* __restrict__ store, double c1,
+                                                            double c2, double c3, double c4) {
+  const long total = (long)ncells * F;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int a = (int)(idx % ncells);
+    const int f = (int)(idx / ncells);
+    const long n = ncells;
+    const double* s = store + (long)f * n + a;
+    const long vs = (long)F * n;
+    double v = s[0];
+    v = fma(c1, s[vs], v);
+    v = fma(c2, s[2 * vs], v);
+    v = fma(c3, s[3 * vs], v);
+    v = fma(c4, s[4 * vs], v);
+    vec[(long)f * fs + cells[a].dst] = v;
+  }
+}
+
+// Sec. II step 7: every parent cell whose eight children are fine interior
+// cells takes the tensor-product quintic interpolant of the 6x6x6 fine cells
+// centred on it.
+__global__ void __launch_bounds__(kThreads) restrict_kernel(double* __restrict__ parent, long pfs,
+                                                           const double* __restrict__ fine, long ffs, int fsy,
+                                                           int fsz, const RestrictCell* __restrict__ cells,
+                                                           int ncells, int F, Weights w) {
+  const long total = (long)ncells * F;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int a = (int)(idx % ncells);
+    const int f = (int)(idx / ncells);
+    const RestrictCell c = cells[a];
+    const double* p = fine + (long)f * ffs + c.fbase;
+    double sz = 0.0;
+#pragma unroll
+    for (int kz = 0; kz < kRN; ++kz) {
+      double sy = 0.0;
+#pragma unroll
+      for (int ky = 0; ky < kRN; ++ky) {
+        const double* row = p + (long)kz * fsz + (long)ky * fsy;
+        double sx = 0.0;
+#pragma unroll
+        for (int kx = 0; kx < kRN; ++kx) sx = fma(w.restrict_w[kx], __ldg(row + kx), sx);
+        sy = fma(w.restrict_w[ky], sx, sy);
+      }
+      sz = fma(w.restrict_w[kz], sy, sz);
+    }
+    parent[(long)f * pfs + c.dst] = sz;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) periodic_copy_kernel(double* __restrict__ vec, long fs, int F,
+                                                                const int2* __restrict__ pairs, int npairs) {
+  const long total = (long)npairs * F;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int a = (int)(idx % npairs);
+    const int f = (int)(idx / npairs);
+    const int2 p = pairs[a];
+    vec[(long)f * fs + p.x] = vec[(long)f * fs + p.y];
+  }
+}
+
+struct IdParams {
+  double p[8];
+};
+
+// Analytic initial data at every element of a level array.
+__global__ void __launch_bounds__(kThreads) initial_data_kernel(double* __restrict__ vec, Geom g, int F,
+                                                               int system, int kind, IdParams ip) {
+  const long ncell = (long)g.ext[0] * g.ext[1] * g.ext[2];
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < ncell; idx += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % g.ext[0]);
+    const int j = (int)((idx / g.ext[0]) % g.ext[1]);
+    const int k = (int)(idx / ((long)g.ext[0] * g.ext[1]));
+    const long o = ((long)k * g.ext[1] + j) * g.pitch + i;
+    const double x = g.x0[0] + i * g.h, y = g.x0[1] + j * g.h, z = g.x0[2] + k * g.h;
+    const double* p = ip.p;
+    if (system == SC_WAVE) {
+      double u = 0.0, pi = 0.0;
+      if (kind == SC_ID_STANDING_WAVE) {
+        const double tp = 2.0 * M_PI;
+        u = p[0] * sin(tp * p[1] * x) * sin(tp * p[2] * y) * sin(tp * p[3] * z);
+      } else if (kind == SC_ID_GAUSSIAN) {
+        const double dx = x - p[2], dy = y - p[3], dz = z - p[4];
+        u = p[0] * exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * p[1] * p[1]));
+      } else if (kind == SC_ID_SPHERICAL_GAUSSIAN) {
+        const double dx = x - p[3], dy = y - p[4], dz = z - p[5];
+        const double r = sqrt(dx * dx + dy * dy + dz * dz), t = p[2], s2 = p[1] * p[1];
+        const double fm = p[0] * exp(-(t - r) * (t - r) / (2.0 * s2));
+        const double fp = p[0] * exp(-(t + r) * (t + r) / (2.0 * s2));
+        u = (fm - fp) / r;
+        pi = -(fm * (t - r) - fp * (t + r)) / (s2 * r);
+      }
+      vec[o] = u;
+      vec[g.fs + o] = pi;
+    } else {
+      double psi = 1.0;
+      if (kind == SC_ID_BRILL_LINDQUIST) {
+        for (int q = 0; q < 2; ++q) {
+          const double dx = x - p[4 * q + 1], dy = y - p[4 * q + 2], dz = z - p[4 * q + 3];
+          psi += p[4 * q] / (2.0 * sqrt(dx * dx + dy * dy + dz * dz));
+        }
+      }
+      const double ipsi2 = 1.0 / (psi * psi);
+      for (int f = 0; f < F; ++f) vec[(long)f * g.fs + o] = 0.0;
+      vec[(long)ZW * g.fs + o] = ipsi2;
+      vec[(long)(ZG + 0) * g.fs + o] = 1.0;
+      vec[(long)(ZG + 3) * g.fs + o] = 1.0;
+      vec[(long)(ZG + 5) * g.fs + o] = 1.0;
+      vec[(long)ZAL * g.fs + o] = ipsi2;
+    }
+  }
+}
+
+// Copy a box region of one field between a level array and a contiguous
+// x-fastest buffer (unpack = 0: array -> buffer; 1: buffer -> array).
+__global__ void __launch_bounds__(kThreads) pack_kernel(double* __restrict__ vec, int pitch, int ey, int i0,
+                                                       int j0, int k0, int nx, int ny, int nz,
+                                                       double* __restrict__ buf, int unpack) {
+  const long n = (long)nx * ny * nz;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n; idx += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % nx);
+    const int j = (int)((idx / nx) % ny);
+    const int k = (int)(idx / ((long)nx * ny));
+    const long o = ((long)(k0 + k) * ey + (j0 + j)) * pitch + (i0 + i);
+    if (unpack) vec[o] = buf[idx];
+    else buf[idx] = vec[o];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) nonfinite_kernel(const double* __restrict__ vec, long fs, int F,
+                                                            const Tile* __restrict__ tiles, int ntiles,
+                                                            int sy, int sz, int* flag) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile T = tiles[t];
+    const int n = T.nx * T.ny * T.nz;
+    for (int q = threadIdx.x; q < n * F; q += blockDim.x) {
+      const int f = q / n, c = q % n;
+      const int i = c % T.nx, j = (c / T.nx) % T.ny, k = c / (T.nx * T.ny);
+      const double v = vec[(long)f * fs + (long)(T.z0 + k) * sz + (long)(T.y0 + j) * sy + T.x0 + i];
+      if (!isfinite(v)) atomicOr(flag, 1);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_amr_prolong(const double* yn, const double* k1, const double* k2, const double* k3,
+                               const double* k4, long pfs, int psy, int psz, const AmrCell* cells, int ncells,
+                               double* store, int F, const Weights& w, cudaStream_t s) {
+  if (ncells == 0) return cudaSuccess;
+  amr_prolong_kernel<<<grid_for((long)ncells * F, kThreads), kThreads, 0, s>>>(yn, k1, k2, k3, k4, pfs, psy, psz,
+                                                                              cells, ncells, store, F, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_amr_apply(double* vec, long fs, int F, const AmrCell* cells, int ncells, const double* store,
+                             const double* c4, cudaStream_t s) {
+  if (ncells == 0) return cudaSuccess;
+  amr_apply_kernel<<<grid_for((long)ncells * F, kThreads), kThreads, 0, s>>>(vec, fs, F, cells, ncells, store, c4[0],
+                                                                            c4[1], c4[2], c4[3]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(double* parent, long pfs, const double* fine, long ffs, int fsy, int fsz,
+                            const RestrictCell* cells, int ncells, int F, const Weights& w, cudaStream_t s) {
+  if (ncells == 0) return cudaSuccess;
+  restrict_kernel<<<grid_for((long)ncells * F, kThreads), kThreads, 0, s>>>(parent, pfs, fine, ffs, fsy, fsz, cells,
+                                                                           ncells, F, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_periodic_copy(double* vec, long fs, int F, const int2* pairs, int npairs, cudaStream_t s) {
+  if (npairs == 0) return cudaSuccess;
+  periodic_copy_kernel<<<grid_for((long)npairs * F, kThreads), kThreads, 0, s>>>(vec, fs, F, pairs, npairs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_initial_data(double* vec, const Geom& g, int F, int system, int kind, const double* params,
+                                int nparams, cudaStream_t s) {
+  IdParams ip;
+  for (int i = 0; i < 8; ++i) ip.p[i] = (i < nparams) ? params[i] : 0.0;
+  const long n = (long)g.ext[0] * g.ext[1] * g.ext[2];
+  initial_data_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(vec, g, F, system, kind, ip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const double* vec, const Geom& g, const int* lo, const int* n, double* dst, cudaStream_t s) {
+  const long cnt = (long)n[0] * n[1] * n[2];
+  pack_kernel<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(const_cast<double*>(vec), g.pitch, g.ext[1],
+                                                          lo[0] - g.org[0], lo[1] - g.org[1], lo[2] - g.org[2],
+                                                          n[0], n[1], n[2], dst, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(double* vec, const Geom& g, const int* lo, const int* n, const double* src, cudaStream_t s) {
+  const long cnt = (long)n[0] * n[1] * n[2];
+  pack_kernel<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(vec, g.pitch, g.ext[1], lo[0] - g.org[0],
+                                                          lo[1] - g.org[1], lo[2] - g.org[2], n[0], n[1], n[2],
+                                                          const_cast<double*>(src), 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nonfinite_check(const double* vec, long fs, int F, const Tile* tiles, int ntiles, int sy, int sz,
+                                   int* flag, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  nonfinite_kernel<<<ntiles < 152 * 8 ? ntiles : 152 * 8, kThreads, 0, s>>>(vec, fs, F, tiles, ntiles, sy, sz, flag);
+  return cudaGetLastError();
+}
+
+}  // namespace sc

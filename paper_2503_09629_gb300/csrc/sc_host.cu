@@ -1,0 +1,987 @@
+// sc_host.cu -- host runtime and C ABI of the subcycling library.
+//
+// Each level is stored as one dense FP64 array per field over the bounding
+// box of its boxes (grown by 3 ghost cells).  Sibling boxes therefore share
+// memory: a ghost cell of one box that is interior to another needs no copy.
+// The remaining ghost cells are classified once at creation:
+//   * refinement boundary (levels >= 1): filled from the parent's dense
+//     output after prolongation (Sec. II steps 2, 3, 5);
+//   * periodic images: copied from the wrapped interior cell;
+//   * outer boundary of a radiative level 0: evolved by the radiative kernel.
+// One coarse step (Sec. II steps 1-7, recursively) is a fixed sequence of
+// kernel launches, captured once into a CUDA graph per parity of the level-0
+// state buffers and replayed by sc_advance.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "sc_internal.h"
+
+using namespace sc;
+
+namespace {
+
+thread_local char g_err[512];
+
+sc_status fail(sc_status code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(SC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+enum CellKind : int8_t { K_UNUSED = 0, K_INTERIOR = 1, K_AMR = 2, K_PERIODIC = 3, K_PHYS = 4 };
+
+// Lagrange basis weights for nodes x[0..n-1] at point p.
+void lagrange_weights(const double* x, int n, double p, double* w) {
+  for (int m = 0; m < n; ++m) {
+    double num = 1.0, den = 1.0;
+    for (int q = 0; q < n; ++q)
+      if (q != m) {
+        num *= p - x[q];
+        den *= x[m] - x[q];
+      }
+    w[m] = num / den;
+  }
+}
+
+Weights make_weights() {
+  Weights w;
+  double x[kPN];
+  // parity 0: fine centre at -1/4 parent cell, nodes c-3..c+2;
+  // parity 1: fine centre at +1/4, nodes c-2..c+3 (offsets from parent c).
+  for (int m = 0; m < kPN; ++m) x[m] = -3.0 + m;
+  lagrange_weights(x, kPN, -0.25, w.prolong[0]);
+  for (int m = 0; m < kPN; ++m) x[m] = -2.0 + m;
+  lagrange_weights(x, kPN, 0.25, w.prolong[1]);
+  // restriction: fine cells 2C-2..2C+3 at offsets -2.5..2.5 fine cells from the parent centre
+  for (int m = 0; m < kRN; ++m) x[m] = -2.5 + m;
+  lagrange_weights(x, kRN, 0.0, w.restrict_w);
+  return w;
+}
+
+// Dense-output weights b_i(theta) and their theta-derivatives (Eqs.
+// denseoutput1/2): b1 = t - 3t^2/2 + 2t^3/3, b2 = b3 = t^2 - 2t^3/3,
+// b4 = -t^2/2 + 2t^3/3.
+void dense_weights(double t, int m, double* b) {
+  switch (m) {
+    case 0:
+      b[0] = t * (1.0 + t * (-1.5 + t * (2.0 / 3.0)));
+      b[1] = b[2] = t * t * (1.0 - t * (2.0 / 3.0));
+      b[3] = t * t * (-0.5 + t * (2.0 / 3.0));
+      break;
+    case 1:
+      b[0] = 1.0 + t * (-3.0 + 2.0 * t);
+      b[1] = b[2] = t * (2.0 - 2.0 * t);
+      b[3] = t * (-1.0 + 2.0 * t);
+      break;
+    case 2:
+      b[0] = -3.0 + 4.0 * t;
+      b[1] = b[2] = 2.0 - 4.0 * t;
+      b[3] = -1.0 + 4.0 * t;
+      break;
+    default:
+      b[0] = 4.0; b[1] = -4.0; b[2] = -4.0; b[3] = 4.0;
+  }
+}
+
+// Coefficients c_j of ghost value = P[y_n] + sum_j c_j P[k_j] for the fine
+// substep starting at progress theta0 of a parent step H (fine step h = H/2):
+//   which = 1..4: stage state Y_which from the Taylor expansions (Eqs. Y1-Y4)
+//                 with y, y', y'', y''' from dense output at theta0 and
+//                 f_y y'' = 4 (k3 - k2) / H^2;
+//   which = 0:    state at the end of the substep, dense output at theta0 + 1/2.
+void fill_coeffs(double H, double theta0, int which, double* c) {
+  double b0[4], b1[4], b2[4], b3[4];
+  if (which == 0) {
+    dense_weights(theta0 + 0.5, 0, b0);
+    for (int j = 0; j < 4; ++j) c[j] = H * b0[j];
+    return;
+  }
+  const double h = 0.5 * H;
+  dense_weights(theta0, 0, b0);
+  dense_weights(theta0, 1, b1);
+  dense_weights(theta0, 2, b2);
+  dense_weights(theta0, 3, b3);
+  const double fyy[4] = {0.0, -4.0, 4.0, 0.0};  // times 1/H^2
+  for (int j = 0; j < 4; ++j) {
+    const double y0 = H * b0[j], y1 = b1[j], y2 = b2[j] / H, y3 = b3[j] / (H * H), fy = fyy[j] / (H * H);
+    switch (which) {
+      case 1: c[j] = y0; break;
+      case 2: c[j] = y0 + 0.5 * h * y1; break;
+      case 3: c[j] = y0 + 0.5 * h * y1 + 0.25 * h * h * y2 + (h * h * h / 16.0) * (y3 - fy); break;
+      default: c[j] = y0 + h * y1 + 0.5 * h * h * y2 + (h * h * h / 8.0) * (y3 + fy); break;
+    }
+  }
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Level {
+  std::vector<sc_box> boxes;
+  Geom g;
+  double dt = 0;
+  std::vector<int8_t> kind;  // per array element (host only)
+  // device arrays: state pair, two stage buffers, k1..k4
+  double* S[2] = {nullptr, nullptr};
+  double* A = nullptr;
+  double* B = nullptr;
+  double* K[4] = {nullptr, nullptr, nullptr, nullptr};
+  // work lists (device) and their sizes
+  Tile* tiles = nullptr;
+  int ntiles = 0;
+  AmrCell* amr = nullptr;
+  int namr = 0;
+  double* amr_store = nullptr;  // 5 * F * namr prolonged parent vectors
+  int2* periodic = nullptr;
+  int nperiodic = 0;
+  int32_t* phys = nullptr;
+  int nphys = 0;
+  RestrictCell* restr = nullptr;  // parent cells restricted from this level
+  int nrestr = 0;
+  long interior_cells = 0;
+  int parity = 0;  // which of S[] holds the current state
+};
+
+enum OpKind { OP_PROLONG, OP_FILL, OP_STAGE, OP_RESTRICT };
+
+struct Op {
+  OpKind kind;
+  int level;
+  int stage;      // OP_STAGE: 1..4
+  double* in;     // stage input / fill target
+  double* yn;
+  double* out;
+  double c[4];    // OP_FILL coefficients
+  double cdt;     // OP_STAGE
+};
+
+}  // namespace
+
+struct sc_ctx {
+  int system = 0, F = 0, nlev = 0, bc = 0;
+  int ncells0[3];
+  double origin[3], h0 = 0, cfl = 0;
+  Z4cParams zp;
+  cudaStream_t stream = nullptr;
+  sc_allocator alloc{};
+  bool has_alloc = false;
+  std::vector<Level> lev;
+  Weights w;
+  double* scratch = nullptr;  // Z4c derivative temporaries
+  long scratch_fs = 0;
+  double* staging = nullptr;  // pack/unpack buffer
+  size_t staging_bytes = 0;
+  int* flag = nullptr;
+  std::vector<DevBuf> bufs;
+  size_t footprint = 0;
+  double t = 0;
+  double zu_finest = 0, zu_actual = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  long launches_per_step = 0;
+
+  void* dalloc(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (has_alloc) {
+      p = alloc.alloc(bytes, alloc.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) {
+      bufs.push_back({p, bytes});
+      footprint += bytes;
+    }
+    return p;
+  }
+  void release() {
+    for (auto& b : bufs) {
+      if (has_alloc) alloc.free(b.p, alloc.user);
+      else cudaFree(b.p);
+    }
+    bufs.clear();
+    footprint = 0;
+  }
+};
+
+namespace {
+
+int wrapi(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+// Global index of array element (i, j, k).
+inline void elem_global(const Geom& g, int i, int j, int k, int* gi) {
+  gi[0] = g.org[0] + i;
+  gi[1] = g.org[1] + j;
+  gi[2] = g.org[2] + k;
+}
+
+inline bool in_array(const Geom& g, const int* gi) {
+  for (int d = 0; d < 3; ++d)
+    if (gi[d] < g.org[d] || gi[d] >= g.org[d] + g.ext[d]) return false;
+  return true;
+}
+
+inline long elem_index(const Geom& g, const int* gi) {
+  return ((long)(gi[2] - g.org[2]) * g.ext[1] + (gi[1] - g.org[1])) * g.ext[0] + (gi[0] - g.org[0]);
+}
+
+sc_status validate(const sc_desc* d) {
+  if (!d) return fail(SC_EINVAL, "null descriptor");
+  if (d->system != SC_WAVE && d->system != SC_Z4C) return fail(SC_EINVAL, "unknown system %d", d->system);
+  if (d->nlevels < 1 || d->nlevels > 16) return fail(SC_EINVAL, "nlevels must be 1..16");
+  if (!d->nboxes || !d->boxes) return fail(SC_EINVAL, "null box arrays");
+  if (d->subcycle != 1) return fail(SC_EINVAL, "only the subcycled scheme is implemented on the GPU");
+  if (d->outer_bc != SC_BC_PERIODIC && d->outer_bc != SC_BC_RADIATIVE) return fail(SC_EINVAL, "unknown outer_bc");
+  if (!(d->h0 > 0) || !(d->cfl > 0)) return fail(SC_EINVAL, "h0 and cfl must be positive");
+  for (int q = 0; q < 3; ++q)
+    if (d->ncells0[q] < 1) return fail(SC_EINVAL, "ncells0 must be positive");
+  if (d->outer_bc == SC_BC_RADIATIVE && d->nboxes[0] != 1) return fail(SC_EINVAL, "radiative boundary needs one level-0 box");
+  int bi = 0;
+  for (int l = 0; l < d->nlevels; ++l) {
+    if (d->nboxes[l] < 1) return fail(SC_EINVAL, "level %d has no boxes", l);
+    for (int b = 0; b < d->nboxes[l]; ++b, ++bi) {
+      const sc_box& B = d->boxes[bi];
+      for (int q = 0; q < 3; ++q) {
+        const long ext = (long)d->ncells0[q] << l;
+        if (B.lo[q] < 0 || B.hi[q] < B.lo[q] || B.hi[q] >= ext)
+          return fail(SC_EINVAL, "box %d of level %d outside the level", b, l);
+        if (l > 0 && ((B.lo[q] & 1) || !(B.hi[q] & 1)))
+          return fail(SC_ENESTING, "box %d of level %d not aligned to parent cells", b, l);
+      }
+    }
+  }
+  return SC_OK;
+}
+
+// Build geometry, classification and work lists of every level (host side).
+struct HostLists {
+  std::vector<Tile> tiles;
+  std::vector<AmrCell> amr;
+  std::vector<int2> periodic;
+  std::vector<int32_t> phys;
+  std::vector<RestrictCell> restr;
+};
+
+sc_status build_level_geometry(sc_ctx* c, int l, const sc_box* boxes, int nb) {
+  Level& L = c->lev[l];
+  L.boxes.assign(boxes, boxes + nb);
+  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+  L.interior_cells = 0;
+  for (const sc_box& B : L.boxes) {
+    for (int q = 0; q < 3; ++q) {
+      lo[q] = std::min(lo[q], B.lo[q]);
+      hi[q] = std::max(hi[q], B.hi[q]);
+    }
+    L.interior_cells += (long)(B.hi[0] - B.lo[0] + 1) * (B.hi[1] - B.lo[1] + 1) * (B.hi[2] - B.lo[2] + 1);
+  }
+  Geom& g = L.g;
+  g.h = c->h0 / (double)(1L << l);
+  for (int q = 0; q < 3; ++q) {
+    g.org[q] = lo[q] - kGhost;
+    g.ext[q] = hi[q] - lo[q] + 1 + 2 * kGhost;
+    g.x0[q] = c->origin[q] + (g.org[q] + 0.5) * g.h;
+  }
+  g.pitch = (g.ext[0] + 7) & ~7;
+  const long plane = (long)g.pitch * g.ext[1] * g.ext[2];
+  if (plane >= (1L << 31)) return fail(SC_EINVAL, "level %d array too large for 32-bit offsets", l);
+  g.fs = (plane + 31) & ~31L;
+  L.dt = c->cfl * g.h;
+  // overlap check and interior marking
+  const long nelem = (long)g.ext[0] * g.ext[1] * g.ext[2];
+  L.kind.assign(nelem, K_UNUSED);
+  for (const sc_box& B : L.boxes)
+    for (int k = B.lo[2]; k <= B.hi[2]; ++k)
+      for (int j = B.lo[1]; j <= B.hi[1]; ++j)
+        for (int i = B.lo[0]; i <= B.hi[0]; ++i) {
+          const int gi[3] = {i, j, k};
+          int8_t& e = L.kind[elem_index(g, gi)];
+          if (e == K_INTERIOR) return fail(SC_EINVAL, "overlapping boxes on level %d", l);
+          e = K_INTERIOR;
+        }
+  return SC_OK;
+}
+
+bool is_interior(const Level& L, const int* gi) {
+  if (!in_array(L.g, gi)) return false;
+  return L.kind[elem_index(L.g, gi)] == K_INTERIOR;
+}
+
+sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
+  Level& L = c->lev[l];
+  const Geom& g = L.g;
+  const bool periodic = c->bc == SC_BC_PERIODIC;
+  int next[3];
+  for (int q = 0; q < 3; ++q) next[q] = c->ncells0[q] << l;
+  // ghost cells: within kGhost (per dimension) of a box interior
+  for (const sc_box& B : L.boxes)
+    for (int k = B.lo[2] - kGhost; k <= B.hi[2] + kGhost; ++k)
+      for (int j = B.lo[1] - kGhost; j <= B.hi[1] + kGhost; ++j)
+        for (int i = B.lo[0] - kGhost; i <= B.hi[0] + kGhost; ++i) {
+          const int gi[3] = {i, j, k};
+          const long e = elem_index(g, gi);
+          if (L.kind[e] != K_UNUSED) continue;
+          int gw[3];
+          bool outside = false;
+          for (int q = 0; q < 3; ++q) {
+            gw[q] = gi[q];
+            if (gi[q] < 0 || gi[q] >= next[q]) {
+              if (periodic) gw[q] = wrapi(gi[q], next[q]);
+              else outside = true;
+            }
+          }
+          if (outside) {
+            if (l != 0) return fail(SC_ENESTING, "level %d reaches the outer boundary", l);
+            L.kind[e] = K_PHYS;
+            continue;
+          }
+          if ((gw[0] != gi[0] || gw[1] != gi[1] || gw[2] != gi[2]) && is_interior(L, gw)) {
+            L.kind[e] = K_PERIODIC;
+            continue;
+          }
+          if (l == 0) return fail(SC_ENESTING, "level 0 does not cover the domain");
+          L.kind[e] = K_AMR;
+        }
+  // work lists
+  for (int k = 0; k < g.ext[2]; ++k)
+    for (int j = 0; j < g.ext[1]; ++j)
+      for (int i = 0; i < g.ext[0]; ++i) {
+        int gi[3];
+        elem_global(g, i, j, k, gi);
+        const int8_t kd = L.kind[elem_index(g, gi)];
+        const int32_t off = (int32_t)g.off(gi[0], gi[1], gi[2]);
+        if (kd == K_PHYS) {
+          hl.phys.push_back(off);
+        } else if (kd == K_PERIODIC) {
+          int gw[3];
+          for (int q = 0; q < 3; ++q) gw[q] = wrapi(gi[q], next[q]);
+          hl.periodic.push_back(make_int2(off, (int32_t)g.off(gw[0], gw[1], gw[2])));
+        } else if (kd == K_AMR) {
+          // wrapped fine index, parent cell and the 6^3 parent stencil
+          int gw[3], first[3], par = 0;
+          for (int q = 0; q < 3; ++q) {
+            gw[q] = periodic ? wrapi(gi[q], next[q]) : gi[q];
+            const int pc = gw[q] >> 1;
+            const int odd = gw[q] & 1;
+            par |= odd << q;
+            first[q] = odd ? pc - 2 : pc - 3;
+          }
+          const Level& P = c->lev[l - 1];
+          for (int a = 0; a < kPN; ++a)
+            for (int b = 0; b < kPN; ++b)
+              for (int d = 0; d < kPN; ++d) {
+                const int pg[3] = {first[0] + d, first[1] + b, first[2] + a};
+                if (!is_interior(P, pg))
+                  return fail(SC_ENESTING,
+                              "level %d: prolongation stencil of ghost cell (%d,%d,%d) leaves the parent interior", l,
+                              gi[0], gi[1], gi[2]);
+              }
+          AmrCell ac;
+          ac.dst = off;
+          ac.pbase = (int32_t)P.g.off(first[0], first[1], first[2]);
+          ac.parity = par;
+          hl.amr.push_back(ac);
+        }
+      }
+  // interior tiles: per box, x tiles of 32 (or the box width), 4 x 2 in y, z
+  for (const sc_box& B : L.boxes)
+    for (int z = B.lo[2]; z <= B.hi[2]; z += 2)
+      for (int y = B.lo[1]; y <= B.hi[1]; y += 4)
+        for (int x = B.lo[0]; x <= B.hi[0]; x += 32) {
+          Tile t;
+          t.x0 = x - g.org[0];
+          t.y0 = y - g.org[1];
+          t.z0 = z - g.org[2];
+          t.nx = std::min(32, B.hi[0] - x + 1);
+          t.ny = std::min(4, B.hi[1] - y + 1);
+          t.nz = std::min(2, B.hi[2] - z + 1);
+          hl.tiles.push_back(t);
+        }
+  // restriction onto the parent: parent cells whose 8 children are interior here
+  if (l > 0) {
+    const Level& P = c->lev[l - 1];
+    const Geom& pg = P.g;
+    for (int k = 0; k < pg.ext[2]; ++k)
+      for (int j = 0; j < pg.ext[1]; ++j)
+        for (int i = 0; i < pg.ext[0]; ++i) {
+          int C[3];
+          elem_global(pg, i, j, k, C);
+          if (P.kind[elem_index(pg, C)] != K_INTERIOR) continue;
+          bool covered = true;
+          for (int q = 0; q < 8 && covered; ++q) {
+            const int fc[3] = {2 * C[0] + (q & 1), 2 * C[1] + ((q >> 1) & 1), 2 * C[2] + ((q >> 2) & 1)};
+            covered = is_interior(L, fc);
+          }
+          if (!covered) continue;
+          const int fb[3] = {2 * C[0] - 2, 2 * C[1] - 2, 2 * C[2] - 2};
+          const int fe[3] = {2 * C[0] + 3, 2 * C[1] + 3, 2 * C[2] + 3};
+          if (!in_array(g, fb) || !in_array(g, fe)) return fail(SC_ENESTING, "restriction stencil outside level %d", l);
+          RestrictCell rc;
+          rc.dst = (int32_t)pg.off(C[0], C[1], C[2]);
+          rc.fbase = (int32_t)g.off(fb[0], fb[1], fb[2]);
+          hl.restr.push_back(rc);
+        }
+  }
+  return SC_OK;
+}
+
+template <class T>
+sc_status upload(sc_ctx* c, const std::vector<T>& v, T** dst) {
+  *dst = nullptr;
+  if (v.empty()) return SC_OK;
+  *dst = (T*)c->dalloc(v.size() * sizeof(T));
+  if (!*dst) return fail(SC_ENOMEM, "device allocation of %zu bytes failed", v.size() * sizeof(T));
+  CU(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  return SC_OK;
+}
+
+// ---------------------------------------------------------------- schedule
+struct Emitter {
+  sc_ctx* c;
+  std::vector<Op> ops;
+  std::vector<int> par;
+
+  void fill(int l, double* vec, int which, double theta0) {
+    Op o{};
+    o.kind = OP_FILL;
+    o.level = l;
+    o.in = vec;
+    o.stage = which;
+    if (l > 0) fill_coeffs(c->lev[l - 1].dt, theta0, which, o.c);
+    ops.push_back(o);
+  }
+  // One RK4 step of level l (Eqs. rk1-rk5); for l >= 1 the fine substep at
+  // progress theta0 of the parent step.
+  void level_step(int l, double theta0) {
+    Level& L = c->lev[l];
+    double* yn = L.S[par[l]];
+    double* ynew = L.S[par[l] ^ 1];
+    double* in[4] = {yn, L.A, L.B, L.A};
+    const double cs[3] = {0.5, 0.5, 1.0};
+    for (int s = 1; s <= 4; ++s) {
+      fill(l, in[s - 1], s, theta0);
+      Op o{};
+      o.kind = OP_STAGE;
+      o.level = l;
+      o.stage = s;
+      o.in = in[s - 1];
+      o.yn = yn;
+      o.out = (s < 4) ? in[s] : ynew;
+      o.cdt = (s < 4) ? cs[s - 1] * L.dt : L.dt / 6.0;
+      ops.push_back(o);
+    }
+    if (l > 0) fill(l, ynew, 0, theta0);  // end-of-substep ghosts, read by restriction
+    par[l] ^= 1;
+  }
+  // Steps 2-7 below level l, after level l has taken a step.
+  void children(int l) {
+    Op p{};
+    p.kind = OP_PROLONG;
+    p.level = l + 1;
+    p.yn = c->lev[l].S[par[l] ^ 1];  // parent's y_n (its state before the step)
+    ops.push_back(p);
+    for (int s = 0; s < 2; ++s) {
+      level_step(l + 1, 0.5 * s);
+      if (l + 2 < c->nlev) children(l + 1);
+    }
+    Op r{};
+    r.kind = OP_RESTRICT;
+    r.level = l + 1;
+    r.in = c->lev[l + 1].S[par[l + 1]];  // fine state at the end of the parent step
+    r.out = c->lev[l].S[par[l]];         // parent's new state
+    ops.push_back(r);
+  }
+  void coarse_step() {
+    level_step(0, 0.0);
+    if (c->nlev > 1) children(0);
+  }
+};
+
+sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
+  Level& L = c->lev[o.level];
+  const Geom& g = L.g;
+  switch (o.kind) {
+    case OP_PROLONG: {
+      const Level& P = c->lev[o.level - 1];
+      CU(launch_amr_prolong(o.yn, P.K[0], P.K[1], P.K[2], P.K[3], P.g.fs, P.g.pitch, P.g.pitch * P.g.ext[1], L.amr,
+                            L.namr, L.amr_store, c->F, c->w, s));
+      break;
+    }
+    case OP_FILL:
+      if (o.level > 0) CU(launch_amr_apply(o.in, g.fs, c->F, L.amr, L.namr, L.amr_store, o.c, s));
+      CU(launch_periodic_copy(o.in, g.fs, c->F, L.periodic, L.nperiodic, s));
+      break;
+    case OP_STAGE: {
+      StageArgs a{};
+      a.Y = o.in;
+      a.yn = o.yn;
+      a.k = L.K[o.stage - 1];
+      a.out = o.out;
+      a.k1 = L.K[0];
+      a.k2 = L.K[1];
+      a.k3 = L.K[2];
+      a.cdt = o.cdt;
+      a.stage = o.stage;
+      a.fs = g.fs;
+      a.sy = g.pitch;
+      a.sz = g.pitch * g.ext[1];
+      a.h = g.h;
+      if (c->system == SC_WAVE) {
+        CU(launch_wave_stage(a, L.tiles, L.ntiles, s));
+      } else {
+        CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, s));
+        CU(launch_z4c_stage(a, c->scratch, c->zp, L.tiles, L.ntiles, s));
+      }
+      if (L.nphys) CU(launch_radiative_stage(a, L.phys, L.nphys, c->F, g, c->system, s));
+      break;
+    }
+    case OP_RESTRICT: {
+      const Level& P = c->lev[o.level - 1];
+      CU(launch_restrict(o.out, P.g.fs, o.in, g.fs, g.pitch, g.pitch * g.ext[1], L.restr, L.nrestr, c->F, c->w, s));
+      break;
+    }
+  }
+  return SC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Graph capture of one coarse step per parity of the level-0 state.
+
+namespace {
+
+sc_status build_graphs(sc_ctx* c) {
+  for (int p = 0; p < 2; ++p) {
+    Emitter em;
+    em.c = c;
+    em.par.assign(c->nlev, 0);
+    em.par[0] = p;
+    em.coarse_step();
+    cudaStream_t cs;
+    CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      return fail(SC_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    }
+    sc_status st = SC_OK;
+    for (const Op& o : em.ops) {
+      st = run_op(c, o, cs);
+      if (st != SC_OK) break;
+    }
+    e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (st != SC_OK) return st;
+    if (e != cudaSuccess) return fail(SC_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    size_t nn = 0;
+    CU(cudaGraphGetNodes(graph, nullptr, &nn));
+    c->launches_per_step = (long)nn;
+    e = cudaGraphInstantiate(&c->graph[p], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(SC_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  return SC_OK;
+}
+
+sc_status check_box(sc_ctx* c, int level, int box, int field) {
+  if (!c) return fail(SC_EINVAL, "null context");
+  if (level < 0 || level >= c->nlev) return fail(SC_EINVAL, "bad level %d", level);
+  if (box < 0 || box >= (int)c->lev[level].boxes.size()) return fail(SC_EINVAL, "bad box %d", box);
+  if (field < 0 || field >= c->F) return fail(SC_EINVAL, "bad field %d", field);
+  return SC_OK;
+}
+
+sc_status ensure_staging(sc_ctx* c, size_t bytes) {
+  if (c->staging_bytes >= bytes) return SC_OK;
+  c->staging = (double*)c->dalloc(bytes);
+  if (!c->staging) return fail(SC_ENOMEM, "staging allocation of %zu bytes failed", bytes);
+  c->staging_bytes = bytes;
+  return SC_OK;
+}
+
+// Region of a box (optionally with ghosts): lo and extents.
+void box_region(const sc_box& B, bool ghosted, int* lo, int* n) {
+  const int g = ghosted ? kGhost : 0;
+  for (int q = 0; q < 3; ++q) {
+    lo[q] = B.lo[q] - g;
+    n[q] = B.hi[q] - B.lo[q] + 1 + 2 * g;
+  }
+}
+
+sc_status copy_field(sc_ctx* c, int level, int box, int field, bool ghosted, const double* src, double* dst,
+                     bool host) {
+  sc_status st = check_box(c, level, box, field);
+  if (st) return st;
+  Level& L = c->lev[level];
+  int lo[3], n[3];
+  box_region(L.boxes[box], ghosted, lo, n);
+  const size_t bytes = sizeof(double) * (size_t)n[0] * n[1] * n[2];
+  double* state = L.S[L.parity] + (long)field * L.g.fs;
+  if (src) {
+    const double* dsrc = src;
+    if (host) {
+      if ((st = ensure_staging(c, bytes))) return st;
+      CU(cudaMemcpyAsync(c->staging, src, bytes, cudaMemcpyHostToDevice, c->stream));
+      dsrc = c->staging;
+    }
+    CU(launch_unpack(state, L.g, lo, n, dsrc, c->stream));
+    if (host) CU(cudaStreamSynchronize(c->stream));
+  } else {
+    double* ddst = dst;
+    if (host) {
+      if ((st = ensure_staging(c, bytes))) return st;
+      ddst = c->staging;
+    }
+    CU(launch_pack(state, L.g, lo, n, ddst, c->stream));
+    if (host) {
+      CU(cudaMemcpyAsync(dst, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+    }
+  }
+  return SC_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+const char* sc_last_error(void) { return g_err; }
+
+sc_status sc_footprint_estimate(const sc_desc* d, size_t* bytes) {
+  sc_status st = validate(d);
+  if (st) return st;
+  const int F = d->system == SC_WAVE ? kNWave : kNZ4c;
+  size_t total = 0, maxfs = 0;
+  int bi = 0;
+  for (int l = 0; l < d->nlevels; ++l) {
+    int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+    long ghost_cells = 0;
+    for (int b = 0; b < d->nboxes[l]; ++b, ++bi) {
+      const sc_box& B = d->boxes[bi];
+      long inner = 1, outer = 1;
+      for (int q = 0; q < 3; ++q) {
+        lo[q] = std::min(lo[q], B.lo[q]);
+        hi[q] = std::max(hi[q], B.hi[q]);
+        inner *= B.hi[q] - B.lo[q] + 1;
+        outer *= B.hi[q] - B.lo[q] + 1 + 2 * kGhost;
+      }
+      ghost_cells += outer - inner;
+    }
+    const long pitch = ((hi[0] - lo[0] + 1 + 2 * kGhost) + 7) & ~7;
+    const long fs = ((pitch * (hi[1] - lo[1] + 1 + 2 * kGhost) * (hi[2] - lo[2] + 1 + 2 * kGhost)) + 31) & ~31L;
+    total += 8 * (size_t)F * fs * sizeof(double);                 // S0, S1, A, B, k1..k4
+    total += (size_t)ghost_cells * (5 * F * sizeof(double) + 32);  // prolonged vectors + lists
+    total += (size_t)fs * 4;                                       // tiles and other lists (bound)
+    maxfs = std::max(maxfs, (size_t)fs);
+  }
+  if (d->system == SC_Z4C) total += (size_t)maxfs * 176 * sizeof(double);
+  *bytes = total;
+  return SC_OK;
+}
+
+sc_status sc_create(const sc_desc* d, sc_ctx** out) {
+  if (!out) return fail(SC_EINVAL, "null output pointer");
+  *out = nullptr;
+  sc_status st = validate(d);
+  if (st) return st;
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  std::unique_ptr<sc_ctx> c(new sc_ctx());
+  c->system = d->system;
+  c->F = d->system == SC_WAVE ? kNWave : kNZ4c;
+  c->nlev = d->nlevels;
+  c->bc = d->outer_bc;
+  for (int q = 0; q < 3; ++q) {
+    c->ncells0[q] = d->ncells0[q];
+    c->origin[q] = d->origin[q];
+  }
+  c->h0 = d->h0;
+  c->cfl = d->cfl;
+  c->zp = Z4cParams{d->kappa1, d->kappa2, d->eta, d->ko_sigma};
+  c->stream = (cudaStream_t)d->cuda_stream;
+  if (d->allocator && d->allocator->alloc && d->allocator->free) {
+    c->alloc = *d->allocator;
+    c->has_alloc = true;
+  }
+  c->w = make_weights();
+  c->lev.resize(c->nlev);
+  int bi = 0;
+  for (int l = 0; l < c->nlev; ++l) {
+    st = build_level_geometry(c.get(), l, d->boxes + bi, d->nboxes[l]);
+    if (st) return st;
+    bi += d->nboxes[l];
+  }
+  long maxfs = 0;
+  for (int l = 0; l < c->nlev; ++l) {
+    HostLists hl;
+    st = classify_level(c.get(), l, hl);
+    if (st) {
+      c->release();
+      return st;
+    }
+    Level& L = c->lev[l];
+    const size_t vbytes = sizeof(double) * (size_t)c->F * L.g.fs;
+    double** vecs[8] = {&L.S[0], &L.S[1], &L.A, &L.B, &L.K[0], &L.K[1], &L.K[2], &L.K[3]};
+    for (double** v : vecs) {
+      *v = (double*)c->dalloc(vbytes);
+      if (!*v) {
+        c->release();
+        return fail(SC_ENOMEM, "level %d: allocation of %zu bytes failed", l, vbytes);
+      }
+      CU(cudaMemsetAsync(*v, 0, vbytes, c->stream));
+    }
+    if ((st = upload(c.get(), hl.tiles, &L.tiles)) || (st = upload(c.get(), hl.amr, &L.amr)) ||
+        (st = upload(c.get(), hl.periodic, &L.periodic)) || (st = upload(c.get(), hl.phys, &L.phys)) ||
+        (st = upload(c.get(), hl.restr, &L.restr))) {
+      c->release();
+      return st;
+    }
+    L.ntiles = (int)hl.tiles.size();
+    L.namr = (int)hl.amr.size();
+    L.nperiodic = (int)hl.periodic.size();
+    L.nphys = (int)hl.phys.size();
+    L.nrestr = (int)hl.restr.size();
+    if (L.namr) {
+      L.amr_store = (double*)c->dalloc(sizeof(double) * 5 * (size_t)c->F * L.namr);
+      if (!L.amr_store) {
+        c->release();
+        return fail(SC_ENOMEM, "level %d: ghost store allocation failed", l);
+      }
+    }
+    maxfs = std::max(maxfs, L.g.fs);
+  }
+  if (c->system == SC_Z4C) {
+    c->scratch_fs = maxfs;
+    c->scratch = (double*)c->dalloc(sizeof(double) * 176 * (size_t)maxfs);
+    if (!c->scratch) {
+      c->release();
+      return fail(SC_ENOMEM, "derivative scratch allocation failed");
+    }
+  }
+  c->flag = (int*)c->dalloc(sizeof(int));
+  if (!c->flag) {
+    c->release();
+    return fail(SC_ENOMEM, "flag allocation failed");
+  }
+  // lists are uploaded from pageable host vectors: finish before they go away
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->release();
+    return fail(SC_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
+  }
+  for (Level& L : c->lev) L.kind.clear(), L.kind.shrink_to_fit();
+  st = build_graphs(c.get());
+  if (st) {
+    c->release();
+    return st;
+  }
+  *out = c.release();
+  return SC_OK;
+}
+
+void sc_destroy(sc_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (int p = 0; p < 2; ++p)
+    if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
+  c->release();
+  delete c;
+}
+
+sc_status sc_set_initial_data(sc_ctx* c, int kind, const double* params, int nparams) {
+  if (!c) return fail(SC_EINVAL, "null context");
+  if (nparams < 0 || nparams > 8 || (nparams > 0 && !params)) return fail(SC_EINVAL, "bad parameters");
+  const bool wave_kind = kind == SC_ID_STANDING_WAVE || kind == SC_ID_GAUSSIAN || kind == SC_ID_SPHERICAL_GAUSSIAN;
+  const bool z4c_kind = kind == SC_ID_BRILL_LINDQUIST || kind == SC_ID_MINKOWSKI;
+  if ((c->system == SC_WAVE && !wave_kind) || (c->system == SC_Z4C && !z4c_kind))
+    return fail(SC_EINVAL, "initial data kind %d does not match the system", kind);
+  const int need[5] = {4, 5, 8, 0, 6};
+  if (nparams < need[kind]) return fail(SC_EINVAL, "initial data kind %d needs %d parameters", kind, need[kind]);
+  for (Level& L : c->lev) {
+    L.parity = 0;
+    CU(launch_initial_data(L.S[0], L.g, c->F, c->system, kind, params, nparams, c->stream));
+  }
+  c->t = 0;
+  c->zu_finest = c->zu_actual = 0;
+  CU(cudaStreamSynchronize(c->stream));
+  return SC_OK;
+}
+
+sc_status sc_set_field(sc_ctx* c, int l, int b, int f, const double* src) {
+  if (!src) return fail(SC_EINVAL, "null source");
+  return copy_field(c, l, b, f, false, src, nullptr, true);
+}
+sc_status sc_set_field_ghosted(sc_ctx* c, int l, int b, int f, const double* src) {
+  if (!src) return fail(SC_EINVAL, "null source");
+  return copy_field(c, l, b, f, true, src, nullptr, true);
+}
+sc_status sc_get_field(sc_ctx* c, int l, int b, int f, double* dst) {
+  if (!dst) return fail(SC_EINVAL, "null destination");
+  return copy_field(c, l, b, f, false, nullptr, dst, true);
+}
+sc_status sc_get_field_ghosted(sc_ctx* c, int l, int b, int f, double* dst) {
+  if (!dst) return fail(SC_EINVAL, "null destination");
+  return copy_field(c, l, b, f, true, nullptr, dst, true);
+}
+sc_status sc_set_field_device(sc_ctx* c, int l, int b, int f, const double* src) {
+  if (!src) return fail(SC_EINVAL, "null source");
+  return copy_field(c, l, b, f, false, src, nullptr, false);
+}
+sc_status sc_get_field_device(sc_ctx* c, int l, int b, int f, double* dst) {
+  if (!dst) return fail(SC_EINVAL, "null destination");
+  return copy_field(c, l, b, f, false, nullptr, dst, false);
+}
+
+sc_status sc_advance(sc_ctx* c, int n) {
+  if (!c) return fail(SC_EINVAL, "null context");
+  if (n < 0) return fail(SC_EINVAL, "negative step count");
+  const int L = c->nlev;
+  for (int s = 0; s < n; ++s) {
+    Level& L0 = c->lev[0];
+    CU(cudaGraphLaunch(c->graph[L0.parity], c->stream));
+    L0.parity ^= 1;
+    c->t += L0.dt;
+    for (int l = 0; l < L; ++l) {
+      c->zu_finest += (double)(1L << (L - 1)) * (double)c->lev[l].interior_cells;
+      c->zu_actual += (double)(1L << l) * (double)c->lev[l].interior_cells;
+    }
+  }
+  return SC_OK;
+}
+
+sc_status sc_synchronize(sc_ctx* c) {
+  if (!c) return fail(SC_EINVAL, "null context");
+  CU(cudaStreamSynchronize(c->stream));
+  return SC_OK;
+}
+
+sc_status sc_get_constraints(sc_ctx* c, int level, int box, double* dst) {
+  sc_status st = check_box(c, level, box, 0);
+  if (st) return st;
+  if (c->system != SC_Z4C) return fail(SC_EINVAL, "constraints need Z4c");
+  if (!dst) return fail(SC_EINVAL, "null destination");
+  Level& L = c->lev[level];
+  const sc_box& B = L.boxes[box];
+  int lo[3], n[3];
+  box_region(B, false, lo, n);
+  const long ncell = (long)n[0] * n[1] * n[2];
+  const size_t bytes = sizeof(double) * kNCons * (size_t)ncell;
+  if ((st = ensure_staging(c, bytes))) return st;
+  // tiles of this box only
+  std::vector<Tile> tl;
+  for (int z = B.lo[2]; z <= B.hi[2]; z += 2)
+    for (int y = B.lo[1]; y <= B.hi[1]; y += 4)
+      for (int x = B.lo[0]; x <= B.hi[0]; x += 32) {
+        Tile t;
+        t.x0 = x - L.g.org[0];
+        t.y0 = y - L.g.org[1];
+        t.z0 = z - L.g.org[2];
+        t.nx = std::min(32, B.hi[0] - x + 1);
+        t.ny = std::min(4, B.hi[1] - y + 1);
+        t.nz = std::min(2, B.hi[2] - z + 1);
+        tl.push_back(t);
+      }
+  Tile* dt = (Tile*)c->dalloc(tl.size() * sizeof(Tile));
+  if (!dt) return fail(SC_ENOMEM, "tile list allocation failed");
+  CU(cudaMemcpyAsync(dt, tl.data(), tl.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
+  const double* Y = L.S[L.parity];
+  const int sy = L.g.pitch, sz = L.g.pitch * L.g.ext[1];
+  const int blo[3] = {B.lo[0] - L.g.org[0], B.lo[1] - L.g.org[1], B.lo[2] - L.g.org[2]};
+  CU(launch_z4c_derivs(Y, c->scratch, L.g.fs, sy, sz, L.g.h, dt, (int)tl.size(), c->stream));
+  CU(launch_z4c_constraints(Y, c->scratch, c->staging, L.g.fs, sy, sz, c->zp, dt, (int)tl.size(), ncell, blo, n,
+                            c->stream));
+  CU(cudaMemcpyAsync(dst, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return SC_OK;
+}
+
+sc_status sc_get_time(sc_ctx* c, double* t) {
+  if (!c || !t) return fail(SC_EINVAL, "null argument");
+  *t = c->t;
+  return SC_OK;
+}
+
+sc_status sc_zone_updates(sc_ctx* c, double* finest, double* actual) {
+  if (!c || !finest || !actual) return fail(SC_EINVAL, "null argument");
+  *finest = c->zu_finest;
+  *actual = c->zu_actual;
+  return SC_OK;
+}
+
+sc_status sc_launches_per_step(sc_ctx* c, long* n) {
+  if (!c || !n) return fail(SC_EINVAL, "null argument");
+  *n = c->launches_per_step;
+  return SC_OK;
+}
+
+sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
+  if (!c || !ms || nrep < 1) return fail(SC_EINVAL, "bad argument");
+  if (level < 0 || level >= c->nlev) return fail(SC_EINVAL, "bad level %d", level);
+  Level& L = c->lev[level];
+  const Geom& g = L.g;
+  StageArgs a{};
+  a.Y = L.A;
+  a.yn = L.S[L.parity];
+  a.k = L.K[1];
+  a.out = L.B;
+  a.k1 = L.K[0];
+  a.k2 = L.K[1];
+  a.k3 = L.K[2];
+  a.cdt = 0.5 * L.dt;
+  a.stage = 2;
+  a.fs = g.fs;
+  a.sy = g.pitch;
+  a.sz = g.pitch * g.ext[1];
+  a.h = g.h;
+  cudaEvent_t e[3];
+  for (auto& x : e) CU(cudaEventCreate(&x));
+  float t0 = 0, t1 = 0;
+  CU(cudaEventRecord(e[0], c->stream));
+  for (int r = 0; r < nrep; ++r) {
+    if (c->system == SC_WAVE) CU(launch_wave_stage(a, L.tiles, L.ntiles, c->stream));
+    else CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, c->stream));
+  }
+  CU(cudaEventRecord(e[1], c->stream));
+  if (c->system == SC_Z4C)
+    for (int r = 0; r < nrep; ++r) CU(launch_z4c_stage(a, c->scratch, c->zp, L.tiles, L.ntiles, c->stream));
+  CU(cudaEventRecord(e[2], c->stream));
+  CU(cudaEventSynchronize(e[2]));
+  CU(cudaEventElapsedTime(&t0, e[0], e[1]));
+  CU(cudaEventElapsedTime(&t1, e[1], e[2]));
+  for (auto& x : e) cudaEventDestroy(x);
+  ms[0] = t0 / nrep;
+  ms[1] = c->system == SC_Z4C ? t1 / nrep : 0.0;
+  return SC_OK;
+}
+
+sc_status sc_footprint(sc_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return fail(SC_EINVAL, "null argument");
+  *bytes = c->footprint;
+  return SC_OK;
+}
+
+}  // extern "C"

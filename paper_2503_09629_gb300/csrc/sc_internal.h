@@ -1,0 +1,115 @@
+// sc_internal.h -- shared declarations of the subcycling library (host runtime
+// and kernel launchers).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "subcyc.h"
+
+namespace sc {
+
+constexpr int kGhost = 3;   // ghost width of every box
+constexpr int kPN = 6;      // prolongation stencil points per dimension (quintic)
+constexpr int kRN = 6;      // restriction stencil points per dimension (quintic)
+constexpr int kNZ4c = 22;   // Z4c evolved fields
+constexpr int kNWave = 2;   // scalar wave fields (u, Pi)
+constexpr int kNCons = 7;   // Z4c constraint outputs (H, M^i, G^i)
+
+// Z4c field order: W, gt(xx,xy,xz,yy,yz,zz), Khat, At(6), Gamt(3), Theta, alpha, beta(3).
+enum { ZW = 0, ZG = 1, ZK = 7, ZA = 8, ZGAM = 14, ZTH = 17, ZAL = 18, ZB = 19 };
+
+// Geometry of one level's dense array.  The array covers the bounding box of
+// the level's box interiors grown by the ghost width; x is fastest.
+struct Geom {
+  int org[3];     // global cell index of array element (0,0,0)
+  int ext[3];     // array extents
+  int pitch;      // row pitch (>= ext[0], multiple of 8)
+  long fs;        // field stride in doubles (multiple of 32)
+  double h;       // grid spacing
+  double x0[3];   // physical centre of array element (0,0,0)
+  long off(int gx, int gy, int gz) const {
+    return ((long)(gz - org[2]) * ext[1] + (gy - org[1])) * pitch + (gx - org[0]);
+  }
+};
+
+// One interior tile: array coordinates of its first cell and its extents.
+struct Tile {
+  int x0, y0, z0, nx, ny, nz;
+};
+
+// Refinement-boundary ghost cell: destination offset in the fine array,
+// offset of the first parent stencil cell in the parent array, parity of
+// the fine index per dimension (bit d set: fine centre at +1/4 parent cell).
+struct AmrCell {
+  int32_t dst;
+  int32_t pbase;
+  int32_t parity;
+};
+
+// Restricted parent cell: its offset in the parent array and the offset of
+// the first fine stencil cell (2C-2 per dimension) in the fine array.
+struct RestrictCell {
+  int32_t dst;
+  int32_t fbase;
+};
+
+struct Weights {
+  double prolong[2][kPN];   // [parity][node]
+  double restrict_w[kRN];
+};
+
+// Arguments of one fused RK4 stage (right-hand side + stage update).
+struct StageArgs {
+  const double* Y;   // stage input, ghosts valid
+  const double* yn;  // state at the start of the step
+  double* k;         // k_stage (output)
+  double* out;       // Y_{stage+1} (stage < 4) or y_{n+1} (stage == 4)
+  const double* k1;
+  const double* k2;
+  const double* k3;
+  double cdt;        // c_stage * dt (stage < 4), dt / 6 (stage == 4)
+  int stage;         // 1..4
+  long fs;
+  int sy, sz;        // strides of y and z in doubles
+  double h;
+};
+
+struct Z4cParams {
+  double kappa1, kappa2, eta, ko_sigma;
+};
+
+// ---- kernel launchers (defined in the .cu files) -------------------------
+cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s);
+
+cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy, int sz, double h,
+                              const Tile* tiles, int ntiles, cudaStream_t s);
+cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4cParams& p,
+                             const Tile* tiles, int ntiles, cudaStream_t s);
+cudaError_t launch_radiative_stage(const StageArgs& a, const int32_t* cells, int ncells, int F,
+                                   const Geom& g, int system, cudaStream_t s);
+cudaError_t launch_z4c_constraints(const double* Y, const double* scratch, double* out, long fs, int sy,
+                                   int sz, const Z4cParams& p, const Tile* tiles, int ntiles, long out_stride,
+                                   const int* box_lo, const int* box_n, cudaStream_t s);
+
+cudaError_t launch_periodic_copy(double* vec, long fs, int F, const int2* pairs, int npairs, cudaStream_t s);
+cudaError_t launch_amr_prolong(const double* yn, const double* k1, const double* k2, const double* k3,
+                               const double* k4, long pfs, int psy, int psz, const AmrCell* cells,
+                               int ncells, double* store, int F, const Weights& w, cudaStream_t s);
+cudaError_t launch_amr_apply(double* vec, long fs, int F, const AmrCell* cells, int ncells,
+                             const double* store, const double* c4, cudaStream_t s);
+cudaError_t launch_restrict(double* parent, long pfs, const double* fine, long ffs, int fsy, int fsz,
+                            const RestrictCell* cells, int ncells, int F, const Weights& w, cudaStream_t s);
+cudaError_t launch_initial_data(double* vec, const Geom& g, int F, int system, int kind, const double* params,
+                                int nparams, cudaStream_t s);
+cudaError_t launch_pack(const double* vec, const Geom& g, const int* lo, const int* n, double* dst,
+                        cudaStream_t s);
+cudaError_t launch_unpack(double* vec, const Geom& g, const int* lo, const int* n, const double* src,
+                          cudaStream_t s);
+cudaError_t launch_nonfinite_check(const double* vec, long fs, int F, const Tile* tiles, int ntiles, int sy,
+                                   int sz, int* flag, cudaStream_t s);
+
+}  // namespace sc

@@ -1,0 +1,114 @@
+// sc_wave.cu -- fused RK4 stage for the scalar wave (Sec. IV.A) and the
+// radiative outer-boundary stage shared by both systems.
+//
+// One launch covers every interior tile of a level: k_i = f(Y_i) with the
+// 4th-order centred Laplacian, then the stage update
+//   Y_{i+1} = y_n + c_i dt k_i        (i < 4, Eqs. rk2-rk4 stage vectors)
+//   y_{n+1} = y_n + dt/6 (k1 + 2 k2 + 2 k3 + k4)   (i = 4, Eq. rk5)
+// k_i is stored because finer levels need k1..k4 for dense output.
+#include "sc_internal.h"
+
+namespace sc {
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads) wave_stage_kernel(StageArgs a, const Tile* __restrict__ tiles,
+                                                             int ntiles) {
+  const double inv12h2 = 1.0 / (12.0 * a.h * a.h);
+  const long sy = a.sy, sz = a.sz;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile T = tiles[t];
+    const int n = T.nx * T.ny * T.nz;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      const int i = q % T.nx;
+      const int j = (q / T.nx) % T.ny;
+      const int k = q / (T.nx * T.ny);
+      const long o = (T.z0 + k) * sz + (T.y0 + j) * sy + (T.x0 + i);
+      const double* u = a.Y;
+      const double u0 = u[o];
+      // -1, 16, -30, 16, -1 over offsets -2..2 in each dimension, / (12 h^2)
+      const double s1 = (u[o - 1] + u[o + 1]) + (u[o - sy] + u[o + sy]) + (u[o - sz] + u[o + sz]);
+      const double s2 = (u[o - 2] + u[o + 2]) + (u[o - 2 * sy] + u[o + 2 * sy]) + (u[o - 2 * sz] + u[o + 2 * sz]);
+      const double lap = fma(-90.0, u0, fma(16.0, s1, -s2)) * inv12h2;
+      const double ku = a.Y[a.fs + o];  // d_t u = Pi
+      const double kp = lap;            // d_t Pi = Laplacian u
+      a.k[o] = ku;
+      a.k[a.fs + o] = kp;
+      if (a.stage < 4) {
+        a.out[o] = fma(a.cdt, ku, a.yn[o]);
+        a.out[a.fs + o] = fma(a.cdt, kp, a.yn[a.fs + o]);
+      } else {
+        const double su = fma(2.0, a.k3[o], fma(2.0, a.k2[o], a.k1[o])) + ku;
+        const double sp = fma(2.0, a.k3[a.fs + o], fma(2.0, a.k2[a.fs + o], a.k1[a.fs + o])) + kp;
+        a.out[o] = fma(a.cdt, su, a.yn[o]);
+        a.out[a.fs + o] = fma(a.cdt, sp, a.yn[a.fs + o]);
+      }
+    }
+  }
+}
+
+// Outgoing radiative condition on the outer ghost shell of a radiative
+// level 0 (the boundary cells are evolved with their own right-hand side):
+//   d_t u = -(x^i / r) d_i u - (u - u_inf) / r
+// with 2nd-order differences, centred where both neighbours exist in the
+// array and one-sided inwards on its outermost layer; u_inf = 1 for W,
+// alpha and the diagonal of gt, 0 otherwise.
+__global__ void __launch_bounds__(kThreads) radiative_stage_kernel(StageArgs a, const int32_t* __restrict__ cells,
+                                                                  int ncells, int F, Geom g, int system) {
+  const double inv2h = 1.0 / (2.0 * a.h);
+  const long str[3] = {1, (long)a.sy, (long)a.sz};
+  const long total = (long)ncells * F;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % ncells);
+    const int f = (int)(idx / ncells);
+    const long o = cells[c];
+    const int ijk[3] = {(int)(o % g.pitch), (int)((o / g.pitch) % g.ext[1]), (int)(o / ((long)g.pitch * g.ext[1]))};
+    double x[3];
+    for (int d = 0; d < 3; ++d) x[d] = g.x0[d] + ijk[d] * g.h;
+    const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    const double ir = rsqrt(r2);
+    const double* p = a.Y + (long)f * a.fs;
+    double adv = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const long s = str[d];
+      double der;
+      if (ijk[d] == 0) der = (-3.0 * p[o] + 4.0 * p[o + s] - p[o + 2 * s]) * inv2h;
+      else if (ijk[d] == g.ext[d] - 1) der = (3.0 * p[o] - 4.0 * p[o - s] + p[o - 2 * s]) * inv2h;
+      else der = (p[o + s] - p[o - s]) * inv2h;
+      adv = fma(x[d], der, adv);
+    }
+    double uinf = 0.0;
+    if (system == SC_Z4C && (f == ZW || f == ZAL || f == ZG + 0 || f == ZG + 3 || f == ZG + 5)) uinf = 1.0;
+    const double kv = -(adv + (p[o] - uinf)) * ir;
+    const long fo = (long)f * a.fs + o;
+    a.k[fo] = kv;
+    if (a.stage < 4) {
+      a.out[fo] = fma(a.cdt, kv, a.yn[fo]);
+    } else {
+      const double s = fma(2.0, a.k3[fo], fma(2.0, a.k2[fo], a.k1[fo])) + kv;
+      a.out[fo] = fma(a.cdt, s, a.yn[fo]);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
+  wave_stage_kernel<<<grid, kThreads, 0, s>>>(a, tiles, ntiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_radiative_stage(const StageArgs& a, const int32_t* cells, int ncells, int F, const Geom& g,
+                                   int system, cudaStream_t s) {
+  if (ncells == 0) return cudaSuccess;
+  const long work = (long)ncells * F;
+  long grid = (work + kThreads - 1) / kThreads;
+  if (grid > 152 * 32) grid = 152 * 32;
+  radiative_stage_kernel<<<(int)grid, kThreads, 0, s>>>(a, cells, ncells, F, g, system);
+  return cudaGetLastError();
+}
+
+}  // namespace sc

@@ -1,0 +1,512 @@
+// sc_z4c.cu -- Z4c right-hand side (Sec. III.A, vacuum, puncture gauge with
+// constant eta), Kreiss-Oliger dissipation (Sec. III.C, r = 4) and the fused
+// RK4 stage update, plus the constraint evaluation.
+//
+// Two passes per stage, both over the interior tiles of a level:
+//   1. z4c_derivs_kernel: one thread per (cell, field) computes the 4th-order
+//      centred first derivatives of every field, the second derivatives of
+//      W, gt_ij, alpha and beta^i, and the KO sum sum_d delta_d^6 u, and
+//      stores them (already scaled by 1/h, 1/h^2) in a scratch array indexed
+//      like the level array: scratch[q * fs + cell].
+//   2. z4c_stage_kernel: one thread per cell reads the 22 fields and their
+//      derivatives, evaluates the right-hand side, adds dissipation and
+//      performs the RK4 stage update.
+// FP64 is the scarce resource on this GPU (the FP64 pipe issues 1/64 of the
+// FP32 rate), so the arithmetic is arranged to minimise FP64 operations:
+// shared pair sums/differences in the stencils, fused multiply-adds, one
+// division for 1/det(gt) and one for 1/W, and the quadratic Christoffel
+// terms of the Ricci tensor contracted through one raised-index array.
+#include "sc_internal.h"
+
+namespace sc {
+namespace {
+
+constexpr int kThreads = 256;
+
+// scratch slots
+constexpr int Q_D1 = 0;    // 3 * f + d: first derivative of field f along d
+constexpr int Q_D2 = 66;   // 6 * s + p: second derivative, s = slot (W, gt x6, alpha, beta x3), p = xx,xy,xz,yy,yz,zz
+constexpr int Q_KO = 132;  // f: sum_d delta_d^6 u_f (unscaled)
+constexpr int Q_NUM = 154;
+
+// slot of field f among the fields with second derivatives, -1 if none
+__host__ __device__ inline int d2_slot(int f) {
+  if (f == ZW) return 0;
+  if (f >= ZG && f < ZG + 6) return 1 + (f - ZG);
+  if (f == ZAL) return 7;
+  if (f >= ZB && f < ZB + 3) return 8 + (f - ZB);
+  return -1;
+}
+
+__global__ void __launch_bounds__(kThreads) z4c_derivs_kernel(const double* __restrict__ Y, double* __restrict__ S,
+                                                             long fs, int sy_, int sz_, double h,
+                                                             const Tile* __restrict__ tiles, int ntiles) {
+  const double i12h = 1.0 / (12.0 * h);
+  const double i12h2 = 1.0 / (12.0 * h * h);
+  const double i144h2 = 1.0 / (144.0 * h * h);
+  const long st[3] = {1, (long)sy_, (long)sz_};
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile T = tiles[t];
+    const int n = T.nx * T.ny * T.nz;
+    for (int q = threadIdx.x; q < n * kNZ4c; q += blockDim.x) {
+      const int f = q / n;
+      const int c = q - f * n;
+      const int i = c % T.nx;
+      const int j = (c / T.nx) % T.ny;
+      const int k = c / (T.nx * T.ny);
+      const long o = (T.z0 + k) * st[2] + (T.y0 + j) * st[1] + (T.x0 + i);
+      const double* u = Y + (long)f * fs + o;
+      const double u0 = u[0];
+      double p1[3], p2[3], P3 = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const long s = st[d];
+        const double a1 = u[-s], b1 = u[s], a2 = u[-2 * s], b2 = u[2 * s];
+        p1[d] = a1 + b1;
+        p2[d] = a2 + b2;
+        P3 += u[-3 * s] + u[3 * s];
+        // (u_-2 - 8 u_-1 + 8 u_1 - u_2) / (12 h)
+        S[(long)(Q_D1 + 3 * f + d) * fs + o] = fma(8.0, b1 - a1, a2 - b2) * i12h;
+      }
+      // Kreiss-Oliger: sum_d (u_-3 - 6 u_-2 + 15 u_-1 - 20 u_0 + 15 u_1 - 6 u_2 + u_3)
+      const double P1 = p1[0] + p1[1] + p1[2], P2 = p2[0] + p2[1] + p2[2];
+      S[(long)(Q_KO + f) * fs + o] = fma(15.0, P1, fma(-6.0, P2, fma(-60.0, u0, P3)));
+      const int sl = d2_slot(f);
+      if (sl < 0) continue;
+      double* d2 = S + (long)(Q_D2 + 6 * sl) * fs + o;
+      // pure: (-u_-2 + 16 u_-1 - 30 u_0 + 16 u_1 - u_2) / (12 h^2)
+      d2[0 * fs] = fma(-30.0, u0, fma(16.0, p1[0], -p2[0])) * i12h2;
+      d2[3 * fs] = fma(-30.0, u0, fma(16.0, p1[1], -p2[1])) * i12h2;
+      d2[5 * fs] = fma(-30.0, u0, fma(16.0, p1[2], -p2[2])) * i12h2;
+      // mixed: product of the two first-derivative stencils / (144 h^2)
+      const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2}, slot[3] = {1, 2, 4};
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const long sa = st[pa[m]], sb = st[pb[m]];
+        double D[4];
+        const int offs[4] = {-2, -1, 1, 2};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const double* v = u + offs[r] * sb;
+          D[r] = fma(8.0, v[sa] - v[-sa], v[-2 * sa] - v[2 * sa]);
+        }
+        d2[slot[m] * fs] = fma(8.0, D[2] - D[1], D[0] - D[3]) * i144h2;
+      }
+    }
+  }
+}
+
+// symmetric index helpers: xx xy xz yy yz zz
+__device__ __forceinline__ int sidx(int i, int j) {
+  return (i == j) ? (i == 0 ? 0 : (i == 1 ? 3 : 5)) : (i + j == 1 ? 1 : (i + j == 2 ? 2 : 4));
+}
+
+struct Z4cPoint {
+  double rhs[kNZ4c];
+};
+
+// Right-hand side of the Z4c system at one cell (Sec. III.A; vacuum, so the
+// matter terms vanish).  u: fields; S + o: derivatives in scratch.
+template <bool kDiag>
+__device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, const double* __restrict__ S, long fs,
+                                              long o, const Z4cParams& P, double* rhs, double* diag) {
+#define FLD(f) Y[(long)(f) * fs + o]
+#define D1(f, d) S[(long)(Q_D1 + 3 * (f) + (d)) * fs + o]
+#define D2(sl, p) S[(long)(Q_D2 + 6 * (sl) + (p)) * fs + o]
+  const double W = FLD(ZW);
+  double g[6], A[6];
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    g[s] = FLD(ZG + s);
+    A[s] = FLD(ZA + s);
+  }
+  const double Kh = FLD(ZK), Th = FLD(ZTH), al = FLD(ZAL);
+  const double Gam[3] = {FLD(ZGAM), FLD(ZGAM + 1), FLD(ZGAM + 2)};
+  const double be[3] = {FLD(ZB), FLD(ZB + 1), FLD(ZB + 2)};
+
+  // inverse conformal metric
+  double gu[6];
+  gu[0] = fma(g[3], g[5], -g[4] * g[4]);
+  gu[1] = fma(g[2], g[4], -g[1] * g[5]);
+  gu[2] = fma(g[1], g[4], -g[2] * g[3]);
+  gu[3] = fma(g[0], g[5], -g[2] * g[2]);
+  gu[4] = fma(g[1], g[2], -g[0] * g[4]);
+  gu[5] = fma(g[0], g[3], -g[1] * g[1]);
+  const double idet = 1.0 / fma(g[0], gu[0], fma(g[1], gu[1], g[2] * gu[2]));
+#pragma unroll
+  for (int s = 0; s < 6; ++s) gu[s] *= idet;
+  const double iW = 1.0 / W;
+
+  // first derivatives of the metric, Christoffel symbols
+  double dg[6][3];
+#pragma unroll
+  for (int s = 0; s < 6; ++s)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dg[s][d] = D1(ZG + s, d);
+  // Gl[k][s(ij)] = Gamma_{k,ij} = (d_i g_jk + d_j g_ik - d_k g_ij) / 2
+  double Gl[3][6], Gu[3][6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j)
+        Gl[k][sidx(i, j)] = 0.5 * (dg[sidx(j, k)][i] + dg[sidx(i, k)][j] - dg[sidx(i, j)][k]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int s = 0; s < 6; ++s)
+      Gu[k][s] = fma(gu[sidx(k, 0)], Gl[0][s], fma(gu[sidx(k, 1)], Gl[1][s], gu[sidx(k, 2)] * Gl[2][s]));
+  // (Gamma_d)^k = gt^ij Gamma^k_ij
+  double Gd[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    Gd[k] = fma(gu[0], Gu[k][0], fma(gu[3], Gu[k][3], fma(gu[5], Gu[k][5],
+            2.0 * fma(gu[1], Gu[k][1], fma(gu[2], Gu[k][2], gu[4] * Gu[k][4])))));
+
+  // U[j][k][l] = gt^{lm} Gamma_{j,km}
+  double U[3][3][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        U[j][k][l] = fma(gu[sidx(l, 0)], Gl[j][sidx(k, 0)],
+                         fma(gu[sidx(l, 1)], Gl[j][sidx(k, 1)], gu[sidx(l, 2)] * Gl[j][sidx(k, 2)]));
+
+  const double dW[3] = {D1(ZW, 0), D1(ZW, 1), D1(ZW, 2)};
+  const double dal[3] = {D1(ZAL, 0), D1(ZAL, 1), D1(ZAL, 2)};
+  // gt^{kl} d_l W and |dW|^2, gt^{kl} d_l W d_k alpha
+  double gudW[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) gudW[k] = fma(gu[sidx(k, 0)], dW[0], fma(gu[sidx(k, 1)], dW[1], gu[sidx(k, 2)] * dW[2]));
+  const double dWdW = fma(gudW[0], dW[0], fma(gudW[1], dW[1], gudW[2] * dW[2]));
+  const double dWdal = fma(gudW[0], dal[0], fma(gudW[1], dal[1], gudW[2] * dal[2]));
+
+  // Ricci tensor R_ij = R^W_ij + Rt_ij, and D_i D_j alpha
+  double R[6], DDal[6];
+  {
+    double DDW[6];
+    double trDDW = 0.0;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+      DDW[s] = D2(0, s) - fma(Gu[0][s], dW[0], fma(Gu[1][s], dW[1], Gu[2][s] * dW[2]));
+      trDDW = fma((s == 1 || s == 2 || s == 4) ? 2.0 * gu[s] : gu[s], DDW[s], trDDW);
+    }
+    const double dGam[3][3] = {{D1(ZGAM, 0), D1(ZGAM, 1), D1(ZGAM, 2)},
+                               {D1(ZGAM + 1, 0), D1(ZGAM + 1, 1), D1(ZGAM + 1, 2)},
+                               {D1(ZGAM + 2, 0), D1(ZGAM + 2, 1), D1(ZGAM + 2, 2)}};
+    // T1[i][j] = Gamma^k_{li} U[j][k][l]
+    double T1[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int l = 0; l < 3; ++l) s = fma(Gu[k][sidx(l, i)], U[j][k][l], s);
+        T1[i][j] = s;
+      }
+    const double m2W = -2.0 * dWdW * iW;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        const int s = sidx(i, j);
+        // -1/2 gt^lm d_l d_m gt_ij
+        double r = -0.5 * (fma(gu[0], D2(1 + s, 0), fma(gu[3], D2(1 + s, 3), gu[5] * D2(1 + s, 5))) +
+                           2.0 * fma(gu[1], D2(1 + s, 1), fma(gu[2], D2(1 + s, 2), gu[4] * D2(1 + s, 4))));
+        // gt_k(i d_j) Gamt^k
+        double a = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a = fma(g[sidx(k, i)], dGam[k][j], fma(g[sidx(k, j)], dGam[k][i], a));
+        r = fma(0.5, a, r);
+        // (Gamma_d)^k Gamma_(ij)k
+        double b = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b = fma(Gd[k], Gl[i][sidx(j, k)] + Gl[j][sidx(i, k)], b);
+        r = fma(0.5, b, r);
+        // gt^lm (2 Gamma^k_l(i Gamma_j)km + Gamma^k_im Gamma_klj)
+        double t3 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int m = 0; m < 3; ++m) t3 = fma(Gu[k][sidx(i, m)], U[k][j][m], t3);
+        r += T1[i][j] + T1[j][i] + t3;
+        // R^W_ij = (D_i D_j W + gt_ij D^l D_l W) / W - 2 gt_ij |dW|^2 / W^2
+        const double rw = fma(fma(g[s], trDDW, DDW[s]), iW, g[s] * m2W * iW);
+        R[s] = r + rw;
+        // D_i D_j alpha with Gamma^k_ij - (delta^k_i d_j W + delta^k_j d_i W - gt_ij gt^kl d_l W) / W
+        const double gd = fma(Gu[0][s], dal[0], fma(Gu[1][s], dal[1], Gu[2][s] * dal[2]));
+        const double wt = fma(dW[j], dal[i], fma(dW[i], dal[j], -g[s] * dWdal));
+        DDal[s] = D2(7, s) - fma(-wt, iW, gd);
+      }
+  }
+  double trR = 0.0, trDDal = 0.0;
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    const double w = (s == 1 || s == 2 || s == 4) ? 2.0 * gu[s] : gu[s];
+    trR = fma(w, R[s], trR);
+    trDDal = fma(w, DDal[s], trDDal);
+  }
+  const double W2 = W * W;
+  const double Rsc = W2 * trR;
+  const double DiDial = W2 * trDDal;
+
+  // At with raised indices: Am[i][j] = At^i_j, Auu = At^ij
+  double Am[3][3], Auu[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Am[i][j] = fma(gu[sidx(i, 0)], A[sidx(0, j)], fma(gu[sidx(i, 1)], A[sidx(1, j)], gu[sidx(i, 2)] * A[sidx(2, j)]));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j)
+      Auu[sidx(i, j)] = fma(Am[i][0], gu[sidx(0, j)], fma(Am[i][1], gu[sidx(1, j)], Am[i][2] * gu[sidx(2, j)]));
+  const double AA = fma(A[0], Auu[0], fma(A[3], Auu[3], fma(A[5], Auu[5],
+                    2.0 * fma(A[1], Auu[1], fma(A[2], Auu[2], A[4] * Auu[4])))));
+
+  double dbe[3][3];  // dbe[i][j] = d_j beta^i
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dbe[i][j] = D1(ZB + i, j);
+  const double divb = dbe[0][0] + dbe[1][1] + dbe[2][2];
+  const double Kt = fma(2.0, Th, Kh);
+  const double third = 1.0 / 3.0, twothird = 2.0 / 3.0;
+
+#define ADV(f) fma(be[0], D1(f, 0), fma(be[1], D1(f, 1), be[2] * D1(f, 2)))
+  // W
+  rhs[ZW] = fma(third * W, fma(al, Kt, -divb), ADV(ZW));
+  // gt_ij and At_ij
+  double X[6], trX = 0.0;
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    X[s] = fma(al, R[s], -DDal[s]);
+    trX = fma((s == 1 || s == 2 || s == 4) ? 2.0 * gu[s] : gu[s], X[s], trX);
+  }
+  const double alKt = al * Kt;
+  const double m2al = -2.0 * al;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int s = sidx(i, j);
+      double lg = 0.0, la = 0.0, aa = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        lg = fma(g[sidx(k, i)], dbe[k][j], fma(g[sidx(k, j)], dbe[k][i], lg));
+        la = fma(A[sidx(k, i)], dbe[k][j], fma(A[sidx(k, j)], dbe[k][i], la));
+        aa = fma(Am[k][i], A[sidx(k, j)], aa);
+      }
+      rhs[ZG + s] = ADV(ZG + s) + fma(m2al, A[s], fma(-twothird * divb, g[s], lg));
+      const double tf = fma(-third * trX, g[s], X[s]);
+      rhs[ZA + s] = ADV(ZA + s) + fma(W2, tf, fma(alKt, A[s], fma(m2al, aa, fma(-twothird * divb, A[s], la))));
+    }
+  // Khat
+  rhs[ZK] = ADV(ZK) - DiDial + al * fma(third * Kt, Kt, AA) + al * (P.kappa1 * (1.0 - P.kappa2)) * Th;
+  // Gamt^i
+  {
+    const double dKh[3] = {D1(ZK, 0), D1(ZK, 1), D1(ZK, 2)};
+    const double dTh[3] = {D1(ZTH, 0), D1(ZTH, 1), D1(ZTH, 2)};
+    double dd[3];  // d_j (2 Khat + Theta)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dd[j] = fma(2.0, dKh[j], dTh[j]);
+    // d_j d_k beta^k for each j
+    double ddivb[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ddivb[j] = D2(8, sidx(j, 0)) + D2(9, sidx(j, 1)) + D2(10, sidx(j, 2));
+    const double m3iW = -3.0 * iW;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double br = 0.0;
+#pragma unroll
+      for (int s = 0; s < 6; ++s) br = fma((s == 1 || s == 2 || s == 4) ? 2.0 * Gu[i][s] : Gu[i][s], Auu[s], br);
+      double r = 0.0, lap = 0.0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double auij = Auu[sidx(i, j)], guij = gu[sidx(i, j)];
+        r = fma(-2.0 * auij, dal[j], r);
+        br = fma(m3iW * auij, dW[j], br);
+        br = fma(-third * guij, dd[j], br);
+        lap = fma(third * guij, ddivb[j], lap);
+        r = fma(-Gd[j], dbe[i][j], r);
+      }
+      // gt^jk d_j d_k beta^i
+      lap += fma(gu[0], D2(8 + i, 0), fma(gu[3], D2(8 + i, 3), gu[5] * D2(8 + i, 5))) +
+             2.0 * fma(gu[1], D2(8 + i, 1), fma(gu[2], D2(8 + i, 2), gu[4] * D2(8 + i, 4)));
+      r = fma(2.0 * al, br, r) + lap;
+      r = fma(twothird * Gd[i], divb, r);
+      r = fma(-2.0 * P.kappa1 * al, Gam[i] - Gd[i], r);
+      rhs[ZGAM + i] = ADV(ZGAM + i) + r;
+    }
+  }
+  // Theta
+  rhs[ZTH] = ADV(ZTH) + 0.5 * al * (Rsc - AA + twothird * Kt * Kt) - al * (P.kappa1 * (2.0 + P.kappa2)) * Th;
+  // lapse (1+log) and shift (Gamma-driver)
+  rhs[ZAL] = fma(m2al, Kh, ADV(ZAL));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) rhs[ZB + i] = ADV(ZB + i) + fma(0.75, Gam[i], -P.eta * be[i]);
+  if (kDiag) {
+    diag[0] = Rsc;
+    diag[1] = AA;
+    diag[2] = Kt;
+  }
+#undef ADV
+#undef FLD
+#undef D1
+#undef D2
+}
+
+__global__ void __launch_bounds__(128) z4c_stage_kernel(StageArgs a, const double* __restrict__ S, Z4cParams P,
+                                                       const Tile* __restrict__ tiles, int ntiles) {
+  const double ko = P.ko_sigma / (64.0 * a.h);
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile T = tiles[t];
+    const int n = T.nx * T.ny * T.nz;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      const int i = q % T.nx;
+      const int j = (q / T.nx) % T.ny;
+      const int k = q / (T.nx * T.ny);
+      const long o = (long)(T.z0 + k) * a.sz + (long)(T.y0 + j) * a.sy + (T.x0 + i);
+      double rhs[kNZ4c];
+      z4c_rhs_point<false>(a.Y, S, a.fs, o, P, rhs, nullptr);
+#pragma unroll
+      for (int f = 0; f < kNZ4c; ++f) {
+        const long fo = (long)f * a.fs + o;
+        const double kv = fma(ko, S[(long)(Q_KO + f) * a.fs + o], rhs[f]);
+        a.k[fo] = kv;
+        if (a.stage < 4) {
+          a.out[fo] = fma(a.cdt, kv, a.yn[fo]);
+        } else {
+          const double s = fma(2.0, a.k3[fo], fma(2.0, a.k2[fo], a.k1[fo])) + kv;
+          a.out[fo] = fma(a.cdt, s, a.yn[fo]);
+        }
+      }
+    }
+  }
+}
+
+// Constraints at the interior cells of one box:
+//   H   = R + 2/3 (Khat + 2 Theta)^2 - At_ij At^ij      (R the Ricci scalar of gamma)
+//   M^i = d_j At^ij + Gamt^i_jk At^jk - 3 At^ij d_j W / W - 2/3 gt^ij d_j (Khat + 2 Theta)
+//   G^i = Gamt^i - gt^jk Gamt^i_jk
+// out[c * out_stride + cell], cells numbered x-fastest within the box.
+__global__ void __launch_bounds__(128) z4c_constraints_kernel(const double* __restrict__ Y,
+                                                             const double* __restrict__ S, double* __restrict__ out,
+                                                             long fs, int sy, int sz, Z4cParams P,
+                                                             const Tile* __restrict__ tiles, int ntiles,
+                                                             long out_stride, int bx, int by, int bz, int nbx,
+                                                             int nby) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile T = tiles[t];
+    const int n = T.nx * T.ny * T.nz;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      const int ax = T.x0 + q % T.nx, ay = T.y0 + (q / T.nx) % T.ny, az = T.z0 + q / (T.nx * T.ny);
+      const long o = (long)az * sz + (long)ay * sy + ax;
+      const long cell = ((long)(az - bz) * nby + (ay - by)) * nbx + (ax - bx);
+#define FLD(f) Y[(long)(f) * fs + o]
+#define D1(f, d) S[(long)(Q_D1 + 3 * (f) + (d)) * fs + o]
+      double rhs[kNZ4c], diag[3];
+      z4c_rhs_point<true>(Y, S, fs, o, P, rhs, diag);
+      out[cell] = diag[0] + (2.0 / 3.0) * diag[2] * diag[2] - diag[1];
+      double g[6], A[6], gu[6];
+      for (int s = 0; s < 6; ++s) {
+        g[s] = FLD(ZG + s);
+        A[s] = FLD(ZA + s);
+      }
+      gu[0] = fma(g[3], g[5], -g[4] * g[4]);
+      gu[1] = fma(g[2], g[4], -g[1] * g[5]);
+      gu[2] = fma(g[1], g[4], -g[2] * g[3]);
+      gu[3] = fma(g[0], g[5], -g[2] * g[2]);
+      gu[4] = fma(g[1], g[2], -g[0] * g[4]);
+      gu[5] = fma(g[0], g[3], -g[1] * g[1]);
+      const double idet = 1.0 / fma(g[0], gu[0], fma(g[1], gu[1], g[2] * gu[2]));
+      for (int s = 0; s < 6; ++s) gu[s] *= idet;
+      const double iW = 1.0 / FLD(ZW);
+      double Gu[3][6];
+      for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 3; ++a)
+          for (int b = a; b < 3; ++b) {
+            double v = 0.0;
+            for (int l = 0; l < 3; ++l)
+              v += gu[sidx(k, l)] * 0.5 * (D1(ZG + sidx(b, l), a) + D1(ZG + sidx(a, l), b) - D1(ZG + sidx(a, b), l));
+            Gu[k][sidx(a, b)] = v;
+          }
+      double Auu[3][3];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double v = 0.0;
+          for (int c = 0; c < 3; ++c)
+            for (int d = 0; d < 3; ++d) v += gu[sidx(a, c)] * gu[sidx(b, d)] * A[sidx(c, d)];
+          Auu[a][b] = v;
+        }
+      double dgu[3][6];  // d_m gt^{ab} = -gt^{ac} gt^{bd} d_m gt_cd
+      for (int m = 0; m < 3; ++m)
+        for (int a = 0; a < 3; ++a)
+          for (int b = a; b < 3; ++b) {
+            double v = 0.0;
+            for (int c = 0; c < 3; ++c)
+              for (int d = 0; d < 3; ++d) v -= gu[sidx(a, c)] * gu[sidx(b, d)] * D1(ZG + sidx(c, d), m);
+            dgu[m][sidx(a, b)] = v;
+          }
+      for (int a = 0; a < 3; ++a) {
+        double v = 0.0;
+        for (int j = 0; j < 3; ++j)  // d_j At^{aj}
+          for (int m = 0; m < 3; ++m)
+            for (int p = 0; p < 3; ++p)
+              v += dgu[j][sidx(a, m)] * gu[sidx(j, p)] * A[sidx(m, p)] +
+                   gu[sidx(a, m)] * dgu[j][sidx(j, p)] * A[sidx(m, p)] +
+                   gu[sidx(a, m)] * gu[sidx(j, p)] * D1(ZA + sidx(m, p), j);
+        for (int b = 0; b < 3; ++b)
+          for (int c = 0; c < 3; ++c) v += Gu[a][sidx(b, c)] * Auu[b][c];
+        for (int b = 0; b < 3; ++b) {
+          v -= 3.0 * Auu[a][b] * D1(ZW, b) * iW;
+          v -= (2.0 / 3.0) * gu[sidx(a, b)] * (D1(ZK, b) + 2.0 * D1(ZTH, b));
+        }
+        out[(1 + a) * out_stride + cell] = v;
+        double gd = 0.0;
+        for (int b = 0; b < 3; ++b)
+          for (int c = 0; c < 3; ++c) gd += gu[sidx(b, c)] * Gu[a][sidx(b, c)];
+        out[(4 + a) * out_stride + cell] = FLD(ZGAM + a) - gd;
+      }
+#undef FLD
+#undef D1
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy, int sz, double h, const Tile* tiles,
+                              int ntiles, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
+  z4c_derivs_kernel<<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4cParams& p, const Tile* tiles,
+                             int ntiles, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
+  z4c_stage_kernel<<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_z4c_constraints(const double* Y, const double* scratch, double* out, long fs, int sy, int sz,
+                                   const Z4cParams& p, const Tile* tiles, int ntiles, long out_stride,
+                                   const int* box_lo, const int* box_n, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
+  z4c_constraints_kernel<<<grid, 128, 0, s>>>(Y, scratch, out, fs, sy, sz, p, tiles, ntiles, out_stride, box_lo[0],
+                                              box_lo[1], box_lo[2], box_n[0], box_n[1]);
+  return cudaGetLastError();
+}
+
+}  // namespace sc

@@ -216,3 +216,32 @@ def bl_3level(n: int = 24, m1: float = 0.5, m2: float = 0.5, sep: float = 2.0, L
                      id_kind=ID_BRILL_LINDQUIST,
                      id_params=[m1, 0.0, 0.0, sep / 2, m2, 0.0, 0.0, -sep / 2],
                      name=f"z4c BL 3-level {n}^3 over [-{L},{L}]^3")
+
+
+def initial_fields(h: Hierarchy, level: int, box: int, ghosted: bool = False, noise_seed=None) -> np.ndarray:
+    """Initial data of one box as an array (F, nz, ny, nx) at cell centres
+    (ghost cells included when ghosted).  Standing wave / Gaussian (plus the
+    seeded smooth noise when noise_seed is given) for the wave, Brill-Lindquist
+    or flat space for Z4c."""
+    X, Y, Z = h.cell_centres(level, box, ghosted)
+    p = h.id_params
+    if h.system == WAVE:
+        if h.id_kind == ID_STANDING_WAVE:
+            u = p[0] * np.sin(2 * np.pi * p[1] * X) * np.sin(2 * np.pi * p[2] * Y) * np.sin(2 * np.pi * p[3] * Z)
+        elif h.id_kind == ID_GAUSSIAN:
+            u = p[0] * np.exp(-((X - p[2]) ** 2 + (Y - p[3]) ** 2 + (Z - p[4]) ** 2) / (2 * p[1] ** 2))
+        else:
+            raise ValueError("unsupported wave initial data")
+        if noise_seed is not None:
+            u = u + noise_field(X, Y, Z, noise_seed)
+        return np.stack([u, np.zeros_like(u)])
+    out = np.zeros((22,) + X.shape)
+    psi = np.ones_like(X)
+    if h.id_kind == ID_BRILL_LINDQUIST:
+        for q in range(2):
+            m, cx, cy, cz = p[4 * q:4 * q + 4]
+            psi += m / (2 * np.sqrt((X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2))
+    out[0] = psi ** -2       # W = gamma^(-1/6) for gamma_ij = psi^4 delta_ij
+    out[1] = out[4] = out[6] = 1.0  # conformal metric = delta
+    out[18] = psi ** -2      # lapse psi^-2
+    return out

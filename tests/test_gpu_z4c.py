@@ -1,0 +1,111 @@
+"""GPU parity of the Z4c path (Sec. III: Z4c, puncture gauge, KO dissipation,
+radiative outer boundary; Sec. II subcycling) against the CPU oracle on the
+same inputs: tolerance 1e-10 in the max relative field difference after 16
+coarse steps.  At the full 7-level size the oracle is too slow, so there the
+tests check properties that hold at any size (flat space stays flat exactly,
+mirror symmetry of the head-on data)."""
+import numpy as np
+import pytest
+
+from helpers import fetch, init_arrays, load, make_oracle, max_rel_diff
+from paper_2503_09629_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def sc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2503_09629_gb300 as m
+    m.build()
+    return m
+
+
+def _parity(sc, orc, h, nsteps):
+    arrays = init_arrays(h)
+    ctx = sc.Context(h)
+    o = make_oracle(orc, h)
+    load(ctx, h, arrays)
+    load(o, h, arrays)
+    ctx.sc_advance(nsteps)
+    o.advance(nsteps)
+    err = max_rel_diff(fetch(ctx, h), fetch(o, h))
+    ctx.close()
+    return err
+
+
+def test_single_level_bl_one_step(sc, orc):
+    h = W.Hierarchy(system=W.Z4C, boxes=[[W.cube(0, 16)]], ncells0=(16, 16, 16), origin=(-4.0, -4.0, -4.0),
+                    h0=0.5, bc=W.BC_RADIATIVE, id_kind=W.ID_BRILL_LINDQUIST,
+                    id_params=[0.5, 0.0, 0.0, 1.0, 0.5, 0.0, 0.0, -1.0])
+    assert _parity(sc, orc, h, 1) <= TOL
+
+
+def test_bl_3level_16_coarse_steps(sc, orc):
+    """Brill-Lindquist head-on, 3 levels of 20^3, 16 coarse steps (Sec. III.B data)."""
+    h = W.bl_3level(20)
+    err = _parity(sc, orc, h, 16)
+    assert err <= TOL, err
+
+
+def test_bl_3level_unequal_masses(sc, orc):
+    h = W.bl_3level(24, m1=0.3, m2=0.7, sep=3.0)
+    err = _parity(sc, orc, h, 3)
+    assert err <= TOL, err
+
+
+def test_constraints_match_oracle(sc, orc):
+    h = W.bl_3level(20)
+    arrays = init_arrays(h)
+    ctx = sc.Context(h)
+    o = make_oracle(orc, h)
+    load(ctx, h, arrays)
+    load(o, h, arrays)
+    ctx.sc_advance(2)
+    o.advance(2)
+    for l in range(3):
+        g = ctx.sc_get_constraints(l, 0)
+        r = o.constraints(l, 0)
+        for q in range(7):
+            scale = max(np.abs(r[q]).max(), 1e-12)
+            assert np.abs(g[q] - r[q]).max() / scale <= 1e-9, (l, q)
+
+
+def test_minkowski_full_7level_exactly_flat(sc):
+    """Full-size hierarchy (64^3 base, 7 levels, finest h = 1/64): flat space
+    is a static solution and every stencil sums to zero exactly."""
+    h = W.bl_7level()
+    ctx = sc.Context(h)
+    ctx.sc_set_initial_data(W.ID_MINKOWSKI, [])
+    ctx.sc_advance(1)
+    flat = np.zeros(22)
+    flat[[0, 1, 4, 6, 18]] = 1.0
+    for l in range(h.nlevels):
+        for b in range(len(h.boxes[l])):
+            for f in (0, 1, 2, 7, 8, 14, 17, 18, 19):
+                assert np.abs(ctx.sc_get_field(l, b, f) - flat[f]).max() == 0.0
+
+
+def test_full_7level_mirror_symmetry(sc):
+    """Full-size head-on Brill-Lindquist run (the benchmark workload, one coarse
+    step): the data and the hierarchy are symmetric under z -> -z, so every
+    z-even field is mirror-even and every z-odd field mirror-odd."""
+    h = W.bl_7level()
+    ctx = sc.Context(h)
+    ctx.sc_set_initial_data(h.id_kind, h.id_params)
+    ctx.sc_advance(1)
+    odd = {3, 5, 10, 12, 16, 21}  # gt_xz, gt_yz, At_xz, At_yz, Gamt^z, beta^z
+    for l in range(6):
+        for f in range(22):
+            a = ctx.sc_get_field(l, 0, f)
+            m = a[::-1] * (-1.0 if f in odd else 1.0)
+            # fields of order one (W, gt, alpha) relative, small ones (Theta,
+            # At, ...) absolute at the 1e-3 floor
+            scale = max(np.abs(a).max(), 1e-3)
+            assert np.abs(a - m).max() / scale <= 1e-12, (l, f)
+    a0, a1 = ctx.sc_get_field(6, 0, 0), ctx.sc_get_field(6, 1, 0)
+    assert np.abs(a0 - a1[::-1]).max() / np.abs(a0).max() <= 1e-12
