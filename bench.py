@@ -36,9 +36,18 @@ UNIT = "zone-updates/s (finest-equivalent)"
 # FP64 peak derived from the unit counts and clocks: 152 SMs x 2070 MHz x
 # 2 DFMA lanes per SM per clock x 2 flops per DFMA.
 FP64_PEAK_GFLOPS = 152 * 2.070 * 2 * 2
-# FP64 flops per cell of each Z4c kernel in this formulation (counted from the
-# kernels' executed FP64 instructions, dadd + dmul + 2 dfma, per interior cell).
-FLOPS_PER_CELL = {"z4c_derivs": 1672.0, "z4c_stage": None}
+# FP64 flops per interior cell of each Z4c kernel in this formulation, from
+# the kernels' executed FP64 instructions (dadd + dmul + 2 dfma) counted by ncu
+# (profiles/z4c_kernels_bl3level64_ncu.md).
+FLOPS_PER_CELL = {"z4c_derivs": 1706.0, "z4c_stage": 1977.0}
+# DRAM bytes (read + write) per interior cell of each kernel from the same
+# ncu capture (262,144-cell launch), scaled to a launch by its cell count;
+# None once the kernel has changed since the counters were taken.
+DRAM_BYTES_PER_CELL = {"z4c_derivs": (107.456768e6 + 287.404032e6) / 262144,
+                       "z4c_stage": (442.189568e6 + 92.051200e6) / 262144}
+# Kernel with the largest share of a coarse step in the ncu launch list
+# (profiles/z4c_bl_7level_launch_list.md).
+DOMINANT = "z4c_derivs"
 
 
 def sample_hierarchy(nlev: int = 5, n: int = 20):
@@ -199,10 +208,11 @@ def run_gpu(args, rank: int, world: int):
         if fpc is None:
             continue
         ach = cells * fpc / (t * 1e-3) / 1e12
+        tb = DRAM_BYTES_PER_CELL.get(name)
         roof[name] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                      "frac": ach * 1e3 / FP64_PEAK_GFLOPS, "traffic": None, "ms_per_launch": t,
-                      "cells_per_launch": cells, "flops_per_cell": fpc}
-    dominant = "z4c_stage" if "z4c_stage" in roof else "z4c_derivs"
+                      "frac": ach * 1e3 / FP64_PEAK_GFLOPS, "traffic": (tb * cells if tb else None),
+                      "ms_per_launch": t, "cells_per_launch": cells, "flops_per_cell": fpc}
+    dominant = DOMINANT if DOMINANT in roof else next(iter(roof))
     roofline = dict(roof[dominant])
     roofline["kernel"] = dominant
     roofline["peak_source"] = "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (nominal 1.25 TFLOP/s)"
