@@ -166,6 +166,34 @@ sc_status sc_footprint_estimate(const sc_desc* desc, size_t* bytes);
  * before reading; call between sc_advance calls.  Synchronises. */
 sc_status sc_time_stage_kernels(sc_ctx* ctx, int level, int nrep, double* ms);
 
+/* Z4c constraints of one box held by the caller, computed without allocating
+ * any device memory.  The paper has no counterpart: this entry point serves
+ * callers that cannot allocate -- a solver embedded in a host application
+ * that owns all device memory and forbids other allocations, a process whose
+ * memory pool is fixed at start-up, or a latency-critical loop in which
+ * cudaMalloc/cudaFree would implicitly synchronise the device.
+ *   dev_state: device pointer, 22 Z4c fields (field order as in the context),
+ *              each a box with 3 ghost layers per side, (n[0]+6)(n[1]+6)(n[2]+6)
+ *              doubles, x fastest, fields contiguous one after another;
+ *              the ghost layers must hold valid data;
+ *   dev_out:   device pointer, 7 * n[0]*n[1]*n[2] doubles, written with
+ *              H, M^x, M^y, M^z, G^x, G^y, G^z at the interior cells
+ *              (constraint-major, x fastest), as sc_get_constraints;
+ *   n:         host pointer, interior extents; h: grid spacing;
+ *   cuda_stream: cudaStream_t the work is ordered on (NULL = legacy stream).
+ * The derivative scratch is a static device array of this library sized for
+ * at most 32,768 cells including ghosts (for example a 26^3 interior), about
+ * 40 MB, which every GPU that loads the library holds until the process
+ * exits; larger boxes are rejected with SC_EINVAL.  Every call shares that
+ * array, so calls that overlap on the GPU race: serialise them (one stream,
+ * or wait for the previous call).  The first call on a device looks up the
+ * array's device address (with that device current) and caches it; make the
+ * first call before any stream capture.  The call is asynchronous: dev_out is
+ * ready when the stream reaches it.  No cudaMalloc, cudaFree or allocating
+ * library routine is called. */
+sc_status sc_z4c_constraints_noalloc(const double* dev_state, double* dev_out, const int* n, double h,
+                                     void* cuda_stream);
+
 const char* sc_last_error(void);
 
 #ifdef __cplusplus

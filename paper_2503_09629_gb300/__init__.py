@@ -106,6 +106,7 @@ def lib():
     L.sc_footprint.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
     L.sc_footprint_estimate.argtypes = [ctypes.POINTER(sc_desc), ctypes.POINTER(ctypes.c_size_t)]
     L.sc_time_stage_kernels.argtypes = [P, I, I, DP]
+    L.sc_z4c_constraints_noalloc.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), D, P]
     _lib = L
     return L
 
@@ -164,6 +165,20 @@ def make_desc(h, stream: Optional[int] = None, allocator=None):
         d.allocator = ctypes.pointer(allocator)
         keep.append(allocator)
     return d, keep
+
+
+def sc_z4c_constraints_noalloc(dev_state: int, dev_out: int, n: Sequence[int], h: float,
+                               stream: Optional[int] = None) -> None:
+    """Z4c constraints of one box in caller-owned device memory, with no
+    device allocation (for callers that cannot allocate: an embedding
+    application that owns all device memory, a fixed memory pool, or a loop
+    that must not trigger the implicit synchronisation of cudaMalloc/cudaFree).
+    dev_state: 22 ghosted fields of (n+6)^3-shaped boxes, contiguous; dev_out:
+    7 * prod(n) doubles.  At most 32,768 cells including ghosts.  Calls share
+    one static scratch array: do not overlap them on the GPU."""
+    nn = (ctypes.c_int * 3)(*[int(v) for v in n])
+    _check(lib().sc_z4c_constraints_noalloc(ctypes.c_void_p(dev_state), ctypes.c_void_p(dev_out), nn, float(h),
+                                            ctypes.c_void_p(stream) if stream else None))
 
 
 def sc_footprint_estimate(h) -> int:

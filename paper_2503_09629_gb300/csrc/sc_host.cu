@@ -664,6 +664,8 @@ sc_status copy_field(sc_ctx* c, int level, int box, int field, bool ghosted, con
 
 }  // namespace
 
+sc_status sc::set_last_error(sc_status code, const char* msg) { return fail(code, "%s", msg); }
+
 // ---------------------------------------------------------------------------
 // C ABI
 

@@ -82,6 +82,9 @@ struct Z4cParams {
   double kappa1, kappa2, eta, ko_sigma;
 };
 
+// Record a message for sc_last_error() and return code (defined in sc_host.cu).
+sc_status set_last_error(sc_status code, const char* msg);
+
 // ---- kernel launchers (defined in the .cu files) -------------------------
 cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s);
 
