@@ -39,15 +39,15 @@ FP64_PEAK_GFLOPS = 152 * 2.070 * 2 * 2
 # FP64 flops per interior cell of each Z4c kernel in this formulation, from
 # the kernels' executed FP64 instructions (dadd + dmul + 2 dfma) counted by ncu
 # (profiles/z4c_kernels_bl3level64_ncu.md).
-FLOPS_PER_CELL = {"z4c_derivs": 1706.0, "z4c_stage": 1977.0}
+FLOPS_PER_CELL = {"z4c_derivs": None, "z4c_stage": 1977.0}
 # DRAM bytes (read + write) per interior cell of each kernel from the same
 # ncu capture (262,144-cell launch), scaled to a launch by its cell count;
 # None once the kernel has changed since the counters were taken.
-DRAM_BYTES_PER_CELL = {"z4c_derivs": (107.456768e6 + 287.404032e6) / 262144,
+DRAM_BYTES_PER_CELL = {"z4c_derivs": None,
                        "z4c_stage": (442.189568e6 + 92.051200e6) / 262144}
 # Kernel with the largest share of a coarse step in the ncu launch list
 # (profiles/z4c_bl_7level_launch_list.md).
-DOMINANT = "z4c_derivs"
+DOMINANT = "z4c_stage"
 
 
 def sample_hierarchy(nlev: int = 5, n: int = 20):
@@ -206,13 +206,14 @@ def run_gpu(args, rank: int, world: int):
     for name, t in (("z4c_derivs", t_der), ("z4c_stage", t_stage)):
         fpc = FLOPS_PER_CELL[name]
         if fpc is None:
+            roof[name] = {"ms_per_launch": t, "cells_per_launch": cells, "flops_per_cell": None}
             continue
         ach = cells * fpc / (t * 1e-3) / 1e12
         tb = DRAM_BYTES_PER_CELL.get(name)
         roof[name] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                       "frac": ach * 1e3 / FP64_PEAK_GFLOPS, "traffic": (tb * cells if tb else None),
                       "ms_per_launch": t, "cells_per_launch": cells, "flops_per_cell": fpc}
-    dominant = DOMINANT if DOMINANT in roof else next(iter(roof))
+    dominant = DOMINANT
     roofline = dict(roof[dominant])
     roofline["kernel"] = dominant
     roofline["peak_source"] = "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (nominal 1.25 TFLOP/s)"

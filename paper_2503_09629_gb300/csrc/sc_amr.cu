@@ -27,11 +27,12 @@ inline int grid_for(long work, int threads) {
 __global__ void __launch_bounds__(kThreads) amr_prolong_kernel(
     const double* __restrict__ yn, const double* __restrict__ k1, const double* __restrict__ k2,
     const double* __restrict__ k3, const double* __restrict__ k4, long pfs, int psy, int psz,
-    const AmrCell* __restrict__ cells, int ncells, double* __restrict__ store, int F, Weights w) {
-  const long total = (long)ncells * F;
+    const AmrCell* __restrict__ cells, int first, int ncells, double* __restrict__ store, int F, Weights w) {
+  const int nc = ncells - first;
+  const long total = (long)nc * F;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int a = (int)(idx % ncells);
-    const int f = (int)(idx / ncells);
+    const int a = first + (int)(idx % nc);
+    const int f = (int)(idx / nc);
     const AmrCell c = cells[a];
     const double* wx = w.prolong[c.parity & 1];
     const double* wy = w.prolong[(c.parity >> 1) & 1];
@@ -56,6 +57,72 @@ __global__ void __launch_bounds__(kThreads) amr_prolong_kernel(
       }
       store[((long)v * F + f) * ncells + a] = sz;
     }
+  }
+}
+
+
+// Separable form of the same interpolation for 4x4x4 fine blocks: one group
+// of 64 threads per (block, vector, field) stages the 8x8x8 parent region in
+// shared memory and interpolates along x, then y, then z (42 FMAs per fine
+// position instead of 258).  The order of operations per fine position is
+// the same as in amr_prolong_kernel (x sums, then y, then z), so both paths
+// give identical results.
+__global__ void __launch_bounds__(256) amr_prolong_block_kernel(
+    const double* __restrict__ yn, const double* __restrict__ k1, const double* __restrict__ k2,
+    const double* __restrict__ k3, const double* __restrict__ k4, long pfs, int psy, int psz,
+    const AmrBlock* __restrict__ blocks, int nblocks, int ncells, double* __restrict__ store, int F, Weights w) {
+  __shared__ double sP[4][512];
+  __shared__ double sX[4][256];
+  __shared__ double sY[4][128];
+  const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int combos = 5 * F;
+  const int ngroups = (combos + 3) / 4;
+  const long items = (long)nblocks * ngroups;
+  for (long item = blockIdx.x; item < items; item += gridDim.x) {
+    const int b = (int)(item / ngroups);
+    const int combo = (int)(item % ngroups) * 4 + grp;
+    const bool active = combo < combos;
+    const AmrBlock B = blocks[b];
+    const int v = active ? combo / F : 0, f = active ? combo % F : 0;
+    if (active) {
+      const double* base = (v == 0 ? yn : v == 1 ? k1 : v == 2 ? k2 : v == 3 ? k3 : k4) + (long)f * pfs + B.pbase;
+#pragma unroll
+      for (int q = t; q < 512; q += 64) sP[grp][q] = __ldg(base + (long)(q >> 6) * psz + (long)((q >> 3) & 7) * psy + (q & 7));
+    }
+    __syncthreads();
+    if (active) {  // x: row (y, z) = (t & 7, t >> 3), 4 fine x positions
+      const double* row = &sP[grp][t * 8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int p = i & 1, o = (i >> 1) + p;
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < kPN; ++m) s = fma(w.prolong[p][m], row[o + m], s);
+        sX[grp][t * 4 + i] = s;  // [z][y][fx]
+      }
+    }
+    __syncthreads();
+    if (active) {  // y: z node = t >> 3, fx = t & 3, fine y pair (t >> 2) & 1
+      const int z = t >> 3, fx = t & 3, jp = (t >> 2) & 1;
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        const int j = 2 * jp + jj, p = j & 1, o = (j >> 1) + p;
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < kPN; ++m) s = fma(w.prolong[p][m], sX[grp][(z * 8 + o + m) * 4 + fx], s);
+        sY[grp][(z * 4 + j) * 4 + fx] = s;  // [z][fy][fx]
+      }
+    }
+    __syncthreads();
+    if (active && ((B.mask >> t) & 1ull)) {  // z: fine position t = fx + 4 fy + 16 fz
+      const int fx = t & 3, fy = (t >> 2) & 3, fz = t >> 4, p = fz & 1, o = (fz >> 1) + p;
+      double s = 0.0;
+#pragma unroll
+      for (int m = 0; m < kPN; ++m) s = fma(w.prolong[p][m], sY[grp][((o + m) * 4 + fy) * 4 + fx], s);
+      const int slot = B.slot0 + __popcll(B.mask & ((1ull << t) - 1ull));
+      store[((long)v * F + f) * ncells + slot] = s;
+    }
+    __syncthreads();
   }
 }
 
@@ -210,11 +277,23 @@ __global__ void __launch_bounds__(kThreads) nonfinite_kernel(const double* __res
 }  // namespace
 
 cudaError_t launch_amr_prolong(const double* yn, const double* k1, const double* k2, const double* k3,
-                               const double* k4, long pfs, int psy, int psz, const AmrCell* cells, int ncells,
-                               double* store, int F, const Weights& w, cudaStream_t s) {
-  if (ncells == 0) return cudaSuccess;
-  amr_prolong_kernel<<<grid_for((long)ncells * F, kThreads), kThreads, 0, s>>>(yn, k1, k2, k3, k4, pfs, psy, psz,
-                                                                              cells, ncells, store, F, w);
+                               const double* k4, long pfs, int psy, int psz, const AmrCell* cells, int first,
+                               int ncells, double* store, int F, const Weights& w, cudaStream_t s) {
+  if (ncells <= first) return cudaSuccess;
+  amr_prolong_kernel<<<grid_for((long)(ncells - first) * F, kThreads), kThreads, 0, s>>>(
+      yn, k1, k2, k3, k4, pfs, psy, psz, cells, first, ncells, store, F, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_amr_prolong_blocks(const double* yn, const double* k1, const double* k2, const double* k3,
+                                      const double* k4, long pfs, int psy, int psz, const AmrBlock* blocks,
+                                      int nblocks, int ncells, double* store, int F, const Weights& w,
+                                      cudaStream_t s) {
+  if (nblocks == 0) return cudaSuccess;
+  const long items = (long)nblocks * ((5 * F + 3) / 4);
+  const int grid = (int)(items < 152L * 8 * 16 ? items : 152L * 8 * 16);
+  amr_prolong_block_kernel<<<grid, 256, 0, s>>>(yn, k1, k2, k3, k4, pfs, psy, psz, blocks, nblocks, ncells, store, F,
+                                                w);
   return cudaGetLastError();
 }
 

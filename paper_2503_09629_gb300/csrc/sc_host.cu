@@ -148,6 +148,11 @@ struct Level {
   int ntiles = 0;
   AmrCell* amr = nullptr;
   int namr = 0;
+  AmrBlock* blocks = nullptr;
+  int nblocks = 0;
+  RowSeg* dxy = nullptr;
+  int ndxy = 0;
+  int namr_blocked = 0;
   double* amr_store = nullptr;  // 5 * F * namr prolonged parent vectors
   int2* periodic = nullptr;
   int nperiodic = 0;
@@ -277,6 +282,10 @@ sc_status validate(const sc_desc* d) {
 struct HostLists {
   std::vector<Tile> tiles;
   std::vector<AmrCell> amr;
+  std::vector<int> amr_gi, amr_gw;  // unwrapped / wrapped global fine index per AMR cell
+  std::vector<AmrBlock> blocks;     // 4x4x4 fine blocks served by the separable kernel
+  std::vector<RowSeg> dxy;          // rows where D_x / D_y of the Hessian fields are stored
+  int namr_blocked = 0;             // AMR cells [0, namr_blocked) belong to blocks
   std::vector<int2> periodic;
   std::vector<int32_t> phys;
   std::vector<RestrictCell> restr;
@@ -324,6 +333,94 @@ sc_status build_level_geometry(sc_ctx* c, int l, const sc_box* boxes, int nb) {
 bool is_interior(const Level& L, const int* gi) {
   if (!in_array(L.g, gi)) return false;
   return L.kind[elem_index(L.g, gi)] == K_INTERIOR;
+}
+
+// Group the refinement-boundary ghost cells of level l into 4x4x4 fine blocks
+// (aligned to multiples of 4 in the level's unwrapped index space) for the
+// separable prolongation kernel.  A block qualifies when all its ghost cells
+// wrap by the same periodic shift and the 8x8x8 parent region that covers the
+// stencils of all 64 fine positions lies inside the parent array.  Ghost
+// cells of qualifying blocks are reordered block by block (bit order
+// x + 4y + 16z inside a block); the remaining cells follow and use the
+// per-cell kernel.
+void group_amr_blocks(sc_ctx* c, int l, HostLists& hl) {
+  const Level& P = c->lev[l - 1];
+  const size_t n = hl.amr.size();
+  struct Key {
+    int b[3];
+    bool operator<(const Key& o) const {
+      if (b[2] != o.b[2]) return b[2] < o.b[2];
+      if (b[1] != o.b[1]) return b[1] < o.b[1];
+      return b[0] < o.b[0];
+    }
+  };
+  auto fdiv4 = [](int v) { return v >= 0 ? v / 4 : -((-v + 3) / 4); };
+  std::vector<std::pair<Key, size_t>> order(n);
+  for (size_t a = 0; a < n; ++a) {
+    Key k;
+    for (int q = 0; q < 3; ++q) k.b[q] = fdiv4(hl.amr_gi[3 * a + q]);
+    order[a] = {k, a};
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<Key, size_t>& x, const std::pair<Key, size_t>& y) { return x.first < y.first; });
+  std::vector<AmrCell> fast, slow;
+  std::vector<AmrBlock> blocks;
+  size_t i = 0;
+  while (i < n) {
+    size_t j = i;
+    while (j < n && !(order[i].first < order[j].first) && !(order[j].first < order[i].first)) ++j;
+    const size_t a0 = order[i].second;
+    int shift[3], borg[3];
+    bool ok = true;
+    for (int q = 0; q < 3; ++q) {
+      shift[q] = hl.amr_gw[3 * a0 + q] - hl.amr_gi[3 * a0 + q];
+      borg[q] = 4 * order[i].first.b[q] + shift[q];  // wrapped fine index of the block origin
+      if (borg[q] & 1) ok = false;
+    }
+    uint64_t mask = 0;
+    for (size_t t = i; t < j && ok; ++t) {
+      const size_t a = order[t].second;
+      int bit = 0, mul = 1;
+      for (int q = 0; q < 3; ++q) {
+        if (hl.amr_gw[3 * a + q] - hl.amr_gi[3 * a + q] != shift[q]) ok = false;
+        bit += (hl.amr_gi[3 * a + q] - 4 * order[i].first.b[q]) * mul;
+        mul *= 4;
+      }
+      mask |= 1ull << bit;
+    }
+    int lo[3], hi[3];
+    for (int q = 0; q < 3; ++q) {
+      lo[q] = borg[q] / 2 - 3;  // parent region [c0 - 3, c0 + 4]
+      hi[q] = borg[q] / 2 + 4;
+    }
+    if (ok && in_array(P.g, lo) && in_array(P.g, hi)) {
+      AmrBlock B;
+      B.pbase = (int32_t)P.g.off(lo[0], lo[1], lo[2]);
+      B.slot0 = (int32_t)fast.size();
+      B.mask = mask;
+      // cells in bit order
+      std::vector<std::pair<int, size_t>> bits;
+      for (size_t t = i; t < j; ++t) {
+        const size_t a = order[t].second;
+        int bit = 0, mul = 1;
+        for (int q = 0; q < 3; ++q) {
+          bit += (hl.amr_gi[3 * a + q] - 4 * order[i].first.b[q]) * mul;
+          mul *= 4;
+        }
+        bits.push_back({bit, a});
+      }
+      std::sort(bits.begin(), bits.end());
+      for (auto& pr : bits) fast.push_back(hl.amr[pr.second]);
+      blocks.push_back(B);
+    } else {
+      for (size_t t = i; t < j; ++t) slow.push_back(hl.amr[order[t].second]);
+    }
+    i = j;
+  }
+  hl.namr_blocked = (int)fast.size();
+  fast.insert(fast.end(), slow.begin(), slow.end());
+  hl.amr.swap(fast);
+  hl.blocks.swap(blocks);
 }
 
 sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
@@ -400,8 +497,13 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
           ac.pbase = (int32_t)P.g.off(first[0], first[1], first[2]);
           ac.parity = par;
           hl.amr.push_back(ac);
+          for (int q = 0; q < 3; ++q) {
+            hl.amr_gi.push_back(gi[q]);
+            hl.amr_gw.push_back(gw[q]);
+          }
         }
       }
+  if (l > 0 && !hl.amr.empty()) group_amr_blocks(c, l, hl);
   // interior tiles: per box, x tiles of 32 (or the box width), 4 x 2 in y, z
   for (const sc_box& B : L.boxes)
     for (int z = B.lo[2]; z <= B.hi[2]; z += 2)
@@ -416,6 +518,38 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
           t.nz = std::min(2, B.hi[2] - z + 1);
           hl.tiles.push_back(t);
         }
+  // rows where the Z4c evolution stores D_x (interior cells and their 2-cell
+  // extension in y or z) and D_y (extension in z) of the Hessian fields
+  if (c->system == SC_Z4C) {
+    auto interior_at = [&](int i, int j, int k) {
+      if (i < 0 || j < 0 || k < 0 || i >= g.ext[0] || j >= g.ext[1] || k >= g.ext[2]) return false;
+      return L.kind[((long)k * g.ext[1] + j) * g.ext[0] + i] == K_INTERIOR;
+    };
+    for (int k = 0; k < g.ext[2]; ++k)
+      for (int j = 0; j < g.ext[1]; ++j) {
+        int run_start = -1, run_which = 0;
+        for (int i = 0; i <= g.ext[0]; ++i) {
+          int which = 0;
+          if (i < g.ext[0]) {
+            bool dz = false, dy = false;
+            for (int d = -2; d <= 2 && !dz; ++d) dz = interior_at(i, j, k + d);
+            for (int d = -2; d <= 2 && !dy; ++d) dy = interior_at(i, j + d, k);
+            which = ((dz || dy) ? 1 : 0) | (dz ? 2 : 0);
+          }
+          if (which != run_which) {
+            if (run_which) {
+              RowSeg sg;
+              sg.off = (int32_t)(((long)k * g.ext[1] + j) * g.pitch + run_start);
+              sg.n = i - run_start;
+              sg.which = run_which;
+              hl.dxy.push_back(sg);
+            }
+            run_start = i;
+            run_which = which;
+          }
+        }
+      }
+  }
   // restriction onto the parent: parent cells whose 8 children are interior here
   if (l > 0) {
     const Level& P = c->lev[l - 1];
@@ -522,8 +656,10 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
   switch (o.kind) {
     case OP_PROLONG: {
       const Level& P = c->lev[o.level - 1];
+      CU(launch_amr_prolong_blocks(o.yn, P.K[0], P.K[1], P.K[2], P.K[3], P.g.fs, P.g.pitch, P.g.pitch * P.g.ext[1],
+                                   L.blocks, L.nblocks, L.namr, L.amr_store, c->F, c->w, s));
       CU(launch_amr_prolong(o.yn, P.K[0], P.K[1], P.K[2], P.K[3], P.g.fs, P.g.pitch, P.g.pitch * P.g.ext[1], L.amr,
-                            L.namr, L.amr_store, c->F, c->w, s));
+                            L.namr_blocked, L.namr, L.amr_store, c->F, c->w, s));
       break;
     }
     case OP_FILL:
@@ -548,7 +684,8 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       if (c->system == SC_WAVE) {
         CU(launch_wave_stage(a, L.tiles, L.ntiles, s));
       } else {
-        CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, s));
+        CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, s));
+        CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, s));
         CU(launch_z4c_stage(a, c->scratch, c->zp, L.tiles, L.ntiles, s));
       }
       if (L.nphys) CU(launch_radiative_stage(a, L.phys, L.nphys, c->F, g, c->system, s));
@@ -758,12 +895,16 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
     }
     if ((st = upload(c.get(), hl.tiles, &L.tiles)) || (st = upload(c.get(), hl.amr, &L.amr)) ||
         (st = upload(c.get(), hl.periodic, &L.periodic)) || (st = upload(c.get(), hl.phys, &L.phys)) ||
-        (st = upload(c.get(), hl.restr, &L.restr))) {
+        (st = upload(c.get(), hl.restr, &L.restr)) || (st = upload(c.get(), hl.blocks, &L.blocks)) ||
+        (st = upload(c.get(), hl.dxy, &L.dxy))) {
       c->release();
       return st;
     }
     L.ntiles = (int)hl.tiles.size();
     L.namr = (int)hl.amr.size();
+    L.nblocks = (int)hl.blocks.size();
+    L.ndxy = (int)hl.dxy.size();
+    L.namr_blocked = hl.namr_blocked;
     L.nperiodic = (int)hl.periodic.size();
     L.nphys = (int)hl.phys.size();
     L.nrestr = (int)hl.restr.size();
@@ -965,7 +1106,10 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   CU(cudaEventRecord(e[0], c->stream));
   for (int r = 0; r < nrep; ++r) {
     if (c->system == SC_WAVE) CU(launch_wave_stage(a, L.tiles, L.ntiles, c->stream));
-    else CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, c->stream));
+    else {
+      CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, c->stream));
+      CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, c->stream));
+    }
   }
   CU(cudaEventRecord(e[1], c->stream));
   if (c->system == SC_Z4C)

@@ -50,11 +50,31 @@ struct AmrCell {
   int32_t parity;
 };
 
+// A 4x4x4 block of fine cells (first fine index even, aligned to 4 in the
+// unwrapped index space) whose refinement-boundary ghost cells are prolonged
+// together: pbase = offset of the first cell of the 8x8x8 parent region
+// [c0-3, c0+4]^3 in the parent array (c0 = parent of the block's first cell),
+// slot0 = store slot of the block's first ghost cell, mask bit x + 4y + 16z
+// set for each fine position that is a ghost cell (slots follow bit order).
+struct AmrBlock {
+  int32_t pbase;
+  int32_t slot0;
+  unsigned long long mask;
+};
+
 // Restricted parent cell: its offset in the parent array and the offset of
 // the first fine stencil cell (2C-2 per dimension) in the fine array.
 struct RestrictCell {
   int32_t dst;
   int32_t fbase;
+};
+
+// A run of consecutive cells of one array row: offset of the first cell,
+// count, and which first derivatives to store there (bit 0: D_x, bit 1: D_y).
+struct RowSeg {
+  int32_t off;
+  int32_t n;
+  int32_t which;
 };
 
 struct Weights {
@@ -90,6 +110,10 @@ cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles,
 
 cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy, int sz, double h,
                               const Tile* tiles, int ntiles, cudaStream_t s);
+cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, double h, const RowSeg* segs, int nsegs,
+                           cudaStream_t s);
+cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz, double h,
+                                    const Tile* tiles, int ntiles, cudaStream_t s);
 cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4cParams& p,
                              const Tile* tiles, int ntiles, cudaStream_t s);
 cudaError_t launch_radiative_stage(const StageArgs& a, const int32_t* cells, int ncells, int F,
@@ -99,9 +123,15 @@ cudaError_t launch_z4c_constraints(const double* Y, const double* scratch, doubl
                                    const int* box_lo, const int* box_n, cudaStream_t s);
 
 cudaError_t launch_periodic_copy(double* vec, long fs, int F, const int2* pairs, int npairs, cudaStream_t s);
+// per-cell prolongation of AMR cells [first, ncells) of the list (store has ncells slots per vector-field)
 cudaError_t launch_amr_prolong(const double* yn, const double* k1, const double* k2, const double* k3,
-                               const double* k4, long pfs, int psy, int psz, const AmrCell* cells,
+                               const double* k4, long pfs, int psy, int psz, const AmrCell* cells, int first,
                                int ncells, double* store, int F, const Weights& w, cudaStream_t s);
+// block-separable prolongation of the ghost cells grouped in 4x4x4 blocks
+cudaError_t launch_amr_prolong_blocks(const double* yn, const double* k1, const double* k2, const double* k3,
+                                      const double* k4, long pfs, int psy, int psz, const AmrBlock* blocks,
+                                      int nblocks, int ncells, double* store, int F, const Weights& w,
+                                      cudaStream_t s);
 cudaError_t launch_amr_apply(double* vec, long fs, int F, const AmrCell* cells, int ncells,
                              const double* store, const double* c4, cudaStream_t s);
 cudaError_t launch_restrict(double* parent, long pfs, const double* fine, long ffs, int fsy, int fsz,

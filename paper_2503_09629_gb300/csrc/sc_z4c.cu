@@ -27,7 +27,6 @@ constexpr int kThreads = 256;
 constexpr int Q_D1 = 0;    // 3 * f + d: first derivative of field f along d
 constexpr int Q_D2 = 66;   // 6 * s + p: second derivative, s = slot (W, gt x6, alpha, beta x3), p = xx,xy,xz,yy,yz,zz
 constexpr int Q_KO = 132;  // f: sum_d delta_d^6 u_f (unscaled)
-constexpr int Q_NUM = 154;
 
 // slot of field f among the fields with second derivatives, -1 if none
 __host__ __device__ inline int d2_slot(int f) {
@@ -92,6 +91,85 @@ __global__ void __launch_bounds__(kThreads) z4c_derivs_kernel(const double* __re
         }
         d2[slot[m] * fs] = fma(8.0, D[2] - D[1], D[0] - D[3]) * i144h2;
       }
+    }
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Evolution form of the derivative pass, in two kernels.  The mixed second
+// derivatives are the product of two first-derivative stencils, so
+//   d_x d_y u = D_y (D_x u),  d_x d_z u = D_z (D_x u),  d_y d_z u = D_z (D_y u)
+// exactly (the same 16-point stencil, summed in another order).  The first
+// kernel stores D_x u and D_y u of the 11 fields with second derivatives on
+// row segments covering the interior and its 2-cell extension in y and z
+// (D_x) or in z (D_y); the second kernel computes everything else per
+// interior cell and differentiates the stored first derivatives for the
+// mixed terms: 4 FP64 operations per mixed derivative instead of 16.
+
+// field of Hessian slot s (W, gt x6, alpha, beta x3): slots 0..6 -> fields 0..6, 7..10 -> 18..21
+__device__ __forceinline__ int d2_field(int s) { return s <= 6 ? s : s + 11; }
+
+__global__ void __launch_bounds__(128) z4c_dxy_kernel(const double* __restrict__ Y, double* __restrict__ S, long fs,
+                                                     int sy_, const RowSeg* __restrict__ segs, int nsegs, double h) {
+  const double i12h = 1.0 / (12.0 * h);
+  const long sy = sy_;
+  for (int sgi = blockIdx.x; sgi < nsegs; sgi += gridDim.x) {
+    const RowSeg sg = segs[sgi];
+    for (int q = threadIdx.x; q < sg.n * 11; q += blockDim.x) {
+      const int slot = q / sg.n;
+      const long o = sg.off + (q - slot * sg.n);
+      const int f = d2_field(slot);
+      const double* u = Y + (long)f * fs + o;
+      if (sg.which & 1) S[(long)(Q_D1 + 3 * f + 0) * fs + o] = fma(8.0, u[1] - u[-1], u[-2] - u[2]) * i12h;
+      if (sg.which & 2) S[(long)(Q_D1 + 3 * f + 1) * fs + o] = fma(8.0, u[sy] - u[-sy], u[-2 * sy] - u[2 * sy]) * i12h;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) z4c_derivs_split_kernel(const double* __restrict__ Y,
+                                                                   double* __restrict__ S, long fs, int sy_, int sz_,
+                                                                   double h, const Tile* __restrict__ tiles,
+                                                                   int ntiles) {
+  const double i12h = 1.0 / (12.0 * h);
+  const double i12h2 = 1.0 / (12.0 * h * h);
+  const long st[3] = {1, (long)sy_, (long)sz_};
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile T = tiles[t];
+    const int n = T.nx * T.ny * T.nz;
+    for (int q = threadIdx.x; q < n * kNZ4c; q += blockDim.x) {
+      const int f = q / n;
+      const int c = q - f * n;
+      const int i = c % T.nx;
+      const int j = (c / T.nx) % T.ny;
+      const int k = c / (T.nx * T.ny);
+      const long o = (T.z0 + k) * st[2] + (T.y0 + j) * st[1] + (T.x0 + i);
+      const double* u = Y + (long)f * fs + o;
+      const double u0 = u[0];
+      const int sl = d2_slot(f);
+      double p1[3], p2[3], P3 = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const long s = st[d];
+        const double a1 = u[-s], b1 = u[s], a2 = u[-2 * s], b2 = u[2 * s];
+        p1[d] = a1 + b1;
+        p2[d] = a2 + b2;
+        P3 += u[-3 * s] + u[3 * s];
+        if (sl < 0 || d == 2) S[(long)(Q_D1 + 3 * f + d) * fs + o] = fma(8.0, b1 - a1, a2 - b2) * i12h;
+      }
+      const double P1 = p1[0] + p1[1] + p1[2], P2 = p2[0] + p2[1] + p2[2];
+      S[(long)(Q_KO + f) * fs + o] = fma(15.0, P1, fma(-6.0, P2, fma(-60.0, u0, P3)));
+      if (sl < 0) continue;
+      double* d2 = S + (long)(Q_D2 + 6 * sl) * fs + o;
+      d2[0 * fs] = fma(-30.0, u0, fma(16.0, p1[0], -p2[0])) * i12h2;
+      d2[3 * fs] = fma(-30.0, u0, fma(16.0, p1[1], -p2[1])) * i12h2;
+      d2[5 * fs] = fma(-30.0, u0, fma(16.0, p1[2], -p2[2])) * i12h2;
+      const double* Dx = S + (long)(Q_D1 + 3 * f + 0) * fs + o;
+      const double* Dy = S + (long)(Q_D1 + 3 * f + 1) * fs + o;
+      const long sy = st[1], sz = st[2];
+      d2[1 * fs] = fma(8.0, Dx[sy] - Dx[-sy], Dx[-2 * sy] - Dx[2 * sy]) * i12h;  // D_y D_x
+      d2[2 * fs] = fma(8.0, Dx[sz] - Dx[-sz], Dx[-2 * sz] - Dx[2 * sz]) * i12h;  // D_z D_x
+      d2[4 * fs] = fma(8.0, Dy[sz] - Dy[-sz], Dy[-2 * sz] - Dy[2 * sz]) * i12h;  // D_z D_y
     }
   }
 }
@@ -488,6 +566,22 @@ cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy,
   if (ntiles == 0) return cudaSuccess;
   const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
   z4c_derivs_kernel<<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, double h, const RowSeg* segs, int nsegs,
+                           cudaStream_t s) {
+  if (nsegs == 0) return cudaSuccess;
+  const int grid = nsegs < 152 * 32 ? nsegs : 152 * 32;
+  z4c_dxy_kernel<<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz, double h,
+                                    const Tile* tiles, int ntiles, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
+  z4c_derivs_split_kernel<<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles);
   return cudaGetLastError();
 }
 
