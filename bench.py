@@ -132,6 +132,69 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def run_ensemble(sc, W, n: int, seed: int, burst: bool, mean_interarrival: float, served: bool,
+                 budget: int = 48 << 30, max_active: int = 32):
+    """Serve the seeded request ensemble; returns latency and throughput.
+
+    served=True: continuous batching (max_active slots, one stream each, CUDA
+    graph per coarse step); served=False: the plain per-box form, one request
+    at a time in arrival order, kernels launched box by box without graphs."""
+    reqs = sorted(W.serving_requests(n, seed, burst=burst, mean_interarrival=mean_interarrival), key=lambda r: r[0])
+    srv = sc.Server(budget, max_active if served else 1, 2)
+    mode = sc.SC_EXEC_GRAPH if served else sc.SC_EXEC_PER_BOX
+    tickets, lat = [], []
+    nxt = 0
+    t0 = time.perf_counter()
+    unfinished = []
+    while nxt < len(reqs) or unfinished:
+        now = time.perf_counter() - t0
+        if now > 600.0:
+            raise RuntimeError("serving ensemble did not finish within 600 s")
+        while nxt < len(reqs) and reqs[nxt][0] <= now:
+            _t, h, steps = reqs[nxt]
+            unfinished.append(srv.sc_server_submit(h, steps, exec_mode=mode))
+            nxt += 1
+        srv.sc_server_tick()
+        still = []
+        for t in unfinished:
+            done, l = srv.sc_server_poll(t)
+            if done:
+                lat.append(l)
+                srv.sc_server_release(t)
+            else:
+                still.append(t)
+        unfinished = still
+    wall = time.perf_counter() - t0
+    st = srv.sc_server_stats()
+    srv.close()
+    lat.sort()
+    pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    return {"requests": n, "arrivals": "burst" if burst else f"poisson mean {mean_interarrival * 1e3:.1f} ms",
+            "form": "served (continuous batching, graphs)" if served else "plain (FIFO, per-box launches)",
+            "p50_s": pct(0.5), "p99_s": pct(0.99), "wall_s": wall,
+            "zone_updates_per_s": st["zu_finest"] / wall, "actual_zone_updates_per_s": st["zu_actual"] / wall,
+            "gpu_launches": st["launches"]}
+
+
+def run_serving(args):
+    import torch
+
+    import paper_2503_09629_gb300 as sc
+    from paper_2503_09629_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    sc.build()
+    n = args.requests
+    plain_burst = run_ensemble(sc, W, n, 0, True, 0.0, served=False)
+    served_burst = run_ensemble(sc, W, n, 0, True, 0.0, served=True)
+    mean_service = plain_burst["wall_s"] / n
+    ia = mean_service / 0.9  # arrival rate 0.9 / mean plain service time
+    plain_poisson = run_ensemble(sc, W, n, 0, False, ia, served=False)
+    served_poisson = run_ensemble(sc, W, n, 0, False, ia, served=True)
+    return {"burst": {"served": served_burst, "plain": plain_burst},
+            "poisson": {"served": served_poisson, "plain": plain_poisson,
+                        "mean_plain_service_s": mean_service}}
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
@@ -253,13 +316,29 @@ def run_gpu(args, rank: int, world: int):
         e2e_s = float(t.item())
     e2e_value = world * fin_per_step * ne2e / e2e_s
 
+    # Served form vs plain per-box form on a seeded ensemble (configs[4] mix).
+    serving = None
+    if rank == 0 and args.serving_requests > 0:
+        ctx.close()
+        ctx = None
+        torch.cuda.empty_cache()
+        n = args.serving_requests
+        plain = run_ensemble(sc, W, n, 0, True, 0.0, served=False)
+        served = run_ensemble(sc, W, n, 0, True, 0.0, served=True)
+        ia = plain["wall_s"] / n / 0.9
+        plain_p = run_ensemble(sc, W, n, 0, False, ia, served=False)
+        served_p = run_ensemble(sc, W, n, 0, False, ia, served=True)
+        serving = {"requests": n, "burst": {"served": served, "plain": plain},
+                   "poisson_load_0.9": {"served": served_p, "plain": plain_p}}
+
     cpu = None
     if rank == 0 and world == 1:
         hs = sample_hierarchy()
         v, dt = oracle_step_rate(hs, 1, 0)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"1 coarse step of {hs.name} ({dt:.1f} s)"}
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -274,7 +353,7 @@ def run_gpu(args, rank: int, world: int):
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": ne2e},
-                "gpu_launches": launches, "clocks": clk}
+                "gpu_launches": launches, "clocks": clk, "serving": serving}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -286,7 +365,17 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--serving", action="store_true", help="only the serving ensemble (configs[4]), one JSON line")
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--serving-requests", type=int, default=64,
+                    help="requests of the served-vs-plain ensemble embedded in the default line (0: skip)")
     args = ap.parse_args()
+    if args.serving:
+        res = run_serving(args)
+        print(json.dumps({"metric": "ensemble p50/p99 latency and zone-updates/s (served vs plain per-box form)",
+                          "unit": "s / zone-updates/s", "data": "synthetic", "dtype": "f64", "serving": res}),
+              flush=True)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

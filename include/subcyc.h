@@ -100,7 +100,12 @@ typedef struct {
   double kappa1, kappa2, eta, ko_sigma;
   void* cuda_stream;
   const sc_allocator* allocator;
+  int exec_mode;  /* SC_EXEC_GRAPH (0, default): one CUDA graph per coarse step, one launch per
+                     level and phase covering all boxes; SC_EXEC_PER_BOX (1): the plain form, stage
+                     kernels launched box by box directly on the stream, no graph (for comparison) */
 } sc_desc;
+
+enum { SC_EXEC_GRAPH = 0, SC_EXEC_PER_BOX = 1 };
 
 /* Build the hierarchy: validate nesting and alignment, allocate every level's
  * state, stage and k1..k4 arrays, build the device work lists.
@@ -193,6 +198,31 @@ sc_status sc_time_stage_kernels(sc_ctx* ctx, int level, int nrep, double* ms);
  * library routine is called. */
 sc_status sc_z4c_constraints_noalloc(const double* dev_state, double* dev_out, const int* n, double h,
                                      void* cuda_stream);
+
+/* ---- serving: continuous batching of independent evolutions ---------------
+ * A server owns max_active slots (one CUDA stream each) and a device-memory
+ * budget.  sc_server_submit queues a request (hierarchy, analytic initial
+ * data, number of coarse steps); it fails with SC_EBUSY if the request's
+ * footprint (sc_footprint_estimate) exceeds the whole budget.  Each
+ * sc_server_tick (non-blocking) retires requests whose last step completed,
+ * admits queued requests in arrival order while a slot is free and their
+ * footprint fits the budget left (allocating their state from a
+ * stream-ordered pool on the slot's stream), and launches the next coarse step
+ * of every active request with fewer than `depth` steps in flight.  Requests
+ * run concurrently on their own streams; a request's result is bitwise the
+ * same as when it runs alone.  A finished request keeps its state resident
+ * until sc_server_release.  latency = completion seen by a tick - submission. */
+typedef struct sc_server sc_server;
+sc_status sc_server_create(size_t hbm_budget_bytes, int max_active, int depth, sc_server** out);
+sc_status sc_server_submit(sc_server* srv, const sc_desc* desc, int id_kind, const double* id_params, int nparams,
+                           int n_coarse_steps, unsigned long long* ticket);
+sc_status sc_server_tick(sc_server* srv, int* n_active, int* n_queued, int* n_launched);
+sc_status sc_server_poll(sc_server* srv, unsigned long long ticket, int* done, double* latency_s);
+sc_status sc_server_read(sc_server* srv, unsigned long long ticket, int level, int box, int field, double* host_dst);
+sc_status sc_server_release(sc_server* srv, unsigned long long ticket);
+sc_status sc_server_stats(sc_server* srv, double* zu_finest_done, double* zu_actual_done, long* launches,
+                          size_t* bytes_in_use);
+sc_status sc_server_destroy(sc_server* srv);
 
 const char* sc_last_error(void);
 

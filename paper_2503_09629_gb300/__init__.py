@@ -27,6 +27,7 @@ LIB_PATH = os.path.join(HERE, "libsubcyc.so")
 SC_OK, SC_EINVAL, SC_ENOMEM, SC_ECUDA, SC_ENESTING, SC_ENONFINITE, SC_ETIMEOUT, SC_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 SC_WAVE, SC_Z4C = 0, 1
 SC_BC_PERIODIC, SC_BC_RADIATIVE = 0, 1
+SC_EXEC_GRAPH, SC_EXEC_PER_BOX = 0, 1
 GHOST = 3
 NCONSTRAINTS = 7
 
@@ -67,6 +68,7 @@ class sc_desc(ctypes.Structure):
         ("ko_sigma", ctypes.c_double),
         ("cuda_stream", ctypes.c_void_p),
         ("allocator", ctypes.POINTER(sc_allocator)),
+        ("exec_mode", ctypes.c_int),
     ]
 
 
@@ -107,6 +109,16 @@ def lib():
     L.sc_footprint_estimate.argtypes = [ctypes.POINTER(sc_desc), ctypes.POINTER(ctypes.c_size_t)]
     L.sc_time_stage_kernels.argtypes = [P, I, I, DP]
     L.sc_z4c_constraints_noalloc.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), D, P]
+    IP = ctypes.POINTER(ctypes.c_int)
+    U64 = ctypes.c_ulonglong
+    L.sc_server_create.argtypes = [ctypes.c_size_t, I, I, ctypes.POINTER(P)]
+    L.sc_server_submit.argtypes = [P, ctypes.POINTER(sc_desc), I, DP, I, I, ctypes.POINTER(U64)]
+    L.sc_server_tick.argtypes = [P, IP, IP, IP]
+    L.sc_server_poll.argtypes = [P, U64, IP, DP]
+    L.sc_server_read.argtypes = [P, U64, I, I, I, DP]
+    L.sc_server_release.argtypes = [P, U64]
+    L.sc_server_stats.argtypes = [P, DP, DP, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_size_t)]
+    L.sc_server_destroy.argtypes = [P]
     _lib = L
     return L
 
@@ -139,7 +151,7 @@ def _torch_allocator():
     return a
 
 
-def make_desc(h, stream: Optional[int] = None, allocator=None):
+def make_desc(h, stream: Optional[int] = None, allocator=None, exec_mode: int = SC_EXEC_GRAPH):
     """sc_desc for a workloads.Hierarchy; returns (desc, keepalive)."""
     nb = (ctypes.c_int * h.nlevels)(*[len(b) for b in h.boxes])
     flat = [bx for lvl in h.boxes for bx in lvl]
@@ -160,6 +172,7 @@ def make_desc(h, stream: Optional[int] = None, allocator=None):
     d.subcycle = 1 if h.subcycle else 0
     d.kappa1, d.kappa2, d.eta, d.ko_sigma = h.kappa1, h.kappa2, h.eta, h.ko_sigma
     d.cuda_stream = stream
+    d.exec_mode = exec_mode
     keep = [nb, boxes]
     if allocator is not None:
         d.allocator = ctypes.pointer(allocator)
@@ -196,7 +209,7 @@ class Context:
     on PyTorch's current CUDA stream.
     """
 
-    def __init__(self, h, use_torch: bool = True, stream: Optional[int] = None):
+    def __init__(self, h, use_torch: bool = True, stream: Optional[int] = None, exec_mode: int = SC_EXEC_GRAPH):
         L = lib()
         self.h = h
         self._alloc = None
@@ -207,7 +220,7 @@ class Context:
             if stream is None:
                 stream = torch.cuda.current_stream().cuda_stream
             self._alloc = _torch_allocator()
-        d, self._keep = make_desc(h, stream, self._alloc)
+        d, self._keep = make_desc(h, stream, self._alloc, exec_mode)
         ctx = ctypes.c_void_p()
         _check(L.sc_create(ctypes.byref(d), ctypes.byref(ctx)))
         self.ctx = ctx
@@ -297,3 +310,90 @@ class Context:
         """[level][box] -> array (F, nz, ny, nx)."""
         return [[np.stack([self.sc_get_field(l, b, f, ghosted) for f in range(self.F)])
                  for b in range(len(self.h.boxes[l]))] for l in range(self.h.nlevels)]
+
+
+class Server:
+    """Continuous-batching server of independent evolutions (wraps ``sc_server*``).
+
+    Requests are admitted in arrival order as slots and device memory free up,
+    each on its own stream; every ``sc_server_tick`` launches the next coarse
+    step of every active request.  Results are bitwise independent of the mix.
+    """
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 16, depth: int = 2):
+        srv = ctypes.c_void_p()
+        _check(lib().sc_server_create(int(hbm_budget_bytes), int(max_active), int(depth), ctypes.byref(srv)))
+        self.srv = srv
+        self.hier = {}
+
+    def close(self):
+        if getattr(self, "srv", None):
+            lib().sc_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sc_server_submit(self, h, n_coarse_steps: int, exec_mode: int = SC_EXEC_GRAPH) -> int:
+        d, keep = make_desc(h, exec_mode=exec_mode)
+        p = np.ascontiguousarray(h.id_params, dtype=np.float64)
+        t = ctypes.c_ulonglong()
+        _check(lib().sc_server_submit(self.srv, ctypes.byref(d), h.id_kind, _dp(p) if len(p) else None, len(p),
+                                      int(n_coarse_steps), ctypes.byref(t)))
+        self.hier[t.value] = h
+        return t.value
+
+    def sc_server_tick(self) -> Tuple[int, int, int]:
+        a, q, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().sc_server_tick(self.srv, ctypes.byref(a), ctypes.byref(q), ctypes.byref(n)))
+        return a.value, q.value, n.value
+
+    def sc_server_poll(self, ticket: int) -> Tuple[bool, float]:
+        d, lat = ctypes.c_int(), ctypes.c_double()
+        _check(lib().sc_server_poll(self.srv, ticket, ctypes.byref(d), ctypes.byref(lat)))
+        return bool(d.value), lat.value
+
+    def sc_server_read(self, ticket: int, level: int, box: int, field: int) -> np.ndarray:
+        h = self.hier[ticket]
+        lo, hi = h.boxes[level][box]
+        a = np.empty((hi[2] - lo[2] + 1, hi[1] - lo[1] + 1, hi[0] - lo[0] + 1))
+        _check(lib().sc_server_read(self.srv, ticket, level, box, field, _dp(a)))
+        return a
+
+    def sc_server_release(self, ticket: int):
+        _check(lib().sc_server_release(self.srv, ticket))
+        self.hier.pop(ticket, None)
+
+    def sc_server_stats(self) -> dict:
+        f, a = ctypes.c_double(), ctypes.c_double()
+        n, b = ctypes.c_long(), ctypes.c_size_t()
+        _check(lib().sc_server_stats(self.srv, ctypes.byref(f), ctypes.byref(a), ctypes.byref(n), ctypes.byref(b)))
+        return {"zu_finest": f.value, "zu_actual": a.value, "launches": n.value, "bytes_in_use": b.value}
+
+    def run_until_done(self, tickets, timeout_s: float = 600.0, on_done=None):
+        """Tick until every ticket has finished; on_done(ticket) is called once
+        per finished request (a client reads and releases it there, so its
+        memory returns to the budget).  Raises if nothing can progress (queued
+        requests blocked by finished requests that were never released) or if
+        timeout_s passes."""
+        import time
+        t0 = time.perf_counter()
+        pending = set(tickets)
+        while pending:
+            active, queued, launched = self.sc_server_tick()
+            for t in list(pending):
+                if self.sc_server_poll(t)[0]:
+                    pending.discard(t)
+                    if on_done is not None:
+                        on_done(t)
+            if pending and active == 0 and queued > 0 and launched == 0:
+                self.sc_server_tick()
+                active, queued, launched = self.sc_server_tick()
+                if active == 0 and launched == 0:
+                    raise SubcycError(SC_EBUSY, "server stalled: queued requests wait for memory held by "
+                                                "finished requests that were not released")
+            if time.perf_counter() - t0 > timeout_s:
+                raise SubcycError(SC_ETIMEOUT, f"requests not finished after {timeout_s} s")

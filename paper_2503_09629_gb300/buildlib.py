@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsubcyc.so")
-SOURCES = ["sc_host.cu", "sc_amr.cu", "sc_wave.cu", "sc_z4c.cu", "sc_noalloc.cu"]
+SOURCES = ["sc_host.cu", "sc_amr.cu", "sc_wave.cu", "sc_z4c.cu", "sc_noalloc.cu", "sc_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", SRC]

@@ -146,6 +146,7 @@ struct Level {
   // work lists (device) and their sizes
   Tile* tiles = nullptr;
   int ntiles = 0;
+  std::vector<int> box_tile_begin;  // tiles of box b: [box_tile_begin[b], box_tile_begin[b + 1])
   AmrCell* amr = nullptr;
   int namr = 0;
   AmrBlock* blocks = nullptr;
@@ -200,6 +201,8 @@ struct sc_ctx {
   double zu_finest = 0, zu_actual = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   long launches_per_step = 0;
+  int exec_mode = SC_EXEC_GRAPH;
+  std::vector<Op> plain_ops[2];  // per-box form: the schedule, run directly
 
   void* dalloc(size_t bytes) {
     bytes = (bytes + 255) & ~(size_t)255;
@@ -505,7 +508,9 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
       }
   if (l > 0 && !hl.amr.empty()) group_amr_blocks(c, l, hl);
   // interior tiles: per box, x tiles of 32 (or the box width), 4 x 2 in y, z
-  for (const sc_box& B : L.boxes)
+  L.box_tile_begin.clear();
+  for (const sc_box& B : L.boxes) {
+    L.box_tile_begin.push_back((int)hl.tiles.size());
     for (int z = B.lo[2]; z <= B.hi[2]; z += 2)
       for (int y = B.lo[1]; y <= B.hi[1]; y += 4)
         for (int x = B.lo[0]; x <= B.hi[0]; x += 32) {
@@ -518,6 +523,8 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
           t.nz = std::min(2, B.hi[2] - z + 1);
           hl.tiles.push_back(t);
         }
+  }
+  L.box_tile_begin.push_back((int)hl.tiles.size());
   // rows where the Z4c evolution stores D_x (interior cells and their 2-cell
   // extension in y or z) and D_y (extension in z) of the Hessian fields
   if (c->system == SC_Z4C) {
@@ -681,12 +688,18 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       a.sy = g.pitch;
       a.sz = g.pitch * g.ext[1];
       a.h = g.h;
-      if (c->system == SC_WAVE) {
-        CU(launch_wave_stage(a, L.tiles, L.ntiles, s));
-      } else {
-        CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, s));
-        CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, s));
-        CU(launch_z4c_stage(a, c->scratch, c->zp, L.tiles, L.ntiles, s));
+      // graph form: one launch over the tiles of all boxes; per-box form: one per box
+      const int nparts = c->exec_mode == SC_EXEC_PER_BOX ? (int)L.boxes.size() : 1;
+      if (c->system == SC_Z4C) CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, s));
+      for (int b = 0; b < nparts; ++b) {
+        const int t0 = nparts == 1 ? 0 : L.box_tile_begin[b];
+        const int nt = nparts == 1 ? L.ntiles : L.box_tile_begin[b + 1] - t0;
+        if (c->system == SC_WAVE) {
+          CU(launch_wave_stage(a, L.tiles + t0, nt, s));
+        } else {
+          CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles + t0, nt, s));
+          CU(launch_z4c_stage(a, c->scratch, c->zp, L.tiles + t0, nt, s));
+        }
       }
       if (L.nphys) CU(launch_radiative_stage(a, L.phys, L.nphys, c->F, g, c->system, s));
       break;
@@ -714,6 +727,23 @@ sc_status build_graphs(sc_ctx* c) {
     em.par.assign(c->nlev, 0);
     em.par[0] = p;
     em.coarse_step();
+    if (c->exec_mode == SC_EXEC_PER_BOX) {
+      c->plain_ops[p] = em.ops;
+      long n = 0;
+      for (const Op& o : em.ops) {
+        const Level& L = c->lev[o.level];
+        if (o.kind == OP_STAGE)
+          n += (long)L.boxes.size() * (c->system == SC_Z4C ? 2 : 1) + (c->system == SC_Z4C ? 1 : 0) + (L.nphys ? 1 : 0);
+        else if (o.kind == OP_PROLONG)
+          n += (L.nblocks ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0);
+        else if (o.kind == OP_FILL)
+          n += (o.level > 0 && L.namr ? 1 : 0) + (L.nperiodic ? 1 : 0);
+        else
+          n += L.nrestr ? 1 : 0;
+      }
+      c->launches_per_step = n;
+      continue;
+    }
     cudaStream_t cs;
     CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaGraph_t graph;
@@ -838,6 +868,14 @@ sc_status sc_footprint_estimate(const sc_desc* d, size_t* bytes) {
     maxfs = std::max(maxfs, (size_t)fs);
   }
   if (d->system == SC_Z4C) total += (size_t)maxfs * 176 * sizeof(double);
+  // staging for field copies and constraints (largest ghosted box, 7 values per cell), plus slack
+  size_t maxbox = 0;
+  for (int b = 0; b < bi; ++b) {
+    size_t v = 1;
+    for (int q = 0; q < 3; ++q) v *= (size_t)(d->boxes[b].hi[q] - d->boxes[b].lo[q] + 1 + 2 * kGhost);
+    maxbox = std::max(maxbox, v);
+  }
+  total += maxbox * 7 * sizeof(double) + (1u << 20);
   *bytes = total;
   return SC_OK;
 }
@@ -862,6 +900,7 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
   c->cfl = d->cfl;
   c->zp = Z4cParams{d->kappa1, d->kappa2, d->eta, d->ko_sigma};
   c->stream = (cudaStream_t)d->cuda_stream;
+  c->exec_mode = d->exec_mode == SC_EXEC_PER_BOX ? SC_EXEC_PER_BOX : SC_EXEC_GRAPH;
   if (d->allocator && d->allocator->alloc && d->allocator->free) {
     c->alloc = *d->allocator;
     c->has_alloc = true;
@@ -1005,7 +1044,14 @@ sc_status sc_advance(sc_ctx* c, int n) {
   const int L = c->nlev;
   for (int s = 0; s < n; ++s) {
     Level& L0 = c->lev[0];
-    CU(cudaGraphLaunch(c->graph[L0.parity], c->stream));
+    if (c->exec_mode == SC_EXEC_PER_BOX) {
+      for (const Op& o : c->plain_ops[L0.parity]) {
+        sc_status st = run_op(c, o, c->stream);
+        if (st != SC_OK) return st;
+      }
+    } else {
+      CU(cudaGraphLaunch(c->graph[L0.parity], c->stream));
+    }
     L0.parity ^= 1;
     c->t += L0.dt;
     for (int l = 0; l < L; ++l) {

@@ -1,0 +1,287 @@
+// sc_server.cu -- continuous batching of independent subcycled evolutions.
+//
+// A request is one complete hierarchy (wave or Z4c) with analytic initial data
+// and a number of coarse steps.  The server keeps a FIFO queue and a set of
+// slots, one CUDA stream each.  Every tick it
+//   1. retires requests whose last coarse step has completed on the device
+//      (their state stays resident until the client releases it),
+//   2. admits queued requests, in arrival order, while a slot is free and the
+//      request's exact device footprint fits the memory budget left,
+//   3. launches the next coarse step (one CUDA graph) of every active request
+//      that has fewer than `depth` steps in flight, on the request's stream.
+// Requests of different sizes therefore run concurrently and their kernels
+// overlap on the GPU; each request's arithmetic is exactly what it would be
+// alone (same kernels, same order), so its result does not depend on the mix.
+// Device memory of requests comes from a stream-ordered pool
+// (cudaMallocAsync on the request's stream), so admission and release never
+// synchronise the whole device.
+#include <chrono>
+#include <deque>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "sc_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct PoolUser {
+  cudaStream_t stream;
+};
+
+void* pool_alloc(size_t bytes, void* user) {
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, static_cast<PoolUser*>(user)->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void pool_free(void* p, void* user) { cudaFreeAsync(p, static_cast<PoolUser*>(user)->stream); }
+
+struct Request {
+  unsigned long long ticket = 0;
+  // deep copy of the descriptor
+  sc_desc desc{};
+  std::vector<int> nboxes;
+  std::vector<sc_box> boxes;
+  int id_kind = 0;
+  std::vector<double> id_params;
+  int steps = 0;
+  size_t footprint = 0;
+  // state
+  int slot = -1;
+  sc_ctx* ctx = nullptr;
+  std::unique_ptr<PoolUser> pool;
+  sc_allocator alloc{};
+  int launched = 0;
+  int completed = 0;
+  std::deque<cudaEvent_t> inflight;
+  bool done = false;
+  Clock::time_point t_submit, t_admit, t_done;
+  double zu_finest = 0, zu_actual = 0;
+};
+
+sc_status err(sc_status code, const char* msg) { return sc::set_last_error(code, msg); }
+
+}  // namespace
+
+struct sc_server {
+  size_t budget = 0;
+  size_t in_use = 0;
+  int depth = 2;
+  std::vector<cudaStream_t> streams;
+  std::vector<bool> slot_busy;
+  std::deque<Request*> queue;
+  std::map<unsigned long long, std::unique_ptr<Request>> all;
+  unsigned long long next_ticket = 1;
+  long launches = 0;
+  double zu_finest_done = 0, zu_actual_done = 0;
+};
+
+namespace {
+
+sc_status admit(sc_server* S, Request* r, int slot) {
+  r->slot = slot;
+  r->pool.reset(new PoolUser{S->streams[slot]});
+  r->alloc.alloc = pool_alloc;
+  r->alloc.free = pool_free;
+  r->alloc.user = r->pool.get();
+  r->desc.nboxes = r->nboxes.data();
+  r->desc.boxes = r->boxes.data();
+  r->desc.cuda_stream = S->streams[slot];
+  r->desc.allocator = &r->alloc;
+  sc_status st = sc_create(&r->desc, &r->ctx);
+  if (st != SC_OK) return st;
+  st = sc_set_initial_data(r->ctx, r->id_kind, r->id_params.empty() ? nullptr : r->id_params.data(),
+                           (int)r->id_params.size());
+  if (st != SC_OK) return st;
+  S->slot_busy[slot] = true;
+  S->in_use += r->footprint;
+  r->t_admit = Clock::now();
+  return SC_OK;
+}
+
+void finish(sc_server* S, Request* r) {
+  r->done = true;
+  r->t_done = Clock::now();
+  S->slot_busy[r->slot] = false;  // the slot's stream is idle; the state stays resident until release
+  double f = 0, a = 0;
+  sc_zone_updates(r->ctx, &f, &a);
+  r->zu_finest = f;
+  r->zu_actual = a;
+  S->zu_finest_done += f;
+  S->zu_actual_done += a;
+}
+
+}  // namespace
+
+extern "C" {
+
+sc_status sc_server_create(size_t hbm_budget_bytes, int max_active, int depth, sc_server** out) {
+  if (!out || max_active < 1 || max_active > 256 || depth < 1) return err(SC_EINVAL, "bad server arguments");
+  std::unique_ptr<sc_server> S(new sc_server());
+  S->budget = hbm_budget_bytes;
+  S->depth = depth;
+  S->streams.resize(max_active);
+  S->slot_busy.assign(max_active, false);
+  for (auto& s : S->streams) {
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return err(SC_ECUDA, cudaGetErrorString(e));
+  }
+  *out = S.release();
+  return SC_OK;
+}
+
+sc_status sc_server_submit(sc_server* S, const sc_desc* d, int id_kind, const double* id_params, int nparams,
+                           int n_coarse_steps, unsigned long long* ticket) {
+  if (!S || !d || !ticket || n_coarse_steps < 0 || nparams < 0 || nparams > 8) return err(SC_EINVAL, "bad submit arguments");
+  size_t fp = 0;
+  sc_status st = sc_footprint_estimate(d, &fp);
+  if (st != SC_OK) return st;
+  if (fp > S->budget) return err(SC_EBUSY, "request footprint exceeds the server's memory budget");
+  std::unique_ptr<Request> r(new Request());
+  r->ticket = S->next_ticket++;
+  r->desc = *d;
+  r->nboxes.assign(d->nboxes, d->nboxes + d->nlevels);
+  int nb = 0;
+  for (int l = 0; l < d->nlevels; ++l) nb += d->nboxes[l];
+  r->boxes.assign(d->boxes, d->boxes + nb);
+  r->id_kind = id_kind;
+  if (nparams) r->id_params.assign(id_params, id_params + nparams);
+  r->steps = n_coarse_steps;
+  r->footprint = fp;
+  r->t_submit = Clock::now();
+  *ticket = r->ticket;
+  S->queue.push_back(r.get());
+  S->all[r->ticket] = std::move(r);
+  return SC_OK;
+}
+
+sc_status sc_server_tick(sc_server* S, int* n_active, int* n_queued, int* n_launched) {
+  if (!S) return err(SC_EINVAL, "null server");
+  int launched = 0;
+  // 1. retire completed steps / requests
+  for (auto& kv : S->all) {
+    Request* r = kv.second.get();
+    if (!r->ctx || r->done) continue;
+    while (!r->inflight.empty()) {
+      cudaError_t e = cudaEventQuery(r->inflight.front());
+      if (e == cudaErrorNotReady) break;
+      if (e != cudaSuccess) return err(SC_ECUDA, cudaGetErrorString(e));
+      cudaEventDestroy(r->inflight.front());
+      r->inflight.pop_front();
+      ++r->completed;
+    }
+    if (r->completed == r->steps) finish(S, r);
+  }
+  // 2. admit in arrival order while a slot is free and the footprint fits
+  while (!S->queue.empty()) {
+    Request* r = S->queue.front();
+    if (S->in_use + r->footprint > S->budget) break;
+    int slot = -1;
+    for (size_t q = 0; q < S->slot_busy.size(); ++q)
+      if (!S->slot_busy[q]) {
+        slot = (int)q;
+        break;
+      }
+    if (slot < 0) break;
+    S->queue.pop_front();
+    sc_status st = admit(S, r, slot);
+    if (st != SC_OK) return st;
+    if (r->steps == 0) finish(S, r);
+  }
+  // 3. launch the next coarse step of every active request
+  int active = 0;
+  for (auto& kv : S->all) {
+    Request* r = kv.second.get();
+    if (!r->ctx || r->done) continue;
+    ++active;
+    if (r->launched < r->steps && (int)r->inflight.size() < S->depth) {
+      sc_status st = sc_advance(r->ctx, 1);
+      if (st != SC_OK) return st;
+      cudaEvent_t ev;
+      cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) return err(SC_ECUDA, cudaGetErrorString(e));
+      e = cudaEventRecord(ev, S->streams[r->slot]);
+      if (e != cudaSuccess) return err(SC_ECUDA, cudaGetErrorString(e));
+      r->inflight.push_back(ev);
+      ++r->launched;
+      long per = 0;
+      sc_launches_per_step(r->ctx, &per);
+      S->launches += per;
+      ++launched;
+    }
+  }
+  if (n_active) *n_active = active;
+  if (n_queued) *n_queued = (int)S->queue.size();
+  if (n_launched) *n_launched = launched;
+  return SC_OK;
+}
+
+sc_status sc_server_poll(sc_server* S, unsigned long long ticket, int* done, double* latency_s) {
+  if (!S || !done) return err(SC_EINVAL, "bad poll arguments");
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) return err(SC_EINVAL, "unknown ticket");
+  Request* r = it->second.get();
+  *done = r->done ? 1 : 0;
+  if (latency_s) *latency_s = r->done ? std::chrono::duration<double>(r->t_done - r->t_submit).count() : -1.0;
+  return SC_OK;
+}
+
+sc_status sc_server_read(sc_server* S, unsigned long long ticket, int level, int box, int field, double* host_dst) {
+  if (!S) return err(SC_EINVAL, "null server");
+  auto it = S->all.find(ticket);
+  if (it == S->all.end() || !it->second->done) return err(SC_EINVAL, "unknown or unfinished ticket");
+  return sc_get_field(it->second->ctx, level, box, field, host_dst);
+}
+
+sc_status sc_server_release(sc_server* S, unsigned long long ticket) {
+  if (!S) return err(SC_EINVAL, "null server");
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) return err(SC_EINVAL, "unknown ticket");
+  Request* r = it->second.get();
+  if (r->ctx && !r->done) return err(SC_EINVAL, "request still running");
+  if (r->ctx) {
+    sc_destroy(r->ctx);
+    S->in_use -= r->footprint;
+  } else {
+    for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+      if (*q == r) {
+        S->queue.erase(q);
+        break;
+      }
+  }
+  S->all.erase(it);
+  return SC_OK;
+}
+
+sc_status sc_server_stats(sc_server* S, double* zu_finest_done, double* zu_actual_done, long* launches,
+                          size_t* bytes_in_use) {
+  if (!S) return err(SC_EINVAL, "null server");
+  if (zu_finest_done) *zu_finest_done = S->zu_finest_done;
+  if (zu_actual_done) *zu_actual_done = S->zu_actual_done;
+  if (launches) *launches = S->launches;
+  if (bytes_in_use) *bytes_in_use = S->in_use;
+  return SC_OK;
+}
+
+sc_status sc_server_destroy(sc_server* S) {
+  if (!S) return SC_OK;
+  for (auto& s : S->streams) cudaStreamSynchronize(s);
+  for (auto& kv : S->all) {
+    Request* r = kv.second.get();
+    for (auto ev : r->inflight) cudaEventDestroy(ev);
+    if (r->ctx) sc_destroy(r->ctx);
+  }
+  S->all.clear();
+  for (auto& s : S->streams) cudaStreamDestroy(s);
+  delete S;
+  return SC_OK;
+}
+
+}  // extern "C"

@@ -245,3 +245,34 @@ def initial_fields(h: Hierarchy, level: int, box: int, ghosted: bool = False, no
     out[1] = out[4] = out[6] = 1.0  # conformal metric = delta
     out[18] = psi ** -2      # lapse psi^-2
     return out
+
+
+def serving_requests(n: int = 256, seed: int = 0, burst: bool = False, mean_interarrival: float = 0.0):
+    """Seeded serving ensemble: (arrival time, hierarchy, coarse steps) triples.
+
+    60% scalar-wave 2-level runs (coarse n^3 with n in 16..64 step 8, fine box
+    over the central half, integer wave numbers 1-4, 8-64 coarse steps) and 40%
+    Z4c Brill-Lindquist 3-level runs (coarse n^3 with n in 32..48 step 8 over
+    [-8,8]^3, masses 0.3-0.7, separation 2-6 on the z axis, 16 coarse steps).
+    Arrivals: all at t = 0 (burst) or Poisson with the given mean interarrival."""
+    rng = np.random.default_rng(20_000 + seed)
+    out = []
+    t = 0.0
+    for _ in range(n):
+        if not burst and mean_interarrival > 0:
+            t += rng.exponential(mean_interarrival)
+        if rng.random() < 0.6:
+            nb = int(rng.choice(np.arange(16, 65, 8)))
+            k = [float(v) for v in rng.integers(1, 5, size=3)]
+            h = standing_wave_2level(nb)
+            h.id_params = [1.0] + k
+            h.name = f"wave 2-level {nb}^3 k={k}"
+            steps = int(rng.integers(8, 65))
+        else:
+            nb = int(rng.choice([32, 40, 48]))
+            m1, m2 = rng.uniform(0.3, 0.7, size=2)
+            sep = float(rng.uniform(2.0, 6.0))
+            h = bl_3level(nb, float(m1), float(m2), sep)
+            steps = 16
+        out.append((0.0 if burst else t, h, steps))
+    return out
