@@ -147,6 +147,9 @@ struct Level {
   Tile* tiles = nullptr;
   int ntiles = 0;
   std::vector<int> box_tile_begin;  // tiles of box b: [box_tile_begin[b], box_tile_begin[b + 1])
+  Tile* ptiles = nullptr;           // 32 x 4 x 1 tiles for the pointwise Z4c kernel (one cell per thread)
+  int nptiles = 0;
+  std::vector<int> box_ptile_begin;
   AmrCell* amr = nullptr;
   int namr = 0;
   AmrBlock* blocks = nullptr;
@@ -284,6 +287,7 @@ sc_status validate(const sc_desc* d) {
 // Build geometry, classification and work lists of every level (host side).
 struct HostLists {
   std::vector<Tile> tiles;
+  std::vector<Tile> ptiles;
   std::vector<AmrCell> amr;
   std::vector<int> amr_gi, amr_gw;  // unwrapped / wrapped global fine index per AMR cell
   std::vector<AmrBlock> blocks;     // 4x4x4 fine blocks served by the separable kernel
@@ -525,6 +529,23 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
         }
   }
   L.box_tile_begin.push_back((int)hl.tiles.size());
+  L.box_ptile_begin.clear();
+  for (const sc_box& B : L.boxes) {
+    L.box_ptile_begin.push_back((int)hl.ptiles.size());
+    for (int z = B.lo[2]; z <= B.hi[2]; ++z)
+      for (int y = B.lo[1]; y <= B.hi[1]; y += 4)
+        for (int x = B.lo[0]; x <= B.hi[0]; x += 32) {
+          Tile t;
+          t.x0 = x - g.org[0];
+          t.y0 = y - g.org[1];
+          t.z0 = z - g.org[2];
+          t.nx = std::min(32, B.hi[0] - x + 1);
+          t.ny = std::min(4, B.hi[1] - y + 1);
+          t.nz = 1;
+          hl.ptiles.push_back(t);
+        }
+  }
+  L.box_ptile_begin.push_back((int)hl.ptiles.size());
   // rows where the Z4c evolution stores D_x (interior cells and their 2-cell
   // extension in y or z) and D_y (extension in z) of the Hessian fields
   if (c->system == SC_Z4C) {
@@ -697,8 +718,10 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
         if (c->system == SC_WAVE) {
           CU(launch_wave_stage(a, L.tiles + t0, nt, s));
         } else {
+          const int p0 = nparts == 1 ? 0 : L.box_ptile_begin[b];
+          const int np = nparts == 1 ? L.nptiles : L.box_ptile_begin[b + 1] - p0;
           CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles + t0, nt, s));
-          CU(launch_z4c_stage(a, c->scratch, c->zp, L.tiles + t0, nt, s));
+          CU(launch_z4c_stage(a, c->scratch, c->zp, L.ptiles + p0, np, s));
         }
       }
       if (L.nphys) CU(launch_radiative_stage(a, L.phys, L.nphys, c->F, g, c->system, s));
@@ -887,6 +910,7 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
   if (st) return st;
   int dev = 0;
   CU(cudaGetDevice(&dev));
+  CU(z4c_init_launch_config());
   std::unique_ptr<sc_ctx> c(new sc_ctx());
   c->system = d->system;
   c->F = d->system == SC_WAVE ? kNWave : kNZ4c;
@@ -935,13 +959,14 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
     if ((st = upload(c.get(), hl.tiles, &L.tiles)) || (st = upload(c.get(), hl.amr, &L.amr)) ||
         (st = upload(c.get(), hl.periodic, &L.periodic)) || (st = upload(c.get(), hl.phys, &L.phys)) ||
         (st = upload(c.get(), hl.restr, &L.restr)) || (st = upload(c.get(), hl.blocks, &L.blocks)) ||
-        (st = upload(c.get(), hl.dxy, &L.dxy))) {
+        (st = upload(c.get(), hl.dxy, &L.dxy)) || (st = upload(c.get(), hl.ptiles, &L.ptiles))) {
       c->release();
       return st;
     }
     L.ntiles = (int)hl.tiles.size();
     L.namr = (int)hl.amr.size();
     L.nblocks = (int)hl.blocks.size();
+    L.nptiles = (int)hl.ptiles.size();
     L.ndxy = (int)hl.dxy.size();
     L.namr_blocked = hl.namr_blocked;
     L.nperiodic = (int)hl.periodic.size();
@@ -1159,7 +1184,7 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   }
   CU(cudaEventRecord(e[1], c->stream));
   if (c->system == SC_Z4C)
-    for (int r = 0; r < nrep; ++r) CU(launch_z4c_stage(a, c->scratch, c->zp, L.tiles, L.ntiles, c->stream));
+    for (int r = 0; r < nrep; ++r) CU(launch_z4c_stage(a, c->scratch, c->zp, L.ptiles, L.nptiles, c->stream));
   CU(cudaEventRecord(e[2], c->stream));
   CU(cudaEventSynchronize(e[2]));
   CU(cudaEventElapsedTime(&t0, e[0], e[1]));

@@ -110,6 +110,9 @@ cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles,
 
 cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy, int sz, double h,
                               const Tile* tiles, int ntiles, cudaStream_t s);
+// Occupancy-derived persistent grid sizes of the Z4c kernels (once per device,
+// before any graph capture).
+cudaError_t z4c_init_launch_config();
 cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, double h, const RowSeg* segs, int nsegs,
                            cudaStream_t s);
 cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz, double h,
