@@ -36,15 +36,18 @@ UNIT = "zone-updates/s (finest-equivalent)"
 # FP64 peak derived from the unit counts and clocks: 152 SMs x 2070 MHz x
 # 2 DFMA lanes per SM per clock x 2 flops per DFMA.
 FP64_PEAK_GFLOPS = 152 * 2.070 * 2 * 2
-# FP64 flops per interior cell of each Z4c kernel in this formulation, from
-# the kernels' executed FP64 instructions (dadd + dmul + 2 dfma) counted by ncu
-# (profiles/z4c_kernels_bl3level64_ncu.md).
-FLOPS_PER_CELL = {"z4c_derivs": None, "z4c_stage": 1977.0}
+# Algorithmic FP64 flops per interior cell of each Z4c pass in this
+# formulation: adds, multiplies and fused multiply-adds (2 flops) counted by
+# ncu on the kernels before their additions were re-expressed as FMAs with a
+# unit multiplier (that rewrite changes the instruction, not the arithmetic).
+# z4c_derivs = row-segment D_x/D_y pass (133) + per-cell pass (1047);
+# profiles/z4c_kernels_bl3level64_ncu.md.
+FLOPS_PER_CELL = {"z4c_derivs": 1180.0, "z4c_stage": 1971.0}
 # DRAM bytes (read + write) per interior cell of each kernel from the same
 # ncu capture (262,144-cell launch), scaled to a launch by its cell count;
 # None once the kernel has changed since the counters were taken.
 DRAM_BYTES_PER_CELL = {"z4c_derivs": None,
-                       "z4c_stage": (442.189568e6 + 92.051200e6) / 262144}
+                       "z4c_stage": (443.535616e6 + 90.504448e6) / 262144}
 # Kernel with the largest share of a coarse step in the ncu launch list
 # (profiles/z4c_bl_7level_launch_list.md).
 DOMINANT = "z4c_stage"
@@ -130,6 +133,22 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def max_over_ranks(dist, x: float, device: str) -> float:
+    """Max of a per-rank float over all ranks (identity without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_step_per_rank: float, steps: int, t_max_ms: float) -> float:
+    """Units processed by all ranks / the slowest rank's time (weak scaling:
+    every replica does the same work)."""
+    return world * units_per_step_per_rank * steps / (t_max_ms * 1e-3)
 
 
 def run_ensemble(sc, W, n: int, seed: int, burst: bool, mean_interarrival: float, served: bool,
@@ -228,6 +247,7 @@ def run_gpu(args, rank: int, world: int):
     h = W.bl_7level()
     fin_per_step, act_per_step = h.zone_updates_per_coarse_step()
     ctx = sc.Context(h)
+    tile, _tune_ms = ctx.sc_autotune()
     ctx.sc_set_initial_data(h.id_kind, h.id_params)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -251,13 +271,9 @@ def run_gpu(args, rank: int, world: int):
     barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(dist, ms, "cuda")
     ms_per_step = t_max / args.steps
-    value = world * fin_per_step * args.steps / (t_max * 1e-3)
+    value = whole_job_rate(world, fin_per_step, args.steps, t_max)
     launches = ctx.sc_launches_per_step() * args.steps
 
     # Roofline of the dominant kernels: FP64-ALU bound.  Per-launch durations
@@ -309,12 +325,8 @@ def run_gpu(args, rank: int, world: int):
             o.numpy()[...] = ctx.sc_get_field(l, b, f)
     torch.cuda.synchronize()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * fin_per_step * ne2e / e2e_s
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
+    e2e_value = whole_job_rate(world, fin_per_step, ne2e, e2e_s * 1e3)
 
     # Served form vs plain per-box form on a seeded ensemble (configs[4] mix).
     serving = None
@@ -349,6 +361,7 @@ def run_gpu(args, rank: int, world: int):
                            "actual_zone_updates_per_step": act_per_step,
                            "actual_zone_updates_per_s": world * act_per_step / (ms_per_step * 1e-3),
                            "l2": "state ~5 GB per replica > 129 MB L2: inputs larger than L2, no flush",
+                           "stencil_tile": list(tile),
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -103,6 +103,7 @@ typedef struct {
   int exec_mode;  /* SC_EXEC_GRAPH (0, default): one CUDA graph per coarse step, one launch per
                      level and phase covering all boxes; SC_EXEC_PER_BOX (1): the plain form, stage
                      kernels launched box by box directly on the stream, no graph (for comparison) */
+  int autotune;   /* 1: run sc_autotune at creation (cached per system and level shapes) */
 } sc_desc;
 
 enum { SC_EXEC_GRAPH = 0, SC_EXEC_PER_BOX = 1 };
@@ -198,6 +199,15 @@ sc_status sc_time_stage_kernels(sc_ctx* ctx, int level, int nrep, double* ms);
  * library routine is called. */
 sc_status sc_z4c_constraints_noalloc(const double* dev_state, double* dev_out, const int* n, double h,
                                      void* cuda_stream);
+
+/* Autotuner: time candidate tile shapes of the stencil kernel (Z4c
+ * derivative pass, or the fused wave stage) on the context's largest level
+ * with CUDA events on its stream, keep the fastest, rebuild the tile lists
+ * and the coarse-step graphs.  The choice is cached for the process per
+ * (system, box shapes of every level); a cached context skips the timing
+ * (*ms_out = -1).  Overwrites only stage/scratch buffers that every coarse
+ * step recomputes; call between sc_advance calls.  tile_out: 3 ints or NULL. */
+sc_status sc_autotune(sc_ctx* ctx, int* tile_out, double* ms_out);
 
 /* ---- serving: continuous batching of independent evolutions ---------------
  * A server owns max_active slots (one CUDA stream each) and a device-memory

@@ -69,6 +69,7 @@ class sc_desc(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p),
         ("allocator", ctypes.POINTER(sc_allocator)),
         ("exec_mode", ctypes.c_int),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -108,6 +109,7 @@ def lib():
     L.sc_footprint.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
     L.sc_footprint_estimate.argtypes = [ctypes.POINTER(sc_desc), ctypes.POINTER(ctypes.c_size_t)]
     L.sc_time_stage_kernels.argtypes = [P, I, I, DP]
+    L.sc_autotune.argtypes = [P, ctypes.POINTER(ctypes.c_int), DP]
     L.sc_z4c_constraints_noalloc.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), D, P]
     IP = ctypes.POINTER(ctypes.c_int)
     U64 = ctypes.c_ulonglong
@@ -295,6 +297,12 @@ class Context:
         n = ctypes.c_size_t()
         _check(lib().sc_footprint(self.ctx, ctypes.byref(n)))
         return n.value
+
+    def sc_autotune(self) -> Tuple[Tuple[int, int, int], float]:
+        t = (ctypes.c_int * 3)()
+        ms = ctypes.c_double()
+        _check(lib().sc_autotune(self.ctx, t, ctypes.byref(ms)))
+        return (t[0], t[1], t[2]), ms.value
 
     def sc_time_stage_kernels(self, level: int, nrep: int = 5) -> Tuple[float, float]:
         ms = np.zeros(2)

@@ -17,7 +17,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -205,6 +208,7 @@ struct sc_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   long launches_per_step = 0;
   int exec_mode = SC_EXEC_GRAPH;
+  int tile[3] = {32, 4, 2};  // stencil-kernel tile shape (autotuned on request)
   std::vector<Op> plain_ops[2];  // per-box form: the schedule, run directly
 
   void* dalloc(size_t bytes) {
@@ -430,6 +434,30 @@ void group_amr_blocks(sc_ctx* c, int l, HostLists& hl) {
   hl.blocks.swap(blocks);
 }
 
+// Interior tiles of the stencil kernels: per box, tiles of shape tile[0..2]
+// clipped to the box (ragged tiles at the high ends).
+void build_stencil_tiles(Level& L, const int* tile, std::vector<Tile>& out) {
+  const Geom& g = L.g;
+  out.clear();
+  L.box_tile_begin.clear();
+  for (const sc_box& B : L.boxes) {
+    L.box_tile_begin.push_back((int)out.size());
+    for (int z = B.lo[2]; z <= B.hi[2]; z += tile[2])
+      for (int y = B.lo[1]; y <= B.hi[1]; y += tile[1])
+        for (int x = B.lo[0]; x <= B.hi[0]; x += tile[0]) {
+          Tile t;
+          t.x0 = x - g.org[0];
+          t.y0 = y - g.org[1];
+          t.z0 = z - g.org[2];
+          t.nx = std::min(tile[0], B.hi[0] - x + 1);
+          t.ny = std::min(tile[1], B.hi[1] - y + 1);
+          t.nz = std::min(tile[2], B.hi[2] - z + 1);
+          out.push_back(t);
+        }
+  }
+  L.box_tile_begin.push_back((int)out.size());
+}
+
 sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
   Level& L = c->lev[l];
   const Geom& g = L.g;
@@ -511,24 +539,7 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
         }
       }
   if (l > 0 && !hl.amr.empty()) group_amr_blocks(c, l, hl);
-  // interior tiles: per box, x tiles of 32 (or the box width), 4 x 2 in y, z
-  L.box_tile_begin.clear();
-  for (const sc_box& B : L.boxes) {
-    L.box_tile_begin.push_back((int)hl.tiles.size());
-    for (int z = B.lo[2]; z <= B.hi[2]; z += 2)
-      for (int y = B.lo[1]; y <= B.hi[1]; y += 4)
-        for (int x = B.lo[0]; x <= B.hi[0]; x += 32) {
-          Tile t;
-          t.x0 = x - g.org[0];
-          t.y0 = y - g.org[1];
-          t.z0 = z - g.org[2];
-          t.nx = std::min(32, B.hi[0] - x + 1);
-          t.ny = std::min(4, B.hi[1] - y + 1);
-          t.nz = std::min(2, B.hi[2] - z + 1);
-          hl.tiles.push_back(t);
-        }
-  }
-  L.box_tile_begin.push_back((int)hl.tiles.size());
+  build_stencil_tiles(L, c->tile, hl.tiles);
   L.box_ptile_begin.clear();
   for (const sc_box& B : L.boxes) {
     L.box_ptile_begin.push_back((int)hl.ptiles.size());
@@ -856,6 +867,136 @@ sc_status copy_field(sc_ctx* c, int level, int box, int field, bool ghosted, con
 
 sc_status sc::set_last_error(sc_status code, const char* msg) { return fail(code, "%s", msg); }
 
+
+// ---------------------------------------------------------------------------
+// Autotuner: tile shape of the stencil kernels.
+
+namespace {
+
+std::mutex g_tune_mutex;
+std::map<std::string, std::array<int, 3>> g_tune_cache;
+
+std::string tune_key(const sc_ctx* c) {
+  std::string k = std::to_string(c->system);
+  for (const Level& L : c->lev) {
+    std::vector<std::array<int, 3>> ext;
+    for (const sc_box& B : L.boxes) ext.push_back({B.hi[0] - B.lo[0] + 1, B.hi[1] - B.lo[1] + 1, B.hi[2] - B.lo[2] + 1});
+    std::sort(ext.begin(), ext.end());
+    k += "|";
+    for (auto& e : ext) k += std::to_string(e[0]) + "x" + std::to_string(e[1]) + "x" + std::to_string(e[2]) + ",";
+  }
+  return k;
+}
+
+// Time the stencil kernel of one level with the given tiles (device array).
+sc_status time_stencil(sc_ctx* c, Level& L, const Tile* tiles, int ntiles, int reps, double* ms) {
+  const Geom& g = L.g;
+  StageArgs a{};
+  a.Y = L.A;
+  a.yn = L.S[L.parity];
+  a.k = L.K[1];
+  a.out = L.B;
+  a.k1 = L.K[0];
+  a.k2 = L.K[1];
+  a.k3 = L.K[2];
+  a.cdt = 0.5 * L.dt;
+  a.stage = 2;
+  a.fs = g.fs;
+  a.sy = g.pitch;
+  a.sz = g.pitch * g.ext[1];
+  a.h = g.h;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  for (int r = -1; r < reps; ++r) {  // one untimed launch first
+    if (r == 0) CU(cudaEventRecord(e0, c->stream));
+    if (c->system == SC_WAVE) CU(launch_wave_stage(a, tiles, ntiles, c->stream));
+    else CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, tiles, ntiles, c->stream));
+  }
+  CU(cudaEventRecord(e1, c->stream));
+  CU(cudaEventSynchronize(e1));
+  float t = 0;
+  CU(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t / reps;
+  return SC_OK;
+}
+
+sc_status apply_tile_shape(sc_ctx* c, const int* shape) {
+  for (int q = 0; q < 3; ++q) c->tile[q] = shape[q];
+  for (Level& L : c->lev) {
+    std::vector<Tile> t;
+    build_stencil_tiles(L, c->tile, t);
+    Tile* d = nullptr;
+    sc_status st = upload(c, t, &d);
+    if (st) return st;
+    L.tiles = d;
+    L.ntiles = (int)t.size();
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  for (int p = 0; p < 2; ++p)
+    if (c->graph[p]) {
+      cudaGraphExecDestroy(c->graph[p]);
+      c->graph[p] = nullptr;
+    }
+  return build_graphs(c);
+}
+
+}  // namespace
+
+extern "C" sc_status sc_autotune(sc_ctx* c, int* tile_out, double* ms_out) {
+  if (!c) return fail(SC_EINVAL, "null context");
+  const std::string key = tune_key(c);
+  std::array<int, 3> best{c->tile[0], c->tile[1], c->tile[2]};
+  double best_ms = -1.0;
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      best = it->second;
+      cached = true;
+    }
+  }
+  if (!cached) {
+    int big = 0;
+    for (int l = 1; l < c->nlev; ++l)
+      if (c->lev[l].interior_cells > c->lev[big].interior_cells) big = l;
+    Level& L = c->lev[big];
+    static const int cand[][3] = {{32, 4, 2}, {32, 2, 4}, {32, 8, 1}, {32, 4, 4}, {32, 2, 2},
+                                  {16, 8, 2}, {64, 2, 2}, {32, 1, 8}, {16, 4, 4}, {64, 4, 1}};
+    std::vector<Tile> t;
+    Tile* d = nullptr;
+    size_t cap = 0;
+    for (const auto& cd : cand) {
+      build_stencil_tiles(L, cd, t);
+      if (t.size() > cap) {
+        cap = t.size() * 2;
+        d = (Tile*)c->dalloc(cap * sizeof(Tile));
+        if (!d) return fail(SC_ENOMEM, "autotune tile buffer");
+      }
+      CU(cudaMemcpyAsync(d, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
+      double ms = 0;
+      sc_status st = time_stencil(c, L, d, (int)t.size(), 3, &ms);
+      if (st) return st;
+      if (best_ms < 0 || ms < best_ms) {
+        best_ms = ms;
+        best = {cd[0], cd[1], cd[2]};
+      }
+    }
+    // restore the level's box ranges for the current shape before rebuilding
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = best;
+  }
+  sc_status st = apply_tile_shape(c, best.data());
+  if (st) return st;
+  if (tile_out)
+    for (int q = 0; q < 3; ++q) tile_out[q] = best[q];
+  if (ms_out) *ms_out = best_ms;
+  return SC_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 
@@ -1002,6 +1143,7 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
   }
   for (Level& L : c->lev) L.kind.clear(), L.kind.shrink_to_fit();
   st = build_graphs(c.get());
+  if (st == SC_OK && d->autotune) st = sc_autotune(c.get(), nullptr, nullptr);
   if (st) {
     c->release();
     return st;

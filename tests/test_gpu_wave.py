@@ -131,3 +131,22 @@ def test_nesting_violation_rejected(sc):
     with pytest.raises(sc.SubcycError) as e:
         sc.Context(h)
     assert e.value.code == sc.SC_ENESTING
+
+
+def test_autotune_keeps_results_bitwise(sc):
+    """The autotuner changes only the tiling; every cell's arithmetic and so
+    the fields are bitwise those of the default tiles."""
+    h = W.gaussian_3level(64, 0)
+    out = []
+    for tune in (False, True):
+        c = sc.Context(h)
+        if tune:
+            tile, _ms = c.sc_autotune()
+            assert len(tile) == 3 and all(t > 0 for t in tile)
+        c.sc_set_initial_data(h.id_kind, h.id_params)
+        c.sc_advance(3)
+        out.append(fetch(c, h))
+        c.close()
+    for la, lb in zip(*out):
+        for a, b in zip(la, lb):
+            assert np.array_equal(a, b)
