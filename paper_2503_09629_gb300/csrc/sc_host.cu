@@ -964,8 +964,8 @@ extern "C" sc_status sc_autotune(sc_ctx* c, int* tile_out, double* ms_out) {
     for (int l = 1; l < c->nlev; ++l)
       if (c->lev[l].interior_cells > c->lev[big].interior_cells) big = l;
     Level& L = c->lev[big];
-    static const int cand[][3] = {{32, 4, 2}, {32, 2, 4}, {32, 8, 1}, {32, 4, 4}, {32, 2, 2},
-                                  {16, 8, 2}, {64, 2, 2}, {32, 1, 8}, {16, 4, 4}, {64, 4, 1}};
+    static const int cand[][3] = {{32, 4, 2}, {32, 2, 4}, {32, 1, 8}, {32, 4, 4}, {32, 2, 8}, {32, 1, 16},
+                                  {16, 4, 8}, {64, 1, 8}, {16, 2, 16}, {32, 1, 32}};
     std::vector<Tile> t;
     Tile* d = nullptr;
     size_t cap = 0;

@@ -145,54 +145,99 @@ __global__ void __launch_bounds__(128) z4c_dxy_kernel(const double* __restrict__
   }
 }
 
-__global__ void __launch_bounds__(kThreads) z4c_derivs_split_kernel(const double* __restrict__ Y,
+__global__ void __launch_bounds__(kThreads, 2) z4c_derivs_split_kernel(const double* __restrict__ Y,
                                                                    double* __restrict__ S, long fs, int sy_, int sz_,
                                                                    double h, const Tile* __restrict__ tiles,
                                                                    int ntiles, FmaK K) {
+  // One thread per (x, y, field) column of a tile, walking z with sliding
+  // windows: u at z-3..z+3 and, for the Hessian fields, the stored D_x, D_y
+  // at z-2..z+2, so each step loads one new z value per window.
   const double i12h = 1.0 / (12.0 * h);
   const double i12h2 = 1.0 / (12.0 * h * h);
-  const long st[3] = {1, (long)sy_, (long)sz_};
+  const long sy = sy_, sz = sz_;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile T = tiles[t];
-    const int n = T.nx * T.ny * T.nz;
-    for (int q = threadIdx.x; q < n * kNZ4c; q += blockDim.x) {
-      const int f = q / n;
-      const int c = q - f * n;
+    const int ncol = T.nx * T.ny;
+    for (int q = threadIdx.x; q < ncol * kNZ4c; q += blockDim.x) {
+      const int f = q / ncol;
+      const int c = q - f * ncol;
       const int i = c % T.nx;
-      const int j = (c / T.nx) % T.ny;
-      const int k = c / (T.nx * T.ny);
-      const long o = (T.z0 + k) * st[2] + (T.y0 + j) * st[1] + (T.x0 + i);
-      const double* u = Y + (long)f * fs + o;
-      const double u0 = u[0];
+      const int j = c / T.nx;
+      const long o0 = (long)T.z0 * sz + (T.y0 + j) * sy + (T.x0 + i);
+      const double* u = Y + (long)f * fs + o0;
       const int sl = d2_slot(f);
-      double p1[3], p2[3], p3[3];
+      double w[7];  // u at z-3..z+3
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const long s = st[d];
-        const double a1 = u[-s], b1 = u[s], a2 = u[-2 * s], b2 = u[2 * s];
-        p1[d] = fadd(a1, b1, K);
-        p2[d] = fadd(a2, b2, K);
-        p3[d] = fadd(u[-3 * s], u[3 * s], K);
-        if (sl < 0 || d == 2)
-          S[(long)(Q_D1 + 3 * f + d) * fs + o] = fmul(fma(8.0, fsub(b1, a1, K), fsub(a2, b2, K)), i12h, K);
+      for (int m = 0; m < 7; ++m) w[m] = u[(m - 3) * sz];
+      const double* Dx = S + (long)(Q_D1 + 3 * f + 0) * fs + o0;
+      const double* Dy = S + (long)(Q_D1 + 3 * f + 1) * fs + o0;
+      double wx[5], wy[5];  // D_x, D_y at z-2..z+2 (Hessian fields)
+      if (sl >= 0) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+          wx[m] = Dx[(m - 2) * sz];
+          wy[m] = Dy[(m - 2) * sz];
+        }
       }
-      // Kreiss-Oliger: sum_d (u_-3 - 6 u_-2 + 15 u_-1 - 20 u_0 + 15 u_1 - 6 u_2 + u_3)
-      const double P1 = fadd(fadd(p1[0], p1[1], K), p1[2], K);
-      const double P2 = fadd(fadd(p2[0], p2[1], K), p2[2], K);
-      const double P3 = fadd(fadd(p3[0], p3[1], K), p3[2], K);
-      S[(long)(Q_KO + f) * fs + o] = fma(15.0, P1, fma(-6.0, P2, fma(-60.0, u0, P3)));
-      if (sl < 0) continue;
-      double* d2 = S + (long)(Q_D2 + 6 * sl) * fs + o;
-      // pure: (-u_-2 + 16 u_-1 - 30 u_0 + 16 u_1 - u_2) / (12 h^2)
-      d2[0 * fs] = fmul(fma(-30.0, u0, fma(16.0, p1[0], -p2[0])), i12h2, K);
-      d2[3 * fs] = fmul(fma(-30.0, u0, fma(16.0, p1[1], -p2[1])), i12h2, K);
-      d2[5 * fs] = fmul(fma(-30.0, u0, fma(16.0, p1[2], -p2[2])), i12h2, K);
-      const double* Dx = S + (long)(Q_D1 + 3 * f + 0) * fs + o;
-      const double* Dy = S + (long)(Q_D1 + 3 * f + 1) * fs + o;
-      const long sy = st[1], sz = st[2];
-      d2[1 * fs] = fmul(fma(8.0, fsub(Dx[sy], Dx[-sy], K), fsub(Dx[-2 * sy], Dx[2 * sy], K)), i12h, K);  // D_y D_x
-      d2[2 * fs] = fmul(fma(8.0, fsub(Dx[sz], Dx[-sz], K), fsub(Dx[-2 * sz], Dx[2 * sz], K)), i12h, K);  // D_z D_x
-      d2[4 * fs] = fmul(fma(8.0, fsub(Dy[sz], Dy[-sz], K), fsub(Dy[-2 * sz], Dy[2 * sz], K)), i12h, K);  // D_z D_y
+#pragma unroll 1
+      for (int k = 0; k < T.nz; ++k) {
+        const long o = o0 + k * sz;
+        const double* v = u + k * sz;
+        const double u0 = w[3];
+        double p1[3], p2[3], p3[3];
+        // x and y from memory, z from the window
+        {
+          const double a1 = v[-1], b1 = v[1], a2 = v[-2], b2 = v[2];
+          p1[0] = fadd(a1, b1, K);
+          p2[0] = fadd(a2, b2, K);
+          p3[0] = fadd(v[-3], v[3], K);
+          if (sl < 0) S[(long)(Q_D1 + 3 * f + 0) * fs + o] = fmul(fma(8.0, fsub(b1, a1, K), fsub(a2, b2, K)), i12h, K);
+        }
+        {
+          const double a1 = v[-sy], b1 = v[sy], a2 = v[-2 * sy], b2 = v[2 * sy];
+          p1[1] = fadd(a1, b1, K);
+          p2[1] = fadd(a2, b2, K);
+          p3[1] = fadd(v[-3 * sy], v[3 * sy], K);
+          if (sl < 0) S[(long)(Q_D1 + 3 * f + 1) * fs + o] = fmul(fma(8.0, fsub(b1, a1, K), fsub(a2, b2, K)), i12h, K);
+        }
+        {
+          const double a1 = w[2], b1 = w[4], a2 = w[1], b2 = w[5];
+          p1[2] = fadd(a1, b1, K);
+          p2[2] = fadd(a2, b2, K);
+          p3[2] = fadd(w[0], w[6], K);
+          S[(long)(Q_D1 + 3 * f + 2) * fs + o] = fmul(fma(8.0, fsub(b1, a1, K), fsub(a2, b2, K)), i12h, K);
+        }
+        // Kreiss-Oliger: sum_d (u_-3 - 6 u_-2 + 15 u_-1 - 20 u_0 + 15 u_1 - 6 u_2 + u_3)
+        const double P1 = fadd(fadd(p1[0], p1[1], K), p1[2], K);
+        const double P2 = fadd(fadd(p2[0], p2[1], K), p2[2], K);
+        const double P3 = fadd(fadd(p3[0], p3[1], K), p3[2], K);
+        S[(long)(Q_KO + f) * fs + o] = fma(15.0, P1, fma(-6.0, P2, fma(-60.0, u0, P3)));
+        if (sl >= 0) {
+          double* d2 = S + (long)(Q_D2 + 6 * sl) * fs + o;
+          // pure: (-u_-2 + 16 u_-1 - 30 u_0 + 16 u_1 - u_2) / (12 h^2)
+          d2[0 * fs] = fmul(fma(-30.0, u0, fma(16.0, p1[0], -p2[0])), i12h2, K);
+          d2[3 * fs] = fmul(fma(-30.0, u0, fma(16.0, p1[1], -p2[1])), i12h2, K);
+          d2[5 * fs] = fmul(fma(-30.0, u0, fma(16.0, p1[2], -p2[2])), i12h2, K);
+          const double* dxk = Dx + k * sz;
+          d2[1 * fs] = fmul(fma(8.0, fsub(dxk[sy], dxk[-sy], K), fsub(dxk[-2 * sy], dxk[2 * sy], K)), i12h, K);  // D_y D_x
+          d2[2 * fs] = fmul(fma(8.0, fsub(wx[3], wx[1], K), fsub(wx[0], wx[4], K)), i12h, K);                      // D_z D_x
+          d2[4 * fs] = fmul(fma(8.0, fsub(wy[3], wy[1], K), fsub(wy[0], wy[4], K)), i12h, K);                      // D_z D_y
+        }
+        if (k + 1 < T.nz) {  // slide the windows one cell up in z
+#pragma unroll
+          for (int m = 0; m < 6; ++m) w[m] = w[m + 1];
+          w[6] = v[4 * sz];
+          if (sl >= 0) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              wx[m] = wx[m + 1];
+              wy[m] = wy[m + 1];
+            }
+            wx[4] = Dx[(k + 3) * sz];
+            wy[4] = Dy[(k + 3) * sz];
+          }
+        }
+      }
     }
   }
 }
