@@ -36,6 +36,19 @@ UNIT = "zone-updates/s (finest-equivalent)"
 # FP64 peak derived from the unit counts and clocks: 152 SMs x 2070 MHz x
 # 2 DFMA lanes per SM per clock x 2 flops per DFMA.
 FP64_PEAK_GFLOPS = 152 * 2.070 * 2 * 2
+
+
+def _measured_hbm_gbs() -> float:
+    """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else
+    the profiling recipe's fallback figure (6.8 TB/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+HBM_GBS = _measured_hbm_gbs()
 # Algorithmic FP64 flops per interior cell of each Z4c pass in this
 # formulation: adds, multiplies and fused multiply-adds (2 flops) counted by
 # ncu on the kernels before their additions were re-expressed as FMAs with a
@@ -292,6 +305,21 @@ def run_gpu(args, rank: int, world: int):
         roof[name] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                       "frac": ach * 1e3 / FP64_PEAK_GFLOPS, "traffic": (tb * cells if tb else None),
                       "ms_per_launch": t, "cells_per_launch": cells, "flops_per_cell": fpc}
+    # Refinement-boundary ghost fill on the finest level: the separable
+    # prolongation (FP64: 42 FMAs per fine position of a 4x4x4 block and
+    # vector-field, 2688 FMAs per block and vector-field) and the
+    # dense-output apply (HBM: 5 reads + 1 write per ghost value, plus the
+    # 12-byte cell record per ghost cell).
+    t_pro, t_app, (n_amr, n_blk, n_slow) = ctx.sc_time_ghost_kernels(fin_level, 5)
+    F = 22
+    pro_flops = n_blk * 5 * F * 2688 * 2 + n_slow * 5 * F * 258 * 2
+    app_bytes = n_amr * F * 6 * 8 + n_amr * 12
+    roof["amr_prolong"] = {"bound": "alu", "achieved": pro_flops / (t_pro * 1e-3) / 1e12,
+                           "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                           "frac": pro_flops / (t_pro * 1e-3) / 1e9 / FP64_PEAK_GFLOPS, "ms_per_launch": t_pro,
+                           "ghost_cells": n_amr, "blocks": n_blk, "fallback_cells": n_slow}
+    roof["amr_apply"] = {"bound": "hbm", "achieved": app_bytes / (t_app * 1e-3) / 1e9, "peak": HBM_GBS,
+                         "unit": "GB/s", "frac": app_bytes / (t_app * 1e-3) / 1e9 / HBM_GBS, "ms_per_launch": t_app}
     dominant = DOMINANT
     roofline = dict(roof[dominant])
     roofline["kernel"] = dominant

@@ -234,6 +234,16 @@ sc_status sc_server_stats(sc_server* srv, double* zu_finest_done, double* zu_act
                           size_t* bytes_in_use);
 sc_status sc_server_destroy(sc_server* srv);
 
+/* Time the refinement-boundary kernels of one refined level outside the
+ * graph, with CUDA events on the context's stream, averaged over nrep:
+ * ms[0] = prolongation of the parent's y_n, k1..k4 to the level's ghost cells
+ * (block-separable kernel plus per-cell fallback), ms[1] = one dense-output
+ * ghost fill.  counts[0] = ghost cells, counts[1] = 4x4x4 blocks of the
+ * separable kernel, counts[2] = ghost cells on the per-cell fallback.
+ * Writes only the level's ghost store and second stage buffer; call between
+ * sc_advance calls.  Synchronises. */
+sc_status sc_time_ghost_kernels(sc_ctx* ctx, int level, int nrep, double* ms, long* counts);
+
 const char* sc_last_error(void);
 
 #ifdef __cplusplus

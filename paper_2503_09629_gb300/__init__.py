@@ -110,6 +110,7 @@ def lib():
     L.sc_footprint_estimate.argtypes = [ctypes.POINTER(sc_desc), ctypes.POINTER(ctypes.c_size_t)]
     L.sc_time_stage_kernels.argtypes = [P, I, I, DP]
     L.sc_autotune.argtypes = [P, ctypes.POINTER(ctypes.c_int), DP]
+    L.sc_time_ghost_kernels.argtypes = [P, I, I, DP, ctypes.POINTER(ctypes.c_long)]
     L.sc_z4c_constraints_noalloc.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), D, P]
     IP = ctypes.POINTER(ctypes.c_int)
     U64 = ctypes.c_ulonglong
@@ -303,6 +304,12 @@ class Context:
         ms = ctypes.c_double()
         _check(lib().sc_autotune(self.ctx, t, ctypes.byref(ms)))
         return (t[0], t[1], t[2]), ms.value
+
+    def sc_time_ghost_kernels(self, level: int, nrep: int = 5):
+        ms = np.zeros(2)
+        cnt = (ctypes.c_long * 3)()
+        _check(lib().sc_time_ghost_kernels(self.ctx, level, nrep, _dp(ms), cnt))
+        return float(ms[0]), float(ms[1]), (cnt[0], cnt[1], cnt[2])
 
     def sc_time_stage_kernels(self, level: int, nrep: int = 5) -> Tuple[float, float]:
         ms = np.zeros(2)

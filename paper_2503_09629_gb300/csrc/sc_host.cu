@@ -1337,6 +1337,39 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   return SC_OK;
 }
 
+sc_status sc_time_ghost_kernels(sc_ctx* c, int level, int nrep, double* ms, long* counts) {
+  if (!c || !ms || !counts || nrep < 1) return fail(SC_EINVAL, "bad argument");
+  if (level < 1 || level >= c->nlev) return fail(SC_EINVAL, "level must be a refined level");
+  Level& L = c->lev[level];
+  const Level& P = c->lev[level - 1];
+  const int psy = P.g.pitch, psz = P.g.pitch * P.g.ext[1];
+  double coef[4];
+  fill_coeffs(P.dt, 0.0, 2, coef);
+  cudaEvent_t e[3];
+  for (auto& x : e) CU(cudaEventCreate(&x));
+  CU(cudaEventRecord(e[0], c->stream));
+  for (int r = 0; r < nrep; ++r) {
+    CU(launch_amr_prolong_blocks(P.S[P.parity], P.K[0], P.K[1], P.K[2], P.K[3], P.g.fs, psy, psz, L.blocks, L.nblocks,
+                                 L.namr, L.amr_store, c->F, c->w, c->stream));
+    CU(launch_amr_prolong(P.S[P.parity], P.K[0], P.K[1], P.K[2], P.K[3], P.g.fs, psy, psz, L.amr, L.namr_blocked,
+                          L.namr, L.amr_store, c->F, c->w, c->stream));
+  }
+  CU(cudaEventRecord(e[1], c->stream));
+  for (int r = 0; r < nrep; ++r) CU(launch_amr_apply(L.A, L.g.fs, c->F, L.amr, L.namr, L.amr_store, coef, c->stream));
+  CU(cudaEventRecord(e[2], c->stream));
+  CU(cudaEventSynchronize(e[2]));
+  float t0 = 0, t1 = 0;
+  CU(cudaEventElapsedTime(&t0, e[0], e[1]));
+  CU(cudaEventElapsedTime(&t1, e[1], e[2]));
+  for (auto& x : e) cudaEventDestroy(x);
+  ms[0] = t0 / nrep;
+  ms[1] = t1 / nrep;
+  counts[0] = L.namr;
+  counts[1] = L.nblocks;
+  counts[2] = L.namr - L.namr_blocked;
+  return SC_OK;
+}
+
 sc_status sc_footprint(sc_ctx* c, size_t* bytes) {
   if (!c || !bytes) return fail(SC_EINVAL, "null argument");
   *bytes = c->footprint;
