@@ -234,6 +234,13 @@ sc_status sc_server_stats(sc_server* srv, double* zu_finest_done, double* zu_act
                           size_t* bytes_in_use);
 sc_status sc_server_destroy(sc_server* srv);
 
+/* Read any of a level's internal vectors for one box and field (inspection
+ * and testing): vec 0 = current state, 1 = the other state buffer (after a
+ * step: the state at the start of the level's last step, with the ghost
+ * values its first stage used), 2/3 = stage buffers, 4..7 = k1..k4 of the
+ * level's last step.  ghosted: include 3 ghost cells per side.  Synchronises. */
+sc_status sc_debug_get_vector(sc_ctx* ctx, int level, int box, int vec, int field, int ghosted, double* host_dst);
+
 /* Time the refinement-boundary kernels of one refined level outside the
  * graph, with CUDA events on the context's stream, averaged over nrep:
  * ms[0] = prolongation of the parent's y_n, k1..k4 to the level's ghost cells

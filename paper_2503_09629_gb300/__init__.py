@@ -111,6 +111,7 @@ def lib():
     L.sc_time_stage_kernels.argtypes = [P, I, I, DP]
     L.sc_autotune.argtypes = [P, ctypes.POINTER(ctypes.c_int), DP]
     L.sc_time_ghost_kernels.argtypes = [P, I, I, DP, ctypes.POINTER(ctypes.c_long)]
+    L.sc_debug_get_vector.argtypes = [P, I, I, I, I, I, DP]
     L.sc_z4c_constraints_noalloc.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), D, P]
     IP = ctypes.POINTER(ctypes.c_int)
     U64 = ctypes.c_ulonglong
@@ -304,6 +305,11 @@ class Context:
         ms = ctypes.c_double()
         _check(lib().sc_autotune(self.ctx, t, ctypes.byref(ms)))
         return (t[0], t[1], t[2]), ms.value
+
+    def sc_debug_get_vector(self, level: int, box: int, vec: int, field: int, ghosted: bool = False) -> np.ndarray:
+        a = np.empty(self.shape(level, box, ghosted))
+        _check(lib().sc_debug_get_vector(self.ctx, level, box, vec, field, 1 if ghosted else 0, _dp(a)))
+        return a
 
     def sc_time_ghost_kernels(self, level: int, nrep: int = 5):
         ms = np.zeros(2)

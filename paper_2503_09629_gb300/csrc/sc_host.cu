@@ -1337,6 +1337,22 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   return SC_OK;
 }
 
+sc_status sc_debug_get_vector(sc_ctx* c, int level, int box, int vec, int field, int ghosted, double* dst) {
+  sc_status st = check_box(c, level, box, field);
+  if (st) return st;
+  if (!dst || vec < 0 || vec > 7) return fail(SC_EINVAL, "bad vector or destination");
+  Level& L = c->lev[level];
+  double* src[8] = {L.S[L.parity], L.S[L.parity ^ 1], L.A, L.B, L.K[0], L.K[1], L.K[2], L.K[3]};
+  int lo[3], n[3];
+  box_region(L.boxes[box], ghosted != 0, lo, n);
+  const size_t bytes = sizeof(double) * (size_t)n[0] * n[1] * n[2];
+  if ((st = ensure_staging(c, bytes))) return st;
+  CU(launch_pack(src[vec] + (long)field * L.g.fs, L.g, lo, n, c->staging, c->stream));
+  CU(cudaMemcpyAsync(dst, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return SC_OK;
+}
+
 sc_status sc_time_ghost_kernels(sc_ctx* c, int level, int nrep, double* ms, long* counts) {
   if (!c || !ms || !counts || nrep < 1) return fail(SC_EINVAL, "bad argument");
   if (level < 1 || level >= c->nlev) return fail(SC_EINVAL, "level must be a refined level");

@@ -109,3 +109,40 @@ def test_full_7level_mirror_symmetry(sc):
             assert np.abs(a - m).max() <= 1e-13 * scale, (l, f)
     a0, a1 = ctx.sc_get_field(6, 0, 0), ctx.sc_get_field(6, 1, 0)
     assert np.abs(a0 - a1[::-1]).max() / np.abs(a0).max() <= 1e-12
+
+
+def test_full_7level_sampled_rhs_parity(sc, orc):
+    """Full-size benchmark hierarchy after one coarse step: on sampled 8^3
+    blocks of the finest level (at a puncture, between the punctures, at the
+    refinement boundary, in a corner) and of level 0 (interior, next to the
+    evolved outer shell), the GPU's k1 of the level's last step must equal the
+    oracle's right-hand side evaluated on the same state, cell by cell.
+
+    Tolerance: 1e-10 of the field's largest value in the block, plus the
+    roundoff floor of 4th-order second differences, 1e-12 x (largest state
+    value in the block) / h^2: near the punctures some right-hand sides (Theta,
+    Khat) are small residuals of Ricci terms that are larger by many orders,
+    and the two implementations sum those stencils in different orders."""
+    h = W.bl_7level()
+    ctx = sc.Context(h)
+    ctx.sc_set_initial_data(h.id_kind, h.id_params)
+    ctx.sc_advance(1)
+    samples = [(6, 1, (28, 28, 28)), (6, 1, (28, 28, 12)), (6, 1, (28, 28, 0)), (6, 0, (28, 28, 56)), (6, 0, (0, 0, 0)),
+               (6, 1, (56, 56, 56)), (0, 0, (28, 28, 28)), (0, 0, (0, 28, 28))]
+    cache = {}
+    for level, box, (i0, j0, k0) in samples:
+        if (level, box) not in cache:
+            yn = np.stack([ctx.sc_debug_get_vector(level, box, 1, f, ghosted=True) for f in range(22)])
+            k1 = np.stack([ctx.sc_debug_get_vector(level, box, 4, f, ghosted=False) for f in range(22)])
+            cache[(level, box)] = (yn, k1)
+        yn, k1 = cache[(level, box)]
+        sub = yn[:, k0:k0 + 14, j0:j0 + 14, i0:i0 + 14]
+        hl = h.h0 / 2 ** level
+        o = orc.Oracle(W.Z4C, [[((0, 0, 0), (7, 7, 7))]], (8, 8, 8), (0.0, 0.0, 0.0), hl, bc=2,
+                       kappa1=h.kappa1, kappa2=h.kappa2, eta=h.eta, ko_sigma=h.ko_sigma)
+        ref = o.rhs_box(0, 0, np.ascontiguousarray(sub))[:, 3:-3, 3:-3, 3:-3]
+        got = k1[:, k0:k0 + 8, j0:j0 + 8, i0:i0 + 8]
+        floor = 1e-12 * np.abs(sub).max() / hl ** 2
+        for f in range(22):
+            tol = 1e-10 * np.abs(ref[f]).max() + floor
+            assert np.abs(got[f] - ref[f]).max() <= tol, (level, box, (i0, j0, k0), f)
