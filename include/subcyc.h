@@ -54,9 +54,11 @@ typedef enum { SC_BC_PERIODIC = 0, SC_BC_RADIATIVE = 1 } sc_outer_bc;
  *  SC_ID_BRILL_LINDQUIST z4c: [m1, x1, y1, z1, m2, x2, y2, z2]  psi = 1 + sum m/(2 r),
  *                       W = psi^-2, gt = delta, alpha = psi^-2, rest 0 (Sec. III.B, lapse psi^-2)
  *  SC_ID_MINKOWSKI      z4c: []  flat space
- *  SC_ID_SPHERICAL_GAUSSIAN wave: [A, sigma, t, cx, cy, cz]  Sec. IV.A exact solution */
+ *  SC_ID_SPHERICAL_GAUSSIAN wave: [A, sigma, t, cx, cy, cz]  Sec. IV.A exact solution
+ *  SC_ID_BRILL_LINDQUIST_AVG_LAPSE z4c: as SC_ID_BRILL_LINDQUIST with the averaged lapse of
+ *                       Sec. III.B, alpha = (1 + (1 - s)/(1 + s))/2, s = sum m/(2 r) */
 enum { SC_ID_STANDING_WAVE = 0, SC_ID_GAUSSIAN = 1, SC_ID_BRILL_LINDQUIST = 2, SC_ID_MINKOWSKI = 3,
-       SC_ID_SPHERICAL_GAUSSIAN = 4 };
+       SC_ID_SPHERICAL_GAUSSIAN = 4, SC_ID_BRILL_LINDQUIST_AVG_LAPSE = 5 };
 
 /* A box: inclusive cell indices in its level's index space. */
 typedef struct {
@@ -104,6 +106,9 @@ typedef struct {
                      level and phase covering all boxes; SC_EXEC_PER_BOX (1): the plain form, stage
                      kernels launched box by box directly on the stream, no graph (for comparison) */
   int autotune;   /* 1: run sc_autotune at creation (cached per system and level shapes) */
+  int eta_profile; /* Z4c: 0 = constant eta; 1 = eta(r) = (eta_c - eta_o) exp(-(r/eta_s)^4) + eta_o
+                      with r the coordinate radius (Sec. III.A) */
+  double eta_c, eta_s, eta_o;
 } sc_desc;
 
 enum { SC_EXEC_GRAPH = 0, SC_EXEC_PER_BOX = 1 };

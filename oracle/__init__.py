@@ -7,7 +7,7 @@ shares no code with the CUDA library.
 The oracle follows arXiv:2503.09629 Sec. II: RK4 (Eqs. rk1-rk5) on every level,
 dense output (Eqs. denseoutput1/2) and the Taylor stage formulas (Eqs. Y1-Y4)
 for the refinement-boundary ghost zones, the seven-step subcycling recursion,
-tensor-product cubic prolongation and restriction; Sec. III for the Z4c
+tensor-product quintic prolongation and restriction; Sec. III for the Z4c
 right-hand side, the puncture gauge and Kreiss-Oliger dissipation; Sec. IV.A
 for the scalar wave.  Parity unpinned: the radiative outer boundary (its
 formula is not in the paper), checked only through GPU-vs-oracle agreement.
@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(HERE, "liboracle.so")
 WAVE, Z4C = 0, 1
 BC_PERIODIC, BC_RADIATIVE, BC_CALLBACK = 0, 1, 2
 ID_STANDING_WAVE, ID_GAUSSIAN, ID_BRILL_LINDQUIST, ID_MINKOWSKI, ID_SPHERICAL_GAUSSIAN = 0, 1, 2, 3, 4
+ID_BRILL_LINDQUIST_AVG_LAPSE = 5
 V_Y, V_YOLD, V_STAGE, V_K1 = 0, 1, 2, 3
 GHOST = 3
 
@@ -61,6 +62,7 @@ def lib():
         L.orc_destroy.argtypes = [P]
         L.orc_nfields.argtypes = [P]
         L.orc_set_bc_callback.argtypes = [P, BC_FN, P]
+        L.orc_set_eta_profile.argtypes = [P, D, D, D]
         L.orc_set_initial_data.argtypes = [P, I, DP, I]
         for name in ("orc_set_field", "orc_get_field", "orc_set_field_ghosted", "orc_get_field_ghosted"):
             getattr(L, name).argtypes = [P, I, I, I, DP]
@@ -113,7 +115,7 @@ class Oracle:
     """
 
     def __init__(self, system, boxes, ncells0, origin, h0, bc=BC_PERIODIC, cfl=0.25,
-                 subcycle=True, kappa1=0.02, kappa2=0.0, eta=2.0, ko_sigma=0.3):
+                 subcycle=True, kappa1=0.02, kappa2=0.0, eta=2.0, ko_sigma=0.3, eta_profile=None):
         L = lib()
         self.system = system
         self.boxes = [[(tuple(lo), tuple(hi)) for lo, hi in lvl] for lvl in boxes]
@@ -134,6 +136,9 @@ class Oracle:
         self.h = h
         self.F = L.orc_nfields(h)
         self._cb = None
+        if eta_profile is not None:
+            if L.orc_set_eta_profile(h, *[float(v) for v in eta_profile]) != 0:
+                raise ValueError("bad eta profile")
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -135,6 +135,8 @@ struct Hier {
   double cfl, h0, origin[3];
   int ncells0[3];
   double kappa1, kappa2, eta, sigma;
+  bool eta_profile;                 // Sec. III.A eta(r) instead of the constant eta
+  double eta_c, eta_s, eta_o;
   std::vector<Level> lev;
   double t;
   double zu_finest, zu_actual;
@@ -484,12 +486,21 @@ void z4c_derivs(const BoxData& B, const double* Y, long c, double h, T (*u)[1], 
   }
 }
 
-void z4c_rhs_cell(const Hier& H, const BoxData& B, const double* Y, double* K, int i, int j, int k, double h) {
+// Gamma-driver damping: the constant eta, or the profile of Sec. III.A,
+// eta(r) = (eta_c - eta_o) exp(-(r / eta_s)^4) + eta_o, r the coordinate radius.
+double eta_at(const Hier& H, const double* x) {
+  if (!H.eta_profile) return H.eta;
+  const double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  return (H.eta_c - H.eta_o) * std::exp(-std::pow(r / H.eta_s, 4.0)) + H.eta_o;
+}
+
+void z4c_rhs_cell(const Hier& H, const BoxData& B, const double* Y, double* K, int i, int j, int k, double h,
+                  const double* x) {
   const long c = B.off(i, j, k);
   double u[NZ4C][1], du[NZ4C][3], dd[NZ4C][6], ko[NZ4C], uu[NZ4C], rhs[NZ4C];
   z4c_derivs<double>(B, Y, c, h, u, du, dd, ko);
   for (int f = 0; f < NZ4C; ++f) uu[f] = u[f][0];
-  z4c_point<double>(uu, du, dd, rhs, H.kappa1, H.kappa2, H.eta);
+  z4c_point<double>(uu, du, dd, rhs, H.kappa1, H.kappa2, eta_at(H, x));
   for (int f = 0; f < NZ4C; ++f) K[(long)f * B.vol + c] = rhs[f] + H.sigma / (64.0 * h) * ko[f];
 }
 
@@ -543,8 +554,13 @@ void rhs_box(const Hier& H, int l, const BoxData& B, const double* Y, double* K)
     for (int j = -G; j < B.n[1] + G; ++j)
       for (int i = -G; i < B.n[0] + G; ++i) {
         if (is_interior(B, i, j, k)) {
-          if (H.system == ORC_WAVE) wave_rhs_cell(B, Y, K, i, j, k, h);
-          else z4c_rhs_cell(H, B, Y, K, i, j, k, h);
+          if (H.system == ORC_WAVE) {
+            wave_rhs_cell(B, Y, K, i, j, k, h);
+          } else {
+            double x[3];
+            cell_centre(H, l, B, i, j, k, x);
+            z4c_rhs_cell(H, B, Y, K, i, j, k, h, x);
+          }
         } else if (evolves_shell(H, l)) {
           double x[3];
           cell_centre(H, l, B, i, j, k, x);
@@ -928,6 +944,8 @@ int orc_create(int system, int nlevels, const int* nboxes, const int* boxes, con
   H->zu_finest = H->zu_actual = 0.0;
   H->cb = nullptr;
   H->cb_user = nullptr;
+  H->eta_profile = false;
+  H->eta_c = H->eta_s = H->eta_o = 0.0;
   H->lev.resize(nlevels);
   int bi = 0;
   for (int l = 0; l < nlevels; ++l) {
@@ -969,6 +987,16 @@ int orc_create(int system, int nlevels, const int* nboxes, const int* boxes, con
 
 void orc_destroy(void* h) { delete static_cast<Hier*>(h); }
 int orc_nfields(void* h) { return static_cast<Hier*>(h)->F; }
+
+int orc_set_eta_profile(void* h, double eta_c, double eta_s, double eta_o) {
+  Hier* H = static_cast<Hier*>(h);
+  if (!(eta_s > 0)) return fail(-1, "eta_s must be positive");
+  H->eta_profile = true;
+  H->eta_c = eta_c;
+  H->eta_s = eta_s;
+  H->eta_o = eta_o;
+  return 0;
+}
 
 int orc_set_bc_callback(void* h, orc_bc_fn fn, void* user) {
   Hier* H = static_cast<Hier*>(h);
@@ -1058,21 +1086,25 @@ int orc_set_initial_data(void* h, int kind, const double* p, int np) {
               const double fp = A * std::exp(-(t + r) * (t + r) / (2.0 * sg * sg));
               val[0] = (fm - fp) / r;
               val[1] = -(fm * (t - r) - fp * (t + r)) / (sg * sg * r);
-            } else if ((kind == ORC_ID_BRILL_LINDQUIST && np >= 8) || kind == ORC_ID_MINKOWSKI) {
+            } else if (((kind == ORC_ID_BRILL_LINDQUIST || kind == ORC_ID_BRILL_LINDQUIST_AVG_LAPSE) && np >= 8) ||
+                       kind == ORC_ID_MINKOWSKI) {
               if (H->system != ORC_Z4C) return fail(-1, "initial data needs Z4c");
-              double psi = 1.0;
-              if (kind == ORC_ID_BRILL_LINDQUIST) {
+              double psi = 1.0, s = 0.0;
+              if (kind != ORC_ID_MINKOWSKI) {
                 for (int q = 0; q < 2; ++q) {
                   const double m = p[4 * q], dx = x[0] - p[4 * q + 1], dy = x[1] - p[4 * q + 2],
                                dz = x[2] - p[4 * q + 3];
-                  psi += m / (2.0 * std::sqrt(dx * dx + dy * dy + dz * dz));
+                  s += m / (2.0 * std::sqrt(dx * dx + dy * dy + dz * dz));
                 }
+                psi += s;
               }
               // gamma_ij = psi^4 delta_ij: W = gamma^{-1/6} = psi^-2, gt_ij = delta_ij,
               // K_ij = 0, Theta = 0, Gamt^i = 0, lapse psi^-2, zero shift.
               val[FW] = 1.0 / (psi * psi);
               val[FG + 0] = val[FG + 3] = val[FG + 5] = 1.0;
               val[FAL] = 1.0 / (psi * psi);
+              // Sec. III.B: the averaged initial lapse 1/2 (1 + (1 - s) / (1 + s))
+              if (kind == ORC_ID_BRILL_LINDQUIST_AVG_LAPSE) val[FAL] = 0.5 * (1.0 + (1.0 - s) / (1.0 + s));
             } else {
               return fail(-1, "unknown initial data");
             }

@@ -22,7 +22,7 @@ extern "C" {
 enum { ORC_WAVE = 0, ORC_Z4C = 1 };
 enum { ORC_BC_PERIODIC = 0, ORC_BC_RADIATIVE = 1, ORC_BC_CALLBACK = 2 };
 enum { ORC_ID_STANDING_WAVE = 0, ORC_ID_GAUSSIAN = 1, ORC_ID_BRILL_LINDQUIST = 2,
-       ORC_ID_MINKOWSKI = 3, ORC_ID_SPHERICAL_GAUSSIAN = 4 };
+       ORC_ID_MINKOWSKI = 3, ORC_ID_SPHERICAL_GAUSSIAN = 4, ORC_ID_BRILL_LINDQUIST_AVG_LAPSE = 5 };
 
 /* Physical boundary callback (ORC_BC_CALLBACK, level 0 only): fill out[f*npts+p]
  * with the value the stage state should take at the given cell centres.
@@ -37,6 +37,8 @@ int orc_create(int system, int nlevels, const int* nboxes, const int* boxes,
 void orc_destroy(void* h);
 int orc_nfields(void* h);
 int orc_set_bc_callback(void* h, orc_bc_fn fn, void* user);
+/* Gamma-driver damping eta(r) = (eta_c - eta_o) exp(-(r/eta_s)^4) + eta_o (Sec. III.A). */
+int orc_set_eta_profile(void* h, double eta_c, double eta_s, double eta_o);
 int orc_set_initial_data(void* h, int kind, const double* params, int nparams);
 int orc_set_field(void* h, int level, int box, int field, const double* src);
 int orc_get_field(void* h, int level, int box, int field, double* dst);

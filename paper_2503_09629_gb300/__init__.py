@@ -70,6 +70,10 @@ class sc_desc(ctypes.Structure):
         ("allocator", ctypes.POINTER(sc_allocator)),
         ("exec_mode", ctypes.c_int),
         ("autotune", ctypes.c_int),
+        ("eta_profile", ctypes.c_int),
+        ("eta_c", ctypes.c_double),
+        ("eta_s", ctypes.c_double),
+        ("eta_o", ctypes.c_double),
     ]
 
 
@@ -177,6 +181,10 @@ def make_desc(h, stream: Optional[int] = None, allocator=None, exec_mode: int = 
     d.kappa1, d.kappa2, d.eta, d.ko_sigma = h.kappa1, h.kappa2, h.eta, h.ko_sigma
     d.cuda_stream = stream
     d.exec_mode = exec_mode
+    prof = getattr(h, "eta_profile", None)
+    if prof is not None:
+        d.eta_profile = 1
+        d.eta_c, d.eta_s, d.eta_o = (float(v) for v in prof)
     keep = [nb, boxes]
     if allocator is not None:
         d.allocator = ctypes.pointer(allocator)

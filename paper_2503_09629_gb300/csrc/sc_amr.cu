@@ -225,26 +225,43 @@ __global__ void __launch_bounds__(kThreads) initial_data_kernel(double* __restri
       vec[o] = u;
       vec[g.fs + o] = pi;
     } else {
-      double psi = 1.0;
-      if (kind == SC_ID_BRILL_LINDQUIST) {
+      double s = 0.0;
+      if (kind == SC_ID_BRILL_LINDQUIST || kind == SC_ID_BRILL_LINDQUIST_AVG_LAPSE) {
         for (int q = 0; q < 2; ++q) {
           const double dx = x - p[4 * q + 1], dy = y - p[4 * q + 2], dz = z - p[4 * q + 3];
-          psi += p[4 * q] / (2.0 * sqrt(dx * dx + dy * dy + dz * dz));
+          s += p[4 * q] / (2.0 * sqrt(dx * dx + dy * dy + dz * dz));
         }
       }
+      const double psi = 1.0 + s;
       const double ipsi2 = 1.0 / (psi * psi);
+      // lapse: psi^-2, or the averaged form (1 + (1 - s)/(1 + s))/2 of Sec. III.B
+      const double lapse = kind == SC_ID_BRILL_LINDQUIST_AVG_LAPSE ? 0.5 * (1.0 + (1.0 - s) / (1.0 + s)) : ipsi2;
       for (int f = 0; f < F; ++f) vec[(long)f * g.fs + o] = 0.0;
       vec[(long)ZW * g.fs + o] = ipsi2;
       vec[(long)(ZG + 0) * g.fs + o] = 1.0;
       vec[(long)(ZG + 3) * g.fs + o] = 1.0;
       vec[(long)(ZG + 5) * g.fs + o] = 1.0;
-      vec[(long)ZAL * g.fs + o] = ipsi2;
+      vec[(long)ZAL * g.fs + o] = lapse;
     }
   }
 }
 
 // Copy a box region of one field between a level array and a contiguous
 // x-fastest buffer (unpack = 0: array -> buffer; 1: buffer -> array).
+// Gamma-driver damping profile of Sec. III.A at every element of a level array.
+__global__ void __launch_bounds__(kThreads) eta_profile_kernel(double* __restrict__ eta, Geom g, double ec, double es,
+                                                              double eo) {
+  const long ncell = (long)g.ext[0] * g.ext[1] * g.ext[2];
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < ncell; idx += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % g.ext[0]);
+    const int j = (int)((idx / g.ext[0]) % g.ext[1]);
+    const int k = (int)(idx / ((long)g.ext[0] * g.ext[1]));
+    const double x = g.x0[0] + i * g.h, y = g.x0[1] + j * g.h, z = g.x0[2] + k * g.h;
+    const double q = (x * x + y * y + z * z) / (es * es);  // (r / eta_s)^2
+    eta[((long)k * g.ext[1] + j) * g.pitch + i] = (ec - eo) * exp(-q * q) + eo;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) pack_kernel(double* __restrict__ vec, int pitch, int ey, int i0,
                                                        int j0, int k0, int nx, int ny, int nz,
                                                        double* __restrict__ buf, int unpack) {
@@ -325,6 +342,12 @@ cudaError_t launch_initial_data(double* vec, const Geom& g, int F, int system, i
   for (int i = 0; i < 8; ++i) ip.p[i] = (i < nparams) ? params[i] : 0.0;
   const long n = (long)g.ext[0] * g.ext[1] * g.ext[2];
   initial_data_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(vec, g, F, system, kind, ip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eta_profile(double* eta, const Geom& g, double eta_c, double eta_s, double eta_o, cudaStream_t s) {
+  const long n = (long)g.ext[0] * g.ext[1] * g.ext[2];
+  eta_profile_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(eta, g, eta_c, eta_s, eta_o);
   return cudaGetLastError();
 }
 

@@ -159,6 +159,7 @@ struct Level {
   int nblocks = 0;
   RowSeg* dxy = nullptr;
   int ndxy = 0;
+  double* eta = nullptr;  // per-element eta(r) (Z4c with the Sec. III.A profile), else null
   int namr_blocked = 0;
   double* amr_store = nullptr;  // 5 * F * namr prolonged parent vectors
   int2* periodic = nullptr;
@@ -271,6 +272,7 @@ sc_status validate(const sc_desc* d) {
   for (int q = 0; q < 3; ++q)
     if (d->ncells0[q] < 1) return fail(SC_EINVAL, "ncells0 must be positive");
   if (d->outer_bc == SC_BC_RADIATIVE && d->nboxes[0] != 1) return fail(SC_EINVAL, "radiative boundary needs one level-0 box");
+  if (d->eta_profile && !(d->eta_s > 0)) return fail(SC_EINVAL, "eta_s must be positive");
   int bi = 0;
   for (int l = 0; l < d->nlevels; ++l) {
     if (d->nboxes[l] < 1) return fail(SC_EINVAL, "level %d has no boxes", l);
@@ -720,6 +722,7 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       a.sy = g.pitch;
       a.sz = g.pitch * g.ext[1];
       a.h = g.h;
+      a.eta = L.eta;
       // graph form: one launch over the tiles of all boxes; per-box form: one per box
       const int nparts = c->exec_mode == SC_EXEC_PER_BOX ? (int)L.boxes.size() : 1;
       if (c->system == SC_Z4C) CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, s));
@@ -1027,6 +1030,7 @@ sc_status sc_footprint_estimate(const sc_desc* d, size_t* bytes) {
     const long pitch = ((hi[0] - lo[0] + 1 + 2 * kGhost) + 7) & ~7;
     const long fs = ((pitch * (hi[1] - lo[1] + 1 + 2 * kGhost) * (hi[2] - lo[2] + 1 + 2 * kGhost)) + 31) & ~31L;
     total += 8 * (size_t)F * fs * sizeof(double);                 // S0, S1, A, B, k1..k4
+    if (d->system == SC_Z4C && d->eta_profile) total += (size_t)fs * sizeof(double);
     total += (size_t)ghost_cells * (5 * F * sizeof(double) + 32);  // prolonged vectors + lists
     total += (size_t)fs * 4;                                       // tiles and other lists (bound)
     maxfs = std::max(maxfs, (size_t)fs);
@@ -1121,6 +1125,14 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
       }
     }
     maxfs = std::max(maxfs, L.g.fs);
+    if (c->system == SC_Z4C && d->eta_profile) {
+      L.eta = (double*)c->dalloc(sizeof(double) * (size_t)L.g.fs);
+      if (!L.eta) {
+        c->release();
+        return fail(SC_ENOMEM, "level %d: eta profile allocation failed", l);
+      }
+      CU(launch_eta_profile(L.eta, L.g, d->eta_c, d->eta_s, d->eta_o, c->stream));
+    }
   }
   if (c->system == SC_Z4C) {
     c->scratch_fs = maxfs;
@@ -1165,10 +1177,10 @@ sc_status sc_set_initial_data(sc_ctx* c, int kind, const double* params, int npa
   if (!c) return fail(SC_EINVAL, "null context");
   if (nparams < 0 || nparams > 8 || (nparams > 0 && !params)) return fail(SC_EINVAL, "bad parameters");
   const bool wave_kind = kind == SC_ID_STANDING_WAVE || kind == SC_ID_GAUSSIAN || kind == SC_ID_SPHERICAL_GAUSSIAN;
-  const bool z4c_kind = kind == SC_ID_BRILL_LINDQUIST || kind == SC_ID_MINKOWSKI;
+  const bool z4c_kind = kind == SC_ID_BRILL_LINDQUIST || kind == SC_ID_MINKOWSKI || kind == SC_ID_BRILL_LINDQUIST_AVG_LAPSE;
   if ((c->system == SC_WAVE && !wave_kind) || (c->system == SC_Z4C && !z4c_kind))
     return fail(SC_EINVAL, "initial data kind %d does not match the system", kind);
-  const int need[5] = {4, 5, 8, 0, 6};
+  const int need[6] = {4, 5, 8, 0, 6, 8};
   if (nparams < need[kind]) return fail(SC_EINVAL, "initial data kind %d needs %d parameters", kind, need[kind]);
   for (Level& L : c->lev) {
     L.parity = 0;
@@ -1313,6 +1325,7 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   a.sy = g.pitch;
   a.sz = g.pitch * g.ext[1];
   a.h = g.h;
+  a.eta = L.eta;
   cudaEvent_t e[3];
   for (auto& x : e) CU(cudaEventCreate(&x));
   float t0 = 0, t1 = 0;

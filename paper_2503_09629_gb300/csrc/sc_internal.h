@@ -96,6 +96,7 @@ struct StageArgs {
   long fs;
   int sy, sz;        // strides of y and z in doubles
   double h;
+  const double* eta; // Z4c: per-cell Gamma-driver damping eta(r), or null for the constant
 };
 
 struct Z4cParams {
@@ -141,6 +142,8 @@ cudaError_t launch_restrict(double* parent, long pfs, const double* fine, long f
                             const RestrictCell* cells, int ncells, int F, const Weights& w, cudaStream_t s);
 cudaError_t launch_initial_data(double* vec, const Geom& g, int F, int system, int kind, const double* params,
                                 int nparams, cudaStream_t s);
+// eta(r) = (eta_c - eta_o) exp(-(r / eta_s)^4) + eta_o at every element of a level array
+cudaError_t launch_eta_profile(double* eta, const Geom& g, double eta_c, double eta_s, double eta_o, cudaStream_t s);
 cudaError_t launch_pack(const double* vec, const Geom& g, const int* lo, const int* n, double* dst,
                         cudaStream_t s);
 cudaError_t launch_unpack(double* vec, const Geom& g, const int* lo, const int* n, const double* src,

@@ -255,7 +255,7 @@ struct Z4cPoint {
 // matter terms vanish).  u: fields; S + o: derivatives in scratch.
 template <bool kDiag>
 __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, const double* __restrict__ S, long fs,
-                                              long o, const Z4cParams& P, double* rhs, double* diag) {
+                                              long o, const Z4cParams& P, double eta, double* rhs, double* diag) {
 #define FLD(f) Y[(long)(f) * fs + o]
 #define D1(f, d) S[(long)(Q_D1 + 3 * (f) + (d)) * fs + o]
 #define D2(sl, p) S[(long)(Q_D2 + 6 * (sl) + (p)) * fs + o]
@@ -497,7 +497,7 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
   // lapse (1+log) and shift (Gamma-driver)
   rhs[ZAL] = fma(m2al, Kh, ADV(ZAL));
 #pragma unroll
-  for (int i = 0; i < 3; ++i) rhs[ZB + i] = ADV(ZB + i) + fma(0.75, Gam[i], -P.eta * be[i]);
+  for (int i = 0; i < 3; ++i) rhs[ZB + i] = ADV(ZB + i) + fma(0.75, Gam[i], -eta * be[i]);
   if (kDiag) {
     diag[0] = Rsc;
     diag[1] = AA;
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(128) z4c_stage_kernel(StageArgs a, const doubl
       const int k = q / (T.nx * T.ny);
       const long o = (long)(T.z0 + k) * a.sz + (long)(T.y0 + j) * a.sy + (T.x0 + i);
       double rhs[kNZ4c];
-      z4c_rhs_point<false>(a.Y, S, a.fs, o, P, rhs, nullptr);
+      z4c_rhs_point<false>(a.Y, S, a.fs, o, P, a.eta ? a.eta[o] : P.eta, rhs, nullptr);
 #pragma unroll
       for (int f = 0; f < kNZ4c; ++f) {
         const long fo = (long)f * a.fs + o;
@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(128) z4c_constraints_kernel(const double* __re
 #define FLD(f) Y[(long)(f) * fs + o]
 #define D1(f, d) S[(long)(Q_D1 + 3 * (f) + (d)) * fs + o]
       double rhs[kNZ4c], diag[3];
-      z4c_rhs_point<true>(Y, S, fs, o, P, rhs, diag);
+      z4c_rhs_point<true>(Y, S, fs, o, P, P.eta, rhs, diag);
       out[cell] = diag[0] + (2.0 / 3.0) * diag[2] * diag[2] - diag[1];
       double g[6], A[6], gu[6];
       for (int s = 0; s < 6; ++s) {

@@ -17,7 +17,7 @@ Workloads (cell-centred grids, refinement factor 2, 3 ghost cells):
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import List, Tuple
+from typing import List, Optional, Tuple
 
 import numpy as np
 
@@ -26,6 +26,7 @@ Box = Tuple[Tuple[int, int, int], Tuple[int, int, int]]
 WAVE, Z4C = 0, 1
 BC_PERIODIC, BC_RADIATIVE = 0, 1
 ID_STANDING_WAVE, ID_GAUSSIAN, ID_BRILL_LINDQUIST, ID_MINKOWSKI, ID_SPHERICAL_GAUSSIAN = 0, 1, 2, 3, 4
+ID_BRILL_LINDQUIST_AVG_LAPSE = 5
 
 
 @dataclass
@@ -42,6 +43,7 @@ class Hierarchy:
     kappa2: float = 0.0
     eta: float = 2.0
     ko_sigma: float = 0.3
+    eta_profile: Optional[Tuple[float, float, float]] = None  # (eta_c, eta_s, eta_o) of Sec. III.A
     id_kind: int = ID_STANDING_WAVE
     id_params: List[float] = field(default_factory=list)
     name: str = ""
@@ -75,8 +77,11 @@ class Hierarchy:
         return X, Y, Z
 
     def kwargs(self) -> dict:
-        return dict(bc=self.bc, cfl=self.cfl, subcycle=self.subcycle, kappa1=self.kappa1,
-                    kappa2=self.kappa2, eta=self.eta, ko_sigma=self.ko_sigma)
+        kw = dict(bc=self.bc, cfl=self.cfl, subcycle=self.subcycle, kappa1=self.kappa1,
+                  kappa2=self.kappa2, eta=self.eta, ko_sigma=self.ko_sigma)
+        if self.eta_profile is not None:
+            kw["eta_profile"] = self.eta_profile
+        return kw
 
 
 def cube(lo: int, n: int) -> Box:
@@ -237,13 +242,16 @@ def initial_fields(h: Hierarchy, level: int, box: int, ghosted: bool = False, no
         return np.stack([u, np.zeros_like(u)])
     out = np.zeros((22,) + X.shape)
     psi = np.ones_like(X)
-    if h.id_kind == ID_BRILL_LINDQUIST:
+    if h.id_kind in (ID_BRILL_LINDQUIST, ID_BRILL_LINDQUIST_AVG_LAPSE):
         for q in range(2):
             m, cx, cy, cz = p[4 * q:4 * q + 4]
             psi += m / (2 * np.sqrt((X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2))
     out[0] = psi ** -2       # W = gamma^(-1/6) for gamma_ij = psi^4 delta_ij
     out[1] = out[4] = out[6] = 1.0  # conformal metric = delta
     out[18] = psi ** -2      # lapse psi^-2
+    if h.id_kind == ID_BRILL_LINDQUIST_AVG_LAPSE:
+        s = psi - 1.0
+        out[18] = 0.5 * (1.0 + (1.0 - s) / (1.0 + s))  # averaged lapse (Sec. III.B)
     return out
 
 

@@ -146,3 +146,22 @@ def test_full_7level_sampled_rhs_parity(sc, orc):
         for f in range(22):
             tol = 1e-10 * np.abs(ref[f]).max() + floor
             assert np.abs(got[f] - ref[f]).max() <= tol, (level, box, (i0, j0, k0), f)
+
+
+def test_eta_profile_and_averaged_lapse_parity(sc, orc):
+    """Sec. III.A eta(r) Gamma-driver profile and Sec. III.B averaged lapse:
+    GPU initial data against the oracle's, then 8 coarse steps."""
+    h = W.bl_3level(20, 0.5, 0.5, 2.0)
+    h.id_kind = W.ID_BRILL_LINDQUIST_AVG_LAPSE
+    h.eta_profile = (2.0, 2.0, 0.25)
+    ctx = sc.Context(h)
+    o = make_oracle(orc, h)
+    ctx.sc_set_initial_data(h.id_kind, h.id_params)
+    o.set_initial_data(h.id_kind, h.id_params)
+    assert max_rel_diff(fetch(ctx, h), fetch(o, h)) <= 1e-14
+    arrays = init_arrays(h)
+    load(ctx, h, arrays)
+    load(o, h, arrays)
+    ctx.sc_advance(8)
+    o.advance(8)
+    assert max_rel_diff(fetch(ctx, h), fetch(o, h)) <= TOL

@@ -447,3 +447,42 @@ def test_z4c_rhs_matches_gauge_wave_time_derivative(orc):
 def test_flop_count_positive(orc):
     c = orc.flop_counts()
     assert c["total"] > 1000 and c["div"] > 0
+
+
+def test_averaged_lapse_equals_inverse_conformal_factor(orc):
+    """Sec. III.B: the averaged lapse (1 + (1 - s)/(1 + s))/2 with
+    s = sum m/(2 r) simplifies to 1/(1 + s) = 1/psi; with W = psi^-2 this is
+    alpha = sqrt(W) at every cell."""
+    h = W.bl_3level(20, 0.4, 0.6, 3.0)
+    o = make(orc, h)
+    o.set_initial_data(W.ID_BRILL_LINDQUIST_AVG_LAPSE, h.id_params)
+    for l in range(3):
+        a = o.get_field(l, 0, 18, ghosted=True)
+        w = o.get_field(l, 0, 0, ghosted=True)
+        np.testing.assert_allclose(a, np.sqrt(w), rtol=1e-14)
+
+
+def test_eta_profile_limits(orc):
+    """Sec. III.A eta(r): a uniform shift on flat space has d_t beta = -eta beta
+    exactly; eta tends to eta_c at the origin and to eta_o far away (paper's
+    eta_s = 40 for the centre, eta_s = 10 for the far field), and it
+    decreases with r."""
+    n = 16
+    for eta_s, check in ((40.0, "centre"), (10.0, "far")):
+        h = W.Hierarchy(system=W.Z4C, boxes=[[W.cube(0, n)]], ncells0=(n, n, n), origin=(-40.0, -40.0, -40.0),
+                        h0=5.0, bc=2, ko_sigma=0.3, eta_profile=(2.0, eta_s, 0.25))
+        o = make(orc, h)
+        X, Y, Z = h.cell_centres(0, 0, ghosted=True)
+        st = np.zeros((22,) + X.shape)
+        st[0] = st[1] = st[4] = st[6] = st[18] = 1.0
+        st[19], st[20], st[21] = 0.3, -0.2, 0.1
+        rhs = o.rhs_box(0, 0, st)[:, 3:-3, 3:-3, 3:-3]
+        eta = -rhs[19] / 0.3
+        np.testing.assert_allclose(-rhs[20] / -0.2, eta, rtol=1e-14)
+        r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)[3:-3, 3:-3, 3:-3]
+        if check == "centre":
+            assert abs(eta[r == r.min()].max() - 2.0) < 1e-3   # r = 2.5 sqrt(3) << eta_s
+        else:
+            assert abs(eta[r == r.max()].min() - 0.25) < 1e-12  # r = 37.5 sqrt(3) >> eta_s
+        order = np.argsort(r.ravel())
+        assert np.all(np.diff(eta.ravel()[order]) <= 1e-15)
