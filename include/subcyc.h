@@ -205,6 +205,23 @@ sc_status sc_time_stage_kernels(sc_ctx* ctx, int level, int nrep, double* ms);
 sc_status sc_z4c_constraints_noalloc(const double* dev_state, double* dev_out, const int* n, double h,
                                      void* cuda_stream);
 
+/* Moving boxes: replace the boxes of every refined level (level 0 must stay
+ * as it is; layout as in sc_desc: nboxes per level, boxes level by level).
+ * Each interior cell of the new layout that was an interior cell of the same
+ * level keeps its state; every other interior cell takes the quintic
+ * prolongation of its parent's state (the parent already regridded).  The
+ * new layout must satisfy the same nesting rules as sc_create (else
+ * SC_ENESTING, with the old layout kept).  Rebuilds the work lists and the
+ * coarse-step graphs; call between sc_advance calls.  Synchronises.  After a
+ * device allocation failure (SC_ENOMEM) the context must be destroyed. */
+sc_status sc_regrid(sc_ctx* ctx, const int* nboxes, const sc_box* boxes);
+
+/* Field values at npts points (xyz: 3 doubles per point, physical
+ * coordinates) by tensor-product quintic Lagrange interpolation on the finest
+ * level whose 6x6x6 cell stencil around the point is interior; SC_EINVAL if
+ * no level holds it.  out: npts doubles (host).  Synchronises. */
+sc_status sc_interpolate(sc_ctx* ctx, int npts, const double* xyz, int field, double* out);
+
 /* Autotuner: time candidate tile shapes of the stencil kernel (Z4c
  * derivative pass, or the fused wave stage) on the context's largest level
  * with CUDA events on its stream, keep the fastest, rebuild the tile lists

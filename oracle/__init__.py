@@ -82,6 +82,8 @@ def lib():
         L.orc_debug_restrict.argtypes = [P, I]
         L.orc_debug_fill_ghosts.argtypes = [P]
         L.orc_flop_counts.argtypes = [DP]
+        L.orc_regrid.argtypes = [P, IP, IP]
+        L.orc_interpolate.argtypes = [P, I, DP, I, DP]
         _lib = L
     return _lib
 
@@ -233,6 +235,23 @@ class Oracle:
 
     def fill_ghosts(self):
         assert lib().orc_debug_fill_ghosts(self.h) == 0
+
+    def regrid(self, boxes):
+        """New boxes for every level (level 0 unchanged)."""
+        nb = (ctypes.c_int * len(boxes))(*[len(b) for b in boxes])
+        flat = [v for lvl in boxes for lo, hi in lvl for v in list(lo) + list(hi)]
+        fb = (ctypes.c_int * len(flat))(*flat)
+        rc = lib().orc_regrid(self.h, nb, fb)
+        if rc != 0:
+            raise ValueError(f"regrid failed ({rc})")
+        self.boxes = [[(tuple(lo), tuple(hi)) for lo, hi in lvl] for lvl in boxes]
+
+    def interpolate(self, points, field):
+        p = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+        out = np.zeros(len(p))
+        if lib().orc_interpolate(self.h, len(p), _dp(p), field, _dp(out)) != 0:
+            raise ValueError("interpolate failed")
+        return out
 
     def cell_centres(self, level, box, h0, origin, ghosted=False):
         """Cell-centre coordinates (z, y, x order arrays) of a box."""

@@ -1294,6 +1294,126 @@ int orc_constraints(void* h, int l, int b, double* out) {
   return 0;
 }
 
+// Moving boxes: replace the boxes of levels >= 1.  Every interior cell of
+// the new hierarchy that was an interior cell of the same level before keeps
+// its state; every other interior cell takes the quintic prolongation of the
+// (already regridded) parent's state.  Level 0 must be unchanged.
+int orc_regrid(void* h, const int* nboxes, const int* boxes) {
+  Hier* H = static_cast<Hier*>(h);
+  const int L = H->nlev;
+  std::vector<int> ncells(3);
+  void* nh = nullptr;
+  double prm[4] = {H->kappa1, H->kappa2, H->eta, H->sigma};
+  const int rc = orc_create(H->system, L, nboxes, boxes, H->ncells0, H->origin, H->h0, H->bc, H->cfl, H->subcycle,
+                            prm, &nh);
+  if (rc) return rc;
+  Hier* N = static_cast<Hier*>(nh);
+  if (N->lev[0].boxes.size() != H->lev[0].boxes.size()) {
+    orc_destroy(nh);
+    return fail(-1, "regrid keeps level 0 unchanged");
+  }
+  for (size_t b = 0; b < N->lev[0].boxes.size(); ++b)
+    for (int d = 0; d < 3; ++d)
+      if (N->lev[0].boxes[b].lo[d] != H->lev[0].boxes[b].lo[d] || N->lev[0].boxes[b].hi[d] != H->lev[0].boxes[b].hi[d]) {
+        orc_destroy(nh);
+        return fail(-1, "regrid keeps level 0 unchanged");
+      }
+  N->lev[0].boxes = H->lev[0].boxes;  // level 0 keeps its data
+  for (int l = 1; l < L; ++l) {
+    for (BoxData& B : N->lev[l].boxes)
+      for (int k = 0; k < B.n[2]; ++k)
+        for (int j = 0; j < B.n[1]; ++j)
+          for (int i = 0; i < B.n[0]; ++i) {
+            const int g[3] = {B.lo[0] + i, B.lo[1] + j, B.lo[2] + k};
+            const long o = B.off(i, j, k);
+            int li[3];
+            const int ob = find_interior(*H, l, g, li);
+            if (ob >= 0) {
+              const BoxData& O = H->lev[l].boxes[ob];
+              const long oo = O.off(li[0], li[1], li[2]);
+              for (int f = 0; f < N->F; ++f) B.v[V_Y][(long)f * B.vol + o] = O.v[V_Y][(long)f * O.vol + oo];
+              continue;
+            }
+            int nodes[3][8];
+            double w[3][8];
+            for (int d = 0; d < 3; ++d) prolong_stencil_1d(g[d], nodes[d], w[d]);
+            for (int f = 0; f < N->F; ++f) B.v[V_Y][(long)f * B.vol + o] = 0.0;
+            for (int cz = 0; cz < g_pn; ++cz)
+              for (int cy = 0; cy < g_pn; ++cy)
+                for (int cx = 0; cx < g_pn; ++cx) {
+                  const int pg[3] = {nodes[0][cx], nodes[1][cy], nodes[2][cz]};
+                  int pl[3];
+                  const int pb = find_interior(*N, l - 1, pg, pl);
+                  if (pb < 0) {
+                    orc_destroy(nh);
+                    return fail(-4, "regrid: new cell cannot be prolonged from the parent interior");
+                  }
+                  const BoxData& P = N->lev[l - 1].boxes[pb];
+                  const long po = P.off(pl[0], pl[1], pl[2]);
+                  const double ww = w[0][cx] * w[1][cy] * w[2][cz];
+                  for (int f = 0; f < N->F; ++f) B.v[V_Y][(long)f * B.vol + o] += ww * P.v[V_Y][(long)f * P.vol + po];
+                }
+          }
+  }
+  // keep time, counters and options; take the new levels
+  N->t = H->t;
+  N->zu_finest = H->zu_finest;
+  N->zu_actual = H->zu_actual;
+  N->cb = H->cb;
+  N->cb_user = H->cb_user;
+  N->eta_profile = H->eta_profile;
+  N->eta_c = H->eta_c;
+  N->eta_s = H->eta_s;
+  N->eta_o = H->eta_o;
+  for (int l = 0; l < L; ++l) N->lev[l].t = H->lev[l].t;
+  std::swap(*H, *N);
+  orc_destroy(nh);
+  return 0;
+}
+
+// Field values at points: tensor-product quintic Lagrange interpolation on
+// the finest level whose 6x6x6 cell stencil around the point is interior.
+int orc_interpolate(void* h, int npts, const double* xyz, int field, double* out) {
+  Hier* H = static_cast<Hier*>(h);
+  if (field < 0 || field >= H->F) return fail(-1, "bad field");
+  for (int a = 0; a < npts; ++a) {
+    bool found = false;
+    for (int l = H->nlev - 1; l >= 0 && !found; --l) {
+      const double hl = H->lev[l].h;
+      double s[3], w[3][8];
+      int first[3];
+      for (int d = 0; d < 3; ++d) {
+        s[d] = (xyz[3 * a + d] - H->origin[d]) / hl - 0.5;
+        first[d] = (int)std::floor(s[d]) - 2;
+        double x[8];
+        for (int m = 0; m < g_pn; ++m) x[m] = first[d] + m;
+        lagrange(x, g_pn, s[d], w[d]);
+      }
+      double acc = 0.0;
+      bool ok = true;
+      for (int cz = 0; cz < g_pn && ok; ++cz)
+        for (int cy = 0; cy < g_pn && ok; ++cy)
+          for (int cx = 0; cx < g_pn && ok; ++cx) {
+            const int g[3] = {first[0] + cx, first[1] + cy, first[2] + cz};
+            int li[3];
+            const int b = find_interior(*H, l, g, li);
+            if (b < 0) {
+              ok = false;
+              break;
+            }
+            const BoxData& B = H->lev[l].boxes[b];
+            acc += w[0][cx] * w[1][cy] * w[2][cz] * B.v[V_Y][(long)field * B.vol + B.off(li[0], li[1], li[2])];
+          }
+      if (ok) {
+        out[a] = acc;
+        found = true;
+      }
+    }
+    if (!found) return fail(-1, "no level holds the interpolation stencil");
+  }
+  return 0;
+}
+
 // Operation counts of one Z4c right-hand side at one cell in this oracle's
 // formulation (derivative stencils, KO and the pointwise equations):
 // counts[0..3] = add/sub, mul, div, total flops.

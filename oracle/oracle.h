@@ -60,6 +60,9 @@ int orc_debug_fill_amr(void* h, int level, int vec, double theta0, int which);
 int orc_debug_restrict(void* h, int level);
 int orc_debug_fill_ghosts(void* h);
 void orc_flop_counts(double* counts);
+/* Moving boxes: new boxes for every level (level 0 unchanged); see oracle.cpp. */
+int orc_regrid(void* h, const int* nboxes, const int* boxes);
+int orc_interpolate(void* h, int npts, const double* xyz, int field, double* out);
 
 #ifdef __cplusplus
 }

@@ -116,6 +116,8 @@ def lib():
     L.sc_autotune.argtypes = [P, ctypes.POINTER(ctypes.c_int), DP]
     L.sc_time_ghost_kernels.argtypes = [P, I, I, DP, ctypes.POINTER(ctypes.c_long)]
     L.sc_debug_get_vector.argtypes = [P, I, I, I, I, I, DP]
+    L.sc_regrid.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(sc_box)]
+    L.sc_interpolate.argtypes = [P, I, DP, I, DP]
     L.sc_z4c_constraints_noalloc.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), D, P]
     IP = ctypes.POINTER(ctypes.c_int)
     U64 = ctypes.c_ulonglong
@@ -313,6 +315,36 @@ class Context:
         ms = ctypes.c_double()
         _check(lib().sc_autotune(self.ctx, t, ctypes.byref(ms)))
         return (t[0], t[1], t[2]), ms.value
+
+    def sc_regrid(self, boxes):
+        """New boxes for every level (level 0 unchanged); updates self.h."""
+        nb = (ctypes.c_int * len(boxes))(*[len(b) for b in boxes])
+        flat = [bx for lvl in boxes for bx in lvl]
+        arr = (sc_box * len(flat))()
+        for i, (lo, hi) in enumerate(flat):
+            arr[i].lo[:] = list(lo)
+            arr[i].hi[:] = list(hi)
+        _check(lib().sc_regrid(self.ctx, nb, arr))
+        import copy
+        h = copy.copy(self.h)
+        h.boxes = [[(tuple(lo), tuple(hi)) for lo, hi in lvl] for lvl in boxes]
+        self.h = h
+
+    def sc_interpolate(self, points, field: int) -> np.ndarray:
+        p = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+        out = np.empty(len(p))
+        _check(lib().sc_interpolate(self.ctx, len(p), _dp(p), field, _dp(out)))
+        return out
+
+    # the same names as the oracle's, so one driver can move either
+    def regrid(self, boxes):
+        self.sc_regrid(boxes)
+
+    def interpolate(self, points, field):
+        return self.sc_interpolate(points, field)
+
+    def advance(self, n):
+        self.sc_advance(n)
 
     def sc_debug_get_vector(self, level: int, box: int, vec: int, field: int, ghosted: bool = False) -> np.ndarray:
         a = np.empty(self.shape(level, box, ghosted))

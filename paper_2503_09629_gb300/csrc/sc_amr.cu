@@ -248,6 +248,74 @@ __global__ void __launch_bounds__(kThreads) initial_data_kernel(double* __restri
 
 // Copy a box region of one field between a level array and a contiguous
 // x-fastest buffer (unpack = 0: array -> buffer; 1: buffer -> array).
+// Regrid: copy the state of cells that stay interior from the old level
+// array (pairs: x = destination offset, y = source offset).
+__global__ void __launch_bounds__(kThreads) transfer_copy_kernel(double* __restrict__ dst, long dfs,
+                                                                const double* __restrict__ src, long sfs,
+                                                                const int2* __restrict__ pairs, int n, int F) {
+  const long total = (long)n * F;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int a = (int)(idx % n);
+    const int f = (int)(idx / n);
+    const int2 p = pairs[a];
+    dst[(long)f * dfs + p.x] = src[(long)f * sfs + p.y];
+  }
+}
+
+// Regrid: new interior cells take the quintic prolongation of the parent's
+// state (the same stencil as the refinement-boundary ghosts).
+__global__ void __launch_bounds__(kThreads) prolong_state_kernel(double* __restrict__ dst, long dfs,
+                                                                const double* __restrict__ parent, long pfs,
+                                                                int psy, int psz, const AmrCell* __restrict__ cells,
+                                                                int n, int F, Weights w) {
+  const long total = (long)n * F;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int a = (int)(idx % n);
+    const int f = (int)(idx / n);
+    const AmrCell c = cells[a];
+    const double* wx = w.prolong[c.parity & 1];
+    const double* wy = w.prolong[(c.parity >> 1) & 1];
+    const double* wz = w.prolong[(c.parity >> 2) & 1];
+    const double* p = parent + (long)f * pfs + c.pbase;
+    double sz = 0.0;
+#pragma unroll
+    for (int kz = 0; kz < kPN; ++kz) {
+      double sy = 0.0;
+#pragma unroll
+      for (int ky = 0; ky < kPN; ++ky) {
+        const double* row = p + (long)kz * psz + (long)ky * psy;
+        double sx = 0.0;
+#pragma unroll
+        for (int kx = 0; kx < kPN; ++kx) sx = fma(wx[kx], __ldg(row + kx), sx);
+        sy = fma(wy[ky], sx, sy);
+      }
+      sz = fma(wz[kz], sy, sz);
+    }
+    dst[(long)f * dfs + c.dst] = sz;
+  }
+}
+
+// Field values at arbitrary points: quintic tensor Lagrange interpolation of
+// 6x6x6 cells of a level array with per-point weights computed on the host.
+__global__ void __launch_bounds__(kThreads) interpolate_kernel(const InterpPoint* __restrict__ pts, int n,
+                                                              double* __restrict__ out) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) {
+    const InterpPoint q = pts[a];
+    double sz = 0.0;
+    for (int kz = 0; kz < kPN; ++kz) {
+      double sy = 0.0;
+      for (int ky = 0; ky < kPN; ++ky) {
+        const double* row = q.base + (long)kz * q.sz + (long)ky * q.sy;
+        double sx = 0.0;
+        for (int kx = 0; kx < kPN; ++kx) sx = fma(q.w[kx], row[kx], sx);
+        sy = fma(q.w[kPN + ky], sx, sy);
+      }
+      sz = fma(q.w[2 * kPN + kz], sy, sz);
+    }
+    out[a] = sz;
+  }
+}
+
 // Gamma-driver damping profile of Sec. III.A at every element of a level array.
 __global__ void __launch_bounds__(kThreads) eta_profile_kernel(double* __restrict__ eta, Geom g, double ec, double es,
                                                               double eo) {
@@ -342,6 +410,27 @@ cudaError_t launch_initial_data(double* vec, const Geom& g, int F, int system, i
   for (int i = 0; i < 8; ++i) ip.p[i] = (i < nparams) ? params[i] : 0.0;
   const long n = (long)g.ext[0] * g.ext[1] * g.ext[2];
   initial_data_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(vec, g, F, system, kind, ip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transfer_copy(double* dst, long dfs, const double* src, long sfs, const int2* pairs, int n, int F,
+                                 cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  transfer_copy_kernel<<<grid_for((long)n * F, kThreads), kThreads, 0, s>>>(dst, dfs, src, sfs, pairs, n, F);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_state(double* dst, long dfs, const double* parent, long pfs, int psy, int psz,
+                                 const AmrCell* cells, int n, int F, const Weights& w, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  prolong_state_kernel<<<grid_for((long)n * F, kThreads), kThreads, 0, s>>>(dst, dfs, parent, pfs, psy, psz, cells, n,
+                                                                           F, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interpolate(const InterpPoint* pts, int n, double* out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  interpolate_kernel<<<grid_for(n, kThreads), kThreads, 0, s>>>(pts, n, out);
   return cudaGetLastError();
 }
 

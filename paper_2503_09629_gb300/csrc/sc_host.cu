@@ -160,6 +160,7 @@ struct Level {
   RowSeg* dxy = nullptr;
   int ndxy = 0;
   double* eta = nullptr;  // per-element eta(r) (Z4c with the Sec. III.A profile), else null
+  std::vector<void*> allocs;  // device buffers owned by this level (freed on regrid)
   int namr_blocked = 0;
   double* amr_store = nullptr;  // 5 * F * namr prolonged parent vectors
   int2* periodic = nullptr;
@@ -210,6 +211,8 @@ struct sc_ctx {
   long launches_per_step = 0;
   int exec_mode = SC_EXEC_GRAPH;
   int tile[3] = {32, 4, 2};  // stencil-kernel tile shape (autotuned on request)
+  int eta_profile = 0;
+  double eta_c = 0, eta_s = 0, eta_o = 0;
   std::vector<Op> plain_ops[2];  // per-box form: the schedule, run directly
 
   void* dalloc(size_t bytes) {
@@ -226,6 +229,16 @@ struct sc_ctx {
       footprint += bytes;
     }
     return p;
+  }
+  void dfree(void* p) {
+    for (size_t i = 0; i < bufs.size(); ++i)
+      if (bufs[i].p == p) {
+        if (has_alloc) alloc.free(p, alloc.user);
+        else cudaFree(p);
+        footprint -= bufs[i].bytes;
+        bufs.erase(bufs.begin() + i);
+        return;
+      }
   }
   void release() {
     for (auto& b : bufs) {
@@ -629,6 +642,68 @@ sc_status upload(sc_ctx* c, const std::vector<T>& v, T** dst) {
   return SC_OK;
 }
 
+// Allocation owned by one level (released when the level is regridded).
+void* level_alloc(sc_ctx* c, Level& L, size_t bytes) {
+  void* p = c->dalloc(bytes);
+  if (p) L.allocs.push_back(p);
+  return p;
+}
+
+template <class T>
+sc_status level_upload(sc_ctx* c, Level& L, const std::vector<T>& v, T** dst) {
+  *dst = nullptr;
+  if (v.empty()) return SC_OK;
+  *dst = (T*)level_alloc(c, L, v.size() * sizeof(T));
+  if (!*dst) return fail(SC_ENOMEM, "device allocation of %zu bytes failed", v.size() * sizeof(T));
+  CU(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  return SC_OK;
+}
+
+void free_level(sc_ctx* c, Level& L) {
+  for (void* p : L.allocs) c->dfree(p);
+  L.allocs.clear();
+}
+
+// Device side of a level: the 8 state/stage/k vectors (zeroed), its work
+// lists, the ghost store and the eta(r) array.
+sc_status setup_level_device(sc_ctx* c, int l, HostLists& hl) {
+  Level& L = c->lev[l];
+  const size_t vbytes = sizeof(double) * (size_t)c->F * L.g.fs;
+  double** vecs[8] = {&L.S[0], &L.S[1], &L.A, &L.B, &L.K[0], &L.K[1], &L.K[2], &L.K[3]};
+  for (double** v : vecs) {
+    *v = (double*)level_alloc(c, L, vbytes);
+    if (!*v) return fail(SC_ENOMEM, "level %d: allocation of %zu bytes failed", l, vbytes);
+    CU(cudaMemsetAsync(*v, 0, vbytes, c->stream));
+  }
+  sc_status st;
+  if ((st = level_upload(c, L, hl.tiles, &L.tiles)) || (st = level_upload(c, L, hl.amr, &L.amr)) ||
+      (st = level_upload(c, L, hl.periodic, &L.periodic)) || (st = level_upload(c, L, hl.phys, &L.phys)) ||
+      (st = level_upload(c, L, hl.restr, &L.restr)) || (st = level_upload(c, L, hl.blocks, &L.blocks)) ||
+      (st = level_upload(c, L, hl.dxy, &L.dxy)) || (st = level_upload(c, L, hl.ptiles, &L.ptiles)))
+    return st;
+  L.ntiles = (int)hl.tiles.size();
+  L.namr = (int)hl.amr.size();
+  L.nblocks = (int)hl.blocks.size();
+  L.nptiles = (int)hl.ptiles.size();
+  L.ndxy = (int)hl.dxy.size();
+  L.namr_blocked = hl.namr_blocked;
+  L.nperiodic = (int)hl.periodic.size();
+  L.nphys = (int)hl.phys.size();
+  L.nrestr = (int)hl.restr.size();
+  L.amr_store = nullptr;
+  if (L.namr) {
+    L.amr_store = (double*)level_alloc(c, L, sizeof(double) * 5 * (size_t)c->F * L.namr);
+    if (!L.amr_store) return fail(SC_ENOMEM, "level %d: ghost store allocation failed", l);
+  }
+  L.eta = nullptr;
+  if (c->system == SC_Z4C && c->eta_profile) {
+    L.eta = (double*)level_alloc(c, L, sizeof(double) * (size_t)L.g.fs);
+    if (!L.eta) return fail(SC_ENOMEM, "level %d: eta profile allocation failed", l);
+    CU(launch_eta_profile(L.eta, L.g, c->eta_c, c->eta_s, c->eta_o, c->stream));
+  }
+  return SC_OK;
+}
+
 // ---------------------------------------------------------------- schedule
 struct Emitter {
   sc_ctx* c;
@@ -1001,6 +1076,181 @@ extern "C" sc_status sc_autotune(sc_ctx* c, int* tile_out, double* ms_out) {
 }
 
 // ---------------------------------------------------------------------------
+// Moving boxes: regrid and point interpolation.
+
+namespace {
+
+// Transfer lists of one regridded level: cells that stay interior copy
+// from the old array; new interior cells are prolonged from the new parent.
+struct Transfer {
+  std::vector<int2> copy;
+  std::vector<AmrCell> prolong;
+};
+
+sc_status build_transfer(sc_ctx* c, int l, const Level& old, Transfer& tr) {
+  const Level& L = c->lev[l];
+  const Level& P = c->lev[l - 1];
+  for (const sc_box& B : L.boxes)
+    for (int k = B.lo[2]; k <= B.hi[2]; ++k)
+      for (int j = B.lo[1]; j <= B.hi[1]; ++j)
+        for (int i = B.lo[0]; i <= B.hi[0]; ++i) {
+          const int gi[3] = {i, j, k};
+          const int32_t dst = (int32_t)L.g.off(i, j, k);
+          if (is_interior(old, gi)) {
+            tr.copy.push_back(make_int2(dst, (int32_t)old.g.off(i, j, k)));
+            continue;
+          }
+          int first[3], par = 0;
+          for (int q = 0; q < 3; ++q) {
+            const int odd = gi[q] & 1;
+            par |= odd << q;
+            first[q] = odd ? (gi[q] >> 1) - 2 : (gi[q] >> 1) - 3;
+          }
+          for (int a = 0; a < kPN; ++a)
+            for (int b = 0; b < kPN; ++b)
+              for (int d = 0; d < kPN; ++d) {
+                const int pg[3] = {first[0] + d, first[1] + b, first[2] + a};
+                if (!is_interior(P, pg))
+                  return fail(SC_ENESTING, "regrid: level %d cell (%d,%d,%d) cannot be prolonged from the parent interior",
+                              l, i, j, k);
+              }
+          AmrCell ac;
+          ac.dst = dst;
+          ac.pbase = (int32_t)P.g.off(first[0], first[1], first[2]);
+          ac.parity = par;
+          tr.prolong.push_back(ac);
+        }
+  return SC_OK;
+}
+
+}  // namespace
+
+extern "C" sc_status sc_regrid(sc_ctx* c, const int* nboxes, const sc_box* boxes) {
+  if (!c || !nboxes || !boxes) return fail(SC_EINVAL, "null argument");
+  sc_desc d{};
+  d.system = c->system;
+  d.nlevels = c->nlev;
+  d.nboxes = nboxes;
+  d.boxes = boxes;
+  for (int q = 0; q < 3; ++q) {
+    d.ncells0[q] = c->ncells0[q];
+    d.origin[q] = c->origin[q];
+  }
+  d.h0 = c->h0;
+  d.outer_bc = c->bc;
+  d.cfl = c->cfl;
+  d.subcycle = 1;
+  sc_status st = validate(&d);
+  if (st) return st;
+  if (nboxes[0] != (int)c->lev[0].boxes.size()) return fail(SC_EINVAL, "regrid keeps level 0 unchanged");
+  for (int b = 0; b < nboxes[0]; ++b)
+    for (int q = 0; q < 3; ++q)
+      if (boxes[b].lo[q] != c->lev[0].boxes[b].lo[q] || boxes[b].hi[q] != c->lev[0].boxes[b].hi[q])
+        return fail(SC_EINVAL, "regrid keeps level 0 unchanged");
+  // phase 1 (host only): new geometry, classification and transfer lists;
+  // on failure the old levels are put back untouched.
+  std::vector<Level> old(c->nlev);
+  for (int l = 1; l < c->nlev; ++l) old[l] = std::move(c->lev[l]);
+  std::vector<HostLists> hls(c->nlev);
+  std::vector<Transfer> trs(c->nlev);
+  int bi = nboxes[0];
+  auto restore = [&]() {
+    for (int l = 1; l < c->nlev; ++l) c->lev[l] = std::move(old[l]);
+  };
+  for (int l = 1; l < c->nlev; ++l) {
+    c->lev[l] = Level();
+    st = build_level_geometry(c, l, boxes + bi, nboxes[l]);
+    if (!st) st = classify_level(c, l, hls[l]);
+    if (!st) st = build_transfer(c, l, old[l], trs[l]);
+    if (st) {
+      restore();
+      return st;
+    }
+    bi += nboxes[l];
+  }
+  // phase 2 (device): allocate the new levels, transfer the state coarse to
+  // fine, release the old levels
+  const long old_scratch_fs = c->scratch_fs;
+  long maxfs = c->lev[0].g.fs;
+  for (int l = 1; l < c->nlev; ++l) {
+    st = setup_level_device(c, l, hls[l]);
+    if (st) return st;  // device allocation failed: the context is unusable (documented)
+    Level& L = c->lev[l];
+    maxfs = std::max(maxfs, L.g.fs);
+    int2* dcopy = nullptr;
+    AmrCell* dpro = nullptr;
+    if ((st = level_upload(c, L, trs[l].copy, &dcopy)) || (st = level_upload(c, L, trs[l].prolong, &dpro))) return st;
+    CU(launch_transfer_copy(L.S[0], L.g.fs, old[l].S[old[l].parity], old[l].g.fs, dcopy, (int)trs[l].copy.size(), c->F,
+                            c->stream));
+    const Level& P = c->lev[l - 1];
+    CU(launch_prolong_state(L.S[0], L.g.fs, P.S[P.parity], P.g.fs, P.g.pitch, P.g.pitch * P.g.ext[1], dpro,
+                            (int)trs[l].prolong.size(), c->F, c->w, c->stream));
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  for (int l = 1; l < c->nlev; ++l) free_level(c, old[l]);
+  if (c->system == SC_Z4C && maxfs > old_scratch_fs) {
+    c->dfree(c->scratch);
+    c->scratch = (double*)c->dalloc(sizeof(double) * 176 * (size_t)maxfs);
+    if (!c->scratch) return fail(SC_ENOMEM, "derivative scratch allocation failed");
+    c->scratch_fs = maxfs;
+  }
+  for (int p = 0; p < 2; ++p)
+    if (c->graph[p]) {
+      cudaGraphExecDestroy(c->graph[p]);
+      c->graph[p] = nullptr;
+    }
+  return build_graphs(c);
+}
+
+extern "C" sc_status sc_interpolate(sc_ctx* c, int npts, const double* xyz, int field, double* out) {
+  if (!c || (npts > 0 && (!xyz || !out)) || npts < 0) return fail(SC_EINVAL, "bad argument");
+  if (field < 0 || field >= c->F) return fail(SC_EINVAL, "bad field %d", field);
+  if (npts == 0) return SC_OK;
+  std::vector<InterpPoint> pts(npts);
+  for (int a = 0; a < npts; ++a) {
+    bool found = false;
+    for (int l = c->nlev - 1; l >= 0 && !found; --l) {
+      const Level& L = c->lev[l];
+      int first[3];
+      double s[3];
+      for (int q = 0; q < 3; ++q) {
+        s[q] = (xyz[3 * a + q] - c->origin[q]) / L.g.h - 0.5;  // position in cell-index units
+        first[q] = (int)floor(s[q]) - 2;
+      }
+      bool ok = true;
+      for (int kz = 0; kz < kPN && ok; ++kz)
+        for (int ky = 0; ky < kPN && ok; ++ky)
+          for (int kx = 0; kx < kPN && ok; ++kx) {
+            const int g[3] = {first[0] + kx, first[1] + ky, first[2] + kz};
+            ok = is_interior(L, g);
+          }
+      if (!ok) continue;
+      InterpPoint& p = pts[a];
+      p.base = L.S[L.parity] + (long)field * L.g.fs + L.g.off(first[0], first[1], first[2]);
+      p.sy = L.g.pitch;
+      p.sz = (long)L.g.pitch * L.g.ext[1];
+      for (int q = 0; q < 3; ++q) {
+        double x[kPN];
+        for (int m = 0; m < kPN; ++m) x[m] = first[q] + m;
+        lagrange_weights(x, kPN, s[q], p.w + q * kPN);
+      }
+      found = true;
+    }
+    if (!found) return fail(SC_EINVAL, "point %d: no level holds its interpolation stencil", a);
+  }
+  const size_t rec = sizeof(InterpPoint) * (size_t)npts, outb = sizeof(double) * (size_t)npts;
+  sc_status st = ensure_staging(c, rec + outb + 256);
+  if (st) return st;
+  InterpPoint* dpts = (InterpPoint*)c->staging;
+  double* dout = (double*)((char*)c->staging + ((rec + 255) & ~(size_t)255));
+  CU(cudaMemcpyAsync(dpts, pts.data(), rec, cudaMemcpyHostToDevice, c->stream));
+  CU(launch_interpolate(dpts, npts, dout, c->stream));
+  CU(cudaMemcpyAsync(out, dout, outb, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return SC_OK;
+}
+
+// ---------------------------------------------------------------------------
 // C ABI
 
 extern "C" {
@@ -1070,6 +1320,10 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
   c->zp = Z4cParams{d->kappa1, d->kappa2, d->eta, d->ko_sigma};
   c->stream = (cudaStream_t)d->cuda_stream;
   c->exec_mode = d->exec_mode == SC_EXEC_PER_BOX ? SC_EXEC_PER_BOX : SC_EXEC_GRAPH;
+  c->eta_profile = d->eta_profile ? 1 : 0;
+  c->eta_c = d->eta_c;
+  c->eta_s = d->eta_s;
+  c->eta_o = d->eta_o;
   if (d->allocator && d->allocator->alloc && d->allocator->free) {
     c->alloc = *d->allocator;
     c->has_alloc = true;
@@ -1090,49 +1344,13 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
       c->release();
       return st;
     }
-    Level& L = c->lev[l];
-    const size_t vbytes = sizeof(double) * (size_t)c->F * L.g.fs;
-    double** vecs[8] = {&L.S[0], &L.S[1], &L.A, &L.B, &L.K[0], &L.K[1], &L.K[2], &L.K[3]};
-    for (double** v : vecs) {
-      *v = (double*)c->dalloc(vbytes);
-      if (!*v) {
-        c->release();
-        return fail(SC_ENOMEM, "level %d: allocation of %zu bytes failed", l, vbytes);
-      }
-      CU(cudaMemsetAsync(*v, 0, vbytes, c->stream));
-    }
-    if ((st = upload(c.get(), hl.tiles, &L.tiles)) || (st = upload(c.get(), hl.amr, &L.amr)) ||
-        (st = upload(c.get(), hl.periodic, &L.periodic)) || (st = upload(c.get(), hl.phys, &L.phys)) ||
-        (st = upload(c.get(), hl.restr, &L.restr)) || (st = upload(c.get(), hl.blocks, &L.blocks)) ||
-        (st = upload(c.get(), hl.dxy, &L.dxy)) || (st = upload(c.get(), hl.ptiles, &L.ptiles))) {
+    st = setup_level_device(c.get(), l, hl);
+    if (st) {
       c->release();
       return st;
     }
-    L.ntiles = (int)hl.tiles.size();
-    L.namr = (int)hl.amr.size();
-    L.nblocks = (int)hl.blocks.size();
-    L.nptiles = (int)hl.ptiles.size();
-    L.ndxy = (int)hl.dxy.size();
-    L.namr_blocked = hl.namr_blocked;
-    L.nperiodic = (int)hl.periodic.size();
-    L.nphys = (int)hl.phys.size();
-    L.nrestr = (int)hl.restr.size();
-    if (L.namr) {
-      L.amr_store = (double*)c->dalloc(sizeof(double) * 5 * (size_t)c->F * L.namr);
-      if (!L.amr_store) {
-        c->release();
-        return fail(SC_ENOMEM, "level %d: ghost store allocation failed", l);
-      }
-    }
+    Level& L = c->lev[l];
     maxfs = std::max(maxfs, L.g.fs);
-    if (c->system == SC_Z4C && d->eta_profile) {
-      L.eta = (double*)c->dalloc(sizeof(double) * (size_t)L.g.fs);
-      if (!L.eta) {
-        c->release();
-        return fail(SC_ENOMEM, "level %d: eta profile allocation failed", l);
-      }
-      CU(launch_eta_profile(L.eta, L.g, d->eta_c, d->eta_s, d->eta_o, c->stream));
-    }
   }
   if (c->system == SC_Z4C) {
     c->scratch_fs = maxfs;
@@ -1153,7 +1371,6 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
     c->release();
     return fail(SC_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
   }
-  for (Level& L : c->lev) L.kind.clear(), L.kind.shrink_to_fit();
   st = build_graphs(c.get());
   if (st == SC_OK && d->autotune) st = sc_autotune(c.get(), nullptr, nullptr);
   if (st) {

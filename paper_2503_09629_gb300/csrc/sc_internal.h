@@ -77,6 +77,14 @@ struct RowSeg {
   int32_t which;
 };
 
+// One interpolation point: first cell of its 6x6x6 stencil in a level array,
+// the array strides, and the quintic weights per dimension (x, y, z).
+struct InterpPoint {
+  const double* base;
+  long sy, sz;
+  double w[3 * kPN];
+};
+
 struct Weights {
   double prolong[2][kPN];   // [parity][node]
   double restrict_w[kRN];
@@ -142,6 +150,11 @@ cudaError_t launch_restrict(double* parent, long pfs, const double* fine, long f
                             const RestrictCell* cells, int ncells, int F, const Weights& w, cudaStream_t s);
 cudaError_t launch_initial_data(double* vec, const Geom& g, int F, int system, int kind, const double* params,
                                 int nparams, cudaStream_t s);
+cudaError_t launch_transfer_copy(double* dst, long dfs, const double* src, long sfs, const int2* pairs, int n, int F,
+                                 cudaStream_t s);
+cudaError_t launch_prolong_state(double* dst, long dfs, const double* parent, long pfs, int psy, int psz,
+                                 const AmrCell* cells, int n, int F, const Weights& w, cudaStream_t s);
+cudaError_t launch_interpolate(const InterpPoint* pts, int n, double* out, cudaStream_t s);
 // eta(r) = (eta_c - eta_o) exp(-(r / eta_s)^4) + eta_o at every element of a level array
 cudaError_t launch_eta_profile(double* eta, const Geom& g, double eta_c, double eta_s, double eta_o, cudaStream_t s);
 cudaError_t launch_pack(const double* vec, const Geom& g, const int* lo, const int* n, double* dst,

@@ -284,3 +284,80 @@ def serving_requests(n: int = 256, seed: int = 0, burst: bool = False, mean_inte
             steps = 16
         out.append((0.0 if burst else t, h, steps))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Moving boxes (configs[3]): box stacks that follow the punctures.
+
+def box_around(centre, radius, level, h0, origin):
+    """Box of level `level` covering [centre - radius, centre + radius] in
+    every dimension, aligned to parent cells (lo even, hi odd)."""
+    h = h0 / 2 ** level
+    lo, hi = [], []
+    for d in range(3):
+        a = int(np.floor((centre[d] - radius - origin[d]) / h))
+        b = int(np.ceil((centre[d] + radius - origin[d]) / h)) - 1
+        a -= a % 2
+        b += 1 - b % 2
+        lo.append(a)
+        hi.append(b)
+    return (tuple(lo), tuple(hi))
+
+
+def _touch(a, b):
+    return all(a[0][d] <= b[1][d] + 1 and b[0][d] <= a[1][d] + 1 for d in range(3))
+
+
+def merged(boxes):
+    """Merge boxes that overlap or touch into their bounding boxes."""
+    boxes = list(boxes)
+    changed = True
+    while changed:
+        changed = False
+        for i in range(len(boxes)):
+            for j in range(i + 1, len(boxes)):
+                if _touch(boxes[i], boxes[j]):
+                    a, b = boxes[i], boxes[j]
+                    boxes[i] = (tuple(min(a[0][d], b[0][d]) for d in range(3)),
+                                tuple(max(a[1][d], b[1][d]) for d in range(3)))
+                    del boxes[j]
+                    changed = True
+                    break
+            if changed:
+                break
+    return sorted(boxes)
+
+
+def moving_layout(h: Hierarchy, positions, radii, first_moving: int):
+    """Boxes of every level: the fixed levels of h below first_moving, and for
+    each level l >= first_moving one box of radius radii[l] around every
+    puncture (merged where they touch)."""
+    out = [list(b) for b in h.boxes[:first_moving]]
+    for l in range(first_moving, h.nlevels):
+        out.append(merged(box_around(p, radii[l], l, h.h0, h.origin) for p in positions))
+    return out
+
+
+def moving_bl(n: int = 32, L: float = 16.0, sep: float = 3.0, m: float = 0.5):
+    """Small moving-box Z4c case: level 0 n^3 over [-L,L]^3, level 1 the
+    central half, levels 2 and 3 box stacks of radius 2.5 and 1.0 (in units
+    of the coordinates) around two Brill-Lindquist punctures on the x axis.
+    Returns (hierarchy, positions, radii, first_moving)."""
+    q = n // 2
+    positions = [(-sep / 2, 0.0, 0.0), (sep / 2, 0.0, 0.0)]
+    radii = [None, None, 2.5, 1.0]
+    base = Hierarchy(system=Z4C, boxes=[[cube(0, n)], [cube(q, n)]], ncells0=(n, n, n), origin=(-L, -L, -L),
+                     h0=2 * L / n, bc=BC_RADIATIVE, id_kind=ID_BRILL_LINDQUIST,
+                     id_params=[m, positions[0][0], 0.0, 0.0, m, positions[1][0], 0.0, 0.0],
+                     name=f"z4c BL moving boxes {n}^3, 4 levels")
+    base.boxes = moving_layout(Hierarchy(**{**base.__dict__, "boxes": base.boxes + [[], []]}), positions, radii, 2)
+    return base, positions, radii, 2
+
+
+def track_punctures(target, positions, dt, shift_fields=(19, 20, 21)):
+    """Move the punctures one coarse step along dx/dt = -beta(x) (forward
+    Euler with the shift interpolated at the start of the step); target is
+    anything with interpolate(points, field)."""
+    pts = np.asarray(positions, dtype=np.float64)
+    beta = np.stack([target.interpolate(pts, f) for f in shift_fields], axis=1)
+    return [tuple(p) for p in pts - dt * beta]

@@ -486,3 +486,57 @@ def test_eta_profile_limits(orc):
             assert abs(eta[r == r.max()].min() - 0.25) < 1e-12  # r = 37.5 sqrt(3) >> eta_s
         order = np.argsort(r.ravel())
         assert np.all(np.diff(eta.ravel()[order]) <= 1e-15)
+
+
+def _moving_case(orc):
+    h, pos, radii, fm = W.moving_bl(32)
+    return h, pos, radii, fm, make(orc, h)
+
+
+def test_regrid_same_layout_is_identity(orc):
+    h, pos, radii, fm, o = _moving_case(orc)
+    o.set_initial_data(h.id_kind, h.id_params)
+    o.advance(1)
+    before = [[o.get_field(l, b, f) for f in range(22)] for l in range(h.nlevels) for b in range(len(h.boxes[l]))]
+    o.regrid(h.boxes)
+    after = [[o.get_field(l, b, f) for f in range(22)] for l in range(h.nlevels) for b in range(len(h.boxes[l]))]
+    for a, b in zip(before, after):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+def test_regrid_prolongs_new_cells_exactly_for_quintics(orc):
+    """Moved boxes: cells that stay interior keep their values, new cells are
+    the quintic prolongation of the parent (exact for tensor quintics)."""
+    h, pos, radii, fm, o = _moving_case(orc)
+    rng = np.random.default_rng(7)
+    coef = {(a, b, c): rng.normal() for a in range(6) for b in range(6) for c in range(6)}
+    for l in range(h.nlevels):
+        for b in range(len(h.boxes[l])):
+            X, Y, Z = h.cell_centres(l, b, ghosted=True)
+            base = _poly(X / 8, Y / 8, Z / 8, coef)
+            for f in range(22):
+                o.set_field(l, b, f, (1.0 + 0.1 * f) * base, ghosted=True)
+    new = W.moving_layout(h, [(p[0] + 0.4, p[1] + 0.2, p[2]) for p in pos], radii, fm)
+    o.regrid(new)
+    h2 = W.Hierarchy(**{**h.__dict__, "boxes": new})
+    for l in range(h.nlevels):
+        for b in range(len(new[l])):
+            X, Y, Z = h2.cell_centres(l, b)
+            ex = _poly(X / 8, Y / 8, Z / 8, coef)
+            err = np.abs(o.get_field(l, b, 0) - ex).max() / np.abs(ex).max()
+            assert err < 1e-12, (l, b, err)
+
+
+def test_interpolation_exact_for_quintics(orc):
+    h, pos, radii, fm, o = _moving_case(orc)
+    rng = np.random.default_rng(8)
+    coef = {(a, b, c): rng.normal() for a in range(6) for b in range(6) for c in range(6)}
+    for l in range(h.nlevels):
+        for b in range(len(h.boxes[l])):
+            X, Y, Z = h.cell_centres(l, b, ghosted=True)
+            o.set_field(l, b, 5, _poly(X / 8, Y / 8, Z / 8, coef), ghosted=True)
+    pts = rng.uniform(-5, 5, size=(20, 3))
+    got = o.interpolate(pts, 5)
+    ex = _poly(pts[:, 0] / 8, pts[:, 1] / 8, pts[:, 2] / 8, coef)
+    np.testing.assert_allclose(got, ex, rtol=1e-12, atol=1e-12 * np.abs(ex).max())
