@@ -288,6 +288,7 @@ def run_gpu(args, rank: int, world: int):
     ms_per_step = t_max / args.steps
     value = whole_job_rate(world, fin_per_step, args.steps, t_max)
     launches = ctx.sc_launches_per_step() * args.steps
+    state_finite = ctx.sc_check_finite()
 
     # Roofline of the dominant kernels: FP64-ALU bound.  Per-launch durations
     # from CUDA events on the library's stream, on the finest level.
@@ -390,6 +391,7 @@ def run_gpu(args, rank: int, world: int):
                            "actual_zone_updates_per_s": world * act_per_step / (ms_per_step * 1e-3),
                            "l2": "state ~5 GB per replica > 129 MB L2: inputs larger than L2, no flush",
                            "stencil_tile": list(tile),
+                           "state_finite_after_timed_steps": state_finite,
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -153,6 +153,10 @@ sc_status sc_advance(sc_ctx* ctx, int n_coarse_steps);
 /* Block until the context's stream is idle; returns SC_ECUDA on a device error. */
 sc_status sc_synchronize(sc_ctx* ctx);
 
+/* Scan the interior state of every level on the device: SC_OK if every
+ * value is finite, SC_ENONFINITE otherwise.  Synchronises. */
+sc_status sc_check_finite(sc_ctx* ctx);
+
 /* Z4c constraints (H, M^x, M^y, M^z, G^x, G^y, G^z) of the current state at
  * the interior cells of one box, to a host buffer of 7 * ncell doubles
  * (constraint-major, x fastest); synchronises.  Z4c only. */

@@ -117,6 +117,7 @@ def lib():
     L.sc_time_ghost_kernels.argtypes = [P, I, I, DP, ctypes.POINTER(ctypes.c_long)]
     L.sc_debug_get_vector.argtypes = [P, I, I, I, I, I, DP]
     L.sc_regrid.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(sc_box)]
+    L.sc_check_finite.argtypes = [P]
     L.sc_interpolate.argtypes = [P, I, DP, I, DP]
     L.sc_z4c_constraints_noalloc.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), D, P]
     IP = ctypes.POINTER(ctypes.c_int)
@@ -315,6 +316,14 @@ class Context:
         ms = ctypes.c_double()
         _check(lib().sc_autotune(self.ctx, t, ctypes.byref(ms)))
         return (t[0], t[1], t[2]), ms.value
+
+    def sc_check_finite(self) -> bool:
+        """True if the evolved state is finite everywhere (device scan)."""
+        rc = lib().sc_check_finite(self.ctx)
+        if rc == SC_ENONFINITE:
+            return False
+        _check(rc)
+        return True
 
     def sc_regrid(self, boxes):
         """New boxes for every level (level 0 unchanged); updates self.h."""

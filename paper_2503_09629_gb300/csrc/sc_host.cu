@@ -1567,6 +1567,19 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   return SC_OK;
 }
 
+sc_status sc_check_finite(sc_ctx* c) {
+  if (!c) return fail(SC_EINVAL, "null context");
+  CU(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+  for (Level& L : c->lev)
+    CU(launch_nonfinite_check(L.S[L.parity], L.g.fs, c->F, L.tiles, L.ntiles, L.g.pitch, L.g.pitch * L.g.ext[1], c->flag,
+                              c->stream));
+  int h = 0;
+  CU(cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (h) return fail(SC_ENONFINITE, "non-finite value in the evolved state");
+  return SC_OK;
+}
+
 sc_status sc_debug_get_vector(sc_ctx* c, int level, int box, int vec, int field, int ghosted, double* dst) {
   sc_status st = check_box(c, level, box, field);
   if (st) return st;

@@ -361,3 +361,31 @@ def track_punctures(target, positions, dt, shift_fields=(19, 20, 21)):
     pts = np.asarray(positions, dtype=np.float64)
     beta = np.stack([target.interpolate(pts, f) for f in shift_fields], axis=1)
     return [tuple(p) for p in pts - dt * beta]
+
+
+def moving_9level(n: int = 32, sep: float = 6.0, m: float = 0.5):
+    """configs[3]-structured moving-box workload at a size one GPU runs in
+    about a second per coarse step: Z4c Brill-Lindquist m = 0.5 at x = +-3,
+    9 levels over [-128,128]^3 (level 0 n^3), levels 0-2 fixed nested cubes,
+    levels 3-8 box stacks around the punctures with radii 12, 6, 3, 1.5,
+    0.75, 0.375 (about 24 cells across at every level; stacks merge where
+    they touch).  The Gamma-driver damping uses the eta(r) profile of
+    Sec. III.A (eta_c = 2, eta_s = 40, eta_o = 0.25): with the constant
+    eta = 2, eta * dt = 4 on level 0 (dt = 2) lies outside RK4's stability
+    interval and the coarse levels blow up after about 15 coarse steps, the
+    time-step limit dt_max ~ 1/eta that the paper discusses.  The face-value configs[3] (finest radius 1.5 at h = 1/128,
+    about 1.7e8 cells and 3e10 cell updates per coarse step) needs about ten
+    minutes per coarse step at this path's rate.
+    Returns (hierarchy, positions, radii, first_moving)."""
+    L = 128.0
+    h0 = 2 * L / n
+    positions = [(-sep / 2, 0.0, 0.0), (sep / 2, 0.0, 0.0)]
+    radii = [None, None, None, 12.0, 6.0, 3.0, 1.5, 0.75, 0.375]
+    fixed = [[cube(0, n)], [cube(n // 2, n)], [cube(3 * n // 2, n)]]
+    base = Hierarchy(system=Z4C, boxes=fixed + [[] for _ in range(6)], ncells0=(n, n, n), origin=(-L, -L, -L),
+                     h0=h0, bc=BC_RADIATIVE, id_kind=ID_BRILL_LINDQUIST,
+                     id_params=[m, positions[0][0], 0.0, 0.0, m, positions[1][0], 0.0, 0.0],
+                     eta_profile=(2.0, 40.0, 0.25),
+                     name=f"z4c BL moving boxes 9-level {n}^3 over [-128,128]^3, eta(r)")
+    base.boxes = moving_layout(base, positions, radii, 3)
+    return base, positions, radii, 3

@@ -165,3 +165,17 @@ def test_eta_profile_and_averaged_lapse_parity(sc, orc):
     ctx.sc_advance(8)
     o.advance(8)
     assert max_rel_diff(fetch(ctx, h), fetch(o, h)) <= TOL
+
+
+def test_check_finite_flags_nan(sc):
+    """sc_check_finite: finite state passes, a NaN planted through the
+    public field API is reported as SC_ENONFINITE (no device fault involved)."""
+    h = W.bl_3level(20)
+    ctx = sc.Context(h)
+    ctx.sc_set_initial_data(h.id_kind, h.id_params)
+    ctx.sc_advance(1)
+    assert ctx.sc_check_finite()
+    a = ctx.sc_get_field(1, 0, 7)
+    a[3, 4, 5] = np.nan
+    ctx.sc_set_field(1, 0, 7, a)
+    assert not ctx.sc_check_finite()
