@@ -357,6 +357,29 @@ def run_gpu(args, rank: int, world: int):
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
     e2e_value = whole_job_rate(world, fin_per_step, ne2e, e2e_s * 1e3)
 
+    # The method's saving: the same hierarchy with every level at the finest
+    # time step (uniform-step mode), timed the same way.
+    uniform = None
+    if rank == 0 and args.uniform_steps > 0:
+        hu = W.bl_7level()
+        hu.subcycle = False
+        cu = sc.Context(hu)
+        cu.sc_autotune()
+        cu.sc_set_initial_data(hu.id_kind, hu.id_params)
+        cu.sc_advance(1)
+        torch.cuda.synchronize()
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u0.record(stream)
+        cu.sc_advance(args.uniform_steps)
+        u1.record(stream)
+        torch.cuda.synchronize()
+        ums = u0.elapsed_time(u1) / args.uniform_steps
+        fin_u, act_u = hu.zone_updates_per_coarse_step()
+        uniform = {"ms_per_coarse_step": ums, "zone_updates_per_s": fin_u / (ums * 1e-3),
+                   "actual_zone_updates_per_coarse_step": act_u, "subcycling_speedup": ums / ms_per_step,
+                   "steps": args.uniform_steps}
+        cu.close()
+
     # Served form vs plain per-box form on a seeded ensemble (configs[4] mix).
     serving = None
     if rank == 0 and args.serving_requests > 0:
@@ -396,7 +419,7 @@ def run_gpu(args, rank: int, world: int):
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": ne2e},
-                "gpu_launches": launches, "clocks": clk, "serving": serving}
+                "gpu_launches": launches, "clocks": clk, "serving": serving, "uniform_step_mode": uniform}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -410,6 +433,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--serving", action="store_true", help="only the serving ensemble (configs[4]), one JSON line")
     ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--uniform-steps", type=int, default=2,
+                    help="coarse steps of the same hierarchy in uniform-step mode (0: skip)")
     ap.add_argument("--serving-requests", type=int, default=64,
                     help="requests of the served-vs-plain ensemble embedded in the default line (0: skip)")
     args = ap.parse_args()

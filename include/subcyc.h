@@ -83,8 +83,10 @@ typedef struct {
  *   ghost cell's prolongation stencil (6 parent cells per dimension) must lie
  *   in the parent level's interior (proper nesting, else SC_ENESTING);
  *   outer_bc: SC_BC_RADIATIVE needs exactly one level-0 box;
- *   cfl: dt_l = cfl * h_l; subcycle must be 1 (the paper's scheme; the
- *   uniform-step comparison mode lives in the CPU oracle only);
+ *   cfl: dt_l = cfl * h_l; subcycle = 1: the paper's subcycling; 0: the
+ *   uniform-step comparison mode (Sec. IV.A): every level steps with the
+ *   finest dt in lockstep, 2^(nlevels-1) steps per coarse step, fine ghosts
+ *   from the prolonged parent stage state of the same stage;
  *   kappa1, kappa2, eta, ko_sigma: Z4c damping, Gamma-driver and
  *   Kreiss-Oliger parameters (Sec. III);
  *   cuda_stream: cudaStream_t all work is ordered on (NULL = legacy stream). */

@@ -27,7 +27,7 @@ inline int grid_for(long work, int threads) {
 __global__ void __launch_bounds__(kThreads) amr_prolong_kernel(
     const double* __restrict__ yn, const double* __restrict__ k1, const double* __restrict__ k2,
     const double* __restrict__ k3, const double* __restrict__ k4, long pfs, int psy, int psz,
-    const AmrCell* __restrict__ cells, int first, int ncells, double* __restrict__ store, int F, Weights w) {
+    const AmrCell* __restrict__ cells, int first, int ncells, double* __restrict__ store, int F, Weights w, int nvec) {
   const int nc = ncells - first;
   const long total = (long)nc * F;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kThreads) amr_prolong_kernel(
     const double* wz = w.prolong[(c.parity >> 2) & 1];
     const double* src[5] = {yn, k1, k2, k3, k4};
 #pragma unroll 1
-    for (int v = 0; v < 5; ++v) {
+    for (int v = 0; v < nvec; ++v) {
       const double* p = src[v] + (long)f * pfs + c.pbase;
       double sz = 0.0;
 #pragma unroll
@@ -70,12 +70,13 @@ __global__ void __launch_bounds__(kThreads) amr_prolong_kernel(
 __global__ void __launch_bounds__(256) amr_prolong_block_kernel(
     const double* __restrict__ yn, const double* __restrict__ k1, const double* __restrict__ k2,
     const double* __restrict__ k3, const double* __restrict__ k4, long pfs, int psy, int psz,
-    const AmrBlock* __restrict__ blocks, int nblocks, int ncells, double* __restrict__ store, int F, Weights w) {
+    const AmrBlock* __restrict__ blocks, int nblocks, int ncells, double* __restrict__ store, int F, Weights w,
+    int nvec) {
   __shared__ double sP[4][512];
   __shared__ double sX[4][256];
   __shared__ double sY[4][128];
   const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
-  const int combos = 5 * F;
+  const int combos = nvec * F;
   const int ngroups = (combos + 3) / 4;
   const long items = (long)nblocks * ngroups;
   for (long item = blockIdx.x; item < items; item += gridDim.x) {
@@ -363,22 +364,22 @@ __global__ void __launch_bounds__(kThreads) nonfinite_kernel(const double* __res
 
 cudaError_t launch_amr_prolong(const double* yn, const double* k1, const double* k2, const double* k3,
                                const double* k4, long pfs, int psy, int psz, const AmrCell* cells, int first,
-                               int ncells, double* store, int F, const Weights& w, cudaStream_t s) {
+                               int ncells, double* store, int F, const Weights& w, cudaStream_t s, int nvec) {
   if (ncells <= first) return cudaSuccess;
   amr_prolong_kernel<<<grid_for((long)(ncells - first) * F, kThreads), kThreads, 0, s>>>(
-      yn, k1, k2, k3, k4, pfs, psy, psz, cells, first, ncells, store, F, w);
+      yn, k1, k2, k3, k4, pfs, psy, psz, cells, first, ncells, store, F, w, nvec);
   return cudaGetLastError();
 }
 
 cudaError_t launch_amr_prolong_blocks(const double* yn, const double* k1, const double* k2, const double* k3,
                                       const double* k4, long pfs, int psy, int psz, const AmrBlock* blocks,
                                       int nblocks, int ncells, double* store, int F, const Weights& w,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, int nvec) {
   if (nblocks == 0) return cudaSuccess;
-  const long items = (long)nblocks * ((5 * F + 3) / 4);
+  const long items = (long)nblocks * ((nvec * F + 3) / 4);
   const int grid = (int)(items < 152L * 8 * 16 ? items : 152L * 8 * 16);
   amr_prolong_block_kernel<<<grid, 256, 0, s>>>(yn, k1, k2, k3, k4, pfs, psy, psz, blocks, nblocks, ncells, store, F,
-                                                w);
+                                                w, nvec);
   return cudaGetLastError();
 }
 

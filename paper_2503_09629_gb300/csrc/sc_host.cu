@@ -173,7 +173,7 @@ struct Level {
   int parity = 0;  // which of S[] holds the current state
 };
 
-enum OpKind { OP_PROLONG, OP_FILL, OP_STAGE, OP_RESTRICT };
+enum OpKind { OP_PROLONG, OP_FILL, OP_STAGE, OP_RESTRICT, OP_PROLONG_DIRECT };
 
 struct Op {
   OpKind kind;
@@ -184,6 +184,7 @@ struct Op {
   double* out;
   double c[4];    // OP_FILL coefficients
   double cdt;     // OP_STAGE
+  bool no_amr;    // OP_FILL: periodic images only (uniform-step mode)
 };
 
 }  // namespace
@@ -210,6 +211,7 @@ struct sc_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   long launches_per_step = 0;
   int exec_mode = SC_EXEC_GRAPH;
+  int subcycle = 1;
   int tile[3] = {32, 4, 2};  // stencil-kernel tile shape (autotuned on request)
   int eta_profile = 0;
   double eta_c = 0, eta_s = 0, eta_o = 0;
@@ -279,7 +281,7 @@ sc_status validate(const sc_desc* d) {
   if (d->system != SC_WAVE && d->system != SC_Z4C) return fail(SC_EINVAL, "unknown system %d", d->system);
   if (d->nlevels < 1 || d->nlevels > 16) return fail(SC_EINVAL, "nlevels must be 1..16");
   if (!d->nboxes || !d->boxes) return fail(SC_EINVAL, "null box arrays");
-  if (d->subcycle != 1) return fail(SC_EINVAL, "only the subcycled scheme is implemented on the GPU");
+  if (d->subcycle != 0 && d->subcycle != 1) return fail(SC_EINVAL, "subcycle must be 0 or 1");
   if (d->outer_bc != SC_BC_PERIODIC && d->outer_bc != SC_BC_RADIATIVE) return fail(SC_EINVAL, "unknown outer_bc");
   if (!(d->h0 > 0) || !(d->cfl > 0)) return fail(SC_EINVAL, "h0 and cfl must be positive");
   for (int q = 0; q < 3; ++q)
@@ -761,8 +763,67 @@ struct Emitter {
     ops.push_back(r);
   }
   void coarse_step() {
+    if (!c->subcycle) {
+      for (int q = 0; q < (1 << (c->nlev - 1)); ++q) uniform_step();
+      return;
+    }
     level_step(0, 0.0);
     if (c->nlev > 1) children(0);
+  }
+  // Uniform time step (the comparison mode of Sec. IV.A): every level steps
+  // with the finest dt, stage by stage in lockstep; refinement-boundary
+  // ghosts of a stage state are the prolonged parent stage state of the same
+  // stage; after the step the new states' ghosts come from the parents' new
+  // states, then restriction runs finest to coarsest.
+  void prolong_direct(int l, double* parent_vec, double* dst) {
+    Op o{};
+    o.kind = OP_PROLONG_DIRECT;
+    o.level = l;
+    o.in = parent_vec;
+    o.out = dst;
+    ops.push_back(o);
+  }
+  void periodic_only(int l, double* vec) {
+    Op o{};
+    o.kind = OP_FILL;
+    o.level = l;
+    o.in = vec;
+    o.no_amr = true;
+    ops.push_back(o);
+  }
+  void uniform_step() {
+    const int L = c->nlev;
+    const double dt = c->lev[L - 1].dt;
+    const double cs[3] = {0.5, 0.5, 1.0};
+    std::vector<std::array<double*, 4>> in(L);
+    for (int l = 0; l < L; ++l) in[l] = {c->lev[l].S[par[l]], c->lev[l].A, c->lev[l].B, c->lev[l].A};
+    for (int s = 1; s <= 4; ++s)
+      for (int l = 0; l < L; ++l) {
+        if (l > 0) prolong_direct(l, in[l - 1][s - 1], in[l][s - 1]);
+        periodic_only(l, in[l][s - 1]);
+        Op o{};
+        o.kind = OP_STAGE;
+        o.level = l;
+        o.stage = s;
+        o.in = in[l][s - 1];
+        o.yn = c->lev[l].S[par[l]];
+        o.out = (s < 4) ? in[l][s] : c->lev[l].S[par[l] ^ 1];
+        o.cdt = (s < 4) ? cs[s - 1] * dt : dt / 6.0;
+        ops.push_back(o);
+      }
+    for (int l = 1; l < L; ++l) {
+      prolong_direct(l, c->lev[l - 1].S[par[l - 1] ^ 1], c->lev[l].S[par[l] ^ 1]);
+      periodic_only(l, c->lev[l].S[par[l] ^ 1]);
+    }
+    for (int l = L - 1; l >= 1; --l) {
+      Op r{};
+      r.kind = OP_RESTRICT;
+      r.level = l;
+      r.in = c->lev[l].S[par[l] ^ 1];
+      r.out = c->lev[l - 1].S[par[l - 1] ^ 1];
+      ops.push_back(r);
+    }
+    for (int l = 0; l < L; ++l) par[l] ^= 1;
   }
 };
 
@@ -778,8 +839,21 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
                             L.namr_blocked, L.namr, L.amr_store, c->F, c->w, s));
       break;
     }
+    case OP_PROLONG_DIRECT: {
+      // one vector through the separable block kernel into the ghost store,
+      // then an apply with zero k coefficients (exactly the prolonged value)
+      const Level& P = c->lev[o.level - 1];
+      const int psy = P.g.pitch, psz = P.g.pitch * P.g.ext[1];
+      CU(launch_amr_prolong_blocks(o.in, o.in, o.in, o.in, o.in, P.g.fs, psy, psz, L.blocks, L.nblocks, L.namr,
+                                   L.amr_store, c->F, c->w, s, 1));
+      CU(launch_amr_prolong(o.in, o.in, o.in, o.in, o.in, P.g.fs, psy, psz, L.amr, L.namr_blocked, L.namr, L.amr_store,
+                            c->F, c->w, s, 1));
+      const double zero[4] = {0.0, 0.0, 0.0, 0.0};
+      CU(launch_amr_apply(o.out, g.fs, c->F, L.amr, L.namr, L.amr_store, zero, s));
+      break;
+    }
     case OP_FILL:
-      if (o.level > 0) CU(launch_amr_apply(o.in, g.fs, c->F, L.amr, L.namr, L.amr_store, o.c, s));
+      if (o.level > 0 && !o.no_amr) CU(launch_amr_apply(o.in, g.fs, c->F, L.amr, L.namr, L.amr_store, o.c, s));
       CU(launch_periodic_copy(o.in, g.fs, c->F, L.periodic, L.nperiodic, s));
       break;
     case OP_STAGE: {
@@ -849,7 +923,9 @@ sc_status build_graphs(sc_ctx* c) {
         else if (o.kind == OP_PROLONG)
           n += (L.nblocks ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0);
         else if (o.kind == OP_FILL)
-          n += (o.level > 0 && L.namr ? 1 : 0) + (L.nperiodic ? 1 : 0);
+          n += (o.level > 0 && L.namr && !o.no_amr ? 1 : 0) + (L.nperiodic ? 1 : 0);
+        else if (o.kind == OP_PROLONG_DIRECT)
+          n += (L.nblocks ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0) + (L.namr ? 1 : 0);
         else
           n += L.nrestr ? 1 : 0;
       }
@@ -1320,6 +1396,7 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
   c->zp = Z4cParams{d->kappa1, d->kappa2, d->eta, d->ko_sigma};
   c->stream = (cudaStream_t)d->cuda_stream;
   c->exec_mode = d->exec_mode == SC_EXEC_PER_BOX ? SC_EXEC_PER_BOX : SC_EXEC_GRAPH;
+  c->subcycle = d->subcycle;
   c->eta_profile = d->eta_profile ? 1 : 0;
   c->eta_c = d->eta_c;
   c->eta_s = d->eta_s;
@@ -1448,11 +1525,12 @@ sc_status sc_advance(sc_ctx* c, int n) {
     } else {
       CU(cudaGraphLaunch(c->graph[L0.parity], c->stream));
     }
-    L0.parity ^= 1;
+    // level 0 takes one step per coarse step when subcycling, 2^(L-1) otherwise
+    if (c->subcycle || L == 1) L0.parity ^= 1;
     c->t += L0.dt;
     for (int l = 0; l < L; ++l) {
       c->zu_finest += (double)(1L << (L - 1)) * (double)c->lev[l].interior_cells;
-      c->zu_actual += (double)(1L << l) * (double)c->lev[l].interior_cells;
+      c->zu_actual += (double)(c->subcycle ? (1L << l) : (1L << (L - 1))) * (double)c->lev[l].interior_cells;
     }
   }
   return SC_OK;

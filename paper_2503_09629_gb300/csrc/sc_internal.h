@@ -135,15 +135,16 @@ cudaError_t launch_z4c_constraints(const double* Y, const double* scratch, doubl
                                    const int* box_lo, const int* box_n, cudaStream_t s);
 
 cudaError_t launch_periodic_copy(double* vec, long fs, int F, const int2* pairs, int npairs, cudaStream_t s);
-// per-cell prolongation of AMR cells [first, ncells) of the list (store has ncells slots per vector-field)
+// per-cell prolongation of AMR cells [first, ncells) of the list (store has ncells slots per vector-field);
+// nvec = 5 prolongs y_n, k1..k4, nvec = 1 only the first vector
 cudaError_t launch_amr_prolong(const double* yn, const double* k1, const double* k2, const double* k3,
                                const double* k4, long pfs, int psy, int psz, const AmrCell* cells, int first,
-                               int ncells, double* store, int F, const Weights& w, cudaStream_t s);
+                               int ncells, double* store, int F, const Weights& w, cudaStream_t s, int nvec = 5);
 // block-separable prolongation of the ghost cells grouped in 4x4x4 blocks
 cudaError_t launch_amr_prolong_blocks(const double* yn, const double* k1, const double* k2, const double* k3,
                                       const double* k4, long pfs, int psy, int psz, const AmrBlock* blocks,
                                       int nblocks, int ncells, double* store, int F, const Weights& w,
-                                      cudaStream_t s);
+                                      cudaStream_t s, int nvec = 5);
 cudaError_t launch_amr_apply(double* vec, long fs, int F, const AmrCell* cells, int ncells,
                              const double* store, const double* c4, cudaStream_t s);
 cudaError_t launch_restrict(double* parent, long pfs, const double* fine, long ffs, int fsy, int fsz,

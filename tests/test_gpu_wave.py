@@ -150,3 +150,31 @@ def test_autotune_keeps_results_bitwise(sc):
     for la, lb in zip(*out):
         for a, b in zip(la, lb):
             assert np.array_equal(a, b)
+
+
+def test_uniform_step_mode_matches_oracle(sc, orc):
+    """Uniform time step on every level (the comparison mode of Sec. IV.A):
+    GPU against the oracle's uniform mode."""
+    h = W.standing_wave_2level(24, subcycle=False)
+    err = _parity(sc, orc, h, 6)
+    assert err <= TOL, err
+
+
+def test_uniform_and_subcycled_agree_to_truncation(sc):
+    """Sec. IV.A: subcycled and uniform-step runs differ by less than the
+    error of either against the exact standing wave."""
+    t_end = 0.125
+    out = {}
+    for sub in (True, False):
+        h = W.standing_wave_2level(32, subcycle=sub)
+        c = sc.Context(h)
+        c.sc_set_initial_data(h.id_kind, h.id_params)
+        c.sc_advance(int(round(t_end / (h.cfl * h.h0))))
+        X, Y, Z = h.cell_centres(1, 0)
+        u = c.sc_get_field(1, 0, 0)
+        exact = np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y) * np.sin(2 * np.pi * Z) * np.cos(
+            2 * np.sqrt(3) * np.pi * c.sc_get_time())
+        out[sub] = (u, np.abs(u - exact).max())
+        c.close()
+    diff = np.abs(out[True][0] - out[False][0]).max()
+    assert diff < out[True][1] and diff < out[False][1]

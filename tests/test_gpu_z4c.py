@@ -179,3 +179,9 @@ def test_check_finite_flags_nan(sc):
     a[3, 4, 5] = np.nan
     ctx.sc_set_field(1, 0, 7, a)
     assert not ctx.sc_check_finite()
+
+
+def test_uniform_step_mode_z4c_matches_oracle(sc, orc):
+    h = W.bl_3level(20)
+    h.subcycle = False
+    assert _parity(sc, orc, h, 1) <= TOL
