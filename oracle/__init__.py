@@ -59,6 +59,7 @@ def lib():
         DP = ctypes.POINTER(ctypes.c_double)
         IP = ctypes.POINTER(ctypes.c_int)
         L.orc_create.argtypes = [I, I, IP, IP, IP, DP, D, I, D, I, DP, ctypes.POINTER(P)]
+        L.orc_create_order.argtypes = [I, I, IP, IP, IP, DP, D, I, D, I, DP, I, ctypes.POINTER(P)]
         L.orc_destroy.argtypes = [P]
         L.orc_nfields.argtypes = [P]
         L.orc_set_bc_callback.argtypes = [P, BC_FN, P]
@@ -117,7 +118,7 @@ class Oracle:
     """
 
     def __init__(self, system, boxes, ncells0, origin, h0, bc=BC_PERIODIC, cfl=0.25,
-                 subcycle=True, kappa1=0.02, kappa2=0.0, eta=2.0, ko_sigma=0.3, eta_profile=None):
+                 subcycle=True, kappa1=0.02, kappa2=0.0, eta=2.0, ko_sigma=0.3, eta_profile=None, fd_order=4):
         L = lib()
         self.system = system
         self.boxes = [[(tuple(lo), tuple(hi)) for lo, hi in lvl] for lvl in boxes]
@@ -131,11 +132,12 @@ class Oracle:
         org = (ctypes.c_double * 3)(*origin)
         prm = (ctypes.c_double * 4)(kappa1, kappa2, eta, ko_sigma)
         h = ctypes.c_void_p()
-        rc = L.orc_create(system, len(boxes), nb, fb, nc, org, h0, bc, cfl, 1 if subcycle else 0, prm,
-                          ctypes.byref(h))
+        rc = L.orc_create_order(system, len(boxes), nb, fb, nc, org, h0, bc, cfl, 1 if subcycle else 0, prm,
+                                int(fd_order), ctypes.byref(h))
         if rc != 0:
             raise ValueError(f"oracle create failed ({rc})")
         self.h = h
+        self.ghost = 4 if fd_order == 8 else 3
         self.F = L.orc_nfields(h)
         self._cb = None
         if eta_profile is not None:
@@ -149,7 +151,7 @@ class Oracle:
 
     def shape(self, level, box, ghosted=False):
         lo, hi = self.boxes[level][box]
-        n = [hi[d] - lo[d] + 1 + (2 * GHOST if ghosted else 0) for d in range(3)]
+        n = [hi[d] - lo[d] + 1 + (2 * self.ghost if ghosted else 0) for d in range(3)]
         return (n[2], n[1], n[0])
 
     def set_bc_callback(self, fn):
@@ -257,7 +259,7 @@ class Oracle:
         """Cell-centre coordinates (z, y, x order arrays) of a box."""
         lo, hi = self.boxes[level][box]
         h = h0 / 2 ** level
-        g = GHOST if ghosted else 0
+        g = self.ghost if ghosted else 0
         ax = [origin[d] + (np.arange(lo[d] - g, hi[d] + 1 + g) + 0.5) * h for d in range(3)]
         Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
         return X, Y, Z

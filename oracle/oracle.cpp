@@ -6,7 +6,8 @@
 // with the CUDA library.  Built with -O2 -ffp-contract=off.
 //
 // Layout: every level is a list of boxes; every box stores each field as its
-// own array over the box interior plus 3 ghost cells per side, x fastest.
+// own array over the box interior plus g ghost cells per side (3 for 4th-order
+// differences, 4 for 8th order), x fastest.
 // Ghost cells are classified once: copied from a sibling box interior (same
 // level, periodic wrap included), filled from the parent level by dense output
 // and prolongation (refinement boundary), or physical (outer boundary).
@@ -25,7 +26,6 @@
 
 namespace {
 
-const int G = 3;  // ghost width
 
 // ---------------------------------------------------------------------------
 // Operation counter (used once, to count the flops of the Z4c formulation).
@@ -108,6 +108,7 @@ double amr_value(double y, const double* k, double H, double theta0, int which) 
 enum { V_Y = 0, V_YOLD = 1, V_STAGE = 2, V_K1 = 3, V_NVEC = 7 };
 
 struct BoxData {
+  int g = 3;  // ghost width: 3 for 4th-order differences, 4 for 8th order
   int lo[3], hi[3];
   int n[3], N[3];
   long vol;
@@ -120,7 +121,7 @@ struct BoxData {
   std::vector<double> amr_P;        // prolonged parent vectors: [cell][5][F]
   std::vector<long> phys_cell;      // outer-boundary ghost cells
   long off(int i, int j, int k) const {
-    return ((long)(k + G) * N[1] + (j + G)) * N[0] + (i + G);
+    return ((long)(k + g) * N[1] + (j + g)) * N[0] + (i + g);
   }
 };
 
@@ -132,6 +133,7 @@ struct Level {
 
 struct Hier {
   int system, F, nlev, bc, subcycle;
+  int order;  // finite-difference order of the right-hand sides: 4 or 8 (Sec. III.C)
   double cfl, h0, origin[3];
   int ncells0[3];
   double kappa1, kappa2, eta, sigma;
@@ -187,7 +189,7 @@ int find_ghosted(const Hier& H, int l, const int* g, int* li) {
       for (int m = -1; m <= 1 && !found; ++m) {
         if (m != 0 && H.bc != ORC_BC_PERIODIC) continue;
         int gg = g[d] + m * L.ext[d];
-        if (gg >= B.lo[d] - G && gg <= B.hi[d] + G) { loc[d] = gg - B.lo[d]; found = true; }
+        if (gg >= B.lo[d] - B.g && gg <= B.hi[d] + B.g) { loc[d] = gg - B.lo[d]; found = true; }
       }
       ok = found;
     }
@@ -242,16 +244,29 @@ void restrict_stencil_1d(int C, int* nodes, double* w) {
 // ---------------------------------------------------------------------------
 // Right-hand sides.
 
-// Scalar wave (Sec. IV.A): d_t u = Pi, d_t Pi = Laplacian u; 4th-order centred.
-void wave_rhs_cell(const BoxData& B, const double* Y, double* K, int i, int j, int k, double h) {
+// Centred derivative stencils.  4th order over offsets -2..2:
+const double D1W[5] = {1.0, -8.0, 0.0, 8.0, -1.0};       // / (12 h)
+const double D2W[5] = {-1.0, 16.0, -30.0, 16.0, -1.0};   // / (12 h^2)
+// 8th order over offsets -4..4 (the paper's production differences, Sec. III.C):
+const double D1W8[9] = {3.0, -32.0, 168.0, -672.0, 0.0, 672.0, -168.0, 32.0, -3.0};              // / (840 h)
+const double D2W8[9] = {-9.0, 128.0, -1008.0, 8064.0, -14350.0, 8064.0, -1008.0, 128.0, -9.0};  // / (5040 h^2)
+
+// Scalar wave (Sec. IV.A): d_t u = Pi, d_t Pi = Laplacian u; centred differences of the chosen order.
+void wave_rhs_cell(const BoxData& B, const double* Y, double* K, int i, int j, int k, double h, int order) {
   const long c = B.off(i, j, k);
   const long s[3] = {1, (long)B.N[0], (long)B.N[0] * B.N[1]};
   const double* u = Y;
   const double* pi = Y + B.vol;
   double lap = 0.0;
   for (int d = 0; d < 3; ++d) {
-    lap += (-u[c - 2 * s[d]] + 16.0 * u[c - s[d]] - 30.0 * u[c] + 16.0 * u[c + s[d]] - u[c + 2 * s[d]]) /
-           (12.0 * h * h);
+    if (order == 8) {
+      double acc = 0.0;
+      for (int m = 0; m < 9; ++m) acc += D2W8[m] * u[c + (m - 4) * s[d]];
+      lap += acc / (5040.0 * h * h);
+    } else {
+      lap += (-u[c - 2 * s[d]] + 16.0 * u[c - s[d]] - 30.0 * u[c] + 16.0 * u[c + s[d]] - u[c + 2 * s[d]]) /
+             (12.0 * h * h);
+    }
   }
   K[c] = pi[c];
   K[B.vol + c] = lap;
@@ -447,36 +462,39 @@ void z4c_point(const T* u, const T (*du)[3], const T (*dd)[6], T* rhs, double ka
   if (diag) { diag[0] = Rsc; diag[1] = AA; diag[2] = Kt; }
 }
 
-// 4th-order centred derivative stencils (weights over offsets -2..2).
-const double D1W[5] = {1.0, -8.0, 0.0, 8.0, -1.0};       // / (12 h)
-const double D2W[5] = {-1.0, 16.0, -30.0, 16.0, -1.0};   // / (12 h^2)
 // Kreiss-Oliger with r = 4 (Sec. III.C): Q u = sigma / (64 h) sum_d delta_d^6 u.
 const double KOW[7] = {1.0, -6.0, 15.0, -20.0, 15.0, -6.0, 1.0};
 
 template <class T>
-void z4c_derivs(const BoxData& B, const double* Y, long c, double h, T (*u)[1], T (*du)[3], T (*dd)[6], T* ko) {
+void z4c_derivs(const BoxData& B, const double* Y, long c, double h, T (*u)[1], T (*du)[3], T (*dd)[6], T* ko,
+                int order = 4) {
   const long s[3] = {1, (long)B.N[0], (long)B.N[0] * B.N[1]};
+  const int R = order / 2;  // reach of the derivative stencils
+  const double* w1 = order == 8 ? D1W8 : D1W;
+  const double* w2 = order == 8 ? D2W8 : D2W;
+  const double n1 = order == 8 ? 840.0 : 12.0, n2 = order == 8 ? 5040.0 : 12.0;
   for (int f = 0; f < NZ4C; ++f) {
     const double* p = Y + (long)f * B.vol;
     u[f][0] = T(p[c]);
     for (int d = 0; d < 3; ++d) {
       T acc = T(0.0);
-      for (int m = 0; m < 5; ++m) acc += T(D1W[m]) * T(p[c + (m - 2) * s[d]]);
-      du[f][d] = acc / T(12.0 * h);
+      for (int m = 0; m <= 2 * R; ++m) acc += T(w1[m]) * T(p[c + (m - R) * s[d]]);
+      du[f][d] = acc / T(n1 * h);
     }
     for (int q = 0; q < 6; ++q) {
       const int a = SYMI[q], b = SYMJ[q];
       T acc = T(0.0);
       if (a == b) {
-        for (int m = 0; m < 5; ++m) acc += T(D2W[m]) * T(p[c + (m - 2) * s[a]]);
-        dd[f][q] = acc / T(12.0 * h * h);
+        for (int m = 0; m <= 2 * R; ++m) acc += T(w2[m]) * T(p[c + (m - R) * s[a]]);
+        dd[f][q] = acc / T(n2 * h * h);
       } else {
-        for (int m = 0; m < 5; ++m)
-          for (int n = 0; n < 5; ++n) {
-            if (D1W[m] == 0.0 || D1W[n] == 0.0) continue;
-            acc += T(D1W[m] * D1W[n]) * T(p[c + (m - 2) * s[a] + (n - 2) * s[b]]);
+        // mixed: product of the two first-derivative stencils
+        for (int m = 0; m <= 2 * R; ++m)
+          for (int n = 0; n <= 2 * R; ++n) {
+            if (w1[m] == 0.0 || w1[n] == 0.0) continue;
+            acc += T(w1[m] * w1[n]) * T(p[c + (m - R) * s[a] + (n - R) * s[b]]);
           }
-        dd[f][q] = acc / T(144.0 * h * h);
+        dd[f][q] = acc / T(n1 * n1 * h * h);
       }
     }
     T k = T(0.0);
@@ -485,6 +503,9 @@ void z4c_derivs(const BoxData& B, const double* Y, long c, double h, T (*u)[1], 
     ko[f] = k;
   }
 }
+
+void z4c_rhs_cell(const Hier& H, const BoxData& B, const double* Y, double* K, int i, int j, int k, double h,
+                  const double* x);
 
 // Gamma-driver damping: the constant eta, or the profile of Sec. III.A,
 // eta(r) = (eta_c - eta_o) exp(-(r / eta_s)^4) + eta_o, r the coordinate radius.
@@ -498,7 +519,7 @@ void z4c_rhs_cell(const Hier& H, const BoxData& B, const double* Y, double* K, i
                   const double* x) {
   const long c = B.off(i, j, k);
   double u[NZ4C][1], du[NZ4C][3], dd[NZ4C][6], ko[NZ4C], uu[NZ4C], rhs[NZ4C];
-  z4c_derivs<double>(B, Y, c, h, u, du, dd, ko);
+  z4c_derivs<double>(B, Y, c, h, u, du, dd, ko, H.order);
   for (int f = 0; f < NZ4C; ++f) uu[f] = u[f][0];
   z4c_point<double>(uu, du, dd, rhs, H.kappa1, H.kappa2, eta_at(H, x));
   for (int f = 0; f < NZ4C; ++f) K[(long)f * B.vol + c] = rhs[f] + H.sigma / (64.0 * h) * ko[f];
@@ -525,8 +546,8 @@ void radiative_rhs_cell(const Hier& H, const BoxData& B, const double* Y, double
     double adv = 0.0;
     for (int d = 0; d < 3; ++d) {
       double der;
-      if (li[d] == -G) der = (-3.0 * p[c] + 4.0 * p[c + s[d]] - p[c + 2 * s[d]]) / (2.0 * h);
-      else if (li[d] == B.n[d] + G - 1) der = (3.0 * p[c] - 4.0 * p[c - s[d]] + p[c - 2 * s[d]]) / (2.0 * h);
+      if (li[d] == -B.g) der = (-3.0 * p[c] + 4.0 * p[c + s[d]] - p[c + 2 * s[d]]) / (2.0 * h);
+      else if (li[d] == B.n[d] + B.g - 1) der = (3.0 * p[c] - 4.0 * p[c - s[d]] + p[c - 2 * s[d]]) / (2.0 * h);
       else der = (p[c + s[d]] - p[c - s[d]]) / (2.0 * h);
       adv += (x[d] / r) * der;
     }
@@ -550,12 +571,12 @@ bool evolves_shell(const Hier& H, int l) { return l == 0 && H.bc == ORC_BC_RADIA
 // k = f(Y) on the evolved cells of one box.
 void rhs_box(const Hier& H, int l, const BoxData& B, const double* Y, double* K) {
   const double h = H.lev[l].h;
-  for (int k = -G; k < B.n[2] + G; ++k)
-    for (int j = -G; j < B.n[1] + G; ++j)
-      for (int i = -G; i < B.n[0] + G; ++i) {
+  for (int k = -B.g; k < B.n[2] + B.g; ++k)
+    for (int j = -B.g; j < B.n[1] + B.g; ++j)
+      for (int i = -B.g; i < B.n[0] + B.g; ++i) {
         if (is_interior(B, i, j, k)) {
           if (H.system == ORC_WAVE) {
-            wave_rhs_cell(B, Y, K, i, j, k, h);
+            wave_rhs_cell(B, Y, K, i, j, k, h, H.order);
           } else {
             double x[3];
             cell_centre(H, l, B, i, j, k, x);
@@ -572,9 +593,9 @@ void rhs_box(const Hier& H, int l, const BoxData& B, const double* Y, double* K)
 // Apply fn(local offset) over the evolved cells of a box.
 template <class Fn>
 void for_evolved(const Hier& H, int l, const BoxData& B, Fn fn) {
-  for (int k = -G; k < B.n[2] + G; ++k)
-    for (int j = -G; j < B.n[1] + G; ++j)
-      for (int i = -G; i < B.n[0] + G; ++i)
+  for (int k = -B.g; k < B.n[2] + B.g; ++k)
+    for (int j = -B.g; j < B.n[1] + B.g; ++j)
+      for (int i = -B.g; i < B.n[0] + B.g; ++i)
         if (is_interior(B, i, j, k) || evolves_shell(H, l)) fn(B.off(i, j, k));
 }
 
@@ -701,9 +722,9 @@ void fill_physical_callback(Hier& H, int vec, int which, double t_n, double dt) 
     std::vector<double> xyz(3 * (size_t)np), out((size_t)H.F * np);
     for (int p = 0; p < np; ++p) {
       long o = B.phys_cell[p];
-      const int i = (int)(o % B.N[0]) - G;
-      const int j = (int)((o / B.N[0]) % B.N[1]) - G;
-      const int k = (int)(o / ((long)B.N[0] * B.N[1])) - G;
+      const int i = (int)(o % B.N[0]) - B.g;
+      const int j = (int)((o / B.N[0]) % B.N[1]) - B.g;
+      const int k = (int)(o / ((long)B.N[0] * B.N[1])) - B.g;
       cell_centre(H, 0, B, i, j, k, &xyz[3 * (size_t)p]);
     }
     H.cb(H.cb_user, which, t_n, dt, np, xyz.data(), out.data());
@@ -871,9 +892,9 @@ int classify(Hier& H) {
     Level& L = H.lev[l];
     for (size_t b = 0; b < L.boxes.size(); ++b) {
       BoxData& B = L.boxes[b];
-      for (int k = -G; k < B.n[2] + G; ++k)
-        for (int j = -G; j < B.n[1] + G; ++j)
-          for (int i = -G; i < B.n[0] + G; ++i) {
+      for (int k = -B.g; k < B.n[2] + B.g; ++k)
+        for (int j = -B.g; j < B.n[1] + B.g; ++j)
+          for (int i = -B.g; i < B.n[0] + B.g; ++i) {
             if (is_interior(B, i, j, k)) continue;
             const long o = B.off(i, j, k);
             int g[3] = {B.lo[0] + i, B.lo[1] + j, B.lo[2] + k};
@@ -925,6 +946,13 @@ extern "C" {
 int orc_create(int system, int nlevels, const int* nboxes, const int* boxes, const int* ncells0,
                const double* origin, double h0, int bc, double cfl, int subcycle, const double* params,
                void** out) {
+  return orc_create_order(system, nlevels, nboxes, boxes, ncells0, origin, h0, bc, cfl, subcycle, params, 4, out);
+}
+
+int orc_create_order(int system, int nlevels, const int* nboxes, const int* boxes, const int* ncells0,
+                     const double* origin, double h0, int bc, double cfl, int subcycle, const double* params,
+                     int fd_order, void** out) {
+  if (fd_order != 4 && fd_order != 8) return fail(-1, "fd_order must be 4 or 8");
   if (!out || nlevels < 1 || !nboxes || !boxes || !ncells0 || !origin) return fail(-1, "bad arguments");
   if (system != ORC_WAVE && system != ORC_Z4C) return fail(-1, "unknown system");
   Hier* H = new Hier();
@@ -933,6 +961,7 @@ int orc_create(int system, int nlevels, const int* nboxes, const int* boxes, con
   H->nlev = nlevels;
   H->bc = bc;
   H->subcycle = subcycle;
+  H->order = fd_order;
   H->cfl = cfl;
   H->h0 = h0;
   for (int d = 0; d < 3; ++d) { H->origin[d] = origin[d]; H->ncells0[d] = ncells0[d]; }
@@ -957,13 +986,14 @@ int orc_create(int system, int nlevels, const int* nboxes, const int* boxes, con
     if (nboxes[l] < 1) { delete H; return fail(-1, "empty level"); }
     for (int b = 0; b < nboxes[l]; ++b, ++bi) {
       BoxData B;
+      B.g = fd_order == 8 ? 4 : 3;
       for (int d = 0; d < 3; ++d) {
         B.lo[d] = boxes[6 * bi + d];
         B.hi[d] = boxes[6 * bi + 3 + d];
         if (B.hi[d] < B.lo[d] || B.lo[d] < 0 || B.hi[d] >= L.ext[d]) { delete H; return fail(-1, "box outside level"); }
         if (l > 0 && ((B.lo[d] & 1) || !(B.hi[d] & 1))) { delete H; return fail(-4, "fine box not aligned to parent cells"); }
         B.n[d] = B.hi[d] - B.lo[d] + 1;
-        B.N[d] = B.n[d] + 2 * G;
+        B.N[d] = B.n[d] + 2 * B.g;
       }
       B.vol = (long)B.N[0] * B.N[1] * B.N[2];
       for (int v = 0; v < V_NVEC; ++v) B.v[v].assign((size_t)H->F * B.vol, 0.0);
@@ -1059,9 +1089,9 @@ int orc_set_initial_data(void* h, int kind, const double* p, int np) {
   Hier* H = static_cast<Hier*>(h);
   for (int l = 0; l < H->nlev; ++l)
     for (BoxData& B : H->lev[l].boxes)
-      for (int k = -G; k < B.n[2] + G; ++k)
-        for (int j = -G; j < B.n[1] + G; ++j)
-          for (int i = -G; i < B.n[0] + G; ++i) {
+      for (int k = -B.g; k < B.n[2] + B.g; ++k)
+        for (int j = -B.g; j < B.n[1] + B.g; ++j)
+          for (int i = -B.g; i < B.n[0] + B.g; ++i) {
             double x[3];
             cell_centre(*H, l, B, i, j, k, x);
             const long o = B.off(i, j, k);
@@ -1208,7 +1238,7 @@ int orc_constraints(void* h, int l, int b, double* out) {
       for (int i = 0; i < B.n[0]; ++i, ++q) {
         const long c = B.off(i, j, k);
         double u[NZ4C][1], du[NZ4C][3], dd[NZ4C][6], ko[NZ4C];
-        z4c_derivs<double>(B, Y, c, hh, u, du, dd, ko);
+        z4c_derivs<double>(B, Y, c, hh, u, du, dd, ko, H->order);
         double uu[NZ4C], rhs[NZ4C], diag[3];
         for (int f = 0; f < NZ4C; ++f) uu[f] = u[f][0];
         z4c_point<double>(uu, du, dd, rhs, H->kappa1, H->kappa2, H->eta, diag);
@@ -1301,11 +1331,10 @@ int orc_constraints(void* h, int l, int b, double* out) {
 int orc_regrid(void* h, const int* nboxes, const int* boxes) {
   Hier* H = static_cast<Hier*>(h);
   const int L = H->nlev;
-  std::vector<int> ncells(3);
   void* nh = nullptr;
   double prm[4] = {H->kappa1, H->kappa2, H->eta, H->sigma};
-  const int rc = orc_create(H->system, L, nboxes, boxes, H->ncells0, H->origin, H->h0, H->bc, H->cfl, H->subcycle,
-                            prm, &nh);
+  const int rc = orc_create_order(H->system, L, nboxes, boxes, H->ncells0, H->origin, H->h0, H->bc, H->cfl,
+                                  H->subcycle, prm, H->order, &nh);
   if (rc) return rc;
   Hier* N = static_cast<Hier*>(nh);
   if (N->lev[0].boxes.size() != H->lev[0].boxes.size()) {
@@ -1420,7 +1449,7 @@ int orc_interpolate(void* h, int npts, const double* xyz, int field, double* out
 void orc_flop_counts(double* counts) {
   for (int q = 0; q < 4; ++q) g_ops[q] = 0.0;
   BoxData B;
-  for (int d = 0; d < 3; ++d) { B.lo[d] = 0; B.hi[d] = 0; B.n[d] = 1; B.N[d] = 1 + 2 * G; }
+  for (int d = 0; d < 3; ++d) { B.lo[d] = 0; B.hi[d] = 0; B.n[d] = 1; B.N[d] = 1 + 2 * B.g; }
   B.vol = (long)B.N[0] * B.N[1] * B.N[2];
   std::vector<double> Y((size_t)NZ4C * B.vol, 1.0);
   Cnt u[NZ4C][1], du[NZ4C][3], dd[NZ4C][6], ko[NZ4C], uu[NZ4C], rhs[NZ4C];

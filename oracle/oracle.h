@@ -34,6 +34,12 @@ typedef void (*orc_bc_fn)(void* user, int which, double t_n, double dt, int npts
 int orc_create(int system, int nlevels, const int* nboxes, const int* boxes,
                const int* ncells0, const double* origin, double h0, int bc,
                double cfl, int subcycle, const double* params, void** out);
+/* As orc_create with the finite-difference order of the right-hand sides:
+ * 4 (3 ghost cells per box) or 8 (the paper's production setting, 4 ghost
+ * cells); Kreiss-Oliger dissipation stays r = 4. */
+int orc_create_order(int system, int nlevels, const int* nboxes, const int* boxes,
+                     const int* ncells0, const double* origin, double h0, int bc,
+                     double cfl, int subcycle, const double* params, int fd_order, void** out);
 void orc_destroy(void* h);
 int orc_nfields(void* h);
 int orc_set_bc_callback(void* h, orc_bc_fn fn, void* user);

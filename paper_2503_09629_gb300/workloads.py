@@ -3,7 +3,8 @@
 This module holds geometry and seeded random inputs only -- none of the
 method's arithmetic.  Both the CUDA path and the CPU oracle are fed from here.
 
-Workloads (cell-centred grids, refinement factor 2, 3 ghost cells):
+Workloads (cell-centred grids, refinement factor 2, 3 ghost cells for 4th-order
+differences and 4 for 8th order):
   * ``standing_wave_2level(n)``: periodic [0,1)^3, level 0 n^3, one fine box
     over [0.25,0.75]^3; u = sin(2 pi x) sin(2 pi y) sin(2 pi z), Pi = 0.
   * ``gaussian_3level(n, seed)``: periodic [0,1)^3, 3 levels; levels 1 and 2
@@ -44,6 +45,7 @@ class Hierarchy:
     eta: float = 2.0
     ko_sigma: float = 0.3
     eta_profile: Optional[Tuple[float, float, float]] = None  # (eta_c, eta_s, eta_o) of Sec. III.A
+    fd_order: int = 4  # finite-difference order of the right-hand sides (4 or 8)
     id_kind: int = ID_STANDING_WAVE
     id_params: List[float] = field(default_factory=list)
     name: str = ""
@@ -68,10 +70,14 @@ class Hierarchy:
     def nfields(self) -> int:
         return 2 if self.system == WAVE else 22
 
+    @property
+    def ghost(self) -> int:
+        return 4 if self.fd_order == 8 else 3
+
     def cell_centres(self, level: int, box: int, ghosted: bool = False):
         lo, hi = self.boxes[level][box]
         h = self.h0 / 2 ** level
-        g = 3 if ghosted else 0
+        g = self.ghost if ghosted else 0
         ax = [self.origin[d] + (np.arange(lo[d] - g, hi[d] + 1 + g) + 0.5) * h for d in range(3)]
         Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
         return X, Y, Z
@@ -81,6 +87,8 @@ class Hierarchy:
                   kappa2=self.kappa2, eta=self.eta, ko_sigma=self.ko_sigma)
         if self.eta_profile is not None:
             kw["eta_profile"] = self.eta_profile
+        if self.fd_order != 4:
+            kw["fd_order"] = self.fd_order
         return kw
 
 

@@ -12,8 +12,8 @@ def init_arrays(h, noise_seed=None):
             for l in range(h.nlevels)]
 
 
-def _interior(a):
-    return a[:, 3:-3, 3:-3, 3:-3]
+def _interior(a, g=3):
+    return a[:, g:-g, g:-g, g:-g]
 
 
 def load(target, h, arrays, ghosted_level0=None):
@@ -27,7 +27,7 @@ def load(target, h, arrays, ghosted_level0=None):
             a = arrays[l][b]
             g = ghosted_level0 and l == 0
             for f in range(a.shape[0]):
-                setf(l, b, f, a[f] if g else _interior(a)[f], ghosted=g)
+                setf(l, b, f, a[f] if g else _interior(a, h.ghost)[f], ghosted=g)
 
 
 def fetch(target, h):

@@ -192,6 +192,36 @@ def test_wave_rhs_exact_on_quintics(orc):
     assert np.abs(rhs6[1][s] - 30 * X[s] ** 4).max() > 1e-4
 
 
+
+def test_wave_rhs_8th_order_exact_to_degree_9(orc):
+    """Sec. III.C production differences (8th order, 9-point stencils, 4
+    ghost cells): the discrete Laplacian is exact on polynomials of degree
+    <= 9 and not on degree 10."""
+    h = W.Hierarchy(system=W.WAVE, boxes=[[W.cube(0, 8)]], ncells0=(8, 8, 8), origin=(0.2, -0.1, 0.3),
+                    h0=0.1, bc=2, fd_order=8)
+    o = make(orc, h)
+    X, Y, Z = h.cell_centres(0, 0, ghosted=True)
+    assert X.shape == (16, 16, 16)
+    u = X ** 9 - 2 * X ** 3 * Y ** 6 + Y * Z ** 8 + 3 * Z ** 2
+    lap = (72 * X ** 7 - 12 * X * Y ** 6 - 60 * X ** 3 * Y ** 4 + 56 * Y * Z ** 6 + 6)
+    pi = np.cos(Y) * Z
+    rhs = o.rhs_box(0, 0, np.stack([u, pi]))
+    s = (slice(4, -4),) * 3
+    np.testing.assert_allclose(rhs[0][s], pi[s], rtol=0, atol=0)
+    np.testing.assert_allclose(rhs[1][s], lap[s], rtol=1e-9, atol=1e-9)
+    u10 = X ** 10
+    rhs10 = o.rhs_box(0, 0, np.stack([u10, pi]))
+    assert np.abs(rhs10[1][s] - 90 * X[s] ** 8).max() > 1e-6
+    # the 4th-order Laplacian is not exact on the degree-9 polynomial
+    h4 = W.Hierarchy(system=W.WAVE, boxes=[[W.cube(0, 10)]], ncells0=(10, 10, 10), origin=(0.1, -0.2, 0.2),
+                     h0=0.1, bc=2)
+    X4, Y4, Z4 = h4.cell_centres(0, 0, ghosted=True)
+    u4 = X4 ** 9 - 2 * X4 ** 3 * Y4 ** 6 + Y4 * Z4 ** 8 + 3 * Z4 ** 2
+    r4 = make(orc, h4).rhs_box(0, 0, np.stack([u4, np.cos(Y4) * Z4]))
+    lap4 = 72 * X4 ** 7 - 12 * X4 * Y4 ** 6 - 60 * X4 ** 3 * Y4 ** 4 + 56 * Y4 * Z4 ** 6 + 6
+    assert np.abs(r4[1] - lap4)[(slice(3, -3),) * 3].max() > 1e-6
+
+
 # --------------------------------------------------------- end-to-end exactness
 def _cubic_wave_solution(rng):
     """u0, Pi0 of total degree 3: Delta^2 = 0, so the semi-discrete system is
@@ -222,14 +252,16 @@ def _cubic_wave_solution(rng):
     return state
 
 
-@pytest.mark.parametrize("nlev", [2, 3])
-def test_subcycling_exact_for_cubic_wave(orc, nlev):
+@pytest.mark.parametrize("nlev,fd_order", [(2, 4), (3, 4), (3, 8)])
+def test_subcycling_exact_for_cubic_wave(orc, nlev, fd_order):
     """Whole algorithm of Sec. II (dense output, Taylor stages, prolongation,
     restriction, recursion) on a problem where every approximation is exact:
-    the subcycled run must reproduce the exact solution to roundoff."""
+    the subcycled run must reproduce the exact solution to roundoff.  With
+    8th-order differences every box carries 4 ghost layers, all of them
+    filled by dense output, sibling copies or the boundary callback."""
     boxes = [[W.cube(0, 24)], [W.cube(12, 24)], [W.cube(36, 24)]][:nlev]
     h = W.Hierarchy(system=W.WAVE, boxes=boxes, ncells0=(24, 24, 24), origin=(-0.75, -0.75, -0.75),
-                    h0=1.0 / 16, bc=2)
+                    h0=1.0 / 16, bc=2, fd_order=fd_order)
     o = make(orc, h)
     state = _cubic_wave_solution(np.random.default_rng(5))
 
@@ -318,13 +350,15 @@ def test_subcycled_matches_uniform_step(standing_runs):
 
 
 # ----------------------------------------------------------- structural identity
-def test_split_boxes_bitwise(orc):
+@pytest.mark.parametrize("fd_order", [4, 8])
+def test_split_boxes_bitwise(orc, fd_order):
     """A level split into several boxes evolves bitwise like one box (ghost
     exchange between siblings replaces the missing neighbours exactly)."""
     one = W.standing_wave_2level(16)
+    one.fd_order = fd_order
     many = W.Hierarchy(system=W.WAVE, boxes=[W.split_uniform(W.cube(0, 16), (2, 3, 2)),
                                              W.split_uniform(W.cube(8, 16), (2, 2, 3))],
-                       ncells0=(16, 16, 16), origin=(0.0, 0.0, 0.0), h0=1.0 / 16)
+                       ncells0=(16, 16, 16), origin=(0.0, 0.0, 0.0), h0=1.0 / 16, fd_order=fd_order)
     a = make(orc, one)
     b = make(orc, many)
     for o in (a, b):
@@ -419,29 +453,33 @@ def _gauge_wave_fields(n, A=0.1):
     return vals, dts
 
 
-def test_z4c_rhs_matches_gauge_wave_time_derivative(orc):
+@pytest.mark.parametrize("fd_order,sizes,min_order", [(4, (12, 24, 48), 3.7), (8, (16, 24, 32), 7.5)])
+def test_z4c_rhs_matches_gauge_wave_time_derivative(orc, fd_order, sizes, min_order):
     """Sec. III.A: for an exact vacuum solution the Z4c right-hand side of
     the non-gauge variables (W, gt, Khat, At, Gamt, Theta) equals their true
-    time derivative up to the 4th-order truncation error of the stencils.
-    The gauge wave exercises the lapse terms, the extrinsic-curvature terms
-    and the full Ricci tensor with all index components."""
+    time derivative up to the truncation error of the stencils: 4th order,
+    or 8th order for the production differences of Sec. III.C (mixed
+    derivatives included -- the wave runs along x + y).  The gauge wave
+    exercises the lapse terms, the extrinsic-curvature terms and the full
+    Ricci tensor with all index components."""
     vals, dts = _gauge_wave_fields(0)
     errs = []
-    for n in (12, 24, 48):
+    for n in sizes:
         h = W.Hierarchy(system=W.Z4C, boxes=[[W.cube(0, n)]], ncells0=(n, n, n), origin=(0.0, 0.0, 0.0),
-                        h0=1.0 / n, bc=2, ko_sigma=0.0)
+                        h0=1.0 / n, bc=2, ko_sigma=0.0, fd_order=fd_order)
         o = make(orc, h)
         X, Y, Z = h.cell_centres(0, 0, ghosted=True)
         st = np.stack([np.broadcast_to(np.asarray(f(X, Y, Z), dtype=float), X.shape) for f in vals])
         rhs = o.rhs_box(0, 0, st)
-        s = (slice(3, -3),) * 3
+        g = h.ghost
+        s = (slice(g, -g),) * 3
         e = 0.0
         for f in range(18):
             ex = np.broadcast_to(np.asarray(dts[f](X, Y, Z), dtype=float), X.shape)[s]
             e = max(e, np.abs(rhs[f][s] - ex).max())
         errs.append(e)
-    order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
-    assert order[-1] > 3.7, (errs, order)
+    order = np.log(np.array(errs[:-1]) / np.array(errs[1:])) / np.log(np.array(sizes[1:]) / np.array(sizes[:-1]))
+    assert order[-1] > min_order, (errs, order)
 
 
 def test_flop_count_positive(orc):
