@@ -258,6 +258,7 @@ def run_gpu(args, rank: int, world: int):
         dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
     sc.build()
     h = W.bl_7level()
+    h.fd_order = args.fd_order
     fin_per_step, act_per_step = h.zone_updates_per_coarse_step()
     ctx = sc.Context(h)
     tile, _tune_ms = ctx.sc_autotune()
@@ -297,7 +298,7 @@ def run_gpu(args, rank: int, world: int):
     t_der, t_stage = ctx.sc_time_stage_kernels(fin_level, 5)
     roof = {}
     for name, t in (("z4c_derivs", t_der), ("z4c_stage", t_stage)):
-        fpc = FLOPS_PER_CELL[name]
+        fpc = FLOPS_PER_CELL[name] if (h.fd_order == 4 or name == "z4c_stage") else None
         if fpc is None:
             roof[name] = {"ms_per_launch": t, "cells_per_launch": cells, "flops_per_cell": None}
             continue
@@ -363,6 +364,7 @@ def run_gpu(args, rank: int, world: int):
     if rank == 0 and args.uniform_steps > 0:
         hu = W.bl_7level()
         hu.subcycle = False
+        hu.fd_order = args.fd_order
         cu = sc.Context(hu)
         cu.sc_autotune()
         cu.sc_set_initial_data(hu.id_kind, hu.id_params)
@@ -408,6 +410,7 @@ def run_gpu(args, rank: int, world: int):
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": h.name, "levels": h.nlevels, "base_cells": 64 ** 3,
+                           "fd_order": h.fd_order,
                            "interior_cells": sum(h.interior_cells(l) for l in range(h.nlevels)),
                            "finest_equiv_zone_updates_per_step": fin_per_step,
                            "actual_zone_updates_per_step": act_per_step,
@@ -435,6 +438,8 @@ def main():
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--uniform-steps", type=int, default=2,
                     help="coarse steps of the same hierarchy in uniform-step mode (0: skip)")
+    ap.add_argument("--fd-order", type=int, default=4, choices=[4, 8],
+                    help="finite-difference order of the Z4c right-hand side (8: the paper's production setting)")
     ap.add_argument("--serving-requests", type=int, default=64,
                     help="requests of the served-vs-plain ensemble embedded in the default line (0: skip)")
     args = ap.parse_args()

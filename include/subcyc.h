@@ -13,7 +13,7 @@
  *     space [0, ncells0[d] * 2^l) per dimension; cell i of level l has centre
  *     origin + (i + 1/2) h_l;
  *   - refinement factor 2 between levels (Sec. II: h^(l) / h^(l+1) = 2);
- *   - 3 ghost cells around every box;
+ *   - 3 ghost cells around every box (4 with 8th-order differences);
  *   - field arrays exchanged with the caller are x-fastest, contiguous,
  *     FP64, one field at a time;
  *   - every call returns an sc_status (0 = success, negative = error) and
@@ -111,6 +111,9 @@ typedef struct {
   int eta_profile; /* Z4c: 0 = constant eta; 1 = eta(r) = (eta_c - eta_o) exp(-(r/eta_s)^4) + eta_o
                       with r the coordinate radius (Sec. III.A) */
   double eta_c, eta_s, eta_o;
+  int fd_order;    /* finite-difference order of the right-hand sides: 4 (0 = default) or 8, the
+                      paper's production setting (Sec. III.C); Kreiss-Oliger stays r = 4.  Every box
+                      then carries 4 ghost layers instead of 3 (the _ghosted field calls use them). */
 } sc_desc;
 
 enum { SC_EXEC_GRAPH = 0, SC_EXEC_PER_BOX = 1 };

@@ -74,6 +74,7 @@ class sc_desc(ctypes.Structure):
         ("eta_c", ctypes.c_double),
         ("eta_s", ctypes.c_double),
         ("eta_o", ctypes.c_double),
+        ("fd_order", ctypes.c_int),
     ]
 
 
@@ -184,6 +185,7 @@ def make_desc(h, stream: Optional[int] = None, allocator=None, exec_mode: int = 
     d.kappa1, d.kappa2, d.eta, d.ko_sigma = h.kappa1, h.kappa2, h.eta, h.ko_sigma
     d.cuda_stream = stream
     d.exec_mode = exec_mode
+    d.fd_order = int(getattr(h, "fd_order", 4))
     prof = getattr(h, "eta_profile", None)
     if prof is not None:
         d.eta_profile = 1
@@ -252,9 +254,14 @@ class Context:
         except Exception:
             pass
 
+    @property
+    def ghost(self) -> int:
+        """Ghost layers per box: 3 (4th-order differences) or 4 (8th order)."""
+        return 4 if int(getattr(self.h, "fd_order", 4)) == 8 else 3
+
     def shape(self, level: int, box: int, ghosted: bool = False) -> Tuple[int, int, int]:
         lo, hi = self.h.boxes[level][box]
-        g = 2 * GHOST if ghosted else 0
+        g = 2 * self.ghost if ghosted else 0
         return (hi[2] - lo[2] + 1 + g, hi[1] - lo[1] + 1 + g, hi[0] - lo[0] + 1 + g)
 
     def sc_set_initial_data(self, kind: int, params: Sequence[float]):

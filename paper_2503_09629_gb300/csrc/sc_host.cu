@@ -212,6 +212,8 @@ struct sc_ctx {
   long launches_per_step = 0;
   int exec_mode = SC_EXEC_GRAPH;
   int subcycle = 1;
+  int order = 4;   // finite-difference order of the right-hand sides (4 or 8)
+  int ghost = 3;   // ghost layers per box: 3 for 4th order, 4 for 8th
   int tile[3] = {32, 4, 2};  // stencil-kernel tile shape (autotuned on request)
   int eta_profile = 0;
   double eta_c = 0, eta_s = 0, eta_o = 0;
@@ -282,6 +284,7 @@ sc_status validate(const sc_desc* d) {
   if (d->nlevels < 1 || d->nlevels > 16) return fail(SC_EINVAL, "nlevels must be 1..16");
   if (!d->nboxes || !d->boxes) return fail(SC_EINVAL, "null box arrays");
   if (d->subcycle != 0 && d->subcycle != 1) return fail(SC_EINVAL, "subcycle must be 0 or 1");
+  if (d->fd_order != 0 && d->fd_order != 4 && d->fd_order != 8) return fail(SC_EINVAL, "fd_order must be 4 or 8");
   if (d->outer_bc != SC_BC_PERIODIC && d->outer_bc != SC_BC_RADIATIVE) return fail(SC_EINVAL, "unknown outer_bc");
   if (!(d->h0 > 0) || !(d->cfl > 0)) return fail(SC_EINVAL, "h0 and cfl must be positive");
   for (int q = 0; q < 3; ++q)
@@ -334,8 +337,8 @@ sc_status build_level_geometry(sc_ctx* c, int l, const sc_box* boxes, int nb) {
   Geom& g = L.g;
   g.h = c->h0 / (double)(1L << l);
   for (int q = 0; q < 3; ++q) {
-    g.org[q] = lo[q] - kGhost;
-    g.ext[q] = hi[q] - lo[q] + 1 + 2 * kGhost;
+    g.org[q] = lo[q] - c->ghost;
+    g.ext[q] = hi[q] - lo[q] + 1 + 2 * c->ghost;
     g.x0[q] = c->origin[q] + (g.org[q] + 0.5) * g.h;
   }
   g.pitch = (g.ext[0] + 7) & ~7;
@@ -481,11 +484,12 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
   const bool periodic = c->bc == SC_BC_PERIODIC;
   int next[3];
   for (int q = 0; q < 3; ++q) next[q] = c->ncells0[q] << l;
-  // ghost cells: within kGhost (per dimension) of a box interior
+  // ghost cells: within c->ghost (per dimension) of a box interior
+  const int G = c->ghost;
   for (const sc_box& B : L.boxes)
-    for (int k = B.lo[2] - kGhost; k <= B.hi[2] + kGhost; ++k)
-      for (int j = B.lo[1] - kGhost; j <= B.hi[1] + kGhost; ++j)
-        for (int i = B.lo[0] - kGhost; i <= B.hi[0] + kGhost; ++i) {
+    for (int k = B.lo[2] - G; k <= B.hi[2] + G; ++k)
+      for (int j = B.lo[1] - G; j <= B.hi[1] + G; ++j)
+        for (int i = B.lo[0] - G; i <= B.hi[0] + G; ++i) {
           const int gi[3] = {i, j, k};
           const long e = elem_index(g, gi);
           if (L.kind[e] != K_UNUSED) continue;
@@ -584,12 +588,13 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
     for (int k = 0; k < g.ext[2]; ++k)
       for (int j = 0; j < g.ext[1]; ++j) {
         int run_start = -1, run_which = 0;
+        const int R = c->order / 2;  // reach of the first-derivative stencil
         for (int i = 0; i <= g.ext[0]; ++i) {
           int which = 0;
           if (i < g.ext[0]) {
             bool dz = false, dy = false;
-            for (int d = -2; d <= 2 && !dz; ++d) dz = interior_at(i, j, k + d);
-            for (int d = -2; d <= 2 && !dy; ++d) dy = interior_at(i, j + d, k);
+            for (int d = -R; d <= R && !dz; ++d) dz = interior_at(i, j, k + d);
+            for (int d = -R; d <= R && !dy; ++d) dy = interior_at(i, j + d, k);
             which = ((dz || dy) ? 1 : 0) | (dz ? 2 : 0);
           }
           if (which != run_which) {
@@ -874,16 +879,16 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       a.eta = L.eta;
       // graph form: one launch over the tiles of all boxes; per-box form: one per box
       const int nparts = c->exec_mode == SC_EXEC_PER_BOX ? (int)L.boxes.size() : 1;
-      if (c->system == SC_Z4C) CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, s));
+      if (c->system == SC_Z4C) CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, s, c->order));
       for (int b = 0; b < nparts; ++b) {
         const int t0 = nparts == 1 ? 0 : L.box_tile_begin[b];
         const int nt = nparts == 1 ? L.ntiles : L.box_tile_begin[b + 1] - t0;
         if (c->system == SC_WAVE) {
-          CU(launch_wave_stage(a, L.tiles + t0, nt, s));
+          CU(launch_wave_stage(a, L.tiles + t0, nt, s, c->order));
         } else {
           const int p0 = nparts == 1 ? 0 : L.box_ptile_begin[b];
           const int np = nparts == 1 ? L.nptiles : L.box_ptile_begin[b + 1] - p0;
-          CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles + t0, nt, s));
+          CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles + t0, nt, s, c->order));
           CU(launch_z4c_stage(a, c->scratch, c->zp, L.ptiles + p0, np, s));
         }
       }
@@ -975,9 +980,9 @@ sc_status ensure_staging(sc_ctx* c, size_t bytes) {
   return SC_OK;
 }
 
-// Region of a box (optionally with ghosts): lo and extents.
-void box_region(const sc_box& B, bool ghosted, int* lo, int* n) {
-  const int g = ghosted ? kGhost : 0;
+// Region of a box (optionally with its ghost layers): lo and extents.
+void box_region(const sc_box& B, int ghost_layers, int* lo, int* n) {
+  const int g = ghost_layers;
   for (int q = 0; q < 3; ++q) {
     lo[q] = B.lo[q] - g;
     n[q] = B.hi[q] - B.lo[q] + 1 + 2 * g;
@@ -990,7 +995,7 @@ sc_status copy_field(sc_ctx* c, int level, int box, int field, bool ghosted, con
   if (st) return st;
   Level& L = c->lev[level];
   int lo[3], n[3];
-  box_region(L.boxes[box], ghosted, lo, n);
+  box_region(L.boxes[box], ghosted ? c->ghost : 0, lo, n);
   const size_t bytes = sizeof(double) * (size_t)n[0] * n[1] * n[2];
   double* state = L.S[L.parity] + (long)field * L.g.fs;
   if (src) {
@@ -1064,8 +1069,8 @@ sc_status time_stencil(sc_ctx* c, Level& L, const Tile* tiles, int ntiles, int r
   CU(cudaEventCreate(&e1));
   for (int r = -1; r < reps; ++r) {  // one untimed launch first
     if (r == 0) CU(cudaEventRecord(e0, c->stream));
-    if (c->system == SC_WAVE) CU(launch_wave_stage(a, tiles, ntiles, c->stream));
-    else CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, tiles, ntiles, c->stream));
+    if (c->system == SC_WAVE) CU(launch_wave_stage(a, tiles, ntiles, c->stream, c->order));
+    else CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, tiles, ntiles, c->stream, c->order));
   }
   CU(cudaEventRecord(e1, c->stream));
   CU(cudaEventSynchronize(e1));
@@ -1216,6 +1221,7 @@ extern "C" sc_status sc_regrid(sc_ctx* c, const int* nboxes, const sc_box* boxes
   d.outer_bc = c->bc;
   d.cfl = c->cfl;
   d.subcycle = 1;
+  d.fd_order = c->order;
   sc_status st = validate(&d);
   if (st) return st;
   if (nboxes[0] != (int)c->lev[0].boxes.size()) return fail(SC_EINVAL, "regrid keeps level 0 unchanged");
@@ -1337,6 +1343,7 @@ sc_status sc_footprint_estimate(const sc_desc* d, size_t* bytes) {
   sc_status st = validate(d);
   if (st) return st;
   const int F = d->system == SC_WAVE ? kNWave : kNZ4c;
+  const int ghost = d->fd_order == 8 ? 4 : 3;
   size_t total = 0, maxfs = 0;
   int bi = 0;
   for (int l = 0; l < d->nlevels; ++l) {
@@ -1349,12 +1356,12 @@ sc_status sc_footprint_estimate(const sc_desc* d, size_t* bytes) {
         lo[q] = std::min(lo[q], B.lo[q]);
         hi[q] = std::max(hi[q], B.hi[q]);
         inner *= B.hi[q] - B.lo[q] + 1;
-        outer *= B.hi[q] - B.lo[q] + 1 + 2 * kGhost;
+        outer *= B.hi[q] - B.lo[q] + 1 + 2 * ghost;
       }
       ghost_cells += outer - inner;
     }
-    const long pitch = ((hi[0] - lo[0] + 1 + 2 * kGhost) + 7) & ~7;
-    const long fs = ((pitch * (hi[1] - lo[1] + 1 + 2 * kGhost) * (hi[2] - lo[2] + 1 + 2 * kGhost)) + 31) & ~31L;
+    const long pitch = ((hi[0] - lo[0] + 1 + 2 * ghost) + 7) & ~7;
+    const long fs = ((pitch * (hi[1] - lo[1] + 1 + 2 * ghost) * (hi[2] - lo[2] + 1 + 2 * ghost)) + 31) & ~31L;
     total += 8 * (size_t)F * fs * sizeof(double);                 // S0, S1, A, B, k1..k4
     if (d->system == SC_Z4C && d->eta_profile) total += (size_t)fs * sizeof(double);
     total += (size_t)ghost_cells * (5 * F * sizeof(double) + 32);  // prolonged vectors + lists
@@ -1366,7 +1373,7 @@ sc_status sc_footprint_estimate(const sc_desc* d, size_t* bytes) {
   size_t maxbox = 0;
   for (int b = 0; b < bi; ++b) {
     size_t v = 1;
-    for (int q = 0; q < 3; ++q) v *= (size_t)(d->boxes[b].hi[q] - d->boxes[b].lo[q] + 1 + 2 * kGhost);
+    for (int q = 0; q < 3; ++q) v *= (size_t)(d->boxes[b].hi[q] - d->boxes[b].lo[q] + 1 + 2 * ghost);
     maxbox = std::max(maxbox, v);
   }
   total += maxbox * 7 * sizeof(double) + (1u << 20);
@@ -1397,6 +1404,8 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
   c->stream = (cudaStream_t)d->cuda_stream;
   c->exec_mode = d->exec_mode == SC_EXEC_PER_BOX ? SC_EXEC_PER_BOX : SC_EXEC_GRAPH;
   c->subcycle = d->subcycle;
+  c->order = d->fd_order == 8 ? 8 : 4;
+  c->ghost = c->order == 8 ? 4 : 3;
   c->eta_profile = d->eta_profile ? 1 : 0;
   c->eta_c = d->eta_c;
   c->eta_s = d->eta_s;
@@ -1550,7 +1559,7 @@ sc_status sc_get_constraints(sc_ctx* c, int level, int box, double* dst) {
   Level& L = c->lev[level];
   const sc_box& B = L.boxes[box];
   int lo[3], n[3];
-  box_region(B, false, lo, n);
+  box_region(B, 0, lo, n);
   const long ncell = (long)n[0] * n[1] * n[2];
   const size_t bytes = sizeof(double) * kNCons * (size_t)ncell;
   if ((st = ensure_staging(c, bytes))) return st;
@@ -1574,7 +1583,12 @@ sc_status sc_get_constraints(sc_ctx* c, int level, int box, double* dst) {
   const double* Y = L.S[L.parity];
   const int sy = L.g.pitch, sz = L.g.pitch * L.g.ext[1];
   const int blo[3] = {B.lo[0] - L.g.org[0], B.lo[1] - L.g.org[1], B.lo[2] - L.g.org[2]};
-  CU(launch_z4c_derivs(Y, c->scratch, L.g.fs, sy, sz, L.g.h, dt, (int)tl.size(), c->stream));
+  if (c->order == 4) {
+    CU(launch_z4c_derivs(Y, c->scratch, L.g.fs, sy, sz, L.g.h, dt, (int)tl.size(), c->stream));
+  } else {
+    CU(launch_z4c_dxy(Y, c->scratch, L.g.fs, sy, L.g.h, L.dxy, L.ndxy, c->stream, c->order));
+    CU(launch_z4c_derivs_split(Y, c->scratch, L.g.fs, sy, sz, L.g.h, dt, (int)tl.size(), c->stream, c->order));
+  }
   CU(launch_z4c_constraints(Y, c->scratch, c->staging, L.g.fs, sy, sz, c->zp, dt, (int)tl.size(), ncell, blo, n,
                             c->stream));
   CU(cudaMemcpyAsync(dst, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -1626,10 +1640,10 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   float t0 = 0, t1 = 0;
   CU(cudaEventRecord(e[0], c->stream));
   for (int r = 0; r < nrep; ++r) {
-    if (c->system == SC_WAVE) CU(launch_wave_stage(a, L.tiles, L.ntiles, c->stream));
+    if (c->system == SC_WAVE) CU(launch_wave_stage(a, L.tiles, L.ntiles, c->stream, c->order));
     else {
-      CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, c->stream));
-      CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, c->stream));
+      CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, c->stream, c->order));
+      CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, c->stream, c->order));
     }
   }
   CU(cudaEventRecord(e[1], c->stream));
@@ -1665,7 +1679,7 @@ sc_status sc_debug_get_vector(sc_ctx* c, int level, int box, int vec, int field,
   Level& L = c->lev[level];
   double* src[8] = {L.S[L.parity], L.S[L.parity ^ 1], L.A, L.B, L.K[0], L.K[1], L.K[2], L.K[3]};
   int lo[3], n[3];
-  box_region(L.boxes[box], ghosted != 0, lo, n);
+  box_region(L.boxes[box], ghosted ? c->ghost : 0, lo, n);
   const size_t bytes = sizeof(double) * (size_t)n[0] * n[1] * n[2];
   if ((st = ensure_staging(c, bytes))) return st;
   CU(launch_pack(src[vec] + (long)field * L.g.fs, L.g, lo, n, c->staging, c->stream));

@@ -115,17 +115,18 @@ struct Z4cParams {
 sc_status set_last_error(sc_status code, const char* msg);
 
 // ---- kernel launchers (defined in the .cu files) -------------------------
-cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s);
+cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s, int order = 4);
 
 cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy, int sz, double h,
                               const Tile* tiles, int ntiles, cudaStream_t s);
 // Occupancy-derived persistent grid sizes of the Z4c kernels (once per device,
 // before any graph capture).
 cudaError_t z4c_init_launch_config();
+// order: finite-difference order of the derivatives, 4 or 8 (Kreiss-Oliger stays r = 4)
 cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, double h, const RowSeg* segs, int nsegs,
-                           cudaStream_t s);
+                           cudaStream_t s, int order = 4);
 cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz, double h,
-                                    const Tile* tiles, int ntiles, cudaStream_t s);
+                                    const Tile* tiles, int ntiles, cudaStream_t s, int order = 4);
 cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4cParams& p,
                              const Tile* tiles, int ntiles, cudaStream_t s);
 cudaError_t launch_radiative_stage(const StageArgs& a, const int32_t* cells, int ncells, int F,

@@ -13,9 +13,10 @@ namespace {
 
 constexpr int kThreads = 256;
 
+template <int ORD>
 __global__ void __launch_bounds__(kThreads) wave_stage_kernel(StageArgs a, const Tile* __restrict__ tiles,
                                                              int ntiles) {
-  const double inv12h2 = 1.0 / (12.0 * a.h * a.h);
+  const double inv12h2 = ORD == 4 ? 1.0 / (12.0 * a.h * a.h) : 1.0 / (5040.0 * a.h * a.h);
   const long sy = a.sy, sz = a.sz;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile T = tiles[t];
@@ -27,10 +28,18 @@ __global__ void __launch_bounds__(kThreads) wave_stage_kernel(StageArgs a, const
       const long o = (T.z0 + k) * sz + (T.y0 + j) * sy + (T.x0 + i);
       const double* u = a.Y;
       const double u0 = u[o];
-      // -1, 16, -30, 16, -1 over offsets -2..2 in each dimension, / (12 h^2)
+      // 4th order: -1, 16, -30, 16, -1 over offsets -2..2 in each dimension, / (12 h^2);
+      // 8th order: -9, 128, -1008, 8064, -14350, ... over -4..4, / (5040 h^2)
       const double s1 = (u[o - 1] + u[o + 1]) + (u[o - sy] + u[o + sy]) + (u[o - sz] + u[o + sz]);
       const double s2 = (u[o - 2] + u[o + 2]) + (u[o - 2 * sy] + u[o + 2 * sy]) + (u[o - 2 * sz] + u[o + 2 * sz]);
-      const double lap = fma(-90.0, u0, fma(16.0, s1, -s2)) * inv12h2;
+      double lap;
+      if (ORD == 4) {
+        lap = fma(-90.0, u0, fma(16.0, s1, -s2)) * inv12h2;
+      } else {
+        const double s3 = (u[o - 3] + u[o + 3]) + (u[o - 3 * sy] + u[o + 3 * sy]) + (u[o - 3 * sz] + u[o + 3 * sz]);
+        const double s4 = (u[o - 4] + u[o + 4]) + (u[o - 4 * sy] + u[o + 4 * sy]) + (u[o - 4 * sz] + u[o + 4 * sz]);
+        lap = fma(-43050.0, u0, fma(8064.0, s1, fma(-1008.0, s2, fma(128.0, s3, -9.0 * s4)))) * inv12h2;
+      }
       const double ku = a.Y[a.fs + o];  // d_t u = Pi
       const double kp = lap;            // d_t Pi = Laplacian u
       a.k[o] = ku;
@@ -94,10 +103,11 @@ __global__ void __launch_bounds__(kThreads) radiative_stage_kernel(StageArgs a, 
 
 }  // namespace
 
-cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s) {
+cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s, int order) {
   if (ntiles == 0) return cudaSuccess;
   const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
-  wave_stage_kernel<<<grid, kThreads, 0, s>>>(a, tiles, ntiles);
+  if (order == 8) wave_stage_kernel<8><<<grid, kThreads, 0, s>>>(a, tiles, ntiles);
+  else wave_stage_kernel<4><<<grid, kThreads, 0, s>>>(a, tiles, ntiles);
   return cudaGetLastError();
 }
 

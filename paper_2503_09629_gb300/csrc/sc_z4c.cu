@@ -123,10 +123,38 @@ __device__ __forceinline__ double fmul(double a, double b, const FmaK& K) { retu
 // field of Hessian slot s (W, gt x6, alpha, beta x3): slots 0..6 -> fields 0..6, 7..10 -> 18..21
 __device__ __forceinline__ int d2_field(int s) { return s <= 6 ? s : s + 11; }
 
+// Centred first derivative from the differences dm = v_m - v_-m, m = 1..R
+// (R = ORD/2): 4th order (8 d1 - d2) / (12 h), 8th order
+// (672 d1 - 168 d2 + 32 d3 - 3 d4) / (840 h); ih = 1/(12 h) or 1/(840 h).
+template <int ORD>
+__device__ __forceinline__ double dfirst(const double* d, double ih, const FmaK& K) {
+  if (ORD == 4) return fmul(fma(8.0, d[0], -d[1]), ih, K);
+  return fmul(fma(672.0, d[0], fma(-168.0, d[1], fma(32.0, d[2], fmul(-3.0, d[3], K)))), ih, K);
+}
+// Centred second derivative from the pair sums pm = v_m + v_-m:
+// 4th order (16 p1 - p2 - 30 u0) / (12 h^2), 8th order
+// (8064 p1 - 1008 p2 + 128 p3 - 9 p4 - 14350 u0) / (5040 h^2).
+template <int ORD>
+__device__ __forceinline__ double dsecond(const double* p, double u0, double ih2, const FmaK& K) {
+  if (ORD == 4) return fmul(fma(-30.0, u0, fma(16.0, p[0], -p[1])), ih2, K);
+  return fmul(fma(-14350.0, u0, fma(8064.0, p[0], fma(-1008.0, p[1], fma(128.0, p[2], fmul(-9.0, p[3], K))))), ih2,
+              K);
+}
+template <int ORD>
+__device__ __forceinline__ double first_scale(double h) {
+  return ORD == 4 ? 1.0 / (12.0 * h) : 1.0 / (840.0 * h);
+}
+template <int ORD>
+__device__ __forceinline__ double second_scale(double h) {
+  return ORD == 4 ? 1.0 / (12.0 * h * h) : 1.0 / (5040.0 * h * h);
+}
+
+template <int ORD>
 __global__ void __launch_bounds__(128) z4c_dxy_kernel(const double* __restrict__ Y, double* __restrict__ S, long fs,
                                                      int sy_, const RowSeg* __restrict__ segs, int nsegs, double h,
                                                      FmaK K) {
-  const double i12h = 1.0 / (12.0 * h);
+  constexpr int R = ORD / 2;
+  const double ih = first_scale<ORD>(h);
   const long sy = sy_;
   for (int sgi = blockIdx.x; sgi < nsegs; sgi += gridDim.x) {
     const RowSeg sg = segs[sgi];
@@ -135,25 +163,37 @@ __global__ void __launch_bounds__(128) z4c_dxy_kernel(const double* __restrict__
       const long o = sg.off + (q - slot * sg.n);
       const int f = d2_field(slot);
       const double* u = Y + (long)f * fs + o;
-      // (u_-2 - 8 u_-1 + 8 u_1 - u_2) / (12 h)
-      if (sg.which & 1)
-        S[(long)(Q_D1 + 3 * f + 0) * fs + o] = fmul(fma(8.0, fsub(u[1], u[-1], K), fsub(u[-2], u[2], K)), i12h, K);
-      if (sg.which & 2)
-        S[(long)(Q_D1 + 3 * f + 1) * fs + o] =
-            fmul(fma(8.0, fsub(u[sy], u[-sy], K), fsub(u[-2 * sy], u[2 * sy], K)), i12h, K);
+      double d[R];
+      if (sg.which & 1) {
+#pragma unroll
+        for (int m = 1; m <= R; ++m) d[m - 1] = fsub(u[m], u[-m], K);
+        S[(long)(Q_D1 + 3 * f + 0) * fs + o] = dfirst<ORD>(d, ih, K);
+      }
+      if (sg.which & 2) {
+#pragma unroll
+        for (int m = 1; m <= R; ++m) d[m - 1] = fsub(u[m * sy], u[-m * sy], K);
+        S[(long)(Q_D1 + 3 * f + 1) * fs + o] = dfirst<ORD>(d, ih, K);
+      }
     }
   }
 }
 
+template <int ORD>
 __global__ void __launch_bounds__(kThreads, 2) z4c_derivs_split_kernel(const double* __restrict__ Y,
-                                                                   double* __restrict__ S, long fs, int sy_, int sz_,
-                                                                   double h, const Tile* __restrict__ tiles,
-                                                                   int ntiles, FmaK K) {
+                                                                      double* __restrict__ S, long fs, int sy_,
+                                                                      int sz_, double h,
+                                                                      const Tile* __restrict__ tiles, int ntiles,
+                                                                      FmaK K) {
   // One thread per (x, y, field) column of a tile, walking z with sliding
-  // windows: u at z-3..z+3 and, for the Hessian fields, the stored D_x, D_y
-  // at z-2..z+2, so each step loads one new z value per window.
-  const double i12h = 1.0 / (12.0 * h);
-  const double i12h2 = 1.0 / (12.0 * h * h);
+  // windows: u at z-W..z+W (W = max(R, 3), R = ORD/2 the derivative radius,
+  // 3 the Kreiss-Oliger radius) and, for the Hessian fields, the stored
+  // D_x, D_y at z-R..z+R, so each step loads one new z value per window.
+  constexpr int R = ORD / 2;
+  constexpr int WR = R > 3 ? R : 3;
+  constexpr int NW = 2 * WR + 1;
+  constexpr int ND = 2 * R + 1;
+  const double ih = first_scale<ORD>(h);
+  const double ih2 = second_scale<ORD>(h);
   const long sy = sy_, sz = sz_;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile T = tiles[t];
@@ -166,75 +206,75 @@ __global__ void __launch_bounds__(kThreads, 2) z4c_derivs_split_kernel(const dou
       const long o0 = (long)T.z0 * sz + (T.y0 + j) * sy + (T.x0 + i);
       const double* u = Y + (long)f * fs + o0;
       const int sl = d2_slot(f);
-      double w[7];  // u at z-3..z+3
+      double w[NW];  // u at z-WR..z+WR
 #pragma unroll
-      for (int m = 0; m < 7; ++m) w[m] = u[(m - 3) * sz];
+      for (int m = 0; m < NW; ++m) w[m] = u[(m - WR) * sz];
       const double* Dx = S + (long)(Q_D1 + 3 * f + 0) * fs + o0;
       const double* Dy = S + (long)(Q_D1 + 3 * f + 1) * fs + o0;
-      double wx[5], wy[5];  // D_x, D_y at z-2..z+2 (Hessian fields)
+      double wx[ND], wy[ND];  // D_x, D_y at z-R..z+R (Hessian fields)
       if (sl >= 0) {
 #pragma unroll
-        for (int m = 0; m < 5; ++m) {
-          wx[m] = Dx[(m - 2) * sz];
-          wy[m] = Dy[(m - 2) * sz];
+        for (int m = 0; m < ND; ++m) {
+          wx[m] = Dx[(m - R) * sz];
+          wy[m] = Dy[(m - R) * sz];
         }
       }
 #pragma unroll 1
       for (int k = 0; k < T.nz; ++k) {
         const long o = o0 + k * sz;
         const double* v = u + k * sz;
-        const double u0 = w[3];
-        double p1[3], p2[3], p3[3];
+        const double u0 = w[WR];
+        double p[3][4], d[4];
         // x and y from memory, z from the window
-        {
-          const double a1 = v[-1], b1 = v[1], a2 = v[-2], b2 = v[2];
-          p1[0] = fadd(a1, b1, K);
-          p2[0] = fadd(a2, b2, K);
-          p3[0] = fadd(v[-3], v[3], K);
-          if (sl < 0) S[(long)(Q_D1 + 3 * f + 0) * fs + o] = fmul(fma(8.0, fsub(b1, a1, K), fsub(a2, b2, K)), i12h, K);
+#pragma unroll
+        for (int dim = 0; dim < 2; ++dim) {
+          const long s = dim == 0 ? 1 : sy;
+#pragma unroll
+          for (int m = 1; m <= WR; ++m) p[dim][m - 1] = fadd(v[-m * s], v[m * s], K);
+          if (sl < 0) {
+#pragma unroll
+            for (int m = 1; m <= R; ++m) d[m - 1] = fsub(v[m * s], v[-m * s], K);
+            S[(long)(Q_D1 + 3 * f + dim) * fs + o] = dfirst<ORD>(d, ih, K);
+          }
         }
-        {
-          const double a1 = v[-sy], b1 = v[sy], a2 = v[-2 * sy], b2 = v[2 * sy];
-          p1[1] = fadd(a1, b1, K);
-          p2[1] = fadd(a2, b2, K);
-          p3[1] = fadd(v[-3 * sy], v[3 * sy], K);
-          if (sl < 0) S[(long)(Q_D1 + 3 * f + 1) * fs + o] = fmul(fma(8.0, fsub(b1, a1, K), fsub(a2, b2, K)), i12h, K);
-        }
-        {
-          const double a1 = w[2], b1 = w[4], a2 = w[1], b2 = w[5];
-          p1[2] = fadd(a1, b1, K);
-          p2[2] = fadd(a2, b2, K);
-          p3[2] = fadd(w[0], w[6], K);
-          S[(long)(Q_D1 + 3 * f + 2) * fs + o] = fmul(fma(8.0, fsub(b1, a1, K), fsub(a2, b2, K)), i12h, K);
-        }
-        // Kreiss-Oliger: sum_d (u_-3 - 6 u_-2 + 15 u_-1 - 20 u_0 + 15 u_1 - 6 u_2 + u_3)
-        const double P1 = fadd(fadd(p1[0], p1[1], K), p1[2], K);
-        const double P2 = fadd(fadd(p2[0], p2[1], K), p2[2], K);
-        const double P3 = fadd(fadd(p3[0], p3[1], K), p3[2], K);
+#pragma unroll
+        for (int m = 1; m <= WR; ++m) p[2][m - 1] = fadd(w[WR - m], w[WR + m], K);
+#pragma unroll
+        for (int m = 1; m <= R; ++m) d[m - 1] = fsub(w[WR + m], w[WR - m], K);
+        S[(long)(Q_D1 + 3 * f + 2) * fs + o] = dfirst<ORD>(d, ih, K);
+        // Kreiss-Oliger (r = 4): sum_d (u_-3 - 6 u_-2 + 15 u_-1 - 20 u_0 + 15 u_1 - 6 u_2 + u_3)
+        const double P1 = fadd(fadd(p[0][0], p[1][0], K), p[2][0], K);
+        const double P2 = fadd(fadd(p[0][1], p[1][1], K), p[2][1], K);
+        const double P3 = fadd(fadd(p[0][2], p[1][2], K), p[2][2], K);
         S[(long)(Q_KO + f) * fs + o] = fma(15.0, P1, fma(-6.0, P2, fma(-60.0, u0, P3)));
         if (sl >= 0) {
           double* d2 = S + (long)(Q_D2 + 6 * sl) * fs + o;
-          // pure: (-u_-2 + 16 u_-1 - 30 u_0 + 16 u_1 - u_2) / (12 h^2)
-          d2[0 * fs] = fmul(fma(-30.0, u0, fma(16.0, p1[0], -p2[0])), i12h2, K);
-          d2[3 * fs] = fmul(fma(-30.0, u0, fma(16.0, p1[1], -p2[1])), i12h2, K);
-          d2[5 * fs] = fmul(fma(-30.0, u0, fma(16.0, p1[2], -p2[2])), i12h2, K);
+          d2[0 * fs] = dsecond<ORD>(p[0], u0, ih2, K);
+          d2[3 * fs] = dsecond<ORD>(p[1], u0, ih2, K);
+          d2[5 * fs] = dsecond<ORD>(p[2], u0, ih2, K);
           const double* dxk = Dx + k * sz;
-          d2[1 * fs] = fmul(fma(8.0, fsub(dxk[sy], dxk[-sy], K), fsub(dxk[-2 * sy], dxk[2 * sy], K)), i12h, K);  // D_y D_x
-          d2[2 * fs] = fmul(fma(8.0, fsub(wx[3], wx[1], K), fsub(wx[0], wx[4], K)), i12h, K);                      // D_z D_x
-          d2[4 * fs] = fmul(fma(8.0, fsub(wy[3], wy[1], K), fsub(wy[0], wy[4], K)), i12h, K);                      // D_z D_y
+#pragma unroll
+          for (int m = 1; m <= R; ++m) d[m - 1] = fsub(dxk[m * sy], dxk[-m * sy], K);
+          d2[1 * fs] = dfirst<ORD>(d, ih, K);  // D_y D_x
+#pragma unroll
+          for (int m = 1; m <= R; ++m) d[m - 1] = fsub(wx[R + m], wx[R - m], K);
+          d2[2 * fs] = dfirst<ORD>(d, ih, K);  // D_z D_x
+#pragma unroll
+          for (int m = 1; m <= R; ++m) d[m - 1] = fsub(wy[R + m], wy[R - m], K);
+          d2[4 * fs] = dfirst<ORD>(d, ih, K);  // D_z D_y
         }
         if (k + 1 < T.nz) {  // slide the windows one cell up in z
 #pragma unroll
-          for (int m = 0; m < 6; ++m) w[m] = w[m + 1];
-          w[6] = v[4 * sz];
+          for (int m = 0; m < NW - 1; ++m) w[m] = w[m + 1];
+          w[NW - 1] = v[(WR + 1) * sz];
           if (sl >= 0) {
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
+            for (int m = 0; m < ND - 1; ++m) {
               wx[m] = wx[m + 1];
               wy[m] = wy[m + 1];
             }
-            wx[4] = Dx[(k + 3) * sz];
-            wy[4] = Dy[(k + 3) * sz];
+            wx[ND - 1] = Dx[(k + 1 + R) * sz];
+            wy[ND - 1] = Dy[(k + 1 + R) * sz];
           }
         }
       }
@@ -653,10 +693,10 @@ cudaError_t z4c_init_launch_config() {
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel, 128, 0)) != cudaSuccess) return e;
   c.stage = nsm * (occ > 0 ? occ : 1);
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_derivs_split_kernel, kThreads, 0)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_derivs_split_kernel<8>, kThreads, 0)) != cudaSuccess)
     return e;
   c.derivs = nsm * (occ > 0 ? occ : 1);
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_dxy_kernel, 128, 0)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_dxy_kernel<8>, 128, 0)) != cudaSuccess) return e;
   c.dxy = nsm * (occ > 0 ? occ : 1);
   c.ready = 1;
   return cudaSuccess;
@@ -671,18 +711,22 @@ cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy,
 }
 
 cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, double h, const RowSeg* segs, int nsegs,
-                           cudaStream_t s) {
+                           cudaStream_t s, int order) {
   if (nsegs == 0) return cudaSuccess;
   const int grid = nsegs < caps().dxy ? nsegs : caps().dxy;
-  z4c_dxy_kernel<<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, h, FmaK{1.0, -1.0, -0.0});
+  if (order == 8) z4c_dxy_kernel<8><<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, h, FmaK{1.0, -1.0, -0.0});
+  else z4c_dxy_kernel<4><<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, h, FmaK{1.0, -1.0, -0.0});
   return cudaGetLastError();
 }
 
 cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz, double h,
-                                    const Tile* tiles, int ntiles, cudaStream_t s) {
+                                    const Tile* tiles, int ntiles, cudaStream_t s, int order) {
   if (ntiles == 0) return cudaSuccess;
   const int grid = ntiles < caps().derivs ? ntiles : caps().derivs;
-  z4c_derivs_split_kernel<<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles, FmaK{1.0, -1.0, -0.0});
+  if (order == 8)
+    z4c_derivs_split_kernel<8><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles, FmaK{1.0, -1.0, -0.0});
+  else
+    z4c_derivs_split_kernel<4><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles, FmaK{1.0, -1.0, -0.0});
   return cudaGetLastError();
 }
 
