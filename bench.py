@@ -61,6 +61,13 @@ FLOPS_PER_CELL = {"z4c_derivs": 1180.0, "z4c_stage": 1971.0}
 # None once the kernel has changed since the counters were taken.
 DRAM_BYTES_PER_CELL = {"z4c_derivs": None,
                        "z4c_stage": (443.535616e6 + 90.504448e6) / 262144}
+# FP64 instructions (DFMA + DMUL + DADD, thread-level / cell) per interior
+# cell of the derivative pass (D_x/D_y row pass + per-cell pass), counted by
+# ncu on the 3-level 64^3 case (profiles/z4c_kernels_bl3level64_ncu.md,
+# profiles/z4c_derivs_fd8_bl3level64_ncu.md).  The pass issues its additions
+# as DFMAs, so its bound is the DFMA issue rate: 152 SMs x 2070 MHz x 2.
+FP64_INSTR_PER_CELL = {4: {"z4c_derivs": 103.0 + 807.0}, 8: {"z4c_derivs": 242.0 + 1324.0}}
+FP64_ISSUE_PEAK_G = 152 * 2.070 * 2
 # Kernel with the largest share of a coarse step in the ncu launch list
 # (profiles/z4c_bl_7level_launch_list.md).
 DOMINANT = "z4c_stage"
@@ -303,10 +310,14 @@ def run_gpu(args, rank: int, world: int):
             roof[name] = {"ms_per_launch": t, "cells_per_launch": cells, "flops_per_cell": None}
             continue
         ach = cells * fpc / (t * 1e-3) / 1e12
-        tb = DRAM_BYTES_PER_CELL.get(name)
+        tb = DRAM_BYTES_PER_CELL.get(name) if h.fd_order == 4 else None
         roof[name] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                       "frac": ach * 1e3 / FP64_PEAK_GFLOPS, "traffic": (tb * cells if tb else None),
                       "ms_per_launch": t, "cells_per_launch": cells, "flops_per_cell": fpc}
+    ipc = FP64_INSTR_PER_CELL[h.fd_order]["z4c_derivs"]
+    issue = cells * ipc / (t_der * 1e-3) / 1e9
+    roof["z4c_derivs"]["fp64_issue"] = {"achieved": issue, "peak": FP64_ISSUE_PEAK_G, "unit": "G FP64 instr/s",
+                                        "frac": issue / FP64_ISSUE_PEAK_G, "instr_per_cell": ipc}
     # Refinement-boundary ghost fill on the finest level: the separable
     # prolongation (FP64: 42 FMAs per fine position of a 4x4x4 block and
     # vector-field, 2688 FMAs per block and vector-field) and the

@@ -644,7 +644,7 @@ long node_offset(const Hier& H, int l, int (*nodes)[8], int blk, const int* li0,
 }
 
 // Step 2 of the algorithm: prolong the parent's y_n and k1..k4 to the
-// refinement-boundary ghost cells of level l (tensor-product cubic Lagrange).
+// refinement-boundary ghost cells of level l (tensor-product quintic Lagrange).
 void prolong_parent_vectors(Hier& H, int l) {
   Level& L = H.lev[l];
   const int src_vec[5] = {V_YOLD, V_K1, V_K1 + 1, V_K1 + 2, V_K1 + 3};
@@ -741,8 +741,8 @@ void fill_ghosts(Hier& H, int l, int vec, double theta0, int which, double t_n, 
 }
 
 // Step 7: restrict level l onto level l-1 (vector y): every parent cell whose
-// 8 children are fine interior cells takes the tensor-product cubic
-// interpolant of the 4^3 fine cells around its centre.
+// 8 children are fine interior cells takes the tensor-product quintic
+// interpolant of the 6^3 fine cells around its centre.
 void restrict_level(Hier& H, int l) {
   Level& P = H.lev[l - 1];
   for (BoxData& PB : P.boxes) {
