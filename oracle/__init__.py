@@ -59,7 +59,7 @@ def lib():
         DP = ctypes.POINTER(ctypes.c_double)
         IP = ctypes.POINTER(ctypes.c_int)
         L.orc_create.argtypes = [I, I, IP, IP, IP, DP, D, I, D, I, DP, ctypes.POINTER(P)]
-        L.orc_create_order.argtypes = [I, I, IP, IP, IP, DP, D, I, D, I, DP, I, ctypes.POINTER(P)]
+        L.orc_create_ex.argtypes = [I, I, IP, IP, IP, DP, D, I, D, I, DP, I, I, ctypes.POINTER(P)]
         L.orc_destroy.argtypes = [P]
         L.orc_nfields.argtypes = [P]
         L.orc_set_bc_callback.argtypes = [P, BC_FN, P]
@@ -74,6 +74,9 @@ def lib():
         L.orc_dense_b.argtypes = [D, I, DP]
         L.orc_amr_value.argtypes = [D, DP, D, D, I]
         L.orc_amr_value.restype = D
+        L.orc_dense_b_rk.argtypes = [I, D, I, DP]
+        L.orc_amr_value_rk.argtypes = [I, D, DP, D, D, I]
+        L.orc_amr_value_rk.restype = D
         L.orc_rhs_box.argtypes = [P, I, I, DP, DP]
         L.orc_constraints.argtypes = [P, I, I, DP]
         L.orc_debug_set_vector.argtypes = [P, I, I, I, I, DP]
@@ -93,15 +96,24 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def dense_b(theta: float, m: int = 0) -> np.ndarray:
+def dense_b(theta: float, m: int = 0, rk: int = 4) -> np.ndarray:
+    """m-th theta-derivative of the dense-output weights b_1..b_4 of the
+    rk-stage method (unused stages have weight 0)."""
     b = np.zeros(4)
-    lib().orc_dense_b(theta, m, _dp(b))
+    if rk == 4:
+        lib().orc_dense_b(theta, m, _dp(b))
+    else:
+        lib().orc_dense_b_rk(rk, theta, m, _dp(b))
     return b
 
 
-def amr_value(y: float, k, H: float, theta0: float, which: int) -> float:
-    k = np.ascontiguousarray(k, dtype=np.float64)
-    return lib().orc_amr_value(y, _dp(k), H, theta0, which)
+def amr_value(y: float, k, H: float, theta0: float, which: int, rk: int = 4) -> float:
+    kk = np.zeros(4)
+    kk[:len(k)] = np.asarray(k, dtype=np.float64)
+    k = kk
+    if rk == 4:
+        return lib().orc_amr_value(y, _dp(k), H, theta0, which)
+    return lib().orc_amr_value_rk(rk, y, _dp(k), H, theta0, which)
 
 
 def flop_counts() -> dict:
@@ -118,7 +130,8 @@ class Oracle:
     """
 
     def __init__(self, system, boxes, ncells0, origin, h0, bc=BC_PERIODIC, cfl=0.25,
-                 subcycle=True, kappa1=0.02, kappa2=0.0, eta=2.0, ko_sigma=0.3, eta_profile=None, fd_order=4):
+                 subcycle=True, kappa1=0.02, kappa2=0.0, eta=2.0, ko_sigma=0.3, eta_profile=None, fd_order=4,
+                 rk_order=4):
         L = lib()
         self.system = system
         self.boxes = [[(tuple(lo), tuple(hi)) for lo, hi in lvl] for lvl in boxes]
@@ -132,8 +145,8 @@ class Oracle:
         org = (ctypes.c_double * 3)(*origin)
         prm = (ctypes.c_double * 4)(kappa1, kappa2, eta, ko_sigma)
         h = ctypes.c_void_p()
-        rc = L.orc_create_order(system, len(boxes), nb, fb, nc, org, h0, bc, cfl, 1 if subcycle else 0, prm,
-                                int(fd_order), ctypes.byref(h))
+        rc = L.orc_create_ex(system, len(boxes), nb, fb, nc, org, h0, bc, cfl, 1 if subcycle else 0, prm,
+                             int(fd_order), int(rk_order), ctypes.byref(h))
         if rc != 0:
             raise ValueError(f"oracle create failed ({rc})")
         self.h = h

@@ -102,6 +102,83 @@ double amr_value(double y, const double* k, double H, double theta0, int which) 
   return NAN;
 }
 
+// RK2 and RK3 subcycling (the extension the paper's Sec. V names as future
+// work).  The paper fixes neither method; the oracle uses
+//   RK2: explicit midpoint, Y2 = y + h/2 k1, y_{n+1} = y + h k2;
+//   RK3: Heun's third-order method, Y2 = y + h/3 k1, Y3 = y + 2h/3 k2,
+//        y_{n+1} = y + h/4 (k1 + 3 k3).
+// Dense output:
+//   RK2: the quadratic continuous extension b1 = theta - theta^2,
+//        b2 = theta^2 (second order, like the method);
+//   RK3: the cubic Hermite interpolant through y_n, y_{n+1} with slopes k1
+//        and k4 = f(y_{n+1}), evaluated once per step on every level that
+//        has a finer level: b1 = theta - 5/4 theta^2 + 1/2 theta^3,
+//        b2 = 0, b3 = 9/4 theta^2 - 3/2 theta^3, b4 = -theta^2 + theta^3
+//        (third order, one order above RK3's own continuous extensions,
+//        which leave the subcycled scheme near order 2.5).
+// m-th theta-derivatives of the weights, as dense_b for RK4.
+void dense_b_rk(int rk, double t, int m, double* b) {
+  b[0] = b[1] = b[2] = b[3] = 0.0;
+  if (rk == 4) { dense_b(t, m, b); return; }
+  if (rk == 2) {
+    if (m == 0) { b[0] = t - t * t; b[1] = t * t; }
+    else if (m == 1) { b[0] = 1.0 - 2.0 * t; b[1] = 2.0 * t; }
+    else if (m == 2) { b[0] = -2.0; b[1] = 2.0; }
+    return;
+  }
+  if (m == 0) {
+    b[0] = t - 1.25 * t * t + 0.5 * t * t * t;
+    b[2] = 2.25 * t * t - 1.5 * t * t * t;
+    b[3] = -t * t + t * t * t;
+  } else if (m == 1) {
+    b[0] = 1.0 - 2.5 * t + 1.5 * t * t;
+    b[2] = 4.5 * t - 4.5 * t * t;
+    b[3] = -2.0 * t + 3.0 * t * t;
+  } else if (m == 2) {
+    b[0] = -2.5 + 3.0 * t;
+    b[2] = 4.5 - 9.0 * t;
+    b[3] = -2.0 + 6.0 * t;
+  } else if (m == 3) {
+    b[0] = 3.0; b[2] = -9.0; b[3] = 6.0;
+  }
+}
+
+// Refinement-boundary ghost value for the RK2 / RK3 fine substep starting at
+// theta0 (step h = H/2).  The fine stage states follow from expanding the
+// method's stages about the substep start, to the order the method needs:
+//   RK2: Y1 = y, Y2 = y + h/2 y';
+//   RK3: Y1 = y, Y2 = y + h/3 y', Y3 = y + 2h/3 y' + 2h^2/9 y''
+// (exact when f is linear), with y, y', y'' from the dense output at theta0.
+// which = 0: the state at the end of the substep (dense output at theta0+1/2).
+double amr_value_rk(int rk, double y, const double* k, double H, double theta0, int which) {
+  if (rk == 4) return amr_value(y, k, H, theta0, which);
+  double b[4];
+  if (which == 0) {
+    dense_b_rk(rk, theta0 + 0.5, 0, b);
+    return y + H * (b[0] * k[0] + b[1] * k[1] + b[2] * k[2] + b[3] * k[3]);
+  }
+  const double h = 0.5 * H;
+  dense_b_rk(rk, theta0, 0, b);
+  const double y0 = y + H * (b[0] * k[0] + b[1] * k[1] + b[2] * k[2] + b[3] * k[3]);
+  dense_b_rk(rk, theta0, 1, b);
+  const double y1 = b[0] * k[0] + b[1] * k[1] + b[2] * k[2] + b[3] * k[3];
+  dense_b_rk(rk, theta0, 2, b);
+  const double y2 = (b[0] * k[0] + b[1] * k[1] + b[2] * k[2] + b[3] * k[3]) / H;
+  if (rk == 2) {
+    switch (which) {
+      case 1: return y0;
+      case 2: return y0 + 0.5 * h * y1;
+    }
+    return NAN;
+  }
+  switch (which) {
+    case 1: return y0;
+    case 2: return y0 + (h / 3.0) * y1;
+    case 3: return y0 + (2.0 * h / 3.0) * y1 + (2.0 * h * h / 9.0) * y2;
+  }
+  return NAN;
+}
+
 // ---------------------------------------------------------------------------
 // Hierarchy.
 
@@ -134,6 +211,7 @@ struct Level {
 struct Hier {
   int system, F, nlev, bc, subcycle;
   int order;  // finite-difference order of the right-hand sides: 4 or 8 (Sec. III.C)
+  int rk;     // Runge-Kutta method: 4 (Sec. II), 3 or 2 (see dense_b_rk)
   double cfl, h0, origin[3];
   int ncells0[3];
   double kappa1, kappa2, eta, sigma;
@@ -643,7 +721,11 @@ long node_offset(const Hier& H, int l, int (*nodes)[8], int blk, const int* li0,
   return H.lev[l].boxes[*box].off(li[0], li[1], li[2]);
 }
 
-// Step 2 of the algorithm: prolong the parent's y_n and k1..k4 to the
+int rk_stages_of(const Hier& H) { return H.rk; }
+// Stage vectors the dense output reads: k1..k4 (RK3: k4 = f(y_{n+1})), k1..k2 for RK2.
+int dense_vectors_of(const Hier& H) { return H.rk == 2 ? 2 : 4; }
+
+// Step 2 of the algorithm: prolong the parent's y_n and k1..k_s to the
 // refinement-boundary ghost cells of level l (tensor-product quintic Lagrange).
 void prolong_parent_vectors(Hier& H, int l) {
   Level& L = H.lev[l];
@@ -664,7 +746,7 @@ void prolong_parent_vectors(Hier& H, int l) {
             const long po = node_offset(H, l - 1, nodes, blk, li0, cx, cy, cz, &pb);
             const BoxData& P = H.lev[l - 1].boxes[pb];
             const double ww = w[0][cx] * w[1][cy] * w[2][cz];
-            for (int v = 0; v < 5; ++v)
+            for (int v = 0; v <= dense_vectors_of(H); ++v)
               for (int f = 0; f < H.F; ++f)
                 B.amr_P[(a * 5 + v) * H.F + f] += ww * P.v[src_vec[v]][(long)f * P.vol + po];
           }
@@ -708,7 +790,7 @@ void fill_amr(Hier& H, int l, int vec, double theta0, int which) {
         const double* P = &B.amr_P[a * 5 * H.F];
         const double y = P[f];
         const double k[4] = {P[H.F + f], P[2 * H.F + f], P[3 * H.F + f], P[4 * H.F + f]};
-        B.v[vec][(long)f * B.vol + B.amr_cell[a]] = amr_value(y, k, Hp, theta0, which);
+        B.v[vec][(long)f * B.vol + B.amr_cell[a]] = amr_value_rk(H.rk, y, k, Hp, theta0, which);
       }
   }
 }
@@ -783,40 +865,70 @@ void restrict_level(Hier& H, int l) {
 
 const double RK_C[3] = {0.5, 0.5, 1.0};
 
-// One RK4 step of level l (Eqs. rk1-rk5).  For l >= 1 the step is the fine
-// substep starting at progress theta0 of the parent step; its refinement-
-// boundary ghosts come from the parent's dense output.  k1..k4 are kept.
+// Stages of the method and the multiplier of k_{s-1} in stage input s >= 2
+// (every method here builds stage s from y_n and k_{s-1} alone).
+int rk_stages(const Hier& H) { return rk_stages_of(H); }
+double rk_stage_c(const Hier& H, int s) {
+  if (H.rk == 4) return RK_C[s - 2];
+  if (H.rk == 3) return s == 2 ? 1.0 / 3.0 : 2.0 / 3.0;
+  return 0.5;
+}
+
+// Stage input s of level l from y_n (V_YOLD) and k_{s-1}.
+void stage_input(Hier& H, int l, BoxData& B, int s, double dt) {
+  if (s == 1) {
+    B.v[V_STAGE] = B.v[V_YOLD];
+    return;
+  }
+  const double c = rk_stage_c(H, s) * dt;
+  for (int f = 0; f < H.F; ++f) {
+    const long fo = (long)f * B.vol;
+    const std::vector<double>& kp = B.v[V_K1 + s - 2];
+    for_evolved(H, l, B, [&](long o) { B.v[V_STAGE][fo + o] = B.v[V_YOLD][fo + o] + c * kp[fo + o]; });
+  }
+}
+
+// y_{n+1} from y_n and the stage vectors: Eq. rk5 for RK4; midpoint and
+// Heun's third-order combinations for RK2 and RK3.
+void final_update(Hier& H, int l, BoxData& B, double dt) {
+  for (int f = 0; f < H.F; ++f) {
+    const long fo = (long)f * B.vol;
+    const std::vector<double>& y0 = B.v[V_YOLD];
+    const std::vector<double>& k1 = B.v[V_K1];
+    const std::vector<double>& k2 = B.v[V_K1 + 1];
+    const std::vector<double>& k3 = B.v[V_K1 + 2];
+    const std::vector<double>& k4 = B.v[V_K1 + 3];
+    std::vector<double>& y = B.v[V_Y];
+    if (H.rk == 4)
+      for_evolved(H, l, B, [&](long o) {
+        y[fo + o] = y0[fo + o] + dt / 6.0 * (k1[fo + o] + 2.0 * k2[fo + o] + 2.0 * k3[fo + o] + k4[fo + o]);
+      });
+    else if (H.rk == 3)
+      for_evolved(H, l, B, [&](long o) { y[fo + o] = y0[fo + o] + dt * (0.25 * k1[fo + o] + 0.75 * k3[fo + o]); });
+    else
+      for_evolved(H, l, B, [&](long o) { y[fo + o] = y0[fo + o] + dt * k2[fo + o]; });
+  }
+}
+
+// One RK step of level l (Eqs. rk1-rk5 for RK4).  For l >= 1 the step is the
+// fine substep starting at progress theta0 of the parent step; its
+// refinement-boundary ghosts come from the parent's dense output.  The stage
+// vectors k_i are kept.
 void step_level(Hier& H, int l, double theta0) {
   Level& L = H.lev[l];
   const double dt = L.dt;
   const double t_n = L.t;
   for (BoxData& B : L.boxes) B.v[V_YOLD] = B.v[V_Y];
-  for (int s = 1; s <= 4; ++s) {
-    for (BoxData& B : L.boxes) {
-      if (s == 1) {
-        B.v[V_STAGE] = B.v[V_YOLD];
-      } else {
-        const double c = RK_C[s - 2] * dt;
-        for (int f = 0; f < H.F; ++f) {
-          const long fo = (long)f * B.vol;
-          const std::vector<double>& kp = B.v[V_K1 + s - 2];
-          for_evolved(H, l, B, [&](long o) { B.v[V_STAGE][fo + o] = B.v[V_YOLD][fo + o] + c * kp[fo + o]; });
-        }
-      }
-    }
+  for (int s = 1; s <= rk_stages(H); ++s) {
+    for (BoxData& B : L.boxes) stage_input(H, l, B, s, dt);
     fill_ghosts(H, l, V_STAGE, theta0, s, t_n, dt);
     for (BoxData& B : L.boxes) rhs_box(H, l, B, B.v[V_STAGE].data(), B.v[V_K1 + s - 1].data());
   }
-  for (BoxData& B : L.boxes)
-    for (int f = 0; f < H.F; ++f) {
-      const long fo = (long)f * B.vol;
-      for_evolved(H, l, B, [&](long o) {
-        B.v[V_Y][fo + o] = B.v[V_YOLD][fo + o] +
-                           dt / 6.0 * (B.v[V_K1][fo + o] + 2.0 * B.v[V_K1 + 1][fo + o] +
-                                       2.0 * B.v[V_K1 + 2][fo + o] + B.v[V_K1 + 3][fo + o]);
-      });
-    }
+  for (BoxData& B : L.boxes) final_update(H, l, B, dt);
   fill_ghosts(H, l, V_Y, theta0, 0, t_n, dt);
+  // RK3 dense output: k4 = f(y_{n+1}) on levels that have a finer level
+  if (H.rk == 3 && l + 1 < H.nlev)
+    for (BoxData& B : L.boxes) rhs_box(H, l, B, B.v[V_Y].data(), B.v[V_K1 + 3].data());
   L.t = t_n + dt;
 }
 
@@ -843,20 +955,9 @@ void global_step_uniform(Hier& H, double dt) {
   const double t_n = H.lev[0].t;
   for (int l = 0; l < H.nlev; ++l)
     for (BoxData& B : H.lev[l].boxes) B.v[V_YOLD] = B.v[V_Y];
-  for (int s = 1; s <= 4; ++s) {
+  for (int s = 1; s <= rk_stages(H); ++s) {
     for (int l = 0; l < H.nlev; ++l) {
-      for (BoxData& B : H.lev[l].boxes) {
-        if (s == 1) {
-          B.v[V_STAGE] = B.v[V_YOLD];
-        } else {
-          const double c = RK_C[s - 2] * dt;
-          for (int f = 0; f < H.F; ++f) {
-            const long fo = (long)f * B.vol;
-            const std::vector<double>& kp = B.v[V_K1 + s - 2];
-            for_evolved(H, l, B, [&](long o) { B.v[V_STAGE][fo + o] = B.v[V_YOLD][fo + o] + c * kp[fo + o]; });
-          }
-        }
-      }
+      for (BoxData& B : H.lev[l].boxes) stage_input(H, l, B, s, dt);
       if (l > 0) prolong_direct(H, l, V_STAGE, V_STAGE);
       if (l == 0) fill_physical_callback(H, V_STAGE, s, t_n, dt);
       copy_siblings(H, l, V_STAGE);
@@ -864,15 +965,7 @@ void global_step_uniform(Hier& H, double dt) {
     }
   }
   for (int l = 0; l < H.nlev; ++l)
-    for (BoxData& B : H.lev[l].boxes)
-      for (int f = 0; f < H.F; ++f) {
-        const long fo = (long)f * B.vol;
-        for_evolved(H, l, B, [&](long o) {
-          B.v[V_Y][fo + o] = B.v[V_YOLD][fo + o] +
-                             dt / 6.0 * (B.v[V_K1][fo + o] + 2.0 * B.v[V_K1 + 1][fo + o] +
-                                         2.0 * B.v[V_K1 + 2][fo + o] + B.v[V_K1 + 3][fo + o]);
-        });
-      }
+    for (BoxData& B : H.lev[l].boxes) final_update(H, l, B, dt);
   // ghosts of the new state first (restriction reads fine ghosts next to the
   // fine interior), from the parent's new state, then restriction.
   for (int l = 0; l < H.nlev; ++l) {
@@ -946,13 +1039,14 @@ extern "C" {
 int orc_create(int system, int nlevels, const int* nboxes, const int* boxes, const int* ncells0,
                const double* origin, double h0, int bc, double cfl, int subcycle, const double* params,
                void** out) {
-  return orc_create_order(system, nlevels, nboxes, boxes, ncells0, origin, h0, bc, cfl, subcycle, params, 4, out);
+  return orc_create_ex(system, nlevels, nboxes, boxes, ncells0, origin, h0, bc, cfl, subcycle, params, 4, 4, out);
 }
 
-int orc_create_order(int system, int nlevels, const int* nboxes, const int* boxes, const int* ncells0,
-                     const double* origin, double h0, int bc, double cfl, int subcycle, const double* params,
-                     int fd_order, void** out) {
+int orc_create_ex(int system, int nlevels, const int* nboxes, const int* boxes, const int* ncells0,
+                  const double* origin, double h0, int bc, double cfl, int subcycle, const double* params,
+                  int fd_order, int rk_order, void** out) {
   if (fd_order != 4 && fd_order != 8) return fail(-1, "fd_order must be 4 or 8");
+  if (rk_order < 2 || rk_order > 4) return fail(-1, "rk_order must be 2, 3 or 4");
   if (!out || nlevels < 1 || !nboxes || !boxes || !ncells0 || !origin) return fail(-1, "bad arguments");
   if (system != ORC_WAVE && system != ORC_Z4C) return fail(-1, "unknown system");
   Hier* H = new Hier();
@@ -962,6 +1056,7 @@ int orc_create_order(int system, int nlevels, const int* nboxes, const int* boxe
   H->bc = bc;
   H->subcycle = subcycle;
   H->order = fd_order;
+  H->rk = rk_order;
   H->cfl = cfl;
   H->h0 = h0;
   for (int d = 0; d < 3; ++d) { H->origin[d] = origin[d]; H->ncells0[d] = ncells0[d]; }
@@ -1177,6 +1272,10 @@ int orc_zone_updates(void* h, double* finest, double* actual) {
 }
 
 void orc_dense_b(double theta, int m, double* b4) { dense_b(theta, m, b4); }
+void orc_dense_b_rk(int rk, double theta, int m, double* b4) { dense_b_rk(rk, theta, m, b4); }
+double orc_amr_value_rk(int rk, double y, const double* k4, double H, double theta0, int which) {
+  return amr_value_rk(rk, y, k4, H, theta0, which);
+}
 
 double orc_amr_value(double y, const double* k4, double H, double theta0, int which) {
   return amr_value(y, k4, H, theta0, which);
@@ -1333,8 +1432,8 @@ int orc_regrid(void* h, const int* nboxes, const int* boxes) {
   const int L = H->nlev;
   void* nh = nullptr;
   double prm[4] = {H->kappa1, H->kappa2, H->eta, H->sigma};
-  const int rc = orc_create_order(H->system, L, nboxes, boxes, H->ncells0, H->origin, H->h0, H->bc, H->cfl,
-                                  H->subcycle, prm, H->order, &nh);
+  const int rc = orc_create_ex(H->system, L, nboxes, boxes, H->ncells0, H->origin, H->h0, H->bc, H->cfl,
+                               H->subcycle, prm, H->order, H->rk, &nh);
   if (rc) return rc;
   Hier* N = static_cast<Hier*>(nh);
   if (N->lev[0].boxes.size() != H->lev[0].boxes.size()) {

@@ -26,7 +26,7 @@ enum { ORC_ID_STANDING_WAVE = 0, ORC_ID_GAUSSIAN = 1, ORC_ID_BRILL_LINDQUIST = 2
 
 /* Physical boundary callback (ORC_BC_CALLBACK, level 0 only): fill out[f*npts+p]
  * with the value the stage state should take at the given cell centres.
- * which = 1..4: stage state Y_which of the step that starts at t_n with step dt;
+ * which = 1..s: stage state Y_which of the step that starts at t_n with step dt;
  * which = 0: the state y(t_n + dt) after the step. */
 typedef void (*orc_bc_fn)(void* user, int which, double t_n, double dt, int npts,
                           const double* xyz, double* out);
@@ -34,12 +34,15 @@ typedef void (*orc_bc_fn)(void* user, int which, double t_n, double dt, int npts
 int orc_create(int system, int nlevels, const int* nboxes, const int* boxes,
                const int* ncells0, const double* origin, double h0, int bc,
                double cfl, int subcycle, const double* params, void** out);
-/* As orc_create with the finite-difference order of the right-hand sides:
- * 4 (3 ghost cells per box) or 8 (the paper's production setting, 4 ghost
- * cells); Kreiss-Oliger dissipation stays r = 4. */
-int orc_create_order(int system, int nlevels, const int* nboxes, const int* boxes,
-                     const int* ncells0, const double* origin, double h0, int bc,
-                     double cfl, int subcycle, const double* params, int fd_order, void** out);
+/* As orc_create with the finite-difference order of the right-hand sides,
+ * fd_order = 4 (3 ghost cells per box) or 8 (the paper's production setting,
+ * 4 ghost cells; Kreiss-Oliger dissipation stays r = 4), and the Runge-Kutta
+ * method, rk_order = 4 (classic RK4, Sec. II), 3 (Heun's third-order method)
+ * or 2 (explicit midpoint), each subcycled with its own dense output. */
+int orc_create_ex(int system, int nlevels, const int* nboxes, const int* boxes,
+                  const int* ncells0, const double* origin, double h0, int bc,
+                  double cfl, int subcycle, const double* params, int fd_order, int rk_order,
+                  void** out);
 void orc_destroy(void* h);
 int orc_nfields(void* h);
 int orc_set_bc_callback(void* h, orc_bc_fn fn, void* user);
@@ -57,6 +60,8 @@ int orc_zone_updates(void* h, double* finest_equiv, double* actual);
 /* Pieces of the method, exposed for the pin tests. */
 void orc_dense_b(double theta, int m, double* b4);
 double orc_amr_value(double y, const double* k4, double H, double theta0, int which);
+void orc_dense_b_rk(int rk, double theta, int m, double* b4);
+double orc_amr_value_rk(int rk, double y, const double* k4, double H, double theta0, int which);
 int orc_rhs_box(void* h, int level, int box, const double* state_ghosted, double* rhs_ghosted);
 int orc_constraints(void* h, int level, int box, double* out);
 int orc_debug_set_vector(void* h, int level, int box, int vec, int field, const double* src);

@@ -46,6 +46,7 @@ class Hierarchy:
     ko_sigma: float = 0.3
     eta_profile: Optional[Tuple[float, float, float]] = None  # (eta_c, eta_s, eta_o) of Sec. III.A
     fd_order: int = 4  # finite-difference order of the right-hand sides (4 or 8)
+    rk_order: int = 4  # Runge-Kutta method: 4 (classic), 3 (Heun's third order), 2 (midpoint)
     id_kind: int = ID_STANDING_WAVE
     id_params: List[float] = field(default_factory=list)
     name: str = ""
@@ -89,6 +90,8 @@ class Hierarchy:
             kw["eta_profile"] = self.eta_profile
         if self.fd_order != 4:
             kw["fd_order"] = self.fd_order
+        if self.rk_order != 4:
+            kw["rk_order"] = self.rk_order
         return kw
 
 
