@@ -114,12 +114,21 @@ typedef struct {
   int fd_order;    /* finite-difference order of the right-hand sides: 4 (0 = default) or 8, the
                       paper's production setting (Sec. III.C); Kreiss-Oliger stays r = 4.  Every box
                       then carries 4 ghost layers instead of 3 (the _ghosted field calls use them). */
+  int rk_order;    /* Runge-Kutta method, subcycled with its own dense output: 4 (0 = default), the
+                      classic RK4 of Sec. II; 3, Heun's third-order method (stage inputs y + h/3 k1,
+                      y + 2h/3 k2; y_{n+1} = y + h/4 (k1 + 3 k3)); 2, the explicit midpoint rule
+                      (y + h/2 k1; y_{n+1} = y + h k2).  RK2 and RK3 are the extension the paper
+                      (Sec. V) leaves to future work: their dense outputs are the second-order
+                      continuous extensions b1 = t - 3t^2/4, b3 = 3t^2/4 (RK3) and b1 = t - t^2,
+                      b2 = t^2 (RK2), and fine stage inputs at refinement boundaries are their
+                      Taylor expansions (RK3: y, y + h/3 y', y + 2h/3 y' + 2h^2/9 y''; RK2: y,
+                      y + h/2 y').  Other values: SC_EINVAL. */
 } sc_desc;
 
 enum { SC_EXEC_GRAPH = 0, SC_EXEC_PER_BOX = 1 };
 
 /* Build the hierarchy: validate nesting and alignment, allocate every level's
- * state, stage and k1..k4 arrays, build the device work lists.
+ * state, stage and k1..k_s arrays (s = rk_order), build the device work lists.
  * Errors: SC_EINVAL, SC_ENESTING, SC_ENOMEM, SC_ECUDA. */
 sc_status sc_create(const sc_desc* desc, sc_ctx** out);
 
@@ -149,7 +158,7 @@ sc_status sc_set_field_device(sc_ctx* ctx, int level, int box, int field, const 
 sc_status sc_get_field_device(sc_ctx* ctx, int level, int box, int field, double* dev_dst);
 
 /* Advance n coarse steps (Sec. II, steps 1-7 per coarse step): level 0
- * takes one RK4 step storing k1..k4, every finer level two substeps per
+ * takes one RK step storing its stage vectors, every finer level two substeps per
  * parent step with refinement-boundary ghosts from the parent's dense
  * output (theta0 = 0 and 1/2), recursively, then restriction.  Each coarse
  * step is one CUDA graph launch on the context's stream; asynchronous. */
@@ -269,12 +278,14 @@ sc_status sc_server_destroy(sc_server* srv);
  * and testing): vec 0 = current state, 1 = the other state buffer (after a
  * step: the state at the start of the level's last step, with the ghost
  * values its first stage used), 2/3 = stage buffers, 4..7 = k1..k4 of the
- * level's last step.  ghosted: include 3 ghost cells per side.  Synchronises. */
+ * level's last step (SC_EINVAL for k's the Runge-Kutta method does not have).
+ * ghosted: include the ghost cells (3 or 4 per side).  Synchronises. */
 sc_status sc_debug_get_vector(sc_ctx* ctx, int level, int box, int vec, int field, int ghosted, double* host_dst);
 
 /* Time the refinement-boundary kernels of one refined level outside the
  * graph, with CUDA events on the context's stream, averaged over nrep:
- * ms[0] = prolongation of the parent's y_n, k1..k4 to the level's ghost cells
+ * ms[0] = prolongation of the parent's y_n and the stage vectors its dense
+ * output uses (k1..k4 for RK4) to the level's ghost cells
  * (block-separable kernel plus per-cell fallback), ms[1] = one dense-output
  * ghost fill.  counts[0] = ghost cells, counts[1] = 4x4x4 blocks of the
  * separable kernel, counts[2] = ghost cells on the per-cell fallback.

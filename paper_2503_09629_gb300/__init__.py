@@ -75,6 +75,7 @@ class sc_desc(ctypes.Structure):
         ("eta_s", ctypes.c_double),
         ("eta_o", ctypes.c_double),
         ("fd_order", ctypes.c_int),
+        ("rk_order", ctypes.c_int),
     ]
 
 
@@ -186,6 +187,7 @@ def make_desc(h, stream: Optional[int] = None, allocator=None, exec_mode: int = 
     d.cuda_stream = stream
     d.exec_mode = exec_mode
     d.fd_order = int(getattr(h, "fd_order", 4))
+    d.rk_order = int(getattr(h, "rk_order", 4))
     prof = getattr(h, "eta_profile", None)
     if prof is not None:
         d.eta_profile = 1

@@ -127,13 +127,15 @@ __global__ void __launch_bounds__(256) amr_prolong_block_kernel(
   }
 }
 
-// Sec. II steps 3/5: ghost value = P[y_n] + sum_j c_j P[k_j]; the four
-// coefficients encode dense output (Eqs. denseoutput1/2) and the Taylor stage
-// formulas (Eqs. Y1-Y4) for one stage of one fine substep.
+// Sec. II steps 3/5: ghost value = P[y_n] + sum_j c_j P[k_j] over the nk
+// prolonged stage vectors in the store (4 for RK4, 3 for RK3, 2 for RK2, 0
+// for a plain prolonged value); the coefficients encode dense output (Eqs.
+// denseoutput1/2) and the Taylor stage formulas (Eqs. Y1-Y4) for one stage of
+// one fine substep.
 __global__ void __launch_bounds__(kThreads) amr_apply_kernel(double* __restrict__ vec, long fs, int F,
                                                             const AmrCell* __restrict__ cells, int ncells,
                                                             const double* __restrict__ store, double c1,
-                                                            double c2, double c3, double c4) {
+                                                            double c2, double c3, double c4, int nk) {
   const long total = (long)ncells * F;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
     const int a = (int)(idx % ncells);
@@ -142,10 +144,10 @@ __global__ void __launch_bounds__(kThreads) amr_apply_kernel(double* __restrict_
     const double* s = store + (long)f * n + a;
     const long vs = (long)F * n;
     double v = s[0];
-    v = fma(c1, s[vs], v);
-    v = fma(c2, s[2 * vs], v);
-    v = fma(c3, s[3 * vs], v);
-    v = fma(c4, s[4 * vs], v);
+    if (nk > 0) v = fma(c1, s[vs], v);
+    if (nk > 1) v = fma(c2, s[2 * vs], v);
+    if (nk > 2) v = fma(c3, s[3 * vs], v);
+    if (nk > 3) v = fma(c4, s[4 * vs], v);
     vec[(long)f * fs + cells[a].dst] = v;
   }
 }
@@ -384,10 +386,10 @@ cudaError_t launch_amr_prolong_blocks(const double* yn, const double* k1, const 
 }
 
 cudaError_t launch_amr_apply(double* vec, long fs, int F, const AmrCell* cells, int ncells, const double* store,
-                             const double* c4, cudaStream_t s) {
+                             const double* c4, cudaStream_t s, int nk) {
   if (ncells == 0) return cudaSuccess;
   amr_apply_kernel<<<grid_for((long)ncells * F, kThreads), kThreads, 0, s>>>(vec, fs, F, cells, ncells, store, c4[0],
-                                                                            c4[1], c4[2], c4[3]);
+                                                                            c4[1], c4[2], c4[3], nk);
   return cudaGetLastError();
 }
 

@@ -101,34 +101,134 @@ void dense_weights(double t, int m, double* b) {
   }
 }
 
-// Coefficients c_j of ghost value = P[y_n] + sum_j c_j P[k_j] for the fine
-// substep starting at progress theta0 of a parent step H (fine step h = H/2):
-//   which = 1..4: stage state Y_which from the Taylor expansions (Eqs. Y1-Y4)
-//                 with y, y', y'', y''' from dense output at theta0 and
-//                 f_y y'' = 4 (k3 - k2) / H^2;
-//   which = 0:    state at the end of the substep, dense output at theta0 + 1/2.
-void fill_coeffs(double H, double theta0, int which, double* c) {
-  double b0[4], b1[4], b2[4], b3[4];
-  if (which == 0) {
-    dense_weights(theta0 + 0.5, 0, b0);
-    for (int j = 0; j < 4; ++j) c[j] = H * b0[j];
+// Runge-Kutta methods (rk = number of stages = order).  Every method here
+// builds stage input s >= 2 from y_n and k_{s-1} alone (RK3 levels with a
+// finer level also evaluate k4 = f(y_{n+1}) for their dense output):
+//   rk = 4: classic RK4 (Eqs. rk1-rk5), multipliers 1/2, 1/2, 1;
+//   rk = 3: Heun's third-order method, multipliers 1/3, 2/3,
+//           y_{n+1} = y_n + dt/4 (k1 + 3 k3);
+//   rk = 2: explicit midpoint, multiplier 1/2, y_{n+1} = y_n + dt k2.
+double stage_mult(int rk, int s) {
+  if (rk == 4) return s == 4 ? 1.0 : 0.5;
+  if (rk == 3) return s == 2 ? 1.0 / 3.0 : 2.0 / 3.0;
+  return 0.5;
+}
+
+// Stage vectors the dense output uses, in the order they are prolonged into
+// the ghost store: k1..k4 for RK4; k1, k3 and k4 = f(y_{n+1}) for RK3; k1
+// and k2 for RK2.
+int dense_vectors(int rk, int* idx) {
+  if (rk == 4) {
+    for (int j = 0; j < 4; ++j) idx[j] = j;
+    return 4;
+  }
+  if (rk == 3) {
+    idx[0] = 0;
+    idx[1] = 2;
+    idx[2] = 3;
+    return 3;
+  }
+  idx[0] = 0;
+  idx[1] = 1;
+  return 2;
+}
+
+int dense_count(int rk) {
+  int idx[4];
+  return dense_vectors(rk, idx);
+}
+
+// Dense-output weights of RK3 and RK2 and their theta-derivatives, per stage
+// vector (index 3 = k4 = f(y_{n+1})):
+//   RK3: the cubic Hermite interpolant through y_n, y_{n+1} with slopes k1
+//        and k4: b1 = t - 5t^2/4 + t^3/2, b3 = 9t^2/4 - 3t^3/2,
+//        b4 = -t^2 + t^3 (third order; RK3's own second-order continuous
+//        extensions leave the subcycled scheme near order 2.5);
+//   RK2: b1 = t - t^2, b2 = t^2 (second order).
+void dense_weights_rk(int rk, double t, int m, double* b) {
+  if (rk == 4) {
+    dense_weights(t, m, b);
     return;
   }
-  const double h = 0.5 * H;
-  dense_weights(theta0, 0, b0);
-  dense_weights(theta0, 1, b1);
-  dense_weights(theta0, 2, b2);
-  dense_weights(theta0, 3, b3);
-  const double fyy[4] = {0.0, -4.0, 4.0, 0.0};  // times 1/H^2
-  for (int j = 0; j < 4; ++j) {
-    const double y0 = H * b0[j], y1 = b1[j], y2 = b2[j] / H, y3 = b3[j] / (H * H), fy = fyy[j] / (H * H);
-    switch (which) {
-      case 1: c[j] = y0; break;
-      case 2: c[j] = y0 + 0.5 * h * y1; break;
-      case 3: c[j] = y0 + 0.5 * h * y1 + 0.25 * h * h * y2 + (h * h * h / 16.0) * (y3 - fy); break;
-      default: c[j] = y0 + h * y1 + 0.5 * h * h * y2 + (h * h * h / 8.0) * (y3 + fy); break;
+  b[0] = b[1] = b[2] = b[3] = 0.0;
+  if (rk == 3) {
+    if (m == 0) {
+      b[0] = t * (1.0 + t * (-1.25 + 0.5 * t));
+      b[2] = t * t * (2.25 - 1.5 * t);
+      b[3] = t * t * (-1.0 + t);
+    } else if (m == 1) {
+      b[0] = 1.0 + t * (-2.5 + 1.5 * t);
+      b[2] = t * (4.5 - 4.5 * t);
+      b[3] = t * (-2.0 + 3.0 * t);
+    } else if (m == 2) {
+      b[0] = -2.5 + 3.0 * t;
+      b[2] = 4.5 - 9.0 * t;
+      b[3] = -2.0 + 6.0 * t;
+    } else if (m == 3) {
+      b[0] = 3.0;
+      b[2] = -9.0;
+      b[3] = 6.0;
+    }
+    return;
+  }
+  if (m == 0) {
+    b[0] = t * (1.0 - t);
+    b[1] = t * t;
+  } else if (m == 1) {
+    b[0] = 1.0 - 2.0 * t;
+    b[1] = 2.0 * t;
+  } else if (m == 2) {
+    b[0] = -2.0;
+    b[1] = 2.0;
+  }
+}
+
+// Coefficients c_j of ghost value = P[y_n] + sum_j c_j P[k_j] for the fine
+// substep starting at progress theta0 of a parent step H (fine step
+// h = H/2), one per prolonged stage vector (dense_vectors order):
+//   which = 1..rk: fine stage input Y_which.  RK4: the Taylor expansions of
+//     Eqs. Y1-Y4 with the first three theta-derivatives of the dense output
+//     at theta0 (Eqs. denseoutput1/2) and f_y y2 = 4 (k3 - k2) / H^2.
+//     RK3: Y1 = y, Y2 = y + h/3 y1, Y3 = y + 2h/3 y1 + 2h^2/9 y2.
+//     RK2: Y1 = y, Y2 = y + h/2 y1.  (y1, y2: first and second time
+//     derivatives; each formula is exact for linear right-hand sides.)
+//   which = 0: state at the end of the substep, dense output at theta0 + 1/2.
+void fill_coeffs(int rk, double H, double theta0, int which, double* c) {
+  double b0[4], b1[4], b2[4], b3[4], full[4];
+  if (which == 0) {
+    dense_weights_rk(rk, theta0 + 0.5, 0, b0);
+    for (int j = 0; j < 4; ++j) full[j] = H * b0[j];
+  } else {
+    const double h = 0.5 * H;
+    dense_weights_rk(rk, theta0, 0, b0);
+    dense_weights_rk(rk, theta0, 1, b1);
+    dense_weights_rk(rk, theta0, 2, b2);
+    if (rk == 4) dense_weights(theta0, 3, b3);
+    const double fyy[4] = {0.0, -4.0, 4.0, 0.0};  // times 1/H^2
+    for (int j = 0; j < 4; ++j) {
+      const double y0 = H * b0[j], y1 = b1[j], y2 = b2[j] / H;
+      if (rk == 4) {
+        const double y3 = b3[j] / (H * H), fy = fyy[j] / (H * H);
+        switch (which) {
+          case 1: full[j] = y0; break;
+          case 2: full[j] = y0 + 0.5 * h * y1; break;
+          case 3: full[j] = y0 + 0.5 * h * y1 + 0.25 * h * h * y2 + (h * h * h / 16.0) * (y3 - fy); break;
+          default: full[j] = y0 + h * y1 + 0.5 * h * h * y2 + (h * h * h / 8.0) * (y3 + fy); break;
+        }
+      } else if (rk == 3) {
+        switch (which) {
+          case 1: full[j] = y0; break;
+          case 2: full[j] = y0 + (h / 3.0) * y1; break;
+          default: full[j] = y0 + (2.0 * h / 3.0) * y1 + (2.0 * h * h / 9.0) * y2; break;
+        }
+      } else {
+        full[j] = which == 1 ? y0 : y0 + 0.5 * h * y1;
+      }
     }
   }
+  int idx[4];
+  const int n = dense_vectors(rk, idx);
+  for (int j = 0; j < 4; ++j) c[j] = j < n ? full[idx[j]] : 0.0;
 }
 
 struct DevBuf {
@@ -141,7 +241,7 @@ struct Level {
   Geom g;
   double dt = 0;
   std::vector<int8_t> kind;  // per array element (host only)
-  // device arrays: state pair, two stage buffers, k1..k4
+  // device arrays: state pair, two stage buffers, k1..k_rk (unused ones null)
   double* S[2] = {nullptr, nullptr};
   double* A = nullptr;
   double* B = nullptr;
@@ -162,7 +262,7 @@ struct Level {
   double* eta = nullptr;  // per-element eta(r) (Z4c with the Sec. III.A profile), else null
   std::vector<void*> allocs;  // device buffers owned by this level (freed on regrid)
   int namr_blocked = 0;
-  double* amr_store = nullptr;  // 5 * F * namr prolonged parent vectors
+  double* amr_store = nullptr;  // (1 + dense vectors) * F * namr prolonged parent vectors
   int2* periodic = nullptr;
   int nperiodic = 0;
   int32_t* phys = nullptr;
@@ -183,7 +283,9 @@ struct Op {
   double* yn;
   double* out;
   double c[4];    // OP_FILL coefficients
-  double cdt;     // OP_STAGE
+  double cdt;     // OP_STAGE update (StageArgs)
+  double c1dt;
+  int form;
   bool no_amr;    // OP_FILL: periodic images only (uniform-step mode)
 };
 
@@ -213,6 +315,7 @@ struct sc_ctx {
   int exec_mode = SC_EXEC_GRAPH;
   int subcycle = 1;
   int order = 4;   // finite-difference order of the right-hand sides (4 or 8)
+  int rk = 4;      // Runge-Kutta method: stages = order = 4, 3 or 2
   int ghost = 3;   // ghost layers per box: 3 for 4th order, 4 for 8th
   int tile[3] = {32, 4, 2};  // stencil-kernel tile shape (autotuned on request)
   int eta_profile = 0;
@@ -285,6 +388,7 @@ sc_status validate(const sc_desc* d) {
   if (!d->nboxes || !d->boxes) return fail(SC_EINVAL, "null box arrays");
   if (d->subcycle != 0 && d->subcycle != 1) return fail(SC_EINVAL, "subcycle must be 0 or 1");
   if (d->fd_order != 0 && d->fd_order != 4 && d->fd_order != 8) return fail(SC_EINVAL, "fd_order must be 4 or 8");
+  if (d->rk_order != 0 && (d->rk_order < 2 || d->rk_order > 4)) return fail(SC_EINVAL, "rk_order must be 2, 3 or 4");
   if (d->outer_bc != SC_BC_PERIODIC && d->outer_bc != SC_BC_RADIATIVE) return fail(SC_EINVAL, "unknown outer_bc");
   if (!(d->h0 > 0) || !(d->cfl > 0)) return fail(SC_EINVAL, "h0 and cfl must be positive");
   for (int q = 0; q < 3; ++q)
@@ -671,13 +775,19 @@ void free_level(sc_ctx* c, Level& L) {
   L.allocs.clear();
 }
 
-// Device side of a level: the 8 state/stage/k vectors (zeroed), its work
-// lists, the ghost store and the eta(r) array.
+// Stage vectors a level keeps: rk, plus k4 = f(y_{n+1}) on RK3 levels that
+// have a finer level.
+int level_kvecs(int rk, int l, int nlev) { return rk == 3 && l + 1 < nlev ? 4 : rk; }
+
+// Device side of a level: the state pair, the two stage buffers and the
+// stage vectors (zeroed), its work lists, the ghost store and the eta(r) array.
 sc_status setup_level_device(sc_ctx* c, int l, HostLists& hl) {
   Level& L = c->lev[l];
   const size_t vbytes = sizeof(double) * (size_t)c->F * L.g.fs;
   double** vecs[8] = {&L.S[0], &L.S[1], &L.A, &L.B, &L.K[0], &L.K[1], &L.K[2], &L.K[3]};
-  for (double** v : vecs) {
+  for (int j = 0; j < 4; ++j) L.K[j] = nullptr;
+  for (int q = 0; q < 4 + level_kvecs(c->rk, l, c->nlev); ++q) {
+    double** v = vecs[q];
     *v = (double*)level_alloc(c, L, vbytes);
     if (!*v) return fail(SC_ENOMEM, "level %d: allocation of %zu bytes failed", l, vbytes);
     CU(cudaMemsetAsync(*v, 0, vbytes, c->stream));
@@ -699,7 +809,9 @@ sc_status setup_level_device(sc_ctx* c, int l, HostLists& hl) {
   L.nrestr = (int)hl.restr.size();
   L.amr_store = nullptr;
   if (L.namr) {
-    L.amr_store = (double*)level_alloc(c, L, sizeof(double) * 5 * (size_t)c->F * L.namr);
+    int idx[4];
+    const int nvec = 1 + dense_vectors(c->rk, idx);
+    L.amr_store = (double*)level_alloc(c, L, sizeof(double) * nvec * (size_t)c->F * L.namr);
     if (!L.amr_store) return fail(SC_ENOMEM, "level %d: ghost store allocation failed", l);
   }
   L.eta = nullptr;
@@ -723,18 +835,36 @@ struct Emitter {
     o.level = l;
     o.in = vec;
     o.stage = which;
-    if (l > 0) fill_coeffs(c->lev[l - 1].dt, theta0, which, o.c);
+    if (l > 0) fill_coeffs(c->rk, c->lev[l - 1].dt, theta0, which, o.c);
     ops.push_back(o);
   }
-  // One RK4 step of level l (Eqs. rk1-rk5); for l >= 1 the fine substep at
-  // progress theta0 of the parent step.
+  // Update of stage s with step dt: the next stage input, or y_{n+1}.
+  void stage_update(Op& o, int s, double dt) {
+    const int S = c->rk;
+    if (s < S) {
+      o.form = kStageSingle;
+      o.cdt = stage_mult(S, s + 1) * dt;
+    } else if (S == 4) {
+      o.form = kStageRk4;
+      o.cdt = dt / 6.0;
+    } else if (S == 3) {
+      o.form = kStageTwo;
+      o.c1dt = 0.25 * dt;
+      o.cdt = 0.75 * dt;
+    } else {
+      o.form = kStageSingle;
+      o.cdt = dt;
+    }
+  }
+  // One RK step of level l (Eqs. rk1-rk5 for RK4); for l >= 1 the fine
+  // substep at progress theta0 of the parent step.
   void level_step(int l, double theta0) {
     Level& L = c->lev[l];
     double* yn = L.S[par[l]];
     double* ynew = L.S[par[l] ^ 1];
     double* in[4] = {yn, L.A, L.B, L.A};
-    const double cs[3] = {0.5, 0.5, 1.0};
-    for (int s = 1; s <= 4; ++s) {
+    const int S = c->rk;
+    for (int s = 1; s <= S; ++s) {
       fill(l, in[s - 1], s, theta0);
       Op o{};
       o.kind = OP_STAGE;
@@ -742,11 +872,24 @@ struct Emitter {
       o.stage = s;
       o.in = in[s - 1];
       o.yn = yn;
-      o.out = (s < 4) ? in[s] : ynew;
-      o.cdt = (s < 4) ? cs[s - 1] * L.dt : L.dt / 6.0;
+      o.out = (s < S) ? in[s] : ynew;
+      stage_update(o, s, L.dt);
       ops.push_back(o);
     }
-    if (l > 0) fill(l, ynew, 0, theta0);  // end-of-substep ghosts, read by restriction
+    const bool k4 = S == 3 && l + 1 < c->nlev;
+    // end-of-substep ghosts (read by restriction; and by k4 below)
+    if (l > 0 || k4) fill(l, ynew, 0, theta0);
+    if (k4) {  // RK3 dense output: k4 = f(y_{n+1}), no state update
+      Op o{};
+      o.kind = OP_STAGE;
+      o.level = l;
+      o.stage = 4;
+      o.in = ynew;
+      o.yn = yn;
+      o.out = nullptr;
+      o.form = kStageNone;
+      ops.push_back(o);
+    }
     par[l] ^= 1;
   }
   // Steps 2-7 below level l, after level l has taken a step.
@@ -799,10 +942,10 @@ struct Emitter {
   void uniform_step() {
     const int L = c->nlev;
     const double dt = c->lev[L - 1].dt;
-    const double cs[3] = {0.5, 0.5, 1.0};
+    const int S = c->rk;
     std::vector<std::array<double*, 4>> in(L);
     for (int l = 0; l < L; ++l) in[l] = {c->lev[l].S[par[l]], c->lev[l].A, c->lev[l].B, c->lev[l].A};
-    for (int s = 1; s <= 4; ++s)
+    for (int s = 1; s <= S; ++s)
       for (int l = 0; l < L; ++l) {
         if (l > 0) prolong_direct(l, in[l - 1][s - 1], in[l][s - 1]);
         periodic_only(l, in[l][s - 1]);
@@ -812,8 +955,8 @@ struct Emitter {
         o.stage = s;
         o.in = in[l][s - 1];
         o.yn = c->lev[l].S[par[l]];
-        o.out = (s < 4) ? in[l][s] : c->lev[l].S[par[l] ^ 1];
-        o.cdt = (s < 4) ? cs[s - 1] * dt : dt / 6.0;
+        o.out = (s < S) ? in[l][s] : c->lev[l].S[par[l] ^ 1];
+        stage_update(o, s, dt);
         ops.push_back(o);
       }
     for (int l = 1; l < L; ++l) {
@@ -832,18 +975,30 @@ struct Emitter {
   }
 };
 
+// Sec. II step 2: prolong the parent's y_n and the stage vectors its dense
+// output uses to the refinement-boundary ghost cells of level l.
+cudaError_t prolong_parent(sc_ctx* c, int l, const double* yn, cudaStream_t s) {
+  Level& L = c->lev[l];
+  const Level& P = c->lev[l - 1];
+  int idx[4];
+  const int nk = dense_vectors(c->rk, idx);
+  const double* v[4] = {yn, yn, yn, yn};
+  for (int j = 0; j < nk; ++j) v[j] = P.K[idx[j]];
+  const int psy = P.g.pitch, psz = P.g.pitch * P.g.ext[1];
+  cudaError_t e = launch_amr_prolong_blocks(yn, v[0], v[1], v[2], v[3], P.g.fs, psy, psz, L.blocks, L.nblocks, L.namr,
+                                            L.amr_store, c->F, c->w, s, 1 + nk);
+  if (e != cudaSuccess) return e;
+  return launch_amr_prolong(yn, v[0], v[1], v[2], v[3], P.g.fs, psy, psz, L.amr, L.namr_blocked, L.namr, L.amr_store,
+                            c->F, c->w, s, 1 + nk);
+}
+
 sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
   Level& L = c->lev[o.level];
   const Geom& g = L.g;
   switch (o.kind) {
-    case OP_PROLONG: {
-      const Level& P = c->lev[o.level - 1];
-      CU(launch_amr_prolong_blocks(o.yn, P.K[0], P.K[1], P.K[2], P.K[3], P.g.fs, P.g.pitch, P.g.pitch * P.g.ext[1],
-                                   L.blocks, L.nblocks, L.namr, L.amr_store, c->F, c->w, s));
-      CU(launch_amr_prolong(o.yn, P.K[0], P.K[1], P.K[2], P.K[3], P.g.fs, P.g.pitch, P.g.pitch * P.g.ext[1], L.amr,
-                            L.namr_blocked, L.namr, L.amr_store, c->F, c->w, s));
+    case OP_PROLONG:
+      CU(prolong_parent(c, o.level, o.yn, s));
       break;
-    }
     case OP_PROLONG_DIRECT: {
       // one vector through the separable block kernel into the ghost store,
       // then an apply with zero k coefficients (exactly the prolonged value)
@@ -854,11 +1009,12 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       CU(launch_amr_prolong(o.in, o.in, o.in, o.in, o.in, P.g.fs, psy, psz, L.amr, L.namr_blocked, L.namr, L.amr_store,
                             c->F, c->w, s, 1));
       const double zero[4] = {0.0, 0.0, 0.0, 0.0};
-      CU(launch_amr_apply(o.out, g.fs, c->F, L.amr, L.namr, L.amr_store, zero, s));
+      CU(launch_amr_apply(o.out, g.fs, c->F, L.amr, L.namr, L.amr_store, zero, s, 0));
       break;
     }
     case OP_FILL:
-      if (o.level > 0 && !o.no_amr) CU(launch_amr_apply(o.in, g.fs, c->F, L.amr, L.namr, L.amr_store, o.c, s));
+      if (o.level > 0 && !o.no_amr)
+        CU(launch_amr_apply(o.in, g.fs, c->F, L.amr, L.namr, L.amr_store, o.c, s, dense_count(c->rk)));
       CU(launch_periodic_copy(o.in, g.fs, c->F, L.periodic, L.nperiodic, s));
       break;
     case OP_STAGE: {
@@ -871,6 +1027,8 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       a.k2 = L.K[1];
       a.k3 = L.K[2];
       a.cdt = o.cdt;
+      a.c1dt = o.c1dt;
+      a.form = o.form;
       a.stage = o.stage;
       a.fs = g.fs;
       a.sy = g.pitch;
@@ -1059,6 +1217,7 @@ sc_status time_stencil(sc_ctx* c, Level& L, const Tile* tiles, int ntiles, int r
   a.k2 = L.K[1];
   a.k3 = L.K[2];
   a.cdt = 0.5 * L.dt;
+  a.form = kStageSingle;
   a.stage = 2;
   a.fs = g.fs;
   a.sy = g.pitch;
@@ -1222,6 +1381,7 @@ extern "C" sc_status sc_regrid(sc_ctx* c, const int* nboxes, const sc_box* boxes
   d.cfl = c->cfl;
   d.subcycle = 1;
   d.fd_order = c->order;
+  d.rk_order = c->rk;
   sc_status st = validate(&d);
   if (st) return st;
   if (nboxes[0] != (int)c->lev[0].boxes.size()) return fail(SC_EINVAL, "regrid keeps level 0 unchanged");
@@ -1344,6 +1504,7 @@ sc_status sc_footprint_estimate(const sc_desc* d, size_t* bytes) {
   if (st) return st;
   const int F = d->system == SC_WAVE ? kNWave : kNZ4c;
   const int ghost = d->fd_order == 8 ? 4 : 3;
+  const int rk = d->rk_order == 0 ? 4 : d->rk_order;
   size_t total = 0, maxfs = 0;
   int bi = 0;
   for (int l = 0; l < d->nlevels; ++l) {
@@ -1362,9 +1523,9 @@ sc_status sc_footprint_estimate(const sc_desc* d, size_t* bytes) {
     }
     const long pitch = ((hi[0] - lo[0] + 1 + 2 * ghost) + 7) & ~7;
     const long fs = ((pitch * (hi[1] - lo[1] + 1 + 2 * ghost) * (hi[2] - lo[2] + 1 + 2 * ghost)) + 31) & ~31L;
-    total += 8 * (size_t)F * fs * sizeof(double);                 // S0, S1, A, B, k1..k4
+    total += (4 + level_kvecs(rk, l, d->nlevels)) * (size_t)F * fs * sizeof(double);  // S0, S1, A, B, k's
     if (d->system == SC_Z4C && d->eta_profile) total += (size_t)fs * sizeof(double);
-    total += (size_t)ghost_cells * (5 * F * sizeof(double) + 32);  // prolonged vectors + lists
+    total += (size_t)ghost_cells * ((1 + dense_count(rk)) * F * sizeof(double) + 32);  // prolonged vectors + lists
     total += (size_t)fs * 4;                                       // tiles and other lists (bound)
     maxfs = std::max(maxfs, (size_t)fs);
   }
@@ -1406,6 +1567,7 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
   c->subcycle = d->subcycle;
   c->order = d->fd_order == 8 ? 8 : 4;
   c->ghost = c->order == 8 ? 4 : 3;
+  c->rk = d->rk_order == 0 ? 4 : d->rk_order;
   c->eta_profile = d->eta_profile ? 1 : 0;
   c->eta_c = d->eta_c;
   c->eta_s = d->eta_s;
@@ -1629,6 +1791,7 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   a.k2 = L.K[1];
   a.k3 = L.K[2];
   a.cdt = 0.5 * L.dt;
+  a.form = kStageSingle;
   a.stage = 2;
   a.fs = g.fs;
   a.sy = g.pitch;
@@ -1678,6 +1841,7 @@ sc_status sc_debug_get_vector(sc_ctx* c, int level, int box, int vec, int field,
   if (!dst || vec < 0 || vec > 7) return fail(SC_EINVAL, "bad vector or destination");
   Level& L = c->lev[level];
   double* src[8] = {L.S[L.parity], L.S[L.parity ^ 1], L.A, L.B, L.K[0], L.K[1], L.K[2], L.K[3]};
+  if (!src[vec]) return fail(SC_EINVAL, "vector %d is not used by this Runge-Kutta method", vec);
   int lo[3], n[3];
   box_region(L.boxes[box], ghosted ? c->ghost : 0, lo, n);
   const size_t bytes = sizeof(double) * (size_t)n[0] * n[1] * n[2];
@@ -1693,20 +1857,15 @@ sc_status sc_time_ghost_kernels(sc_ctx* c, int level, int nrep, double* ms, long
   if (level < 1 || level >= c->nlev) return fail(SC_EINVAL, "level must be a refined level");
   Level& L = c->lev[level];
   const Level& P = c->lev[level - 1];
-  const int psy = P.g.pitch, psz = P.g.pitch * P.g.ext[1];
   double coef[4];
-  fill_coeffs(P.dt, 0.0, 2, coef);
+  fill_coeffs(c->rk, P.dt, 0.0, 2, coef);
   cudaEvent_t e[3];
   for (auto& x : e) CU(cudaEventCreate(&x));
   CU(cudaEventRecord(e[0], c->stream));
-  for (int r = 0; r < nrep; ++r) {
-    CU(launch_amr_prolong_blocks(P.S[P.parity], P.K[0], P.K[1], P.K[2], P.K[3], P.g.fs, psy, psz, L.blocks, L.nblocks,
-                                 L.namr, L.amr_store, c->F, c->w, c->stream));
-    CU(launch_amr_prolong(P.S[P.parity], P.K[0], P.K[1], P.K[2], P.K[3], P.g.fs, psy, psz, L.amr, L.namr_blocked,
-                          L.namr, L.amr_store, c->F, c->w, c->stream));
-  }
+  for (int r = 0; r < nrep; ++r) CU(prolong_parent(c, level, P.S[P.parity], c->stream));
   CU(cudaEventRecord(e[1], c->stream));
-  for (int r = 0; r < nrep; ++r) CU(launch_amr_apply(L.A, L.g.fs, c->F, L.amr, L.namr, L.amr_store, coef, c->stream));
+  for (int r = 0; r < nrep; ++r)
+    CU(launch_amr_apply(L.A, L.g.fs, c->F, L.amr, L.namr, L.amr_store, coef, c->stream, dense_count(c->rk)));
   CU(cudaEventRecord(e[2], c->stream));
   CU(cudaEventSynchronize(e[2]));
   float t0 = 0, t1 = 0;

@@ -95,17 +95,26 @@ struct StageArgs {
   const double* Y;   // stage input, ghosts valid
   const double* yn;  // state at the start of the step
   double* k;         // k_stage (output)
-  double* out;       // Y_{stage+1} (stage < 4) or y_{n+1} (stage == 4)
+  double* out;       // next stage input, or y_{n+1} after the last stage
   const double* k1;
   const double* k2;
   const double* k3;
-  double cdt;        // c_stage * dt (stage < 4), dt / 6 (stage == 4)
-  int stage;         // 1..4
+  // Update written to out (kStage* below):
+  //   kStageSingle: out = yn + cdt k           (stage inputs; RK2's last stage)
+  //   kStageRk4:    out = yn + cdt (k1 + 2 k2 + 2 k3 + k), cdt = dt / 6
+  //   kStageTwo:    out = yn + c1dt k1 + cdt k (RK3's last stage)
+  //   kStageNone:   k only, out unused (RK3's k4 = f(y_{n+1}))
+  double cdt;
+  double c1dt;
+  int form;
+  int stage;         // 1..s
   long fs;
   int sy, sz;        // strides of y and z in doubles
   double h;
   const double* eta; // Z4c: per-cell Gamma-driver damping eta(r), or null for the constant
 };
+
+enum { kStageSingle = 0, kStageRk4 = 1, kStageTwo = 2, kStageNone = 3 };
 
 struct Z4cParams {
   double kappa1, kappa2, eta, ko_sigma;
@@ -147,7 +156,7 @@ cudaError_t launch_amr_prolong_blocks(const double* yn, const double* k1, const 
                                       int nblocks, int ncells, double* store, int F, const Weights& w,
                                       cudaStream_t s, int nvec = 5);
 cudaError_t launch_amr_apply(double* vec, long fs, int F, const AmrCell* cells, int ncells,
-                             const double* store, const double* c4, cudaStream_t s);
+                             const double* store, const double* c4, cudaStream_t s, int nk = 4);
 cudaError_t launch_restrict(double* parent, long pfs, const double* fine, long ffs, int fsy, int fsz,
                             const RestrictCell* cells, int ncells, int F, const Weights& w, cudaStream_t s);
 cudaError_t launch_initial_data(double* vec, const Geom& g, int F, int system, int kind, const double* params,

@@ -2,10 +2,12 @@
 // radiative outer-boundary stage shared by both systems.
 //
 // One launch covers every interior tile of a level: k_i = f(Y_i) with the
-// 4th-order centred Laplacian, then the stage update
-//   Y_{i+1} = y_n + c_i dt k_i        (i < 4, Eqs. rk2-rk4 stage vectors)
-//   y_{n+1} = y_n + dt/6 (k1 + 2 k2 + 2 k3 + k4)   (i = 4, Eq. rk5)
-// k_i is stored because finer levels need k1..k4 for dense output.
+// centred Laplacian (4th or 8th order), then the stage update
+//   Y_{i+1} = y_n + c_{i+1} dt k_i                 (Eqs. rk2-rk4 stage vectors)
+//   y_{n+1} = y_n + dt/6 (k1 + 2 k2 + 2 k3 + k4)   (RK4's last stage, Eq. rk5)
+// or the last-stage combinations of RK3 (y_n + dt/4 k1 + 3dt/4 k3) and RK2
+// (y_n + dt k2), or no update (RK3's k4 = f(y_{n+1})).  k_i is stored because
+// finer levels need it for dense output.
 #include "sc_internal.h"
 
 namespace sc {
@@ -44,14 +46,17 @@ __global__ void __launch_bounds__(kThreads) wave_stage_kernel(StageArgs a, const
       const double kp = lap;            // d_t Pi = Laplacian u
       a.k[o] = ku;
       a.k[a.fs + o] = kp;
-      if (a.stage < 4) {
+      if (a.form == kStageSingle) {
         a.out[o] = fma(a.cdt, ku, a.yn[o]);
         a.out[a.fs + o] = fma(a.cdt, kp, a.yn[a.fs + o]);
-      } else {
+      } else if (a.form == kStageRk4) {
         const double su = fma(2.0, a.k3[o], fma(2.0, a.k2[o], a.k1[o])) + ku;
         const double sp = fma(2.0, a.k3[a.fs + o], fma(2.0, a.k2[a.fs + o], a.k1[a.fs + o])) + kp;
         a.out[o] = fma(a.cdt, su, a.yn[o]);
         a.out[a.fs + o] = fma(a.cdt, sp, a.yn[a.fs + o]);
+      } else if (a.form == kStageTwo) {
+        a.out[o] = fma(a.cdt, ku, fma(a.c1dt, a.k1[o], a.yn[o]));
+        a.out[a.fs + o] = fma(a.cdt, kp, fma(a.c1dt, a.k1[a.fs + o], a.yn[a.fs + o]));
       }
     }
   }
@@ -92,11 +97,13 @@ __global__ void __launch_bounds__(kThreads) radiative_stage_kernel(StageArgs a, 
     const double kv = -(adv + (p[o] - uinf)) * ir;
     const long fo = (long)f * a.fs + o;
     a.k[fo] = kv;
-    if (a.stage < 4) {
+    if (a.form == kStageSingle) {
       a.out[fo] = fma(a.cdt, kv, a.yn[fo]);
-    } else {
+    } else if (a.form == kStageRk4) {
       const double s = fma(2.0, a.k3[fo], fma(2.0, a.k2[fo], a.k1[fo])) + kv;
       a.out[fo] = fma(a.cdt, s, a.yn[fo]);
+    } else if (a.form == kStageTwo) {
+      a.out[fo] = fma(a.cdt, kv, fma(a.c1dt, a.k1[fo], a.yn[fo]));
     }
   }
 }

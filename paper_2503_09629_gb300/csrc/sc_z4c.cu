@@ -549,6 +549,10 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
 #undef D2
 }
 
+// FORM: the stage update of StageArgs (kStageSingle, kStageRk4, kStageTwo,
+// kStageNone),
+// fixed at compile time so the update adds no registers to the RHS.
+template <int FORM>
 __global__ void __launch_bounds__(128) z4c_stage_kernel(StageArgs a, const double* __restrict__ S, Z4cParams P,
                                                        const Tile* __restrict__ tiles, int ntiles) {
   const double ko = P.ko_sigma / (64.0 * a.h);
@@ -567,11 +571,13 @@ __global__ void __launch_bounds__(128) z4c_stage_kernel(StageArgs a, const doubl
         const long fo = (long)f * a.fs + o;
         const double kv = fma(ko, S[(long)(Q_KO + f) * a.fs + o], rhs[f]);
         a.k[fo] = kv;
-        if (a.stage < 4) {
+        if (FORM == kStageSingle) {
           a.out[fo] = fma(a.cdt, kv, a.yn[fo]);
-        } else {
+        } else if (FORM == kStageRk4) {
           const double s = fma(2.0, a.k3[fo], fma(2.0, a.k2[fo], a.k1[fo])) + kv;
           a.out[fo] = fma(a.cdt, s, a.yn[fo]);
+        } else if (FORM == kStageTwo) {
+          a.out[fo] = fma(a.cdt, kv, fma(a.c1dt, a.k1[fo], a.yn[fo]));
         }
       }
     }
@@ -691,7 +697,8 @@ cudaError_t z4c_init_launch_config() {
   GridCaps& c = g_caps[dev & 63];
   if (c.ready) return cudaSuccess;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel, 128, 0)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel<kStageSingle>, 128, 0)) != cudaSuccess)
+    return e;
   c.stage = nsm * (occ > 0 ? occ : 1);
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_derivs_split_kernel<8>, kThreads, 0)) != cudaSuccess)
     return e;
@@ -734,7 +741,10 @@ cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4
                              int ntiles, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
   const int grid = ntiles < caps().stage ? ntiles : caps().stage;
-  z4c_stage_kernel<<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles);
+  if (a.form == kStageRk4) z4c_stage_kernel<kStageRk4><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles);
+  else if (a.form == kStageTwo) z4c_stage_kernel<kStageTwo><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles);
+  else if (a.form == kStageNone) z4c_stage_kernel<kStageNone><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles);
+  else z4c_stage_kernel<kStageSingle><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles);
   return cudaGetLastError();
 }
 
