@@ -249,6 +249,7 @@ struct Level {
   // work lists (device) and their sizes
   Tile* tiles = nullptr;
   int ntiles = 0;
+  int tile_cols = 0;                // largest nx * ny of the tiles
   std::vector<int> box_tile_begin;  // tiles of box b: [box_tile_begin[b], box_tile_begin[b + 1])
   Tile* ptiles = nullptr;           // 32 x 4 x 1 tiles for the pointwise Z4c kernel (one cell per thread)
   int nptiles = 0;
@@ -560,6 +561,12 @@ void group_amr_blocks(sc_ctx* c, int l, HostLists& hl) {
 
 // Interior tiles of the stencil kernels: per box, tiles of shape tile[0..2]
 // clipped to the box (ragged tiles at the high ends).
+int max_tile_cols(const std::vector<Tile>& v) {
+  int m = 1;
+  for (const Tile& t : v) m = std::max(m, t.nx * t.ny);
+  return m;
+}
+
 void build_stencil_tiles(Level& L, const int* tile, std::vector<Tile>& out) {
   const Geom& g = L.g;
   out.clear();
@@ -580,6 +587,7 @@ void build_stencil_tiles(Level& L, const int* tile, std::vector<Tile>& out) {
         }
   }
   L.box_tile_begin.push_back((int)out.size());
+  L.tile_cols = max_tile_cols(out);
 }
 
 sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
@@ -1046,7 +1054,8 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
         } else {
           const int p0 = nparts == 1 ? 0 : L.box_ptile_begin[b];
           const int np = nparts == 1 ? L.nptiles : L.box_ptile_begin[b + 1] - p0;
-          CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles + t0, nt, s, c->order));
+          CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles + t0, nt, s, c->order,
+                                     L.tile_cols));
           CU(launch_z4c_stage(a, c->scratch, c->zp, L.ptiles + p0, np, s));
         }
       }
@@ -1206,7 +1215,7 @@ std::string tune_key(const sc_ctx* c) {
 }
 
 // Time the stencil kernel of one level with the given tiles (device array).
-sc_status time_stencil(sc_ctx* c, Level& L, const Tile* tiles, int ntiles, int reps, double* ms) {
+sc_status time_stencil(sc_ctx* c, Level& L, const Tile* tiles, int ntiles, int cols, int reps, double* ms) {
   const Geom& g = L.g;
   StageArgs a{};
   a.Y = L.A;
@@ -1229,7 +1238,8 @@ sc_status time_stencil(sc_ctx* c, Level& L, const Tile* tiles, int ntiles, int r
   for (int r = -1; r < reps; ++r) {  // one untimed launch first
     if (r == 0) CU(cudaEventRecord(e0, c->stream));
     if (c->system == SC_WAVE) CU(launch_wave_stage(a, tiles, ntiles, c->stream, c->order));
-    else CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, tiles, ntiles, c->stream, c->order));
+    else
+      CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, tiles, ntiles, c->stream, c->order, cols));
   }
   CU(cudaEventRecord(e1, c->stream));
   CU(cudaEventSynchronize(e1));
@@ -1296,7 +1306,7 @@ extern "C" sc_status sc_autotune(sc_ctx* c, int* tile_out, double* ms_out) {
       }
       CU(cudaMemcpyAsync(d, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
       double ms = 0;
-      sc_status st = time_stencil(c, L, d, (int)t.size(), 3, &ms);
+      sc_status st = time_stencil(c, L, d, (int)t.size(), max_tile_cols(t), 3, &ms);
       if (st) return st;
       if (best_ms < 0 || ms < best_ms) {
         best_ms = ms;
@@ -1749,7 +1759,8 @@ sc_status sc_get_constraints(sc_ctx* c, int level, int box, double* dst) {
     CU(launch_z4c_derivs(Y, c->scratch, L.g.fs, sy, sz, L.g.h, dt, (int)tl.size(), c->stream));
   } else {
     CU(launch_z4c_dxy(Y, c->scratch, L.g.fs, sy, L.g.h, L.dxy, L.ndxy, c->stream, c->order));
-    CU(launch_z4c_derivs_split(Y, c->scratch, L.g.fs, sy, sz, L.g.h, dt, (int)tl.size(), c->stream, c->order));
+    CU(launch_z4c_derivs_split(Y, c->scratch, L.g.fs, sy, sz, L.g.h, dt, (int)tl.size(), c->stream, c->order,
+                               max_tile_cols(tl)));
   }
   CU(launch_z4c_constraints(Y, c->scratch, c->staging, L.g.fs, sy, sz, c->zp, dt, (int)tl.size(), ncell, blo, n,
                             c->stream));
@@ -1806,7 +1817,8 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
     if (c->system == SC_WAVE) CU(launch_wave_stage(a, L.tiles, L.ntiles, c->stream, c->order));
     else {
       CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, c->stream, c->order));
-      CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, c->stream, c->order));
+      CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, c->stream, c->order,
+                                 L.tile_cols));
     }
   }
   CU(cudaEventRecord(e[1], c->stream));

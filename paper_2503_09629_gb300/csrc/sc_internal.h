@@ -134,8 +134,10 @@ cudaError_t z4c_init_launch_config();
 // order: finite-difference order of the derivatives, 4 or 8 (Kreiss-Oliger stays r = 4)
 cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, double h, const RowSeg* segs, int nsegs,
                            cudaStream_t s, int order = 4);
+// max_cols: the largest nx * ny of the tiles (work is dealt out per tile in
+// chunks sized by it); cudaErrorInvalidValue if below 1.
 cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz, double h,
-                                    const Tile* tiles, int ntiles, cudaStream_t s, int order = 4);
+                                    const Tile* tiles, int ntiles, cudaStream_t s, int order, int max_cols);
 cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4cParams& p,
                              const Tile* tiles, int ntiles, cudaStream_t s);
 cudaError_t launch_radiative_stage(const StageArgs& a, const int32_t* cells, int ncells, int F,

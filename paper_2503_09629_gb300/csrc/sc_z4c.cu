@@ -183,11 +183,14 @@ __global__ void __launch_bounds__(kThreads, 2) z4c_derivs_split_kernel(const dou
                                                                       double* __restrict__ S, long fs, int sy_,
                                                                       int sz_, double h,
                                                                       const Tile* __restrict__ tiles, int ntiles,
-                                                                      FmaK K) {
+                                                                      int max_cols, FmaK K) {
   // One thread per (x, y, field) column of a tile, walking z with sliding
   // windows: u at z-W..z+W (W = max(R, 3), R = ORD/2 the derivative radius,
   // 3 the Kreiss-Oliger radius) and, for the Hessian fields, the stored
   // D_x, D_y at z-R..z+R, so each step loads one new z value per window.
+  // Work is dealt out in units of (tile, chunk of blockDim (field, column)
+  // pairs), U chunks per tile (max_cols = the largest tile's columns), so
+  // the persistent blocks end together whatever the tile count.
   constexpr int R = ORD / 2;
   constexpr int WR = R > 3 ? R : 3;
   constexpr int NW = 2 * WR + 1;
@@ -195,10 +198,13 @@ __global__ void __launch_bounds__(kThreads, 2) z4c_derivs_split_kernel(const dou
   const double ih = first_scale<ORD>(h);
   const double ih2 = second_scale<ORD>(h);
   const long sy = sy_, sz = sz_;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  const int U = (max_cols * kNZ4c + blockDim.x - 1) / blockDim.x;
+  for (long u = blockIdx.x; u < (long)ntiles * U; u += gridDim.x) {
+    const int t = (int)(u / U);
     const Tile T = tiles[t];
     const int ncol = T.nx * T.ny;
-    for (int q = threadIdx.x; q < ncol * kNZ4c; q += blockDim.x) {
+    const int q = (int)(u - (long)t * U) * blockDim.x + threadIdx.x;
+    if (q < ncol * kNZ4c) {
       const int f = q / ncol;
       const int c = q - f * ncol;
       const int i = c % T.nx;
@@ -727,13 +733,16 @@ cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, do
 }
 
 cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz, double h,
-                                    const Tile* tiles, int ntiles, cudaStream_t s, int order) {
+                                    const Tile* tiles, int ntiles, cudaStream_t s, int order, int max_cols) {
   if (ntiles == 0) return cudaSuccess;
-  const int grid = ntiles < caps().derivs ? ntiles : caps().derivs;
+  if (max_cols < 1) return cudaErrorInvalidValue;
+  const long units = (long)ntiles * ((max_cols * kNZ4c + kThreads - 1) / kThreads);
+  const int grid = units < caps().derivs ? (int)units : caps().derivs;
+  const FmaK K{1.0, -1.0, -0.0};
   if (order == 8)
-    z4c_derivs_split_kernel<8><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles, FmaK{1.0, -1.0, -0.0});
+    z4c_derivs_split_kernel<8><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles, max_cols, K);
   else
-    z4c_derivs_split_kernel<4><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles, FmaK{1.0, -1.0, -0.0});
+    z4c_derivs_split_kernel<4><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles, max_cols, K);
   return cudaGetLastError();
 }
 
