@@ -340,30 +340,23 @@ def run_gpu(args, rank: int, world: int):
     roofline["other_kernels"] = {k: v for k, v in roof.items() if k != dominant}
 
     # End to end through the public API with host buffers: each step uploads
-    # the state from pinned host memory, advances one coarse step and reads
-    # the state back.
-    host = {}
-    h2d = 0
-    for l in range(h.nlevels):
-        for b in range(len(h.boxes[l])):
-            g = (l == 0)
-            for f in range(22):
-                a = torch.empty(ctx.shape(l, b, g), dtype=torch.float64).pin_memory()
-                a.copy_(torch.from_numpy(ctx.sc_get_field(l, b, f, ghosted=g)))
-                host[(l, b, f)] = (a, g)
-                h2d += a.numel() * 8
-    outs = {k: torch.empty(ctx.shape(k[0], k[1], False), dtype=torch.float64).pin_memory() for k in host}
-    d2h = sum(v.numel() * 8 for v in outs.values())
+    # the whole state from page-locked host memory (sc_set_state: level 0
+    # with its evolved ghost shell), advances one coarse step and reads the
+    # state back (sc_get_state: interiors).
+    n_in = ctx.sc_state_bytes(True) // 8
+    n_out = ctx.sc_state_bytes(False) // 8
+    host_in = torch.empty(n_in, dtype=torch.float64).pin_memory()
+    host_out = torch.empty(n_out, dtype=torch.float64).pin_memory()
+    ctx.sc_get_state(host_in.data_ptr(), ghosted_level0=True)
+    h2d, d2h = n_in * 8, n_out * 8
     ne2e = max(1, min(args.steps, 5))
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(ne2e):
-        for (l, b, f), (a, g) in host.items():
-            ctx.sc_set_field(l, b, f, a.numpy(), ghosted=g)
+        ctx.sc_set_state(host_in.data_ptr(), ghosted_level0=True)
         ctx.sc_advance(1)
-        for (l, b, f), o in outs.items():
-            o.numpy()[...] = ctx.sc_get_field(l, b, f)
+        ctx.sc_get_state(host_out.data_ptr())
     torch.cuda.synchronize()
     barrier()
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")

@@ -143,9 +143,10 @@ sc_status sc_set_initial_data(sc_ctx* ctx, int kind, const double* params, int n
  * (hi-lo+1) cells per dimension, x fastest.  Stream-ordered, synchronous with
  * respect to the host buffer (returns after the copy has been consumed). */
 sc_status sc_set_field(sc_ctx* ctx, int level, int box, int field, const double* host_src);
-/* As sc_set_field, including 3 ghost cells per side: src has (hi-lo+7) cells
- * per dimension.  Needed for the evolved outer ghost shell of a radiative
- * level 0 and for checkpoint/resume. */
+/* As sc_set_field, including the ghost cells (3 per side, 4 with 8th-order
+ * differences): src has (hi-lo+7) or (hi-lo+9) cells per dimension.  Needed for
+ * the evolved outer ghost shell of a radiative level 0 and for
+ * checkpoint/resume. */
 sc_status sc_set_field_ghosted(sc_ctx* ctx, int level, int box, int field, const double* host_src);
 
 /* Copy one field of one box (interior) to host memory; synchronises. */
@@ -156,6 +157,25 @@ sc_status sc_get_field_ghosted(sc_ctx* ctx, int level, int box, int field, doubl
  * buffer of the same shape; stream-ordered, no host synchronisation. */
 sc_status sc_set_field_device(sc_ctx* ctx, int level, int box, int field, const double* dev_src);
 sc_status sc_get_field_device(sc_ctx* ctx, int level, int box, int field, double* dev_dst);
+
+/* Whole-state transfer (no counterpart in the paper, which keeps the state on
+ * the device; this is the upload/download of a host application that owns
+ * its data).  The packed layout concatenates, for every level l (coarse to
+ * fine), every box b (creation order) and every field f, the box region x
+ * fastest: with its ghost cells on level 0 when ghosted_level0 = 1 (the
+ * evolved shell of a radiative boundary lives there), its interior
+ * elsewhere.  *bytes = size of that buffer.
+ * sc_set_state copies it in with one host-to-device copy into a device
+ * staging buffer of the same size (allocated on first use, kept with the
+ * context) and one unpack kernel per box; sc_get_state packs with one kernel
+ * per box and one device-to-host copy.  Page-locked host memory makes each
+ * copy one DMA transfer; pageable memory works, slower.  Both return after
+ * the host buffer has been consumed or filled (they synchronise the
+ * context's stream).  Errors: SC_EINVAL (null pointer, ghosted_level0 not
+ * 0/1), SC_ENOMEM (staging), SC_ECUDA. */
+sc_status sc_state_bytes(sc_ctx* ctx, int ghosted_level0, size_t* bytes);
+sc_status sc_set_state(sc_ctx* ctx, const double* host_src, int ghosted_level0);
+sc_status sc_get_state(sc_ctx* ctx, double* host_dst, int ghosted_level0);
 
 /* Advance n coarse steps (Sec. II, steps 1-7 per coarse step): level 0
  * takes one RK step storing its stage vectors, every finer level two substeps per

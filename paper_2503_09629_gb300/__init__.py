@@ -121,6 +121,9 @@ def lib():
     L.sc_regrid.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(sc_box)]
     L.sc_check_finite.argtypes = [P]
     L.sc_interpolate.argtypes = [P, I, DP, I, DP]
+    L.sc_state_bytes.argtypes = [P, I, ctypes.POINTER(ctypes.c_size_t)]
+    L.sc_set_state.argtypes = [P, P, I]
+    L.sc_get_state.argtypes = [P, P, I]
     L.sc_z4c_constraints_noalloc.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), D, P]
     IP = ctypes.POINTER(ctypes.c_int)
     U64 = ctypes.c_ulonglong
@@ -288,6 +291,33 @@ class Context:
 
     def sc_get_field_device(self, level, box, field, dev_ptr: int):
         _check(lib().sc_get_field_device(self.ctx, level, box, field, ctypes.c_void_p(dev_ptr)))
+
+    def sc_state_bytes(self, ghosted_level0: bool = False) -> int:
+        n = ctypes.c_size_t(0)
+        _check(lib().sc_state_bytes(self.ctx, 1 if ghosted_level0 else 0, ctypes.byref(n)))
+        return n.value
+
+    def sc_set_state(self, host_ptr, ghosted_level0: bool = False):
+        """Whole state from a packed host buffer: a numpy float64 array or a
+        raw address (e.g. of a page-locked torch tensor)."""
+        if isinstance(host_ptr, np.ndarray):
+            assert host_ptr.dtype == np.float64 and host_ptr.flags.c_contiguous
+            assert host_ptr.nbytes == self.sc_state_bytes(ghosted_level0)
+            host_ptr = host_ptr.ctypes.data
+        _check(lib().sc_set_state(self.ctx, ctypes.c_void_p(host_ptr), 1 if ghosted_level0 else 0))
+
+    def sc_get_state(self, host_ptr=None, ghosted_level0: bool = False):
+        """Whole state into a packed host buffer (allocated when None)."""
+        out = None
+        if host_ptr is None:
+            out = np.empty(self.sc_state_bytes(ghosted_level0) // 8)
+            host_ptr = out.ctypes.data
+        elif isinstance(host_ptr, np.ndarray):
+            assert host_ptr.dtype == np.float64 and host_ptr.flags.c_contiguous
+            assert host_ptr.nbytes == self.sc_state_bytes(ghosted_level0)
+            out, host_ptr = host_ptr, host_ptr.ctypes.data
+        _check(lib().sc_get_state(self.ctx, ctypes.c_void_p(host_ptr), 1 if ghosted_level0 else 0))
+        return out
 
     def sc_advance(self, n: int):
         _check(lib().sc_advance(self.ctx, n))

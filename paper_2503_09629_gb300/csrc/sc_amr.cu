@@ -347,6 +347,25 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(double* __restrict__ vec
   }
 }
 
+// All F fields of one box region: field f of the region is the f-th block of
+// nx*ny*nz values in buf (unpack = 0: array -> buffer; 1: buffer -> array).
+__global__ void __launch_bounds__(kThreads) pack_fields_kernel(double* __restrict__ vec, long fs, int F, int pitch,
+                                                              int ey, int i0, int j0, int k0, int nx, int ny,
+                                                              int nz, double* __restrict__ buf, int unpack) {
+  const long n = (long)nx * ny * nz;
+  const long total = n * F;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int f = (int)(idx / n);
+    const long r = idx - (long)f * n;
+    const int i = (int)(r % nx);
+    const int j = (int)((r / nx) % ny);
+    const int k = (int)(r / ((long)nx * ny));
+    const long o = (long)f * fs + ((long)(k0 + k) * ey + (j0 + j)) * pitch + (i0 + i);
+    if (unpack) vec[o] = buf[idx];
+    else buf[idx] = vec[o];
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) nonfinite_kernel(const double* __restrict__ vec, long fs, int F,
                                                             const Tile* __restrict__ tiles, int ntiles,
                                                             int sy, int sz, int* flag) {
@@ -456,6 +475,16 @@ cudaError_t launch_unpack(double* vec, const Geom& g, const int* lo, const int* 
   pack_kernel<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(vec, g.pitch, g.ext[1], lo[0] - g.org[0],
                                                           lo[1] - g.org[1], lo[2] - g.org[2], n[0], n[1], n[2],
                                                           const_cast<double*>(src), 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_fields(double* vec, long fs, int F, const Geom& g, const int* lo, const int* n, double* buf,
+                               int unpack, cudaStream_t s) {
+  const long cnt = (long)n[0] * n[1] * n[2] * F;
+  if (cnt == 0) return cudaSuccess;
+  pack_fields_kernel<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(vec, fs, F, g.pitch, g.ext[1], lo[0] - g.org[0],
+                                                                 lo[1] - g.org[1], lo[2] - g.org[2], n[0], n[1],
+                                                                 n[2], buf, unpack);
   return cudaGetLastError();
 }
 

@@ -1141,6 +1141,12 @@ sc_status check_box(sc_ctx* c, int level, int box, int field) {
 
 sc_status ensure_staging(sc_ctx* c, size_t bytes) {
   if (c->staging_bytes >= bytes) return SC_OK;
+  if (c->staging) {  // the stream may still read the old buffer
+    CU(cudaStreamSynchronize(c->stream));
+    c->dfree(c->staging);
+    c->staging = nullptr;
+    c->staging_bytes = 0;
+  }
   c->staging = (double*)c->dalloc(bytes);
   if (!c->staging) return fail(SC_ENOMEM, "staging allocation of %zu bytes failed", bytes);
   c->staging_bytes = bytes;
@@ -1690,6 +1696,57 @@ sc_status sc_set_field_device(sc_ctx* c, int l, int b, int f, const double* src)
 sc_status sc_get_field_device(sc_ctx* c, int l, int b, int f, double* dst) {
   if (!dst) return fail(SC_EINVAL, "null destination");
   return copy_field(c, l, b, f, false, nullptr, dst, false);
+}
+
+namespace {
+
+// Packed whole-state transfer (sc_set_state / sc_get_state).
+sc_status state_transfer(sc_ctx* c, double* host, int ghosted_level0, bool to_device) {
+  if (!c || !host) return fail(SC_EINVAL, "null argument");
+  if (ghosted_level0 != 0 && ghosted_level0 != 1) return fail(SC_EINVAL, "ghosted_level0 must be 0 or 1");
+  size_t bytes = 0;
+  sc_status st = sc_state_bytes(c, ghosted_level0, &bytes);
+  if (st) return st;
+  if ((st = ensure_staging(c, bytes))) return st;
+  if (to_device) CU(cudaMemcpyAsync(c->staging, host, bytes, cudaMemcpyHostToDevice, c->stream));
+  size_t off = 0;
+  for (int l = 0; l < c->nlev; ++l) {
+    Level& L = c->lev[l];
+    for (const sc_box& B : L.boxes) {
+      int lo[3], n[3];
+      box_region(B, (l == 0 && ghosted_level0) ? c->ghost : 0, lo, n);
+      CU(launch_pack_fields(L.S[L.parity], L.g.fs, c->F, L.g, lo, n, c->staging + off, to_device ? 1 : 0,
+                            c->stream));
+      off += (size_t)n[0] * n[1] * n[2] * c->F;
+    }
+  }
+  if (!to_device) CU(cudaMemcpyAsync(host, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return SC_OK;
+}
+
+}  // namespace
+
+sc_status sc_state_bytes(sc_ctx* c, int ghosted_level0, size_t* bytes) {
+  if (!c || !bytes) return fail(SC_EINVAL, "null argument");
+  if (ghosted_level0 != 0 && ghosted_level0 != 1) return fail(SC_EINVAL, "ghosted_level0 must be 0 or 1");
+  size_t v = 0;
+  for (int l = 0; l < c->nlev; ++l)
+    for (const sc_box& B : c->lev[l].boxes) {
+      int lo[3], n[3];
+      box_region(B, (l == 0 && ghosted_level0) ? c->ghost : 0, lo, n);
+      v += (size_t)n[0] * n[1] * n[2] * c->F;
+    }
+  *bytes = v * sizeof(double);
+  return SC_OK;
+}
+
+sc_status sc_set_state(sc_ctx* c, const double* src, int ghosted_level0) {
+  return state_transfer(c, const_cast<double*>(src), ghosted_level0, true);
+}
+
+sc_status sc_get_state(sc_ctx* c, double* dst, int ghosted_level0) {
+  return state_transfer(c, dst, ghosted_level0, false);
 }
 
 sc_status sc_advance(sc_ctx* c, int n) {

@@ -174,6 +174,10 @@ cudaError_t launch_pack(const double* vec, const Geom& g, const int* lo, const i
                         cudaStream_t s);
 cudaError_t launch_unpack(double* vec, const Geom& g, const int* lo, const int* n, const double* src,
                           cudaStream_t s);
+// All F fields (stride fs) of a box region to or from a packed buffer (F
+// consecutive x-fastest blocks); unpack = 1 writes the array.
+cudaError_t launch_pack_fields(double* vec, long fs, int F, const Geom& g, const int* lo, const int* n, double* buf,
+                               int unpack, cudaStream_t s);
 cudaError_t launch_nonfinite_check(const double* vec, long fs, int F, const Tile* tiles, int ntiles, int sy,
                                    int sz, int* flag, cudaStream_t s);
 
