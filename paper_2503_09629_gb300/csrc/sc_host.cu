@@ -312,6 +312,7 @@ struct sc_ctx {
   double t = 0;
   double zu_finest = 0, zu_actual = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graph_stale[2] = {true, true};  // the schedule changed since graph[p] was built
   long launches_per_step = 0;
   int exec_mode = SC_EXEC_GRAPH;
   int subcycle = 1;
@@ -471,6 +472,43 @@ bool is_interior(const Level& L, const int* gi) {
   return L.kind[elem_index(L.g, gi)] == K_INTERIOR;
 }
 
+// Summed-volume table of a level's interior cells: S(i,j,k) = number of
+// interior array elements with index < (i,j,k) componentwise, so any box of
+// elements is counted in O(1) (the proper-nesting check of a ghost cell's
+// 6x6x6 prolongation stencil).
+struct InteriorCount {
+  Geom g;
+  std::vector<int32_t> sat;  // (ext0+1) x (ext1+1) x (ext2+1)
+  long at(int i, int j, int k) const {
+    return sat[((long)k * (g.ext[1] + 1) + j) * (g.ext[0] + 1) + i];
+  }
+  explicit InteriorCount(const Level& L) : g(L.g) {
+    const int X = g.ext[0] + 1, Y = g.ext[1] + 1, Z = g.ext[2] + 1;
+    sat.assign((size_t)X * Y * Z, 0);
+    for (int k = 1; k < Z; ++k)
+      for (int j = 1; j < Y; ++j)
+        for (int i = 1; i < X; ++i) {
+          const long e = ((long)(k - 1) * g.ext[1] + (j - 1)) * g.ext[0] + (i - 1);
+          const int32_t v = L.kind[e] == K_INTERIOR ? 1 : 0;
+          sat[((long)k * Y + j) * X + i] = v + at(i - 1, j, k) + at(i, j - 1, k) + at(i, j, k - 1) -
+                                           at(i - 1, j - 1, k) - at(i - 1, j, k - 1) - at(i, j - 1, k - 1) +
+                                           at(i - 1, j - 1, k - 1);
+        }
+  }
+  // true when every cell of the global box [lo, lo + n) is interior
+  bool all_interior(const int* lo, int n) const {
+    int a[3], b[3];
+    for (int d = 0; d < 3; ++d) {
+      a[d] = lo[d] - g.org[d];
+      b[d] = a[d] + n;
+      if (a[d] < 0 || b[d] > g.ext[d]) return false;
+    }
+    const long c = at(b[0], b[1], b[2]) - at(a[0], b[1], b[2]) - at(b[0], a[1], b[2]) - at(b[0], b[1], a[2]) +
+                   at(a[0], a[1], b[2]) + at(a[0], b[1], a[2]) + at(b[0], a[1], a[2]) - at(a[0], a[1], a[2]);
+    return c == (long)n * n * n;
+  }
+};
+
 // Group the refinement-boundary ghost cells of level l into 4x4x4 fine blocks
 // (aligned to multiples of 4 in the level's unwrapped index space) for the
 // separable prolongation kernel.  A block qualifies when all its ghost cells
@@ -627,6 +665,8 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
           L.kind[e] = K_AMR;
         }
   // work lists
+  std::unique_ptr<InteriorCount> pcount;
+  if (l > 0) pcount.reset(new InteriorCount(c->lev[l - 1]));
   for (int k = 0; k < g.ext[2]; ++k)
     for (int j = 0; j < g.ext[1]; ++j)
       for (int i = 0; i < g.ext[0]; ++i) {
@@ -651,15 +691,10 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
             first[q] = odd ? pc - 2 : pc - 3;
           }
           const Level& P = c->lev[l - 1];
-          for (int a = 0; a < kPN; ++a)
-            for (int b = 0; b < kPN; ++b)
-              for (int d = 0; d < kPN; ++d) {
-                const int pg[3] = {first[0] + d, first[1] + b, first[2] + a};
-                if (!is_interior(P, pg))
-                  return fail(SC_ENESTING,
-                              "level %d: prolongation stencil of ghost cell (%d,%d,%d) leaves the parent interior", l,
-                              gi[0], gi[1], gi[2]);
-              }
+          if (!pcount->all_interior(first, kPN))
+            return fail(SC_ENESTING,
+                        "level %d: prolongation stencil of ghost cell (%d,%d,%d) leaves the parent interior", l,
+                        gi[0], gi[1], gi[2]);
           AmrCell ac;
           ac.dst = off;
           ac.pbase = (int32_t)P.g.off(first[0], first[1], first[2]);
@@ -1078,57 +1113,83 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
 
 namespace {
 
-sc_status build_graphs(sc_ctx* c) {
-  for (int p = 0; p < 2; ++p) {
-    Emitter em;
-    em.c = c;
-    em.par.assign(c->nlev, 0);
-    em.par[0] = p;
-    em.coarse_step();
-    if (c->exec_mode == SC_EXEC_PER_BOX) {
-      c->plain_ops[p] = em.ops;
-      long n = 0;
-      for (const Op& o : em.ops) {
-        const Level& L = c->lev[o.level];
-        if (o.kind == OP_STAGE)
-          n += (long)L.boxes.size() * (c->system == SC_Z4C ? 2 : 1) + (c->system == SC_Z4C ? 1 : 0) + (L.nphys ? 1 : 0);
-        else if (o.kind == OP_PROLONG)
-          n += (L.nblocks ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0);
-        else if (o.kind == OP_FILL)
-          n += (o.level > 0 && L.namr && !o.no_amr ? 1 : 0) + (L.nperiodic ? 1 : 0);
-        else if (o.kind == OP_PROLONG_DIRECT)
-          n += (L.nblocks ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0) + (L.namr ? 1 : 0);
-        else
-          n += L.nrestr ? 1 : 0;
-      }
-      c->launches_per_step = n;
-      continue;
-    }
-    cudaStream_t cs;
-    CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t graph;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) {
-      cudaStreamDestroy(cs);
-      return fail(SC_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
-    }
-    sc_status st = SC_OK;
+// Build (or refresh) the coarse-step schedule of level-0 parity p: the op
+// list for the per-box form, else one CUDA graph captured from it.  An
+// existing executable graph is updated in place when the new capture has the
+// same topology (the usual case after a regrid: same levels, same phases,
+// new work lists and sizes), which is much cheaper than instantiating.
+sc_status build_schedule(sc_ctx* c, int p) {
+  Emitter em;
+  em.c = c;
+  em.par.assign(c->nlev, 0);
+  em.par[0] = p;
+  em.coarse_step();
+  if (c->exec_mode == SC_EXEC_PER_BOX) {
+    c->plain_ops[p] = em.ops;
+    long n = 0;
     for (const Op& o : em.ops) {
-      st = run_op(c, o, cs);
-      if (st != SC_OK) break;
+      const Level& L = c->lev[o.level];
+      if (o.kind == OP_STAGE)
+        n += (long)L.boxes.size() * (c->system == SC_Z4C ? 2 : 1) + (c->system == SC_Z4C ? 1 : 0) + (L.nphys ? 1 : 0);
+      else if (o.kind == OP_PROLONG)
+        n += (L.nblocks ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0);
+      else if (o.kind == OP_FILL)
+        n += (o.level > 0 && L.namr && !o.no_amr ? 1 : 0) + (L.nperiodic ? 1 : 0);
+      else if (o.kind == OP_PROLONG_DIRECT)
+        n += (L.nblocks ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0) + (L.namr ? 1 : 0);
+      else
+        n += L.nrestr ? 1 : 0;
     }
-    e = cudaStreamEndCapture(cs, &graph);
-    cudaStreamDestroy(cs);
-    if (st != SC_OK) return st;
-    if (e != cudaSuccess) return fail(SC_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
-    size_t nn = 0;
-    CU(cudaGraphGetNodes(graph, nullptr, &nn));
-    c->launches_per_step = (long)nn;
-    e = cudaGraphInstantiate(&c->graph[p], graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(SC_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    c->launches_per_step = n;
+    c->graph_stale[p] = false;
+    return SC_OK;
   }
+  cudaStream_t cs;
+  CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return fail(SC_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+  }
+  sc_status st = SC_OK;
+  for (const Op& o : em.ops) {
+    st = run_op(c, o, cs);
+    if (st != SC_OK) break;
+  }
+  e = cudaStreamEndCapture(cs, &graph);
+  cudaStreamDestroy(cs);
+  if (st != SC_OK) return st;
+  if (e != cudaSuccess) return fail(SC_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  size_t nn = 0;
+  CU(cudaGraphGetNodes(graph, nullptr, &nn));
+  c->launches_per_step = (long)nn;
+  bool updated = false;
+  if (c->graph[p]) {
+    cudaGraphExecUpdateResultInfo info;
+    updated = cudaGraphExecUpdate(c->graph[p], graph, &info) == cudaSuccess;
+    if (!updated) {
+      cudaGetLastError();  // a topology change is not an error: instantiate anew
+      cudaGraphExecDestroy(c->graph[p]);
+      c->graph[p] = nullptr;
+    }
+  }
+  if (!updated) e = cudaGraphInstantiate(&c->graph[p], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(SC_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  c->graph_stale[p] = false;
   return SC_OK;
+}
+
+// The schedule changed (creation, regrid, new tile shape): rebuild the
+// schedule of the current level-0 parity now (errors surface here), the
+// other one at its first use, or now as well when both = true.
+sc_status build_graphs(sc_ctx* c, bool both = true) {
+  c->graph_stale[0] = c->graph_stale[1] = true;
+  const int p = c->lev[0].parity;
+  sc_status st = build_schedule(c, p);
+  if (st == SC_OK && both) st = build_schedule(c, p ^ 1);
+  return st;
 }
 
 sc_status check_box(sc_ctx* c, int level, int box, int field) {
@@ -1269,12 +1330,7 @@ sc_status apply_tile_shape(sc_ctx* c, const int* shape) {
     L.ntiles = (int)t.size();
   }
   CU(cudaStreamSynchronize(c->stream));
-  for (int p = 0; p < 2; ++p)
-    if (c->graph[p]) {
-      cudaGraphExecDestroy(c->graph[p]);
-      c->graph[p] = nullptr;
-    }
-  return build_graphs(c);
+  return build_graphs(c, false);
 }
 
 }  // namespace
@@ -1452,12 +1508,7 @@ extern "C" sc_status sc_regrid(sc_ctx* c, const int* nboxes, const sc_box* boxes
     if (!c->scratch) return fail(SC_ENOMEM, "derivative scratch allocation failed");
     c->scratch_fs = maxfs;
   }
-  for (int p = 0; p < 2; ++p)
-    if (c->graph[p]) {
-      cudaGraphExecDestroy(c->graph[p]);
-      c->graph[p] = nullptr;
-    }
-  return build_graphs(c);
+  return build_graphs(c, false);
 }
 
 extern "C" sc_status sc_interpolate(sc_ctx* c, int npts, const double* xyz, int field, double* out) {
@@ -1755,6 +1806,10 @@ sc_status sc_advance(sc_ctx* c, int n) {
   const int L = c->nlev;
   for (int s = 0; s < n; ++s) {
     Level& L0 = c->lev[0];
+    if (c->graph_stale[L0.parity]) {
+      sc_status st = build_schedule(c, L0.parity);
+      if (st != SC_OK) return st;
+    }
     if (c->exec_mode == SC_EXEC_PER_BOX) {
       for (const Op& o : c->plain_ops[L0.parity]) {
         sc_status st = run_op(c, o, c->stream);
