@@ -577,6 +577,37 @@ def test_constraints_vanish_for_shifted_flat_space(shifted_flat_runs):
     assert np.all(order[-1] > 3.6), (c, order)
 
 
+def test_radiative_shell_exact_for_outgoing_spherical_waves(orc):
+    """The radiative outer boundary (Z4c, evolved ghost shell of level 0):
+    d_t u = -(x^i/r) d_i u - (u - u_inf)/r holds exactly for every outgoing
+    spherical wave u = u_inf + f(r - t)/r, whose time derivative at t = 0 is
+    -f'(r)/r.  With such data in every field (u_inf = 1 for W, alpha and the
+    diagonal of gt, 0 otherwise; f = 0.1 c_q sin(r / 2) with a different
+    amplitude c_q per field) the shell's right-hand side must converge to
+    -f'(r)/r at 2nd order, the order of its centred and one-sided
+    differences.  (The shell moves inwards with h, so a wave that varies
+    slowly over the shell's range keeps the error constants comparable.)"""
+    uinf = np.zeros(22)
+    uinf[[0, 1, 4, 6, 18]] = 1.0
+    errs = []
+    for n in (16, 32, 64):
+        L = 4.0
+        h = W.Hierarchy(system=W.Z4C, boxes=[[W.cube(0, n)]], ncells0=(n, n, n), origin=(-L, -L, -L),
+                        h0=2 * L / n, bc=W.BC_RADIATIVE, ko_sigma=0.0)
+        o = make(orc, h)
+        X, Y, Z = h.cell_centres(0, 0, ghosted=True)
+        r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+        f, fp = 0.1 * np.sin(0.5 * r), 0.05 * np.cos(0.5 * r)
+        c = 1.0 + 0.1 * np.arange(22)
+        st = np.stack([uinf[q] + c[q] * f / r for q in range(22)])
+        rhs = o.rhs_box(0, 0, st)
+        shell = np.ones(X.shape, dtype=bool)
+        shell[3:-3, 3:-3, 3:-3] = False
+        errs.append(max(np.abs(rhs[q][shell] + c[q] * fp[shell] / r[shell]).max() for q in range(22)))
+    order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(order > 1.8), (errs, order)
+
+
 def test_flop_count_positive(orc):
     c = orc.flop_counts()
     assert c["total"] > 1000 and c["div"] > 0
