@@ -12,10 +12,11 @@
 // level, periodic wrap included), filled from the parent level by dense output
 // and prolongation (refinement boundary), or physical (outer boundary).
 //
-// Parity status of each part (what pins it) is listed in the test suite; the
-// radiative outer boundary, the gauge terms and KO dissipation are pinned only
-// by special cases (Minkowski, constants), the rest by closed forms,
-// polynomial exactness and convergence.
+// Parity status of each part (what pins it) is listed in the test suite: the
+// gauge terms and KO dissipation are pinned only by special cases (Minkowski,
+// constants, a uniform shift); the radiative outer boundary by exact outgoing
+// spherical waves; the rest by closed forms, polynomial exactness, exact
+// solutions (gauge wave, flat space in moving coordinates) and convergence.
 
 #include "oracle.h"
 
