@@ -13,10 +13,11 @@
 // and prolongation (refinement boundary), or physical (outer boundary).
 //
 // Parity status of each part (what pins it) is listed in the test suite: the
-// gauge terms and KO dissipation are pinned only by special cases (Minkowski,
-// constants, a uniform shift); the radiative outer boundary by exact outgoing
-// spherical waves; the rest by closed forms, polynomial exactness, exact
-// solutions (gauge wave, flat space in moving coordinates) and convergence.
+// gauge terms are pinned only by special cases (Minkowski, a uniform shift);
+// the radiative outer boundary by exact outgoing spherical waves; KO
+// dissipation by its closed form on plane waves; the rest by closed forms,
+// polynomial exactness, exact solutions (gauge wave, flat space in moving
+// coordinates) and convergence.
 
 #include "oracle.h"
 

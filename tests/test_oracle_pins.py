@@ -608,6 +608,37 @@ def test_radiative_shell_exact_for_outgoing_spherical_waves(orc):
     assert np.all(order > 1.8), (errs, order)
 
 
+@pytest.mark.parametrize("fd_order", [4, 8])
+def test_kreiss_oliger_closed_form_on_plane_waves(orc, fd_order):
+    """Sec. III.C Kreiss-Oliger term with r = 4: sigma/(64 h) sum_d delta_d^6
+    applied to cos(k.x + phi) is exactly -(sigma/h) sum_d sin^6(k_d h/2)
+    cos(k.x + phi).  The term is additive, so the difference of two
+    right-hand sides of the same state, with sigma = 0.3 and sigma = 0,
+    isolates it; every field carries its own plane wave on flat space.  The
+    same operator with either finite-difference order."""
+    n, hh, sig = 12, 0.1, 0.3
+    rng = np.random.default_rng(31)
+    rhs = {}
+    for sigma in (sig, 0.0):
+        h = W.Hierarchy(system=W.Z4C, boxes=[[W.cube(0, n)]], ncells0=(n, n, n), origin=(0.3, -0.2, 0.1), h0=hh,
+                        bc=2, ko_sigma=sigma, fd_order=fd_order)
+        o = make(orc, h)
+        X, Y, Z = h.cell_centres(0, 0, ghosted=True)
+        flat = np.zeros((22,) + X.shape)
+        flat[[0, 1, 4, 6, 18]] = 1.0
+        if sigma == sig:
+            ks = rng.uniform(-25.0, 25.0, (22, 3))
+            ph = rng.uniform(0, 2 * np.pi, 22)
+        waves = np.stack([np.cos(ks[q, 0] * X + ks[q, 1] * Y + ks[q, 2] * Z + ph[q]) for q in range(22)])
+        rhs[sigma] = o.rhs_box(0, 0, flat + 1e-3 * waves)
+        g = h.ghost
+    s = (slice(g, -g),) * 3
+    for q in range(22):
+        expect = -(sig / hh) * np.sum(np.sin(ks[q] * hh / 2) ** 6) * 1e-3 * waves[q][s]
+        got = rhs[sig][q][s] - rhs[0.0][q][s]
+        np.testing.assert_allclose(got, expect, rtol=0, atol=1e-12 * max(1.0, np.abs(rhs[0.0][q][s]).max()))
+
+
 def test_flop_count_positive(orc):
     c = orc.flop_counts()
     assert c["total"] > 1000 and c["div"] > 0
