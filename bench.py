@@ -60,7 +60,7 @@ FLOPS_PER_CELL = {"z4c_derivs": 1180.0, "z4c_stage": 1971.0}
 # ncu capture (262,144-cell launch), scaled to a launch by its cell count;
 # None once the kernel has changed since the counters were taken.
 DRAM_BYTES_PER_CELL = {"z4c_derivs": (31.963392e6 + 5.807616e6 + 161.104896e6 + 248.131584e6) / 262144,
-                       "z4c_stage": None}
+                       "z4c_stage": (512.791552e6 + 230.223872e6) / 262144}
 # FP64 instructions (DFMA + DMUL + DADD, thread-level / cell) per interior
 # cell of the derivative pass (D_x/D_y row pass + per-cell pass), counted by
 # ncu on the 3-level 64^3 case (profiles/z4c_kernels_bl3level64_ncu.md,
@@ -354,12 +354,19 @@ def run_gpu(args, rank: int, world: int):
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ne2e)]
     t0 = time.perf_counter()
+    t_set = t_get = 0.0
     for q in range(ne2e):
+        ta = time.perf_counter()
         ctx.sc_set_state(host_in.data_ptr(), ghosted_level0=True)
+        tb = time.perf_counter()
         ev[q][0].record(stream)
         ctx.sc_advance(1)
         ev[q][1].record(stream)
+        ev[q][1].synchronize()
+        tc = time.perf_counter()
         ctx.sc_get_state(host_out.data_ptr())
+        t_set += tb - ta
+        t_get += time.perf_counter() - tc
     torch.cuda.synchronize()
     barrier()
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
@@ -429,7 +436,8 @@ def run_gpu(args, rank: int, world: int):
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "steps": ne2e, "ms_per_step": e2e_s * 1e3 / ne2e, "device_ms_per_step": e2e_step_ms},
+                        "steps": ne2e, "ms_per_step": e2e_s * 1e3 / ne2e, "device_ms_per_step": e2e_step_ms,
+                        "set_state_ms": t_set * 1e3 / ne2e, "get_state_ms": t_get * 1e3 / ne2e},
                 "gpu_launches": launches, "clocks": clk, "serving": serving, "uniform_step_mode": uniform}
         print(json.dumps(line), flush=True)
     if dist is not None:
