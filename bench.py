@@ -397,7 +397,7 @@ def run_gpu(args, rank: int, world: int):
                    "steps": args.uniform_steps}
         cu.close()
 
-    # Served form vs plain per-box form on a seeded ensemble (configs[4] mix).
+    # Served form vs plain per-box form on a seeded ensemble (60% wave, 40% Z4c requests).
     serving = None
     if rank == 0 and args.serving_requests > 0:
         ctx.close()
@@ -450,7 +450,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--serving", action="store_true", help="only the serving ensemble (configs[4]), one JSON line")
+    ap.add_argument("--serving", action="store_true", help="only the 256-request serving ensemble, one JSON line")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--uniform-steps", type=int, default=2,
                     help="coarse steps of the same hierarchy in uniform-step mode (0: skip)")

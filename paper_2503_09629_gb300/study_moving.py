@@ -1,4 +1,4 @@
-"""Moving-box run with the structure of configs[3] (9 levels, two box stacks
+"""Moving-box run of the 9-level binary-black-hole layout (two box stacks
 following the punctures, regridded every coarse step).
 
     python -m paper_2503_09629_gb300.study_moving [--steps 32]

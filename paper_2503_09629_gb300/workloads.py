@@ -298,7 +298,7 @@ def serving_requests(n: int = 256, seed: int = 0, burst: bool = False, mean_inte
 
 
 # ---------------------------------------------------------------------------
-# Moving boxes (configs[3]): box stacks that follow the punctures.
+# Moving boxes: box stacks that follow the punctures.
 
 def box_around(centre, radius, level, h0, origin):
     """Box of level `level` covering [centre - radius, centre + radius] in
@@ -375,7 +375,7 @@ def track_punctures(target, positions, dt, shift_fields=(19, 20, 21)):
 
 
 def moving_9level(n: int = 32, sep: float = 6.0, m: float = 0.5):
-    """configs[3]-structured moving-box workload at a size one GPU runs in
+    """9-level moving-box Brill-Lindquist workload at a size one GPU runs in
     about a second per coarse step: Z4c Brill-Lindquist m = 0.5 at x = +-3,
     9 levels over [-128,128]^3 (level 0 n^3), levels 0-2 fixed nested cubes,
     levels 3-8 box stacks around the punctures with radii 12, 6, 3, 1.5,
@@ -384,7 +384,7 @@ def moving_9level(n: int = 32, sep: float = 6.0, m: float = 0.5):
     Sec. III.A (eta_c = 2, eta_s = 40, eta_o = 0.25): with the constant
     eta = 2, eta * dt = 4 on level 0 (dt = 2) lies outside RK4's stability
     interval and the coarse levels blow up after about 15 coarse steps, the
-    time-step limit dt_max ~ 1/eta that the paper discusses.  The face-value configs[3] (finest radius 1.5 at h = 1/128,
+    time-step limit dt_max ~ 1/eta that the paper discusses.  The full-size layout (base 128^3, finest radius 1.5 at h = 1/128,
     about 1.7e8 cells and 3e10 cell updates per coarse step) needs about ten
     minutes per coarse step at this path's rate.
     Returns (hierarchy, positions, radii, first_moving)."""

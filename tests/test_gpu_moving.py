@@ -1,4 +1,4 @@
-"""Moving boxes (configs[3] mechanism): regrid and point interpolation on the
+"""Moving boxes (puncture-tracking box stacks): regrid and point interpolation on the
 GPU against the CPU oracle, and puncture tracking."""
 import numpy as np
 import pytest
