@@ -268,8 +268,10 @@ struct Level {
   int nperiodic = 0;
   int32_t* phys = nullptr;
   int nphys = 0;
-  RestrictCell* restr = nullptr;  // parent cells restricted from this level
+  RestrictCell* restr = nullptr;  // parent cells restricted from this level (per-cell kernel)
   int nrestr = 0;
+  RestrictBlock* rblocks = nullptr;  // the rest, in 4x4x4 parent blocks (separable kernel)
+  int nrblocks = 0;
   long interior_cells = 0;
   int parity = 0;  // which of S[] holds the current state
 };
@@ -425,7 +427,8 @@ struct HostLists {
   int namr_blocked = 0;             // AMR cells [0, namr_blocked) belong to blocks
   std::vector<int2> periodic;
   std::vector<int32_t> phys;
-  std::vector<RestrictCell> restr;
+  std::vector<RestrictCell> restr;   // restricted parent cells outside blocks
+  std::vector<RestrictBlock> rblocks;  // 4x4x4 parent blocks for the separable kernel
 };
 
 sc_status build_level_geometry(sc_ctx* c, int l, const sc_box* boxes, int nb) {
@@ -760,6 +763,7 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
   }
   // restriction onto the parent: parent cells whose 8 children are interior here
   if (l > 0) {
+    std::vector<std::array<int, 3>> rcells;
     const Level& P = c->lev[l - 1];
     const Geom& pg = P.g;
     for (int k = 0; k < pg.ext[2]; ++k)
@@ -777,11 +781,36 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
           const int fb[3] = {2 * C[0] - 2, 2 * C[1] - 2, 2 * C[2] - 2};
           const int fe[3] = {2 * C[0] + 3, 2 * C[1] + 3, 2 * C[2] + 3};
           if (!in_array(g, fb) || !in_array(g, fe)) return fail(SC_ENESTING, "restriction stencil outside level %d", l);
-          RestrictCell rc;
-          rc.dst = (int32_t)pg.off(C[0], C[1], C[2]);
-          rc.fbase = (int32_t)g.off(fb[0], fb[1], fb[2]);
-          hl.restr.push_back(rc);
+          rcells.push_back({C[0], C[1], C[2]});
         }
+    // 4x4x4 parent blocks whose 12^3 fine region lies in the fine array go to
+    // the separable kernel; the other cells to the per-cell kernel
+    std::map<std::array<int, 3>, unsigned long long> blk;
+    for (const auto& C : rcells) {
+      const std::array<int, 3> key{C[0] >> 2, C[1] >> 2, C[2] >> 2};
+      blk[key] |= 1ull << ((C[0] & 3) + 4 * (C[1] & 3) + 16 * (C[2] & 3));
+    }
+    for (const auto& kv : blk) {
+      const int C0[3] = {4 * kv.first[0], 4 * kv.first[1], 4 * kv.first[2]};
+      const int fb[3] = {2 * C0[0] - 2, 2 * C0[1] - 2, 2 * C0[2] - 2};
+      const int fe[3] = {2 * C0[0] + 9, 2 * C0[1] + 9, 2 * C0[2] + 9};
+      if (in_array(g, fb) && in_array(g, fe)) {
+        RestrictBlock rb;
+        rb.pbase = (int32_t)pg.off(C0[0], C0[1], C0[2]);
+        rb.fbase = (int32_t)g.off(fb[0], fb[1], fb[2]);
+        rb.mask = kv.second;
+        hl.rblocks.push_back(rb);
+        continue;
+      }
+      for (int q = 0; q < 64; ++q) {
+        if (!((kv.second >> q) & 1ull)) continue;
+        const int C[3] = {C0[0] + (q & 3), C0[1] + ((q >> 2) & 3), C0[2] + (q >> 4)};
+        RestrictCell rc;
+        rc.dst = (int32_t)pg.off(C[0], C[1], C[2]);
+        rc.fbase = (int32_t)g.off(2 * C[0] - 2, 2 * C[1] - 2, 2 * C[2] - 2);
+        hl.restr.push_back(rc);
+      }
+    }
   }
   return SC_OK;
 }
@@ -838,7 +867,8 @@ sc_status setup_level_device(sc_ctx* c, int l, HostLists& hl) {
   sc_status st;
   if ((st = level_upload(c, L, hl.tiles, &L.tiles)) || (st = level_upload(c, L, hl.amr, &L.amr)) ||
       (st = level_upload(c, L, hl.periodic, &L.periodic)) || (st = level_upload(c, L, hl.phys, &L.phys)) ||
-      (st = level_upload(c, L, hl.restr, &L.restr)) || (st = level_upload(c, L, hl.blocks, &L.blocks)) ||
+      (st = level_upload(c, L, hl.restr, &L.restr)) || (st = level_upload(c, L, hl.rblocks, &L.rblocks)) ||
+      (st = level_upload(c, L, hl.blocks, &L.blocks)) ||
       (st = level_upload(c, L, hl.dxy, &L.dxy)) || (st = level_upload(c, L, hl.ptiles, &L.ptiles)))
     return st;
   L.ntiles = (int)hl.tiles.size();
@@ -850,6 +880,7 @@ sc_status setup_level_device(sc_ctx* c, int l, HostLists& hl) {
   L.nperiodic = (int)hl.periodic.size();
   L.nphys = (int)hl.phys.size();
   L.nrestr = (int)hl.restr.size();
+  L.nrblocks = (int)hl.rblocks.size();
   L.amr_store = nullptr;
   if (L.namr) {
     int idx[4];
@@ -1099,6 +1130,8 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
     }
     case OP_RESTRICT: {
       const Level& P = c->lev[o.level - 1];
+      CU(launch_restrict_blocks(o.out, P.g.fs, P.g.pitch, P.g.pitch * P.g.ext[1], o.in, g.fs, g.pitch,
+                                g.pitch * g.ext[1], L.rblocks, L.nrblocks, c->F, c->w, s));
       CU(launch_restrict(o.out, P.g.fs, o.in, g.fs, g.pitch, g.pitch * g.ext[1], L.restr, L.nrestr, c->F, c->w, s));
       break;
     }
@@ -1138,7 +1171,7 @@ sc_status build_schedule(sc_ctx* c, int p) {
       else if (o.kind == OP_PROLONG_DIRECT)
         n += (L.nblocks ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0) + (L.namr ? 1 : 0);
       else
-        n += L.nrestr ? 1 : 0;
+        n += (L.nrestr ? 1 : 0) + (L.nrblocks ? 1 : 0);
     }
     c->launches_per_step = n;
     c->graph_stale[p] = false;

@@ -69,6 +69,17 @@ struct RestrictCell {
   int32_t fbase;
 };
 
+// 4x4x4 parent cells restricted together (aligned to multiples of 4 in the
+// parent index space): offset of the block's first parent cell in the parent
+// array (may lie outside it; only masked cells are written), offset of the
+// first of the 12x12x12 fine cells their stencils cover, and which of the 64
+// parent cells (bit x + 4y + 16z) are restricted.
+struct RestrictBlock {
+  int32_t pbase;
+  int32_t fbase;
+  unsigned long long mask;
+};
+
 // A run of consecutive cells of one array row: offset of the first cell,
 // count, and which first derivatives to store there (bit 0: D_x, bit 1: D_y).
 struct RowSeg {
@@ -161,6 +172,11 @@ cudaError_t launch_amr_apply(double* vec, long fs, int F, const AmrCell* cells, 
                              const double* store, const double* c4, cudaStream_t s, int nk = 4);
 cudaError_t launch_restrict(double* parent, long pfs, const double* fine, long ffs, int fsy, int fsz,
                             const RestrictCell* cells, int ncells, int F, const Weights& w, cudaStream_t s);
+// Separable form of the restriction over RestrictBlocks (bitwise the same
+// results as launch_restrict for the same cells).
+cudaError_t launch_restrict_blocks(double* parent, long pfs, int psy, int psz, const double* fine, long ffs, int fsy,
+                                   int fsz, const RestrictBlock* blocks, int nblocks, int F, const Weights& w,
+                                   cudaStream_t s);
 cudaError_t launch_initial_data(double* vec, const Geom& g, int F, int system, int kind, const double* params,
                                 int nparams, cudaStream_t s);
 cudaError_t launch_transfer_copy(double* dst, long dfs, const double* src, long sfs, const int2* pairs, int n, int F,
