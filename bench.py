@@ -60,7 +60,7 @@ FLOPS_PER_CELL = {"z4c_derivs": 1180.0, "z4c_stage": 1971.0}
 # ncu capture (262,144-cell launch), scaled to a launch by its cell count;
 # None once the kernel has changed since the counters were taken.
 DRAM_BYTES_PER_CELL = {"z4c_derivs": (31.963392e6 + 5.807616e6 + 161.104896e6 + 248.131584e6) / 262144,
-                       "z4c_stage": (512.791552e6 + 230.223872e6) / 262144}
+                       "z4c_stage": (510.467584e6 + 230.338304e6) / 262144}
 # FP64 instructions (DFMA + DMUL + DADD, thread-level / cell) per interior
 # cell of the derivative pass (D_x/D_y row pass + per-cell pass), counted by
 # ncu on the 3-level 64^3 case (profiles/z4c_kernels_bl3level64_ncu.md,

@@ -17,7 +17,7 @@ constexpr int kThreads = 256;
 
 template <int ORD>
 __global__ void __launch_bounds__(kThreads) wave_stage_kernel(StageArgs a, const Tile* __restrict__ tiles,
-                                                             int ntiles) {
+                                                             int ntiles, FmaK K) {
   const double inv12h2 = ORD == 4 ? 1.0 / (12.0 * a.h * a.h) : 1.0 / (5040.0 * a.h * a.h);
   const long sy = a.sy, sz = a.sz;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -32,15 +32,19 @@ __global__ void __launch_bounds__(kThreads) wave_stage_kernel(StageArgs a, const
       const double u0 = u[o];
       // 4th order: -1, 16, -30, 16, -1 over offsets -2..2 in each dimension, / (12 h^2);
       // 8th order: -9, 128, -1008, 8064, -14350, ... over -4..4, / (5040 h^2)
-      const double s1 = (u[o - 1] + u[o + 1]) + (u[o - sy] + u[o + sy]) + (u[o - sz] + u[o + sz]);
-      const double s2 = (u[o - 2] + u[o + 2]) + (u[o - 2 * sy] + u[o + 2 * sy]) + (u[o - 2 * sz] + u[o + 2 * sz]);
+      // sm = sum over the 6 neighbours at distance m, in FMA form (bitwise the plain sums)
+      auto ring = [&](int m) {
+        return fadd(fadd(fadd(u[o - m], u[o + m], K), fadd(u[o - m * sy], u[o + m * sy], K), K),
+                    fadd(u[o - m * sz], u[o + m * sz], K), K);
+      };
+      const double s1 = ring(1), s2 = ring(2);
       double lap;
       if (ORD == 4) {
-        lap = fma(-90.0, u0, fma(16.0, s1, -s2)) * inv12h2;
+        lap = fmul(fma(-90.0, u0, fma(16.0, s1, -s2)), inv12h2, K);
       } else {
-        const double s3 = (u[o - 3] + u[o + 3]) + (u[o - 3 * sy] + u[o + 3 * sy]) + (u[o - 3 * sz] + u[o + 3 * sz]);
-        const double s4 = (u[o - 4] + u[o + 4]) + (u[o - 4 * sy] + u[o + 4 * sy]) + (u[o - 4 * sz] + u[o + 4 * sz]);
-        lap = fma(-43050.0, u0, fma(8064.0, s1, fma(-1008.0, s2, fma(128.0, s3, -9.0 * s4)))) * inv12h2;
+        const double s3 = ring(3), s4 = ring(4);
+        lap = fmul(fma(-43050.0, u0, fma(8064.0, s1, fma(-1008.0, s2, fma(128.0, s3, fmul(-9.0, s4, K))))), inv12h2,
+                   K);
       }
       const double ku = a.Y[a.fs + o];  // d_t u = Pi
       const double kp = lap;            // d_t Pi = Laplacian u
@@ -50,8 +54,8 @@ __global__ void __launch_bounds__(kThreads) wave_stage_kernel(StageArgs a, const
         a.out[o] = fma(a.cdt, ku, a.yn[o]);
         a.out[a.fs + o] = fma(a.cdt, kp, a.yn[a.fs + o]);
       } else if (a.form == kStageRk4) {
-        const double su = fma(2.0, a.k3[o], fma(2.0, a.k2[o], a.k1[o])) + ku;
-        const double sp = fma(2.0, a.k3[a.fs + o], fma(2.0, a.k2[a.fs + o], a.k1[a.fs + o])) + kp;
+        const double su = fadd(fma(2.0, a.k3[o], fma(2.0, a.k2[o], a.k1[o])), ku, K);
+        const double sp = fadd(fma(2.0, a.k3[a.fs + o], fma(2.0, a.k2[a.fs + o], a.k1[a.fs + o])), kp, K);
         a.out[o] = fma(a.cdt, su, a.yn[o]);
         a.out[a.fs + o] = fma(a.cdt, sp, a.yn[a.fs + o]);
       } else if (a.form == kStageTwo) {
@@ -113,8 +117,9 @@ __global__ void __launch_bounds__(kThreads) radiative_stage_kernel(StageArgs a, 
 cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s, int order) {
   if (ntiles == 0) return cudaSuccess;
   const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
-  if (order == 8) wave_stage_kernel<8><<<grid, kThreads, 0, s>>>(a, tiles, ntiles);
-  else wave_stage_kernel<4><<<grid, kThreads, 0, s>>>(a, tiles, ntiles);
+  const FmaK K{1.0, -1.0, -0.0};
+  if (order == 8) wave_stage_kernel<8><<<grid, kThreads, 0, s>>>(a, tiles, ntiles, K);
+  else wave_stage_kernel<4><<<grid, kThreads, 0, s>>>(a, tiles, ntiles, K);
   return cudaGetLastError();
 }
 

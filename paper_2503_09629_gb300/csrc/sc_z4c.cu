@@ -107,19 +107,6 @@ __global__ void __launch_bounds__(kThreads) z4c_derivs_kernel(const double* __re
 // interior cell and differentiates the stored first derivatives for the
 // mixed terms: 4 FP64 operations per mixed derivative instead of 16.
 
-// On this GPU a DFMA issues faster than a DADD or DMUL (measured 600 vs 506
-// G instructions/s), so the stencil kernels write additions, subtractions
-// and scalings as fused multiply-adds with constants the compiler cannot see
-// (+1, -1, -0 arrive as kernel arguments): fma(a, 1, b) = a + b,
-// fma(b, -1, a) = a - b and fma(x, y, -0) = x * y exactly, so the results
-// are bitwise those of the plain operations.
-struct FmaK {
-  double one, mone, mzero;
-};
-__device__ __forceinline__ double fadd(double a, double b, const FmaK& K) { return fma(a, K.one, b); }
-__device__ __forceinline__ double fsub(double a, double b, const FmaK& K) { return fma(b, K.mone, a); }
-__device__ __forceinline__ double fmul(double a, double b, const FmaK& K) { return fma(a, b, K.mzero); }
-
 // field of Hessian slot s (W, gt x6, alpha, beta x3): slots 0..6 -> fields 0..6, 7..10 -> 18..21
 __device__ __forceinline__ int d2_field(int s) { return s <= 6 ? s : s + 11; }
 
@@ -298,10 +285,14 @@ struct Z4cPoint {
 };
 
 // Right-hand side of the Z4c system at one cell (Sec. III.A; vacuum, so the
-// matter terms vanish).  u: fields; S + o: derivatives in scratch.
+// matter terms vanish).  u: fields; S + o: derivatives in scratch.  Sums,
+// differences and products that do not fuse with a neighbour are written as
+// FMAs with the run-time unit constants of K (fadd, fsub, fmul): a DFMA
+// issues faster than a DADD or DMUL on this GPU.
 template <bool kDiag>
 __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, const double* __restrict__ S, long fs,
-                                              long o, const Z4cParams& P, double eta, double* rhs, double* diag) {
+                                              long o, const Z4cParams& P, double eta, double* rhs, double* diag,
+                                              const FmaK& K) {
 #define FLD(f) Y[(long)(f) * fs + o]
 #define D1(f, d) S[(long)(Q_D1 + 3 * (f) + (d)) * fs + o]
 #define D2(sl, p) S[(long)(Q_D2 + 6 * (sl) + (p)) * fs + o]
@@ -318,16 +309,22 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
 
   // inverse conformal metric
   double gu[6];
-  gu[0] = fma(g[3], g[5], -g[4] * g[4]);
-  gu[1] = fma(g[2], g[4], -g[1] * g[5]);
-  gu[2] = fma(g[1], g[4], -g[2] * g[3]);
-  gu[3] = fma(g[0], g[5], -g[2] * g[2]);
-  gu[4] = fma(g[1], g[2], -g[0] * g[4]);
-  gu[5] = fma(g[0], g[3], -g[1] * g[1]);
-  const double idet = 1.0 / fma(g[0], gu[0], fma(g[1], gu[1], g[2] * gu[2]));
+  gu[0] = fma(g[3], g[5], fmul(-g[4], g[4], K));
+  gu[1] = fma(g[2], g[4], fmul(-g[1], g[5], K));
+  gu[2] = fma(g[1], g[4], fmul(-g[2], g[3], K));
+  gu[3] = fma(g[0], g[5], fmul(-g[2], g[2], K));
+  gu[4] = fma(g[1], g[2], fmul(-g[0], g[4], K));
+  gu[5] = fma(g[0], g[3], fmul(-g[1], g[1], K));
+  const double det = fma(g[0], gu[0], fma(g[1], gu[1], fmul(g[2], gu[2], K)));
+  const double rdw = 1.0 / fmul(det, W, K);  // one division for 1/det and 1/W
+  const double idet = fmul(W, rdw, K);
+  const double iW = fmul(det, rdw, K);
 #pragma unroll
-  for (int s = 0; s < 6; ++s) gu[s] *= idet;
-  const double iW = 1.0 / W;
+  for (int s = 0; s < 6; ++s) gu[s] = fmul(gu[s], idet, K);
+  // trace weights: gt^ij X_ij = sum_s gw[s] X[s] over the 6 symmetric slots
+  double gw[6];
+#pragma unroll
+  for (int s = 0; s < 6; ++s) gw[s] = (s == 1 || s == 2 || s == 4) ? fmul(2.0, gu[s], K) : gu[s];
 
   // first derivatives of the metric, Christoffel symbols
   double dg[6][3];
@@ -343,18 +340,18 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = i; j < 3; ++j)
-        Gl[k][sidx(i, j)] = 0.5 * (dg[sidx(j, k)][i] + dg[sidx(i, k)][j] - dg[sidx(i, j)][k]);
+        Gl[k][sidx(i, j)] = fma(0.5, dg[sidx(j, k)][i], fma(0.5, dg[sidx(i, k)][j], fmul(-0.5, dg[sidx(i, j)][k], K)));
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
     for (int s = 0; s < 6; ++s)
-      Gu[k][s] = fma(gu[sidx(k, 0)], Gl[0][s], fma(gu[sidx(k, 1)], Gl[1][s], gu[sidx(k, 2)] * Gl[2][s]));
+      Gu[k][s] = fma(gu[sidx(k, 0)], Gl[0][s], fma(gu[sidx(k, 1)], Gl[1][s], fmul(gu[sidx(k, 2)], Gl[2][s], K)));
   // (Gamma_d)^k = gt^ij Gamma^k_ij
   double Gd[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
-    Gd[k] = fma(gu[0], Gu[k][0], fma(gu[3], Gu[k][3], fma(gu[5], Gu[k][5],
-            2.0 * fma(gu[1], Gu[k][1], fma(gu[2], Gu[k][2], gu[4] * Gu[k][4])))));
+    Gd[k] = fma(2.0, fma(gu[1], Gu[k][1], fma(gu[2], Gu[k][2], fmul(gu[4], Gu[k][4], K))),
+                fma(gu[0], Gu[k][0], fma(gu[3], Gu[k][3], fmul(gu[5], Gu[k][5], K))));
 
   // U[j][k][l] = gt^{lm} Gamma_{j,km}
   double U[3][3][3];
@@ -365,16 +362,17 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
 #pragma unroll
       for (int l = 0; l < 3; ++l)
         U[j][k][l] = fma(gu[sidx(l, 0)], Gl[j][sidx(k, 0)],
-                         fma(gu[sidx(l, 1)], Gl[j][sidx(k, 1)], gu[sidx(l, 2)] * Gl[j][sidx(k, 2)]));
+                         fma(gu[sidx(l, 1)], Gl[j][sidx(k, 1)], fmul(gu[sidx(l, 2)], Gl[j][sidx(k, 2)], K)));
 
   const double dW[3] = {D1(ZW, 0), D1(ZW, 1), D1(ZW, 2)};
   const double dal[3] = {D1(ZAL, 0), D1(ZAL, 1), D1(ZAL, 2)};
   // gt^{kl} d_l W and |dW|^2, gt^{kl} d_l W d_k alpha
   double gudW[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) gudW[k] = fma(gu[sidx(k, 0)], dW[0], fma(gu[sidx(k, 1)], dW[1], gu[sidx(k, 2)] * dW[2]));
-  const double dWdW = fma(gudW[0], dW[0], fma(gudW[1], dW[1], gudW[2] * dW[2]));
-  const double dWdal = fma(gudW[0], dal[0], fma(gudW[1], dal[1], gudW[2] * dal[2]));
+  for (int k = 0; k < 3; ++k)
+    gudW[k] = fma(gu[sidx(k, 0)], dW[0], fma(gu[sidx(k, 1)], dW[1], fmul(gu[sidx(k, 2)], dW[2], K)));
+  const double dWdW = fma(gudW[0], dW[0], fma(gudW[1], dW[1], fmul(gudW[2], dW[2], K)));
+  const double dWdal = fma(gudW[0], dal[0], fma(gudW[1], dal[1], fmul(gudW[2], dal[2], K)));
 
   // Ricci tensor R_ij = R^W_ij + Rt_ij, and D_i D_j alpha
   double R[6], DDal[6];
@@ -383,8 +381,8 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
     double trDDW = 0.0;
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
-      DDW[s] = D2(0, s) - fma(Gu[0][s], dW[0], fma(Gu[1][s], dW[1], Gu[2][s] * dW[2]));
-      trDDW = fma((s == 1 || s == 2 || s == 4) ? 2.0 * gu[s] : gu[s], DDW[s], trDDW);
+      DDW[s] = fsub(D2(0, s), fma(Gu[0][s], dW[0], fma(Gu[1][s], dW[1], fmul(Gu[2][s], dW[2], K))), K);
+      trDDW = fma(gw[s], DDW[s], trDDW);
     }
     const double dGam[3][3] = {{D1(ZGAM, 0), D1(ZGAM, 1), D1(ZGAM, 2)},
                                {D1(ZGAM + 1, 0), D1(ZGAM + 1, 1), D1(ZGAM + 1, 2)},
@@ -402,15 +400,15 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
           for (int l = 0; l < 3; ++l) s = fma(Gu[k][sidx(l, i)], U[j][k][l], s);
         T1[i][j] = s;
       }
-    const double m2W = -2.0 * dWdW * iW;
+    const double m2WiW = fmul(fmul(fmul(-2.0, dWdW, K), iW, K), iW, K);  // -2 |dW|^2 / W^2
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = i; j < 3; ++j) {
         const int s = sidx(i, j);
         // -1/2 gt^lm d_l d_m gt_ij
-        double r = -0.5 * (fma(gu[0], D2(1 + s, 0), fma(gu[3], D2(1 + s, 3), gu[5] * D2(1 + s, 5))) +
-                           2.0 * fma(gu[1], D2(1 + s, 1), fma(gu[2], D2(1 + s, 2), gu[4] * D2(1 + s, 4))));
+        double r = fma(-0.5, fma(gu[0], D2(1 + s, 0), fma(gu[3], D2(1 + s, 3), fmul(gu[5], D2(1 + s, 5), K))),
+                       -fma(gu[1], D2(1 + s, 1), fma(gu[2], D2(1 + s, 2), fmul(gu[4], D2(1 + s, 4), K))));
         // gt_k(i d_j) Gamt^k
         double a = 0.0;
 #pragma unroll
@@ -419,7 +417,7 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
         // (Gamma_d)^k Gamma_(ij)k
         double b = 0.0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) b = fma(Gd[k], Gl[i][sidx(j, k)] + Gl[j][sidx(i, k)], b);
+        for (int k = 0; k < 3; ++k) b = fma(Gd[k], fadd(Gl[i][sidx(j, k)], Gl[j][sidx(i, k)], K), b);
         r = fma(0.5, b, r);
         // gt^lm (2 Gamma^k_l(i Gamma_j)km + Gamma^k_im Gamma_klj)
         double t3 = 0.0;
@@ -427,26 +425,25 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
         for (int k = 0; k < 3; ++k)
 #pragma unroll
           for (int m = 0; m < 3; ++m) t3 = fma(Gu[k][sidx(i, m)], U[k][j][m], t3);
-        r += T1[i][j] + T1[j][i] + t3;
+        r = fadd(r, fadd(fadd(T1[i][j], T1[j][i], K), t3, K), K);
         // R^W_ij = (D_i D_j W + gt_ij D^l D_l W) / W - 2 gt_ij |dW|^2 / W^2
-        const double rw = fma(fma(g[s], trDDW, DDW[s]), iW, g[s] * m2W * iW);
-        R[s] = r + rw;
+        const double rw = fma(fma(g[s], trDDW, DDW[s]), iW, fmul(g[s], m2WiW, K));
+        R[s] = fadd(r, rw, K);
         // D_i D_j alpha with Gamma^k_ij - (delta^k_i d_j W + delta^k_j d_i W - gt_ij gt^kl d_l W) / W
-        const double gd = fma(Gu[0][s], dal[0], fma(Gu[1][s], dal[1], Gu[2][s] * dal[2]));
-        const double wt = fma(dW[j], dal[i], fma(dW[i], dal[j], -g[s] * dWdal));
-        DDal[s] = D2(7, s) - fma(-wt, iW, gd);
+        const double gd = fma(Gu[0][s], dal[0], fma(Gu[1][s], dal[1], fmul(Gu[2][s], dal[2], K)));
+        const double wt = fma(dW[j], dal[i], fma(dW[i], dal[j], fmul(-g[s], dWdal, K)));
+        DDal[s] = fsub(D2(7, s), fma(-wt, iW, gd), K);
       }
   }
   double trR = 0.0, trDDal = 0.0;
 #pragma unroll
   for (int s = 0; s < 6; ++s) {
-    const double w = (s == 1 || s == 2 || s == 4) ? 2.0 * gu[s] : gu[s];
-    trR = fma(w, R[s], trR);
-    trDDal = fma(w, DDal[s], trDDal);
+    trR = fma(gw[s], R[s], trR);
+    trDDal = fma(gw[s], DDal[s], trDDal);
   }
-  const double W2 = W * W;
-  const double Rsc = W2 * trR;
-  const double DiDial = W2 * trDDal;
+  const double W2 = fmul(W, W, K);
+  const double Rsc = fmul(W2, trR, K);
+  const double DiDial = fmul(W2, trDDal, K);
 
   // At with raised indices: Am[i][j] = At^i_j, Auu = At^ij
   double Am[3][3], Auu[6];
@@ -454,36 +451,40 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-      Am[i][j] = fma(gu[sidx(i, 0)], A[sidx(0, j)], fma(gu[sidx(i, 1)], A[sidx(1, j)], gu[sidx(i, 2)] * A[sidx(2, j)]));
+      Am[i][j] = fma(gu[sidx(i, 0)], A[sidx(0, j)],
+                     fma(gu[sidx(i, 1)], A[sidx(1, j)], fmul(gu[sidx(i, 2)], A[sidx(2, j)], K)));
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = i; j < 3; ++j)
-      Auu[sidx(i, j)] = fma(Am[i][0], gu[sidx(0, j)], fma(Am[i][1], gu[sidx(1, j)], Am[i][2] * gu[sidx(2, j)]));
-  const double AA = fma(A[0], Auu[0], fma(A[3], Auu[3], fma(A[5], Auu[5],
-                    2.0 * fma(A[1], Auu[1], fma(A[2], Auu[2], A[4] * Auu[4])))));
+      Auu[sidx(i, j)] =
+          fma(Am[i][0], gu[sidx(0, j)], fma(Am[i][1], gu[sidx(1, j)], fmul(Am[i][2], gu[sidx(2, j)], K)));
+  const double AA = fma(2.0, fma(A[1], Auu[1], fma(A[2], Auu[2], fmul(A[4], Auu[4], K))),
+                        fma(A[0], Auu[0], fma(A[3], Auu[3], fmul(A[5], Auu[5], K))));
 
   double dbe[3][3];  // dbe[i][j] = d_j beta^i
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) dbe[i][j] = D1(ZB + i, j);
-  const double divb = dbe[0][0] + dbe[1][1] + dbe[2][2];
+  const double divb = fadd(fadd(dbe[0][0], dbe[1][1], K), dbe[2][2], K);
   const double Kt = fma(2.0, Th, Kh);
   const double third = 1.0 / 3.0, twothird = 2.0 / 3.0;
 
-#define ADV(f) fma(be[0], D1(f, 0), fma(be[1], D1(f, 1), be[2] * D1(f, 2)))
+#define ADV(f) fma(be[0], D1(f, 0), fma(be[1], D1(f, 1), fmul(be[2], D1(f, 2), K)))
   // W
-  rhs[ZW] = fma(third * W, fma(al, Kt, -divb), ADV(ZW));
+  rhs[ZW] = fma(fmul(third, W, K), fma(al, Kt, -divb), ADV(ZW));
   // gt_ij and At_ij
   double X[6], trX = 0.0;
 #pragma unroll
   for (int s = 0; s < 6; ++s) {
     X[s] = fma(al, R[s], -DDal[s]);
-    trX = fma((s == 1 || s == 2 || s == 4) ? 2.0 * gu[s] : gu[s], X[s], trX);
+    trX = fma(gw[s], X[s], trX);
   }
-  const double alKt = al * Kt;
-  const double m2al = -2.0 * al;
+  const double alKt = fmul(al, Kt, K);
+  const double m2al = fmul(-2.0, al, K);
+  const double m23divb = fmul(-twothird, divb, K);
+  const double m13trX = fmul(-third, trX, K);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -496,12 +497,13 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
         la = fma(A[sidx(k, i)], dbe[k][j], fma(A[sidx(k, j)], dbe[k][i], la));
         aa = fma(Am[k][i], A[sidx(k, j)], aa);
       }
-      rhs[ZG + s] = ADV(ZG + s) + fma(m2al, A[s], fma(-twothird * divb, g[s], lg));
-      const double tf = fma(-third * trX, g[s], X[s]);
-      rhs[ZA + s] = ADV(ZA + s) + fma(W2, tf, fma(alKt, A[s], fma(m2al, aa, fma(-twothird * divb, A[s], la))));
+      rhs[ZG + s] = fadd(ADV(ZG + s), fma(m2al, A[s], fma(m23divb, g[s], lg)), K);
+      const double tf = fma(m13trX, g[s], X[s]);
+      rhs[ZA + s] = fadd(ADV(ZA + s), fma(W2, tf, fma(alKt, A[s], fma(m2al, aa, fma(m23divb, A[s], la)))), K);
     }
   // Khat
-  rhs[ZK] = ADV(ZK) - DiDial + al * fma(third * Kt, Kt, AA) + al * (P.kappa1 * (1.0 - P.kappa2)) * Th;
+  rhs[ZK] = fma(al, fma(fmul(third, Kt, K), Kt, AA),
+                fma(fmul(al, P.kappa1 * (1.0 - P.kappa2), K), Th, fsub(ADV(ZK), DiDial, K)));
   // Gamt^i
   {
     const double dKh[3] = {D1(ZK, 0), D1(ZK, 1), D1(ZK, 2)};
@@ -512,38 +514,46 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
     // d_j d_k beta^k for each j
     double ddivb[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) ddivb[j] = D2(8, sidx(j, 0)) + D2(9, sidx(j, 1)) + D2(10, sidx(j, 2));
-    const double m3iW = -3.0 * iW;
+    for (int j = 0; j < 3; ++j) ddivb[j] = fadd(fadd(D2(8, sidx(j, 0)), D2(9, sidx(j, 1)), K), D2(10, sidx(j, 2)), K);
+    const double m3iW = fmul(-3.0, iW, K);
+    const double twoal = fmul(2.0, al, K);
+    const double twothirddivb = fmul(twothird, divb, K);
+    const double m2k1al = fmul(-2.0 * P.kappa1, al, K);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      double br = 0.0;
-#pragma unroll
-      for (int s = 0; s < 6; ++s) br = fma((s == 1 || s == 2 || s == 4) ? 2.0 * Gu[i][s] : Gu[i][s], Auu[s], br);
-      double r = 0.0, lap = 0.0;
+      // Gamt^i_jk At^jk
+      double br = fma(2.0, fma(Gu[i][1], Auu[1], fma(Gu[i][2], Auu[2], fmul(Gu[i][4], Auu[4], K))),
+                      fma(Gu[i][0], Auu[0], fma(Gu[i][3], Auu[3], fmul(Gu[i][5], Auu[5], K))));
+      double sA = 0.0, sW = 0.0, sD = 0.0, sL = 0.0, r = 0.0;
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const double auij = Auu[sidx(i, j)], guij = gu[sidx(i, j)];
-        r = fma(-2.0 * auij, dal[j], r);
-        br = fma(m3iW * auij, dW[j], br);
-        br = fma(-third * guij, dd[j], br);
-        lap = fma(third * guij, ddivb[j], lap);
+        sA = fma(auij, dal[j], sA);     // At^ij d_j alpha
+        sW = fma(auij, dW[j], sW);      // At^ij d_j W
+        sD = fma(guij, dd[j], sD);      // gt^ij d_j (2 Khat + Theta)
+        sL = fma(guij, ddivb[j], sL);   // gt^ij d_j d_k beta^k
         r = fma(-Gd[j], dbe[i][j], r);
       }
-      // gt^jk d_j d_k beta^i
-      lap += fma(gu[0], D2(8 + i, 0), fma(gu[3], D2(8 + i, 3), gu[5] * D2(8 + i, 5))) +
-             2.0 * fma(gu[1], D2(8 + i, 1), fma(gu[2], D2(8 + i, 2), gu[4] * D2(8 + i, 4)));
-      r = fma(2.0 * al, br, r) + lap;
-      r = fma(twothird * Gd[i], divb, r);
-      r = fma(-2.0 * P.kappa1 * al, Gam[i] - Gd[i], r);
-      rhs[ZGAM + i] = ADV(ZGAM + i) + r;
+      r = fma(-2.0, sA, r);
+      br = fma(m3iW, sW, br);
+      br = fma(-third, sD, br);
+      // 1/3 gt^ij d_j d_k beta^k + gt^jk d_j d_k beta^i
+      const double lap = fma(third, sL,
+                             fma(2.0, fma(gu[1], D2(8 + i, 1), fma(gu[2], D2(8 + i, 2), fmul(gu[4], D2(8 + i, 4), K))),
+                                 fma(gu[0], D2(8 + i, 0), fma(gu[3], D2(8 + i, 3), fmul(gu[5], D2(8 + i, 5), K)))));
+      r = fadd(fma(twoal, br, r), lap, K);
+      r = fma(Gd[i], twothirddivb, r);
+      r = fma(m2k1al, fsub(Gam[i], Gd[i], K), r);
+      rhs[ZGAM + i] = fadd(ADV(ZGAM + i), r, K);
     }
   }
   // Theta
-  rhs[ZTH] = ADV(ZTH) + 0.5 * al * (Rsc - AA + twothird * Kt * Kt) - al * (P.kappa1 * (2.0 + P.kappa2)) * Th;
+  rhs[ZTH] = fma(fmul(0.5, al, K), fma(fmul(twothird, Kt, K), Kt, fsub(Rsc, AA, K)),
+                 fma(fmul(-al, P.kappa1 * (2.0 + P.kappa2), K), Th, ADV(ZTH)));
   // lapse (1+log) and shift (Gamma-driver)
   rhs[ZAL] = fma(m2al, Kh, ADV(ZAL));
 #pragma unroll
-  for (int i = 0; i < 3; ++i) rhs[ZB + i] = ADV(ZB + i) + fma(0.75, Gam[i], -eta * be[i]);
+  for (int i = 0; i < 3; ++i) rhs[ZB + i] = fadd(ADV(ZB + i), fma(0.75, Gam[i], fmul(-eta, be[i], K)), K);
   if (kDiag) {
     diag[0] = Rsc;
     diag[1] = AA;
@@ -564,7 +574,7 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
 // unconstrained 252-register build on the 524,288-cell benchmark level.
 template <int FORM>
 __global__ void __launch_bounds__(128, 3) z4c_stage_kernel(StageArgs a, const double* __restrict__ S, Z4cParams P,
-                                                       const Tile* __restrict__ tiles, int ntiles) {
+                                                          const Tile* __restrict__ tiles, int ntiles, FmaK K) {
   const double ko = P.ko_sigma / (64.0 * a.h);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile T = tiles[t];
@@ -575,7 +585,7 @@ __global__ void __launch_bounds__(128, 3) z4c_stage_kernel(StageArgs a, const do
       const int k = q / (T.nx * T.ny);
       const long o = (long)(T.z0 + k) * a.sz + (long)(T.y0 + j) * a.sy + (T.x0 + i);
       double rhs[kNZ4c];
-      z4c_rhs_point<false>(a.Y, S, a.fs, o, P, a.eta ? a.eta[o] : P.eta, rhs, nullptr);
+      z4c_rhs_point<false>(a.Y, S, a.fs, o, P, a.eta ? a.eta[o] : P.eta, rhs, nullptr, K);
 #pragma unroll
       for (int f = 0; f < kNZ4c; ++f) {
         const long fo = (long)f * a.fs + o;
@@ -584,7 +594,7 @@ __global__ void __launch_bounds__(128, 3) z4c_stage_kernel(StageArgs a, const do
         if (FORM == kStageSingle) {
           a.out[fo] = fma(a.cdt, kv, a.yn[fo]);
         } else if (FORM == kStageRk4) {
-          const double s = fma(2.0, a.k3[fo], fma(2.0, a.k2[fo], a.k1[fo])) + kv;
+          const double s = fadd(fma(2.0, a.k3[fo], fma(2.0, a.k2[fo], a.k1[fo])), kv, K);
           a.out[fo] = fma(a.cdt, s, a.yn[fo]);
         } else if (FORM == kStageTwo) {
           a.out[fo] = fma(a.cdt, kv, fma(a.c1dt, a.k1[fo], a.yn[fo]));
@@ -604,7 +614,7 @@ __global__ void __launch_bounds__(128) z4c_constraints_kernel(const double* __re
                                                              long fs, int sy, int sz, Z4cParams P,
                                                              const Tile* __restrict__ tiles, int ntiles,
                                                              long out_stride, int bx, int by, int bz, int nbx,
-                                                             int nby) {
+                                                             int nby, FmaK K) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile T = tiles[t];
     const int n = T.nx * T.ny * T.nz;
@@ -615,7 +625,7 @@ __global__ void __launch_bounds__(128) z4c_constraints_kernel(const double* __re
 #define FLD(f) Y[(long)(f) * fs + o]
 #define D1(f, d) S[(long)(Q_D1 + 3 * (f) + (d)) * fs + o]
       double rhs[kNZ4c], diag[3];
-      z4c_rhs_point<true>(Y, S, fs, o, P, P.eta, rhs, diag);
+      z4c_rhs_point<true>(Y, S, fs, o, P, P.eta, rhs, diag, K);
       out[cell] = diag[0] + (2.0 / 3.0) * diag[2] * diag[2] - diag[1];
       double g[6], A[6], gu[6];
       for (int s = 0; s < 6; ++s) {
@@ -754,10 +764,11 @@ cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4
                              int ntiles, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
   const int grid = ntiles < caps().stage ? ntiles : caps().stage;
-  if (a.form == kStageRk4) z4c_stage_kernel<kStageRk4><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles);
-  else if (a.form == kStageTwo) z4c_stage_kernel<kStageTwo><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles);
-  else if (a.form == kStageNone) z4c_stage_kernel<kStageNone><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles);
-  else z4c_stage_kernel<kStageSingle><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles);
+  const FmaK K{1.0, -1.0, -0.0};
+  if (a.form == kStageRk4) z4c_stage_kernel<kStageRk4><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+  else if (a.form == kStageTwo) z4c_stage_kernel<kStageTwo><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+  else if (a.form == kStageNone) z4c_stage_kernel<kStageNone><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+  else z4c_stage_kernel<kStageSingle><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
   return cudaGetLastError();
 }
 
@@ -767,7 +778,7 @@ cudaError_t launch_z4c_constraints(const double* Y, const double* scratch, doubl
   if (ntiles == 0) return cudaSuccess;
   const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
   z4c_constraints_kernel<<<grid, 128, 0, s>>>(Y, scratch, out, fs, sy, sz, p, tiles, ntiles, out_stride, box_lo[0],
-                                              box_lo[1], box_lo[2], box_n[0], box_n[1]);
+                                              box_lo[1], box_lo[2], box_n[0], box_n[1], FmaK{1.0, -1.0, -0.0});
   return cudaGetLastError();
 }
 
