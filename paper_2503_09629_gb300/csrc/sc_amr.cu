@@ -1,5 +1,5 @@
 // sc_amr.cu -- refinement-boundary kernels (prolongation of the parent's
-// y_n and k1..k4, dense-output ghost fill, restriction), periodic ghost copy,
+// y_n and stage vectors, dense-output ghost fill, restriction), periodic ghost copy,
 // analytic initial data, box pack/unpack and the finiteness check.
 //
 // Every kernel works on one level's dense FP64 array (one array per field,
@@ -20,8 +20,9 @@ inline int grid_for(long work, int threads) {
   return (int)b;
 }
 
-// Sec. II step 2: prolong y_n and k1..k4 of the parent step to every
-// refinement-boundary ghost cell of the fine level: tensor-product quintic
+// Sec. II step 2: prolong y_n and the stage vectors the dense output reads
+// (k1..k4 for RK4; the pointers k1..k4 are the first nvec - 1 of them) of the
+// parent step to every refinement-boundary ghost cell of the fine level: tensor-product quintic
 // Lagrange interpolation from 6x6x6 parent cells.  One thread per
 // (ghost cell, field); results go to store[(v * F + f) * ncells + cell].
 __global__ void __launch_bounds__(kThreads) amr_prolong_kernel(

@@ -1,7 +1,8 @@
 // sc_host.cu -- host runtime and C ABI of the subcycling library.
 //
 // Each level is stored as one dense FP64 array per field over the bounding
-// box of its boxes (grown by 3 ghost cells).  Sibling boxes therefore share
+// box of its boxes (grown by the ghost width: 3 cells, 4 with 8th-order
+// differences).  Sibling boxes therefore share
 // memory: a ghost cell of one box that is interior to another needs no copy.
 // The remaining ghost cells are classified once at creation:
 //   * refinement boundary (levels >= 1): filled from the parent's dense

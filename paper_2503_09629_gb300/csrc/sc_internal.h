@@ -174,7 +174,8 @@ cudaError_t launch_z4c_constraints(const double* Y, const double* scratch, doubl
 
 cudaError_t launch_periodic_copy(double* vec, long fs, int F, const int2* pairs, int npairs, cudaStream_t s);
 // per-cell prolongation of AMR cells [first, ncells) of the list (store has ncells slots per vector-field);
-// nvec = 5 prolongs y_n, k1..k4, nvec = 1 only the first vector
+// nvec = 1 + the number of stage vectors the dense output reads (5 for RK4, 4 for RK3, 3 for RK2), passed
+// in order as k1..k4; nvec = 1 prolongs only the first vector
 cudaError_t launch_amr_prolong(const double* yn, const double* k1, const double* k2, const double* k3,
                                const double* k4, long pfs, int psy, int psz, const AmrCell* cells, int first,
                                int ncells, double* store, int F, const Weights& w, cudaStream_t s, int nvec = 5);
