@@ -289,8 +289,8 @@ struct Z4cPoint {
 // Right-hand side of the Z4c system at one cell (Sec. III.A; vacuum, so the
 // matter terms vanish).  u: fields; S + o: derivatives in scratch.  Sums,
 // differences and products that do not fuse with a neighbour are written as
-// FMAs with the run-time unit constants of K (fadd, fsub, fmul): a DFMA
-// issues faster than a DADD or DMUL on this GPU.
+// FMAs with the run-time unit constants of K (fadd, fsub, fmul; measured
+// faster than plain DADD/DMUL in this kernel, see FmaK).
 template <bool kDiag>
 __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, const double* __restrict__ S, long fs,
                                               long o, const Z4cParams& P, double eta, double* rhs, double* diag,
