@@ -397,6 +397,32 @@ def run_gpu(args, rank: int, world: int):
                    "steps": args.uniform_steps}
         cu.close()
 
+    # The same hierarchy in the plain per-box form: every kernel launched box
+    # by box directly on the stream, no CUDA graph (same arithmetic, so the
+    # same fields), timed the same way.
+    per_box = None
+    if rank == 0 and args.per_box_steps > 0:
+        hp = W.bl_7level()
+        hp.fd_order = args.fd_order
+        cp = sc.Context(hp, exec_mode=sc.SC_EXEC_PER_BOX)
+        cp.sc_autotune()
+        cp.sc_set_initial_data(hp.id_kind, hp.id_params)
+        cp.sc_advance(1)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_host = time.perf_counter()
+        p0.record(stream)
+        cp.sc_advance(args.per_box_steps)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        t_host = time.perf_counter() - t_host
+        pms = p0.elapsed_time(p1) / args.per_box_steps
+        per_box = {"ms_per_coarse_step": pms, "zone_updates_per_s": fin_per_step / (pms * 1e-3),
+                   "host_ms_per_coarse_step": t_host * 1e3 / args.per_box_steps,
+                   "launches_per_coarse_step": cp.sc_launches_per_step(), "graph_speedup": pms / ms_per_step,
+                   "steps": args.per_box_steps}
+        cp.close()
+
     # Served form vs plain per-box form on a seeded ensemble (60% wave, 40% Z4c requests).
     serving = None
     if rank == 0 and args.serving_requests > 0:
@@ -438,7 +464,8 @@ def run_gpu(args, rank: int, world: int):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": ne2e, "ms_per_step": e2e_s * 1e3 / ne2e, "device_ms_per_step": e2e_step_ms,
                         "set_state_ms": t_set * 1e3 / ne2e, "get_state_ms": t_get * 1e3 / ne2e},
-                "gpu_launches": launches, "clocks": clk, "serving": serving, "uniform_step_mode": uniform}
+                "gpu_launches": launches, "clocks": clk, "serving": serving, "uniform_step_mode": uniform,
+                "per_box_form": per_box}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -454,6 +481,8 @@ def main():
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--uniform-steps", type=int, default=2,
                     help="coarse steps of the same hierarchy in uniform-step mode (0: skip)")
+    ap.add_argument("--per-box-steps", type=int, default=2,
+                    help="coarse steps of the same hierarchy in the plain per-box form, no graph (0: skip)")
     ap.add_argument("--fd-order", type=int, default=4, choices=[4, 8],
                     help="finite-difference order of the Z4c right-hand side (8: the paper's production setting)")
     ap.add_argument("--serving-requests", type=int, default=64,
