@@ -38,3 +38,29 @@ def test_invalid_descriptors_are_rejected_with_a_message(sc, field, value, msg):
     with pytest.raises(sc.SubcycError) as e:
         sc.sc_footprint_estimate(h)
     assert e.value.code == -1 and msg in str(e.value)
+
+
+def test_no_cpu_fallback_when_the_library_cannot_be_built(tmp_path):
+    """The product path has no CPU fallback: with no library and no nvcc the
+    binding raises instead of computing anything (run in a subprocess with
+    the library path pointed at an empty directory and nvcc hidden)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys, shutil\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "import paper_2503_09629_gb300 as m\n"
+        "from paper_2503_09629_gb300 import buildlib\n"
+        f"m.LIB_PATH = {str(tmp_path / 'missing.so')!r}\n"
+        "shutil.which = lambda name, *a, **k: None\n"
+        "buildlib.nvcc = lambda: (_ for _ in ()).throw(RuntimeError('nvcc not found'))\n"
+        "try:\n"
+        "    m.lib()\n"
+        "except Exception as e:\n"
+        "    print('raised', type(e).__name__)\n"
+        "    sys.exit(0)\n"
+        "sys.exit(3)\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "raised" in r.stdout, (r.stdout, r.stderr)
