@@ -56,11 +56,12 @@ HBM_GBS = _measured_hbm_gbs()
 # z4c_derivs = row-segment D_x/D_y pass (133) + per-cell pass (1047);
 # profiles/z4c_kernels_bl3level64_ncu.md.
 FLOPS_PER_CELL = {"z4c_derivs": 1180.0, "z4c_stage": 1971.0}
-# DRAM bytes (read + write) per interior cell of each kernel from the same
-# ncu capture (262,144-cell launch), scaled to a launch by its cell count;
-# None once the kernel has changed since the counters were taken.
-DRAM_BYTES_PER_CELL = {"z4c_derivs": (31.963392e6 + 5.807616e6 + 161.104896e6 + 248.131584e6) / 262144,
-                       "z4c_stage": (510.467584e6 + 230.338304e6) / 262144}
+# DRAM bytes (read + write) per interior cell of each kernel from an ncu
+# capture of a 262,144-cell launch without cache flushes (--cache-control
+# none; profiles/z4c_kernels_bl3level64_ncu.md), scaled to a launch by its
+# cell count; None once the kernel has changed since the counters were taken.
+DRAM_BYTES_PER_CELL = {"z4c_derivs": None,
+                       "z4c_stage": (514.633984e6 + 278.21952e6) / 262144}
 # FP64 instructions (DFMA + DMUL + DADD, thread-level / cell) per interior
 # cell of the derivative pass (D_x/D_y row pass + per-cell pass), counted by
 # ncu on the 3-level 64^3 case (profiles/z4c_kernels_bl3level64_ncu.md,

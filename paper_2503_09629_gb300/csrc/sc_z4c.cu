@@ -571,9 +571,10 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
 // kStageNone),
 // fixed at compile time so the update adds no registers to the RHS.
 // Three 128-thread blocks per SM (at most 168 registers): the RHS then spills
-// about 700 bytes per thread to L1, but 3 warps per scheduler instead of 2
-// hide the FP64 dependency latency better; measured 5% faster than the
-// unconstrained 252-register build on the 524,288-cell benchmark level.
+// about 700 bytes per thread (written back to DRAM; the kernel is FP64-bound
+// and DRAM has room), but 3 warps per scheduler instead of 2 hide the FP64
+// dependency latency better; measured 5% faster than the unconstrained
+// 252-register build on the 524,288-cell benchmark level.
 template <int FORM>
 __global__ void __launch_bounds__(128, 3) z4c_stage_kernel(StageArgs a, const double* __restrict__ S, Z4cParams P,
                                                           const Tile* __restrict__ tiles, int ntiles, FmaK K) {
