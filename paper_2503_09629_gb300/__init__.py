@@ -253,6 +253,13 @@ class Context:
             lib().sc_destroy(self.ctx)
             self.ctx = None
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
     def __del__(self):
         try:
             self.close()
@@ -439,6 +446,13 @@ class Server:
         if getattr(self, "srv", None):
             lib().sc_server_destroy(self.srv)
             self.srv = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
     def __del__(self):
         try:
