@@ -14,13 +14,18 @@ import sys
 from paper_2503_09629_gb300 import buildlib
 
 
-def main() -> int:
+def build() -> str:
+    """Compile the microbenchmark for sm_103a into the package's build folder."""
     src = os.path.join(buildlib.SRC, "fp64_microbench.cu")
     os.makedirs(buildlib.OUT_DIR, exist_ok=True)
     exe = os.path.join(buildlib.OUT_DIR, "fp64_microbench")
     if buildlib._stale(exe, [src]):
         subprocess.check_call([buildlib.nvcc()] + buildlib.ARCH + ["-O3", "-std=c++17", "-o", exe, src])
-    return subprocess.call([exe])
+    return exe
+
+
+def main() -> int:
+    return subprocess.call([build()])
 
 
 if __name__ == "__main__":
