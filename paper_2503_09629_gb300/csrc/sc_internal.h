@@ -131,7 +131,7 @@ struct StageArgs {
 // fma(x, y, -0) = x * y exactly, so the results are bitwise those of the
 // plain operations.  Measured on this GPU: the Z4c derivative and stage
 // kernels run 6% and 4% faster this way than with plain DADD/DSUB/DMUL
-// (identical fields), although an isolated chain of fma(x, 1, a) issues no
+// (bitwise-identical arithmetic), although an isolated chain of fma(x, 1, a) issues no
 // faster than DADD (504 G/s; a general DFMA 597 G/s).
 struct FmaK {
   double one, mone, mzero;
