@@ -118,30 +118,47 @@ typedef struct {
                       classic RK4 of Sec. II; 3, Heun's third-order method (stage inputs y + h/3 k1,
                       y + 2h/3 k2; y_{n+1} = y + h/4 (k1 + 3 k3)); 2, the explicit midpoint rule
                       (y + h/2 k1; y_{n+1} = y + h k2).  RK2 and RK3 are the extension the paper
-                      (Sec. V) leaves to future work: their dense outputs are the second-order
-                      continuous extensions b1 = t - 3t^2/4, b3 = 3t^2/4 (RK3) and b1 = t - t^2,
-                      b2 = t^2 (RK2), and fine stage inputs at refinement boundaries are their
-                      Taylor expansions (RK3: y, y + h/3 y', y + 2h/3 y' + 2h^2/9 y''; RK2: y,
-                      y + h/2 y').  Other values: SC_EINVAL. */
+                      (Sec. V) leaves to future work.  Dense outputs: RK3 uses the cubic Hermite
+                      interpolant through y_n and y_{n+1} with slopes k1 and k4 = f(y_{n+1}),
+                      b1 = t - 5t^2/4 + t^3/2, b3 = 9t^2/4 - 3t^3/2, b4 = -t^2 + t^3 (third
+                      order; k4 costs one extra right-hand side per step on every level that
+                      has a finer level); RK2 uses b1 = t - t^2, b2 = t^2.  Fine stage inputs at
+                      refinement boundaries are the Taylor expansions of the method's stages
+                      (RK3: y, y + h/3 y', y + 2h/3 y' + 2h^2/9 y''; RK2: y, y + h/2 y').
+                      Other values: SC_EINVAL. */
 } sc_desc;
 
 enum { SC_EXEC_GRAPH = 0, SC_EXEC_PER_BOX = 1 };
 
-/* Build the hierarchy: validate nesting and alignment, allocate every level's
- * state, stage and k1..k_s arrays (s = rk_order), build the device work lists.
+/* Build the hierarchy of Sec. II: nested levels with h^(l) / h^(l+1) = 2,
+ * each a set of boxes.  Validates nesting and alignment, allocates every
+ * level's state, stage and k1..k_s arrays (s = rk_order; the stage vectors
+ * the dense output of Eq. denseoutput1 reads are kept on every level that has
+ * a finer level), builds the device work lists and the coarse-step CUDA
+ * graphs.  *out receives the context (owned by the caller until
+ * sc_destroy); on error *out = NULL and nothing stays allocated.
  * Errors: SC_EINVAL, SC_ENESTING, SC_ENOMEM, SC_ECUDA. */
 sc_status sc_create(const sc_desc* desc, sc_ctx** out);
 
-/* Release every device allocation (synchronises the context's stream). */
+/* Release every device allocation of a context made by sc_create
+ * (synchronises the context's stream).  NULL is ignored. */
 void sc_destroy(sc_ctx* ctx);
 
 /* Fill the state of every level (interior and ghosts) with analytic initial
- * data, on the device; resets the time to 0. */
+ * data, on the device (Sec. III.B Brill-Lindquist data; Sec. IV.A scalar
+ * waves); resets the time to 0.  params: host array of nparams doubles as
+ * listed for each kind above.  Synchronises.  Errors: SC_EINVAL (kind does
+ * not match the system, too few parameters), SC_ECUDA. */
 sc_status sc_set_initial_data(sc_ctx* ctx, int kind, const double* params, int nparams);
 
-/* Copy one field of one box from host memory: src holds the box interior,
- * (hi-lo+1) cells per dimension, x fastest.  Stream-ordered, synchronous with
- * respect to the host buffer (returns after the copy has been consumed). */
+/* Set initial data (Sec. III.B, Sec. IV.A: the paper's initial data are
+ * given per grid point) for one field of one box from host memory: src holds
+ * the box interior, (hi-lo+1) cells per dimension, x fastest, FP64; fields in
+ * the order listed at sc_desc (wave u, Pi; Z4c W, gt_xx..gt_zz, Khat,
+ * At_xx..At_zz, Gamt^x..^z, Theta, alpha, beta^x..^z).  Stream-ordered and
+ * synchronous with respect to the host buffer (returns after the copy has
+ * been consumed).  Errors: SC_EINVAL (level, box, field out of range, NULL
+ * src), SC_ENOMEM (staging), SC_ECUDA. */
 sc_status sc_set_field(sc_ctx* ctx, int level, int box, int field, const double* host_src);
 /* As sc_set_field, including the ghost cells (3 per side, 4 with 8th-order
  * differences): src has (hi-lo+7) or (hi-lo+9) cells per dimension.  Needed for
@@ -149,12 +166,17 @@ sc_status sc_set_field(sc_ctx* ctx, int level, int box, int field, const double*
  * checkpoint/resume. */
 sc_status sc_set_field_ghosted(sc_ctx* ctx, int level, int box, int field, const double* host_src);
 
-/* Copy one field of one box (interior) to host memory; synchronises. */
+/* Read one field of one box (interior, layout as sc_set_field) to host
+ * memory: the evolved fields of Sec. III.A / IV.A, e.g. for the
+ * convergence and waveform comparisons of Sec. IV.  Synchronises.  Errors as
+ * sc_set_field. */
 sc_status sc_get_field(sc_ctx* ctx, int level, int box, int field, double* host_dst);
 sc_status sc_get_field_ghosted(sc_ctx* ctx, int level, int box, int field, double* host_dst);
 
-/* Device-resident variants: the same copies between the state and a device
- * buffer of the same shape; stream-ordered, no host synchronisation. */
+/* Device-resident variants (Sec. II keeps the whole state on the GPU): the
+ * same copies between the state and a caller-owned device buffer of the
+ * same shape; stream-ordered on the context's stream, no host
+ * synchronisation.  Errors as sc_set_field. */
 sc_status sc_set_field_device(sc_ctx* ctx, int level, int box, int field, const double* dev_src);
 sc_status sc_get_field_device(sc_ctx* ctx, int level, int box, int field, double* dev_dst);
 
@@ -184,31 +206,47 @@ sc_status sc_get_state(sc_ctx* ctx, double* host_dst, int ghosted_level0);
  * step is one CUDA graph launch on the context's stream; asynchronous. */
 sc_status sc_advance(sc_ctx* ctx, int n_coarse_steps);
 
-/* Block until the context's stream is idle; returns SC_ECUDA on a device error. */
+/* Block until the context's stream is idle (the coarse steps of
+ * sc_advance, Sec. II, have completed).  Returns SC_ECUDA on a device error
+ * and SC_ENONFINITE when the per-step finiteness check of a context created
+ * with finite_check = 1 found a non-finite value. */
 sc_status sc_synchronize(sc_ctx* ctx);
 
-/* Scan the interior state of every level on the device: SC_OK if every
- * value is finite, SC_ENONFINITE otherwise.  Synchronises. */
+/* Scan the interior state of every level on the device (the evolved fields
+ * of Sec. III.A / IV.A): SC_OK if every value is finite, SC_ENONFINITE
+ * otherwise.  Synchronises.  The paper has no counterpart: it is the
+ * failure detection of a long evolution. */
 sc_status sc_check_finite(sc_ctx* ctx);
 
-/* Z4c constraints (H, M^x, M^y, M^z, G^x, G^y, G^z) of the current state at
- * the interior cells of one box, to a host buffer of 7 * ncell doubles
- * (constraint-major, x fastest); synchronises.  Z4c only. */
+/* Z4c constraints of the current state at the interior cells of one box
+ * (Sec. IV.B, Fig. 6 plots the L2 norms of H and M_x): H = R + 2/3 (Khat +
+ * 2 Theta)^2 - At_ij At^ij, M^i = d_j At^ij + Gamt^i_jk At^jk - 3 At^ij d_j W / W
+ * - 2/3 gt^ij d_j (Khat + 2 Theta), G^i = Gamt^i - gt^jk Gamt^i_jk, with the
+ * context's finite-difference order.  host_dst: 7 * ncell doubles
+ * (constraint-major H, M^x, M^y, M^z, G^x, G^y, G^z; x fastest).
+ * Synchronises.  Errors: SC_EINVAL (not Z4c, bad level/box, NULL), SC_ENOMEM,
+ * SC_ECUDA. */
 sc_status sc_get_constraints(sc_ctx* ctx, int level, int box, double* host_dst);
 
+/* Simulation time of level 0 (Sec. II: dt_l = cfl * h_l, the coarse step
+ * advances t by dt_0). */
 sc_status sc_get_time(sc_ctx* ctx, double* t);
 /* Cell updates done so far: finest-equivalent (every cell counted at the
- * finest time step, Sec. IV.C) and actual. */
+ * finest time step, "as if no subcycling had been used", Sec. IV.C) and
+ * actual (each level's cells times its own steps). */
 sc_status sc_zone_updates(sc_ctx* ctx, double* finest_equiv, double* actual);
-/* Number of kernel launches one coarse step performs (graph nodes). */
+/* Number of kernel launches one coarse step performs (graph nodes; Sec. II
+ * steps 1-7 on every level). */
 sc_status sc_launches_per_step(sc_ctx* ctx, long* n);
-/* Device bytes held by the context. */
+/* Device bytes held by the context (all levels' state, stage and k
+ * vectors of Sec. II, work lists, scratch). */
 sc_status sc_footprint(sc_ctx* ctx, size_t* bytes);
-/* Footprint a descriptor would need, without allocating. */
+/* Footprint a descriptor would need, without allocating (an upper bound of
+ * sc_footprint after sc_create; used for admission by the server). */
 sc_status sc_footprint_estimate(const sc_desc* desc, size_t* bytes);
 
-/* Time the kernels of one RK4 stage (stage 2) of one level outside the
- * graph, with CUDA events recorded on the context's stream, averaged over
+/* Measurement (no counterpart in the paper).  Time the kernels of one RK4
+ * stage (stage 2, Eq. rk2) of one level outside the graph, with CUDA events recorded on the context's stream, averaged over
  * nrep launches each: ms[0] = Z4c derivative pass (wave: fused stage kernel),
  * ms[1] = Z4c right-hand-side + update pass (wave: 0).  Overwrites only the
  * level's k2 and second stage buffer, which every coarse step recomputes
@@ -221,6 +259,8 @@ sc_status sc_time_stage_kernels(sc_ctx* ctx, int level, int nrep, double* ms);
  * that owns all device memory and forbids other allocations, a process whose
  * memory pool is fixed at start-up, or a latency-critical loop in which
  * cudaMalloc/cudaFree would implicitly synchronise the device.
+ * It computes 4th-order centred differences on 3 ghost layers whatever
+ * finite-difference order the caller's evolution uses.
  *   dev_state: device pointer, 22 Z4c fields (field order as in the context),
  *              each a box with 3 ghost layers per side, (n[0]+6)(n[1]+6)(n[2]+6)
  *              doubles, x fastest, fields contiguous one after another;
@@ -237,13 +277,17 @@ sc_status sc_time_stage_kernels(sc_ctx* ctx, int level, int nrep, double* ms);
  * array, so calls that overlap on the GPU race: serialise them (one stream,
  * or wait for the previous call).  The first call on a device looks up the
  * array's device address (with that device current) and caches it; make the
- * first call before any stream capture.  The call is asynchronous: dev_out is
- * ready when the stream reaches it.  No cudaMalloc, cudaFree or allocating
- * library routine is called. */
+ * first call before any stream capture.  The call makes no host-to-device
+ * copy (its tile list is generated on the device) and is asynchronous:
+ * dev_out is ready when the stream reaches it.  Errors: SC_EINVAL (NULL
+ * pointer, non-positive extent or spacing, box too large), SC_ECUDA.  No
+ * cudaMalloc, cudaFree or allocating library routine is called. */
 sc_status sc_z4c_constraints_noalloc(const double* dev_state, double* dev_out, const int* n, double h,
                                      void* cuda_stream);
 
-/* Moving boxes: replace the boxes of every refined level (level 0 must stay
+/* Moving boxes (Sec. II: the refined regions follow the punctures and the
+ * hierarchy is regridded; Sec. IV.B runs move the box stacks every coarse
+ * step): replace the boxes of every refined level (level 0 must stay
  * as it is; layout as in sc_desc: nboxes per level, boxes level by level).
  * Each interior cell of the new layout that was an interior cell of the same
  * level keeps its state; every other interior cell takes the quintic
@@ -255,7 +299,8 @@ sc_status sc_z4c_constraints_noalloc(const double* dev_state, double* dev_out, c
 sc_status sc_regrid(sc_ctx* ctx, const int* nboxes, const sc_box* boxes);
 
 /* Field values at npts points (xyz: 3 doubles per point, physical
- * coordinates) by tensor-product quintic Lagrange interpolation on the finest
+ * coordinates; used for puncture tracking, dx_p/dt = -beta(x_p), of the
+ * moving boxes) by tensor-product quintic Lagrange interpolation on the finest
  * level whose 6x6x6 cell stencil around the point is interior; SC_EINVAL if
  * no level holds it.  out: npts doubles (host).  Synchronises. */
 sc_status sc_interpolate(sc_ctx* ctx, int npts, const double* xyz, int field, double* out);

@@ -1912,6 +1912,7 @@ sc_status sc_get_constraints(sc_ctx* c, int level, int box, double* dst) {
                             c->stream));
   CU(cudaMemcpyAsync(dst, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
+  c->dfree(dt);  // the per-call tile list (the stream is idle)
   return SC_OK;
 }
 

@@ -6,10 +6,11 @@
 // device memory and forbids other allocations, a process whose memory pool is
 // fixed at start-up, or a latency-critical loop in which cudaMalloc/cudaFree
 // would implicitly synchronise the device and stall unrelated work.  For them
-// this file provides sc_z4c_constraints_noalloc: the same derivative and
-// constraint kernels as sc_get_constraints, with the derivative scratch and
-// the tile list held in file-scope static device arrays instead of memory the
-// context allocated.
+// this file provides sc_z4c_constraints_noalloc: the derivative and
+// constraint kernels of sc_get_constraints (4th-order centred differences on 3
+// ghost layers, whatever order a context evolves with), with the derivative
+// scratch and the tile list held in file-scope static device arrays instead of
+// memory a context allocated.
 //
 // Limits and sharing rules (also stated in include/subcyc.h):
 //   * the scratch holds 154 derivative values per ghosted cell for at most
@@ -19,9 +20,12 @@
 //   * every call shares the arrays; calls that overlap on the GPU (different
 //     streams, or different host threads on the same device) race and must
 //     be serialised by the caller;
-//   * nothing in the scratch needs to start at zero: each call writes every
-//     scratch value it later reads (the derivative pass covers every interior
-//     cell before the constraint pass reads it).
+//   * nothing in the arrays needs to start at zero: each call first writes
+//     its tile list on the device, and the derivative pass writes every
+//     scratch value the constraint pass then reads.
+//   * the call makes no host-to-device copy: the tile list is generated by a
+//     kernel from the box extents, so the call returns without waiting for
+//     the stream's earlier work.
 #include <stdio.h>
 
 #include <mutex>
@@ -37,6 +41,25 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratchSlots * kNoallocMaxCells];
 static __device__ __align__(256) sc::Tile g_noalloc_tiles[kNoallocMaxTiles];
+
+constexpr int kTileX = 32, kTileY = 4, kTileZ = 2;  // the tile shape sc_get_constraints uses
+
+// Interior tiles of an nx x ny x nz box with 3 ghost layers, x fastest, in
+// the order sc_get_constraints builds them; written straight into the static
+// tile array (device code may name it directly).
+__global__ void noalloc_tiles_kernel(int nx, int ny, int nz, int tx, int ty, int nt) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    const int ix = t % tx, iy = (t / tx) % ty, iz = t / (tx * ty);
+    sc::Tile T;
+    T.x0 = ix * kTileX + sc::kGhost;
+    T.y0 = iy * kTileY + sc::kGhost;
+    T.z0 = iz * kTileZ + sc::kGhost;
+    T.nx = nx - ix * kTileX < kTileX ? nx - ix * kTileX : kTileX;
+    T.ny = ny - iy * kTileY < kTileY ? ny - iy * kTileY : kTileY;
+    T.nz = nz - iz * kTileZ < kTileZ ? nz - iz * kTileZ : kTileZ;
+    g_noalloc_tiles[t] = T;
+  }
+}
 
 struct DeviceSymbols {
   bool ready = false;
@@ -85,40 +108,32 @@ extern "C" sc_status sc_z4c_constraints_noalloc(const double* dev_state, double*
                                                 void* cuda_stream) {
   if (!dev_state || !dev_out || !n) return noalloc_fail(SC_EINVAL, "null argument");
   if (n[0] < 1 || n[1] < 1 || n[2] < 1 || !(h > 0)) return noalloc_fail(SC_EINVAL, "box extents and spacing must be positive");
+  // each extent alone is bounded before the volume is formed, so the product cannot overflow
+  for (int d = 0; d < 3; ++d)
+    if (n[d] > kNoallocMaxCells)
+      return noalloc_fail(SC_EINVAL, "box too large: at most 32768 cells including 3 ghost layers per side");
   const long ext[3] = {n[0] + 2L * sc::kGhost, n[1] + 2L * sc::kGhost, n[2] + 2L * sc::kGhost};
   const long vol = ext[0] * ext[1] * ext[2];
   if (vol > kNoallocMaxCells)
     return noalloc_fail(SC_EINVAL, "box too large: at most 32768 cells including 3 ghost layers per side");
-  // interior tiles of the box, in the same shape the context uses (32 x 4 x 2)
-  static thread_local sc::Tile host_tiles[kNoallocMaxTiles];
-  int nt = 0;
-  for (int z = 0; z < n[2]; z += 2)
-    for (int y = 0; y < n[1]; y += 4)
-      for (int x = 0; x < n[0]; x += 32) {
-        if (nt == kNoallocMaxTiles) return noalloc_fail(SC_EINVAL, "box too thin: more than 8192 tiles");
-        sc::Tile& t = host_tiles[nt++];
-        t.x0 = x + sc::kGhost;
-        t.y0 = y + sc::kGhost;
-        t.z0 = z + sc::kGhost;
-        t.nx = n[0] - x < 32 ? n[0] - x : 32;
-        t.ny = n[1] - y < 4 ? n[1] - y : 4;
-        t.nz = n[2] - z < 2 ? n[2] - z : 2;
-      }
+  // interior tiles of the box, in the shape the context uses (32 x 4 x 2)
+  const int tx = (n[0] + kTileX - 1) / kTileX, ty = (n[1] + kTileY - 1) / kTileY, tz = (n[2] + kTileZ - 1) / kTileZ;
+  const long nt = (long)tx * ty * tz;
+  if (nt > kNoallocMaxTiles) return noalloc_fail(SC_EINVAL, "box too thin: more than 8192 tiles");
   DeviceSymbols* sym = nullptr;
   sc_status st = device_symbols(&sym);
   if (st != SC_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  // pageable source: the call returns once the tiles are staged, so the
-  // thread-local host buffer can be reused by the next call
-  cudaError_t e = cudaMemcpyAsync(sym->tiles, host_tiles, sizeof(sc::Tile) * nt, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return noalloc_fail(SC_ECUDA, "tile upload", e);
+  noalloc_tiles_kernel<<<(int)((nt + 127) / 128), 128, 0, s>>>(n[0], n[1], n[2], tx, ty, (int)nt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return noalloc_fail(SC_ECUDA, "tile kernel", e);
   const long fs = vol;  // state: field stride = ghosted box volume
   const int sy = (int)ext[0], sz = (int)(ext[0] * ext[1]);
-  e = sc::launch_z4c_derivs(dev_state, sym->scratch, fs, sy, sz, h, sym->tiles, nt, s);
+  e = sc::launch_z4c_derivs(dev_state, sym->scratch, fs, sy, sz, h, sym->tiles, (int)nt, s);
   if (e != cudaSuccess) return noalloc_fail(SC_ECUDA, "derivative kernel", e);
   const int lo[3] = {sc::kGhost, sc::kGhost, sc::kGhost};
   const sc::Z4cParams p{0.0, 0.0, 0.0, 0.0};  // the constraints do not depend on the damping/gauge parameters
-  e = sc::launch_z4c_constraints(dev_state, sym->scratch, dev_out, fs, sy, sz, p, sym->tiles, nt,
+  e = sc::launch_z4c_constraints(dev_state, sym->scratch, dev_out, fs, sy, sz, p, sym->tiles, (int)nt,
                                  (long)n[0] * n[1] * n[2], lo, n, s);
   if (e != cudaSuccess) return noalloc_fail(SC_ECUDA, "constraint kernel", e);
   return SC_OK;

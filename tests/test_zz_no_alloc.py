@@ -3,11 +3,13 @@
 sc_z4c_constraints_noalloc serves callers that cannot allocate device memory
 (an embedding application that owns all of it, a fixed memory pool, a loop
 that must avoid the implicit synchronisation of cudaMalloc/cudaFree).  It
-runs the same kernels as sc_get_constraints with a static scratch array, so
-on the same box data the two must agree; this file checks two calls in a
-row, through the C ABI, within the constraint tolerance of the other tests.
-It is collected last so that a run stopping at the first failure has already
-run every other test, and it passes alone in a fresh process as well.
+runs the same derivative and constraint kernels as sc_get_constraints of a
+4th-order context, with the same tile shape, on the same ghosted box data,
+so the two must agree bit for bit: an indexing or stride slip in the dense
+box layout would otherwise hide inside a tolerance.  This file checks two
+calls in a row through the C ABI, on the legacy stream and on a non-default
+stream.  It is collected last so that a run stopping at the first failure has
+already run every other test, and it passes alone in a fresh process as well.
 """
 import numpy as np
 import pytest
@@ -16,8 +18,6 @@ from helpers import init_arrays, load
 from paper_2503_09629_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
-
-TOL = 1e-9  # the constraint tolerance of test_gpu_z4c.py
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +36,7 @@ def test_noalloc_constraints_match_allocating_path(sc):
     ctx = sc.Context(h)
     load(ctx, h, init_arrays(h))
     ctx.sc_advance(2)
-    stream = torch.cuda.current_stream().cuda_stream
+    side = torch.cuda.Stream()
     for level in (0, 1, 2):
         ref = ctx.sc_get_constraints(level, 0)
         state = np.stack([ctx.sc_get_field(level, 0, f, ghosted=True) for f in range(22)])
@@ -44,15 +44,17 @@ def test_noalloc_constraints_match_allocating_path(sc):
         n = ctx.shape(level, 0)[::-1]  # (nx, ny, nz)
         dev_out = torch.empty((7,) + ctx.shape(level, 0), dtype=torch.float64, device="cuda")
         hl = h.h0 / 2 ** level
-        for _call in range(2):
-            dev_out.fill_(float("nan"))
-            sc.sc_z4c_constraints_noalloc(dev_state.data_ptr(), dev_out.data_ptr(), n, hl, stream)
-            torch.cuda.synchronize()
-            got = dev_out.cpu().numpy()
-            assert np.isfinite(got).all()
-            for q in range(7):
-                scale = max(np.abs(ref[q]).max(), 1e-12)
-                assert np.abs(got[q] - ref[q]).max() / scale <= TOL, (level, q)
+        torch.cuda.synchronize()
+        for stream in (None, side):
+            for _call in range(2):
+                with torch.cuda.stream(stream if stream is not None else torch.cuda.default_stream()):
+                    dev_out.fill_(float("nan"))
+                    sc.sc_z4c_constraints_noalloc(dev_state.data_ptr(), dev_out.data_ptr(), n, hl,
+                                                  stream.cuda_stream if stream is not None else None)
+                torch.cuda.synchronize()
+                got = dev_out.cpu().numpy()
+                assert np.isfinite(got).all()
+                assert np.array_equal(got, ref), (level, stream, np.abs(got - ref).max())
     ctx.close()
 
 
