@@ -9,8 +9,10 @@ dense output (Eqs. denseoutput1/2) and the Taylor stage formulas (Eqs. Y1-Y4)
 for the refinement-boundary ghost zones, the seven-step subcycling recursion,
 tensor-product quintic prolongation and restriction; Sec. III for the Z4c
 right-hand side, the puncture gauge and Kreiss-Oliger dissipation; Sec. IV.A
-for the scalar wave.  Parity unpinned: the radiative outer boundary (its
-formula is not in the paper), checked only through GPU-vs-oracle agreement.
+for the scalar wave.  Every part is pinned by the CPU tests (closed forms,
+polynomial exactness, exact solutions, convergence orders); the radiative
+outer boundary is pinned against its stated reading (outgoing spherical
+waves satisfy it exactly), since the paper does not print its formula.
 """
 from __future__ import annotations
 

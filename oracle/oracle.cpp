@@ -13,11 +13,12 @@
 // and prolongation (refinement boundary), or physical (outer boundary).
 //
 // Parity status of each part (what pins it) is listed in the test suite: the
-// gauge terms are pinned only by special cases (Minkowski, a uniform shift);
-// the radiative outer boundary by exact outgoing spherical waves; KO
-// dissipation by its closed form on plane waves; the rest by closed forms,
-// polynomial exactness, exact solutions (gauge wave, flat space in moving
-// coordinates) and convergence.
+// puncture gauge (Eqs. punclapse/puncshift) by 4th-order convergence to the
+// equations evaluated with exact derivatives on data that varies in every
+// field (a reversed sign in any term fails); the radiative outer boundary by
+// exact outgoing spherical waves; KO dissipation by its closed form on plane
+// waves; the rest by closed forms, polynomial exactness, exact solutions
+// (gauge wave, flat space in moving coordinates) and convergence.
 
 #include "oracle.h"
 

@@ -577,6 +577,138 @@ def test_constraints_vanish_for_shifted_flat_space(shifted_flat_runs):
     assert np.all(order[-1] > 3.6), (c, order)
 
 
+def _gauge_test_fields():
+    """Smooth periodic data on [0,1)^3 that solves nothing: every Z4c variable
+    varies in space (positive W, lapse and metric), with the lapse, Khat,
+    Gamt^i and a shift of about 0.3 all non-zero and non-uniform.  Returns
+    the 22 fields and, from the paper's puncture gauge (Sec. III.A, Eqs.
+    punclapse and puncshift, with the exact derivatives of these fields),
+    d_t alpha = beta^j d_j alpha - 2 alpha Khat and
+    d_t beta^i = beta^j d_j beta^i + 3/4 Gamt^i - eta beta^i, term by term."""
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z", real=True)
+    tp = 2 * sp.pi
+    S = sp.sin
+    C = sp.cos
+    Wf = 1 + S(tp * (x + 2 * y)) / 10
+    gt = [1 + S(tp * (y + z)) / 10, S(tp * (x - z)) * 3 / 100, C(tp * y) / 50,
+          1 + C(tp * (x + z)) * 2 / 25, S(tp * (x + y + z)) / 25, 1 + S(tp * (x + y)) / 20]
+    Kh = sp.Rational(1, 10) + 3 * C(tp * (x - y + z)) / 10
+    At = [S(tp * (x + y)) / 20, C(tp * z) / 30, S(tp * (y - z)) / 40, C(tp * (x + z)) / 25, S(tp * x) / 35,
+          C(tp * (y + 2 * z)) / 45]
+    Gam = [S(tp * (x + z)) / 5, 3 * C(tp * (y - x)) / 20, S(tp * (2 * z + y)) / 10]
+    Th = S(tp * x) / 20
+    al = 1 + S(tp * (x + y - z)) / 5
+    be = [3 * S(tp * (y + z)) / 10, C(tp * (x - z)) / 5, S(tp * (x + y + z)) / 4]
+    X3 = (x, y, z)
+    fields = [Wf] + gt + [Kh] + At + Gam + [Th, al] + be
+    adv_al = sum(be[j] * sp.diff(al, X3[j]) for j in range(3))
+    terms = {
+        "adv_alpha": adv_al,
+        "lapse_K": -2 * al * Kh,
+        "adv_beta": [sum(be[j] * sp.diff(be[i], X3[j]) for j in range(3)) for i in range(3)],
+        "shift_Gam": [sp.Rational(3, 4) * Gam[i] for i in range(3)],
+        "shift_damp": [-be[i] for i in range(3)],  # times eta
+    }
+    f = sp.lambdify((x, y, z), fields, "numpy")
+    t = {k: sp.lambdify((x, y, z), v, "numpy") for k, v in terms.items()}
+
+    def arr(v, X):
+        return np.broadcast_to(np.asarray(v, dtype=float), X.shape)
+
+    def state(X, Y, Z):
+        return np.stack([arr(v, X) for v in f(X, Y, Z)])
+
+    def gauge_terms(X, Y, Z):
+        out = {}
+        for k, fn in t.items():
+            v = fn(X, Y, Z)
+            out[k] = np.stack([arr(q, X) for q in v]) if isinstance(v, list) else arr(v, X)
+        return out
+
+    return state, gauge_terms
+
+
+@pytest.fixture(scope="module")
+def gauge_runs(orc):
+    """Oracle right-hand sides of alpha and beta^i (no dissipation) on the
+    gauge test data at three resolutions, with the exact terms of Eqs.
+    punclapse and puncshift at the interior cells."""
+    state, gauge_terms = _gauge_test_fields()
+    runs = []
+    for n in (16, 32, 64):
+        h = W.Hierarchy(system=W.Z4C, boxes=[[W.cube(0, n)]], ncells0=(n, n, n), origin=(0.0, 0.0, 0.0),
+                        h0=1.0 / n, bc=2, ko_sigma=0.0, eta=2.0)
+        o = make(orc, h)
+        X, Y, Z = h.cell_centres(0, 0, ghosted=True)
+        rhs = o.rhs_box(0, 0, state(X, Y, Z))
+        s = (slice(3, -3),) * 3
+        T = gauge_terms(X[s], Y[s], Z[s])
+        runs.append((rhs[18][s], rhs[19:22][(slice(None),) + s], T, h.eta))
+    return runs
+
+
+def _gauge_exact(T, eta, flip=None):
+    """d_t alpha and d_t beta^i from the paper's gauge terms; flip names one
+    term whose sign is reversed (a plausible slip the pin must catch)."""
+    sg = {k: (-1.0 if k == flip else 1.0) for k in ("adv_alpha", "lapse_K", "adv_beta", "shift_Gam", "shift_damp")}
+    dal = sg["adv_alpha"] * T["adv_alpha"] + sg["lapse_K"] * T["lapse_K"]
+    dbe = sg["adv_beta"] * T["adv_beta"] + sg["shift_Gam"] * T["shift_Gam"] + sg["shift_damp"] * eta * T["shift_damp"]
+    return dal, dbe
+
+
+def test_puncture_gauge_rhs_converges_to_paper_equations(gauge_runs):
+    """Sec. III.A, Eqs. punclapse/puncshift: on data that varies in every
+    field, the oracle's d_t alpha and d_t beta^i converge at 4th order (the
+    centred advection stencils) to beta^j d_j alpha - 2 alpha Khat and
+    beta^j d_j beta^i + 3/4 Gamt^i - eta beta^i evaluated with exact
+    derivatives."""
+    ea, eb = [], []
+    for ral, rbe, T, eta in gauge_runs:
+        dal, dbe = _gauge_exact(T, eta)
+        ea.append(np.abs(ral - dal).max())
+        eb.append(np.abs(rbe - dbe).max())
+    ea, eb = np.array(ea), np.array(eb)
+    oa, ob = np.log2(ea[:-1] / ea[1:]), np.log2(eb[:-1] / eb[1:])
+    assert oa[-1] > 3.7 and ob[-1] > 3.7, (ea, eb, oa, ob)
+    assert ea[-1] < 1e-5 and eb[-1] < 1e-5, (ea, eb)
+
+
+@pytest.mark.parametrize("flip", ["adv_alpha", "lapse_K", "adv_beta", "shift_Gam", "shift_damp"])
+def test_puncture_gauge_pin_catches_a_flipped_term(gauge_runs, flip):
+    """The pin discriminates: with the sign of any one term of Eqs.
+    punclapse/puncshift reversed (advection of alpha, -2 alpha Khat,
+    advection of beta, 3/4 Gamt^i, -eta beta^i) the finest-resolution oracle
+    result misses the altered equations by O(0.1), four orders above the
+    discretisation error the correct equations leave."""
+    ral, rbe, T, eta = gauge_runs[-1]
+    dal, dbe = _gauge_exact(T, eta, flip)
+    miss = max(np.abs(ral - dal).max(), np.abs(rbe - dbe).max())
+    assert miss > 1e-2, (flip, miss)
+
+
+def test_puncture_gauge_with_eta_profile(orc):
+    """Sec. III.A with the eta(r) profile: the shift equation's damping term
+    uses eta at each cell's coordinate radius, (eta_c - eta_o)
+    exp(-(r/eta_s)^4) + eta_o; the rest of d_t beta^i is unchanged."""
+    state, gauge_terms = _gauge_test_fields()
+    ec, es, eo = 2.0, 0.6, 0.25
+    errs = []
+    for n in (32, 64):
+        h = W.Hierarchy(system=W.Z4C, boxes=[[W.cube(0, n)]], ncells0=(n, n, n), origin=(0.0, 0.0, 0.0),
+                        h0=1.0 / n, bc=2, ko_sigma=0.0, eta_profile=(ec, es, eo))
+        o = make(orc, h)
+        X, Y, Z = h.cell_centres(0, 0, ghosted=True)
+        rhs = o.rhs_box(0, 0, state(X, Y, Z))
+        s = (slice(3, -3),) * 3
+        T = gauge_terms(X[s], Y[s], Z[s])
+        r = np.sqrt(X[s] ** 2 + Y[s] ** 2 + Z[s] ** 2)
+        eta = (ec - eo) * np.exp(-(r / es) ** 4) + eo
+        dbe = T["adv_beta"] + T["shift_Gam"] + eta * T["shift_damp"]
+        errs.append(np.abs(rhs[19:22][(slice(None),) + s] - dbe).max())
+    assert np.log2(errs[0] / errs[1]) > 3.7 and errs[1] < 1e-5, errs
+
+
 def test_radiative_shell_exact_for_outgoing_spherical_waves(orc):
     """The radiative outer boundary (Z4c, evolved ghost shell of level 0):
     d_t u = -(x^i/r) d_i u - (u - u_inf)/r holds exactly for every outgoing
