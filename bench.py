@@ -356,9 +356,15 @@ def run_gpu(args, rank: int, world: int):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ne2e)]
     t0 = time.perf_counter()
     t_set = t_get = 0.0
+    xfer = {"set": [0.0, 0.0], "get": [0.0, 0.0]}  # [DMA ms, pack/unpack kernel ms], CUDA events in the library
+    direct = True
     for q in range(ne2e):
         ta = time.perf_counter()
         ctx.sc_set_state(host_in.data_ptr(), ghosted_level0=True)
+        st = ctx.sc_transfer_stats()
+        xfer["set"][0] += st["copy_ms"]
+        xfer["set"][1] += st["kernel_ms"]
+        direct = direct and st["direct"]
         tb = time.perf_counter()
         ev[q][0].record(stream)
         ctx.sc_advance(1)
@@ -366,6 +372,10 @@ def run_gpu(args, rank: int, world: int):
         ev[q][1].synchronize()
         tc = time.perf_counter()
         ctx.sc_get_state(host_out.data_ptr())
+        st = ctx.sc_transfer_stats()
+        xfer["get"][0] += st["copy_ms"]
+        xfer["get"][1] += st["kernel_ms"]
+        direct = direct and st["direct"]
         t_set += tb - ta
         t_get += time.perf_counter() - tc
     torch.cuda.synchronize()
@@ -373,6 +383,23 @@ def run_gpu(args, rank: int, world: int):
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
     e2e_value = whole_job_rate(world, fin_per_step, ne2e, e2e_s * 1e3)
     e2e_step_ms = sum(a.elapsed_time(b) for a, b in ev) / ne2e  # device time of the step inside the e2e loop
+    split = {}
+    for k, nbytes in (("set", h2d), ("get", d2h)):
+        dma, ker = xfer[k][0] / ne2e, xfer[k][1] / ne2e
+        split[k] = {"dma_ms": dma, "kernel_ms": ker, "gb_per_s": nbytes / ((dma + ker) * 1e-3) / 1e9}
+    # The other transfer form once, for comparison: one DMA to a device
+    # staging buffer plus unpack/pack kernels (the form pageable memory takes).
+    ctx.sc_set_transfer_mode(sc.SC_XFER_STAGED)
+    staged = {}
+    for k, fn, ptr, g0, nbytes in (("set", ctx.sc_set_state, host_in, True, h2d),
+                                   ("get", ctx.sc_get_state, host_out, False, d2h)):
+        ta = time.perf_counter()
+        fn(ptr.data_ptr(), ghosted_level0=g0)
+        wall = time.perf_counter() - ta
+        st = ctx.sc_transfer_stats()
+        staged[k] = {"dma_ms": st["copy_ms"], "kernel_ms": st["kernel_ms"], "host_ms": wall * 1e3,
+                     "gb_per_s": nbytes / ((st["copy_ms"] + st["kernel_ms"]) * 1e-3) / 1e9}
+    ctx.sc_set_transfer_mode(sc.SC_XFER_AUTO)
 
     # The method's saving: the same hierarchy with every level at the finest
     # time step (uniform-step mode), timed the same way.
@@ -464,7 +491,9 @@ def run_gpu(args, rank: int, world: int):
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": ne2e, "ms_per_step": e2e_s * 1e3 / ne2e, "device_ms_per_step": e2e_step_ms,
-                        "set_state_ms": t_set * 1e3 / ne2e, "get_state_ms": t_get * 1e3 / ne2e},
+                        "set_state_ms": t_set * 1e3 / ne2e, "get_state_ms": t_get * 1e3 / ne2e,
+                        "transfer_form": "direct (kernels access page-locked host memory)" if direct else "staged",
+                        "transfer_split": split, "staged_form_once": staged},
                 "gpu_launches": launches, "clocks": clk, "serving": serving, "uniform_step_mode": uniform,
                 "per_box_form": per_box}
         print(json.dumps(line), flush=True)

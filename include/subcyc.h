@@ -126,6 +126,9 @@ typedef struct {
                       refinement boundaries are the Taylor expansions of the method's stages
                       (RK3: y, y + h/3 y', y + 2h/3 y' + 2h^2/9 y''; RK2: y, y + h/2 y').
                       Other values: SC_EINVAL. */
+  int finite_check; /* 1: every coarse step ends with a device scan of every level's state for
+                       non-finite values (failure detection of a long evolution; no host
+                       synchronisation); the next sc_synchronize reports SC_ENONFINITE */
 } sc_desc;
 
 enum { SC_EXEC_GRAPH = 0, SC_EXEC_PER_BOX = 1 };
@@ -182,22 +185,32 @@ sc_status sc_get_field_device(sc_ctx* ctx, int level, int box, int field, double
 
 /* Whole-state transfer (no counterpart in the paper, which keeps the state on
  * the device; this is the upload/download of a host application that owns
- * its data).  The packed layout concatenates, for every level l (coarse to
- * fine), every box b (creation order) and every field f, the box region x
- * fastest: with its ghost cells on level 0 when ghosted_level0 = 1 (the
- * evolved shell of a radiative boundary lives there), its interior
- * elsewhere.  *bytes = size of that buffer.
- * sc_set_state copies it in with one host-to-device copy into a device
- * staging buffer of the same size (allocated on first use, kept with the
- * context) and one unpack kernel per box; sc_get_state packs with one kernel
- * per box and one device-to-host copy.  Page-locked host memory makes each
- * copy one DMA transfer; pageable memory works, slower.  Both return after
- * the host buffer has been consumed or filled (they synchronise the
- * context's stream).  Errors: SC_EINVAL (null pointer, ghosted_level0 not
- * 0/1), SC_ENOMEM (staging), SC_ECUDA. */
+ * its data, and the checkpoint/restart path).  The packed layout
+ * concatenates, for every level l (coarse to fine), every box b (creation
+ * order) and every field f, the box region x fastest: with its ghost cells on
+ * level 0 when ghosted_level0 = 1 (the evolved shell of a radiative boundary
+ * lives there), its interior elsewhere.  *bytes = size of that buffer.
+ * Two forms, chosen by sc_set_transfer_mode:
+ *   direct (the default for page-locked or registered host memory): one
+ *     pack/unpack kernel per box reads or writes the host buffer through its
+ *     device mapping, so the data crosses the CPU-GPU link once and no
+ *     device staging memory is used;
+ *   staged (pageable memory, or SC_XFER_STAGED): one DMA copy between the
+ *     host buffer and a device staging buffer of the same size (allocated on
+ *     first use, kept with the context) plus one kernel per box.
+ * Both return after the host buffer has been consumed or filled (they
+ * synchronise the context's stream); sc_transfer_stats then gives the
+ * split of the last transfer, timed with CUDA events on the stream: DMA
+ * milliseconds (0 in the direct form), pack/unpack kernel milliseconds, the
+ * bytes moved and whether the direct form ran.  Errors: SC_EINVAL (null
+ * pointer, ghosted_level0 not 0/1, SC_XFER_DIRECT with pageable memory),
+ * SC_ENOMEM (staging), SC_ECUDA. */
+enum { SC_XFER_AUTO = 0, SC_XFER_STAGED = 1, SC_XFER_DIRECT = 2 };
 sc_status sc_state_bytes(sc_ctx* ctx, int ghosted_level0, size_t* bytes);
 sc_status sc_set_state(sc_ctx* ctx, const double* host_src, int ghosted_level0);
 sc_status sc_get_state(sc_ctx* ctx, double* host_dst, int ghosted_level0);
+sc_status sc_set_transfer_mode(sc_ctx* ctx, int mode);
+sc_status sc_transfer_stats(sc_ctx* ctx, double* copy_ms, double* kernel_ms, size_t* bytes, int* direct);
 
 /* Advance n coarse steps (Sec. II, steps 1-7 per coarse step): level 0
  * takes one RK step storing its stage vectors, every finer level two substeps per
@@ -211,6 +224,10 @@ sc_status sc_advance(sc_ctx* ctx, int n_coarse_steps);
  * and SC_ENONFINITE when the per-step finiteness check of a context created
  * with finite_check = 1 found a non-finite value. */
 sc_status sc_synchronize(sc_ctx* ctx);
+/* As sc_synchronize with a bounded host-side wait: SC_ETIMEOUT (work still
+ * queued, the context stays usable) if the stream is not idle after
+ * timeout_s seconds. */
+sc_status sc_synchronize_timeout(sc_ctx* ctx, double timeout_s);
 
 /* Scan the interior state of every level on the device (the evolved fields
  * of Sec. III.A / IV.A): SC_OK if every value is finite, SC_ENONFINITE
@@ -315,6 +332,8 @@ sc_status sc_interpolate(sc_ctx* ctx, int npts, const double* xyz, int field, do
 sc_status sc_autotune(sc_ctx* ctx, int* tile_out, double* ms_out);
 
 /* ---- serving: continuous batching of independent evolutions ---------------
+ * The paper has no counterpart: this is the serving form of the method, many
+ * small independent evolutions (each one hierarchy of Sec. II) sharing one GPU.
  * A server owns max_active slots (one CUDA stream each) and a device-memory
  * budget.  sc_server_submit queues a request (hierarchy, analytic initial
  * data, number of coarse steps); it fails with SC_EBUSY if the request's
@@ -332,7 +351,19 @@ sc_status sc_server_create(size_t hbm_budget_bytes, int max_active, int depth, s
 sc_status sc_server_submit(sc_server* srv, const sc_desc* desc, int id_kind, const double* id_params, int nparams,
                            int n_coarse_steps, unsigned long long* ticket);
 sc_status sc_server_tick(sc_server* srv, int* n_active, int* n_queued, int* n_launched);
+/* done = 1 once the request finished; returns the request's status: SC_OK,
+ * or SC_ENOMEM when its state could not be allocated while no other request
+ * was running (it then holds nothing; release it). */
 sc_status sc_server_poll(sc_server* srv, unsigned long long ticket, int* done, double* latency_s);
+/* Tick and poll until the request is done or timeout_s seconds have passed
+ * (SC_ETIMEOUT; the request keeps running).  Host-side wait, bounded. */
+sc_status sc_server_wait(sc_server* srv, unsigned long long ticket, double timeout_s, double* latency_s);
+/* Host-side fault injection for tests of the admission path: the k-th device
+ * allocation the server makes from now on fails as if the pool were
+ * exhausted (k = 0 disables).  A request whose allocation fails is retried
+ * after running requests free memory, or fails with SC_ENOMEM when none is
+ * running. */
+sc_status sc_server_inject_alloc_failure(sc_server* srv, long k);
 sc_status sc_server_read(sc_server* srv, unsigned long long ticket, int level, int box, int field, double* host_dst);
 sc_status sc_server_release(sc_server* srv, unsigned long long ticket);
 sc_status sc_server_stats(sc_server* srv, double* zu_finest_done, double* zu_actual_done, long* launches,

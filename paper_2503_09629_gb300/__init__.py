@@ -28,6 +28,7 @@ SC_OK, SC_EINVAL, SC_ENOMEM, SC_ECUDA, SC_ENESTING, SC_ENONFINITE, SC_ETIMEOUT, 
 SC_WAVE, SC_Z4C = 0, 1
 SC_BC_PERIODIC, SC_BC_RADIATIVE = 0, 1
 SC_EXEC_GRAPH, SC_EXEC_PER_BOX = 0, 1
+SC_XFER_AUTO, SC_XFER_STAGED, SC_XFER_DIRECT = 0, 1, 2
 GHOST = 3
 NCONSTRAINTS = 7
 
@@ -76,6 +77,7 @@ class sc_desc(ctypes.Structure):
         ("eta_o", ctypes.c_double),
         ("fd_order", ctypes.c_int),
         ("rk_order", ctypes.c_int),
+        ("finite_check", ctypes.c_int),
     ]
 
 
@@ -108,6 +110,7 @@ def lib():
         getattr(L, name).argtypes = [P, I, I, I, P]
     L.sc_advance.argtypes = [P, I]
     L.sc_synchronize.argtypes = [P]
+    L.sc_synchronize_timeout.argtypes = [P, D]
     L.sc_get_constraints.argtypes = [P, I, I, DP]
     L.sc_get_time.argtypes = [P, DP]
     L.sc_zone_updates.argtypes = [P, DP, DP]
@@ -124,6 +127,8 @@ def lib():
     L.sc_state_bytes.argtypes = [P, I, ctypes.POINTER(ctypes.c_size_t)]
     L.sc_set_state.argtypes = [P, P, I]
     L.sc_get_state.argtypes = [P, P, I]
+    L.sc_set_transfer_mode.argtypes = [P, I]
+    L.sc_transfer_stats.argtypes = [P, DP, DP, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int)]
     L.sc_z4c_constraints_noalloc.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), D, P]
     IP = ctypes.POINTER(ctypes.c_int)
     U64 = ctypes.c_ulonglong
@@ -131,6 +136,8 @@ def lib():
     L.sc_server_submit.argtypes = [P, ctypes.POINTER(sc_desc), I, DP, I, I, ctypes.POINTER(U64)]
     L.sc_server_tick.argtypes = [P, IP, IP, IP]
     L.sc_server_poll.argtypes = [P, U64, IP, DP]
+    L.sc_server_wait.argtypes = [P, U64, D, DP]
+    L.sc_server_inject_alloc_failure.argtypes = [P, ctypes.c_long]
     L.sc_server_read.argtypes = [P, U64, I, I, I, DP]
     L.sc_server_release.argtypes = [P, U64]
     L.sc_server_stats.argtypes = [P, DP, DP, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_size_t)]
@@ -167,7 +174,8 @@ def _torch_allocator():
     return a
 
 
-def make_desc(h, stream: Optional[int] = None, allocator=None, exec_mode: int = SC_EXEC_GRAPH):
+def make_desc(h, stream: Optional[int] = None, allocator=None, exec_mode: int = SC_EXEC_GRAPH,
+              finite_check: bool = False):
     """sc_desc for a workloads.Hierarchy; returns (desc, keepalive)."""
     nb = (ctypes.c_int * h.nlevels)(*[len(b) for b in h.boxes])
     flat = [bx for lvl in h.boxes for bx in lvl]
@@ -191,6 +199,7 @@ def make_desc(h, stream: Optional[int] = None, allocator=None, exec_mode: int = 
     d.exec_mode = exec_mode
     d.fd_order = int(getattr(h, "fd_order", 4))
     d.rk_order = int(getattr(h, "rk_order", 4))
+    d.finite_check = 1 if finite_check else 0
     prof = getattr(h, "eta_profile", None)
     if prof is not None:
         d.eta_profile = 1
@@ -231,7 +240,8 @@ class Context:
     on PyTorch's current CUDA stream.
     """
 
-    def __init__(self, h, use_torch: bool = True, stream: Optional[int] = None, exec_mode: int = SC_EXEC_GRAPH):
+    def __init__(self, h, use_torch: bool = True, stream: Optional[int] = None, exec_mode: int = SC_EXEC_GRAPH,
+                 finite_check: bool = True, allocator=None):
         L = lib()
         self.h = h
         self._alloc = None
@@ -242,7 +252,9 @@ class Context:
             if stream is None:
                 stream = torch.cuda.current_stream().cuda_stream
             self._alloc = _torch_allocator()
-        d, self._keep = make_desc(h, stream, self._alloc, exec_mode)
+        if allocator is not None:
+            self._alloc = allocator
+        d, self._keep = make_desc(h, stream, self._alloc, exec_mode, finite_check)
         ctx = ctypes.c_void_p()
         _check(L.sc_create(ctypes.byref(d), ctypes.byref(ctx)))
         self.ctx = ctx
@@ -326,11 +338,28 @@ class Context:
         _check(lib().sc_get_state(self.ctx, ctypes.c_void_p(host_ptr), 1 if ghosted_level0 else 0))
         return out
 
+    def sc_set_transfer_mode(self, mode: int):
+        """SC_XFER_AUTO (direct for page-locked host memory), SC_XFER_STAGED or SC_XFER_DIRECT."""
+        _check(lib().sc_set_transfer_mode(self.ctx, int(mode)))
+
+    def sc_transfer_stats(self) -> dict:
+        """Split timing of the last sc_set_state / sc_get_state (CUDA events)."""
+        c, k = ctypes.c_double(), ctypes.c_double()
+        n, d = ctypes.c_size_t(), ctypes.c_int()
+        _check(lib().sc_transfer_stats(self.ctx, ctypes.byref(c), ctypes.byref(k), ctypes.byref(n), ctypes.byref(d)))
+        return {"copy_ms": c.value, "kernel_ms": k.value, "bytes": n.value, "direct": bool(d.value)}
+
     def sc_advance(self, n: int):
         _check(lib().sc_advance(self.ctx, n))
 
     def sc_synchronize(self):
+        """Wait for the context's stream; raises SubcycError with SC_ENONFINITE
+        when the per-step finiteness check found a non-finite value."""
         _check(lib().sc_synchronize(self.ctx))
+
+    def sc_synchronize_timeout(self, timeout_s: float):
+        """As sc_synchronize with a bounded wait (SC_ETIMEOUT when it runs out)."""
+        _check(lib().sc_synchronize_timeout(self.ctx, float(timeout_s)))
 
     def sc_get_constraints(self, level, box) -> np.ndarray:
         a = np.empty((NCONSTRAINTS,) + self.shape(level, box))
@@ -478,6 +507,15 @@ class Server:
         d, lat = ctypes.c_int(), ctypes.c_double()
         _check(lib().sc_server_poll(self.srv, ticket, ctypes.byref(d), ctypes.byref(lat)))
         return bool(d.value), lat.value
+
+    def sc_server_wait(self, ticket: int, timeout_s: float) -> float:
+        """Tick until the request is done (its latency) or raise SC_ETIMEOUT."""
+        lat = ctypes.c_double()
+        _check(lib().sc_server_wait(self.srv, ticket, float(timeout_s), ctypes.byref(lat)))
+        return lat.value
+
+    def sc_server_inject_alloc_failure(self, k: int):
+        _check(lib().sc_server_inject_alloc_failure(self.srv, int(k)))
 
     def sc_server_read(self, ticket: int, level: int, box: int, field: int) -> np.ndarray:
         h = self.hier[ticket]

@@ -412,20 +412,28 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(double* __restrict__ vec
 
 // All F fields of one box region: field f of the region is the f-th block of
 // nx*ny*nz values in buf (unpack = 0: array -> buffer; 1: buffer -> array).
+// One warp per row of nx values (a row index covers field, z and y), lanes
+// along x: both sides are read and written in contiguous runs, and the index
+// arithmetic is done once per row.  buf may be device memory or page-locked
+// host memory mapped into the device address space (read and written over
+// the CPU-GPU link directly).
 __global__ void __launch_bounds__(kThreads) pack_fields_kernel(double* __restrict__ vec, long fs, int F, int pitch,
                                                               int ey, int i0, int j0, int k0, int nx, int ny,
                                                               int nz, double* __restrict__ buf, int unpack) {
-  const long n = (long)nx * ny * nz;
-  const long total = n * F;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int f = (int)(idx / n);
-    const long r = idx - (long)f * n;
-    const int i = (int)(r % nx);
-    const int j = (int)((r / nx) % ny);
-    const int k = (int)(r / ((long)nx * ny));
-    const long o = (long)f * fs + ((long)(k0 + k) * ey + (j0 + j)) * pitch + (i0 + i);
-    if (unpack) vec[o] = buf[idx];
-    else buf[idx] = vec[o];
+  const long rows = (long)F * nz * ny;
+  const int lane = threadIdx.x & 31;
+  const long warps = (long)gridDim.x * (blockDim.x >> 5);
+  for (long r = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    const int j = (int)(r % ny);
+    const long fk = r / ny;
+    const int k = (int)(fk % nz);
+    const int f = (int)(fk / nz);
+    double* v = vec + (long)f * fs + ((long)(k0 + k) * ey + (j0 + j)) * pitch + i0;
+    double* b = buf + r * nx;
+    if (unpack)
+      for (int i = lane; i < nx; i += 32) v[i] = b[i];
+    else
+      for (int i = lane; i < nx; i += 32) b[i] = v[i];
   }
 }
 
@@ -553,11 +561,13 @@ cudaError_t launch_unpack(double* vec, const Geom& g, const int* lo, const int* 
 
 cudaError_t launch_pack_fields(double* vec, long fs, int F, const Geom& g, const int* lo, const int* n, double* buf,
                                int unpack, cudaStream_t s) {
-  const long cnt = (long)n[0] * n[1] * n[2] * F;
-  if (cnt == 0) return cudaSuccess;
-  pack_fields_kernel<<<grid_for(cnt, kThreads), kThreads, 0, s>>>(vec, fs, F, g.pitch, g.ext[1], lo[0] - g.org[0],
-                                                                 lo[1] - g.org[1], lo[2] - g.org[2], n[0], n[1],
-                                                                 n[2], buf, unpack);
+  const long rows = (long)n[1] * n[2] * F;
+  if (rows == 0 || n[0] == 0) return cudaSuccess;
+  const long warps_per_block = kThreads / 32;
+  long blocks = (rows + warps_per_block - 1) / warps_per_block;
+  if (blocks > 152L * 16) blocks = 152L * 16;
+  pack_fields_kernel<<<(int)blocks, kThreads, 0, s>>>(vec, fs, F, g.pitch, g.ext[1], lo[0] - g.org[0], lo[1] - g.org[1],
+                                                      lo[2] - g.org[2], n[0], n[1], n[2], buf, unpack);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <thread>
 #include <array>
 #include <map>
 #include <memory>
@@ -277,7 +279,7 @@ struct Level {
   int parity = 0;  // which of S[] holds the current state
 };
 
-enum OpKind { OP_PROLONG, OP_FILL, OP_STAGE, OP_RESTRICT, OP_PROLONG_DIRECT };
+enum OpKind { OP_PROLONG, OP_FILL, OP_STAGE, OP_RESTRICT, OP_PROLONG_DIRECT, OP_CHECK };
 
 struct Op {
   OpKind kind;
@@ -309,7 +311,9 @@ struct sc_ctx {
   long scratch_fs = 0;
   double* staging = nullptr;  // pack/unpack buffer
   size_t staging_bytes = 0;
-  int* flag = nullptr;
+  int* flag = nullptr;         // sc_check_finite's result
+  int* status = nullptr;       // per-step device status word (kStatus* bits), read by sc_synchronize
+  int finite_check = 0;        // check the state for non-finite values after every coarse step
   std::vector<DevBuf> bufs;
   size_t footprint = 0;
   double t = 0;
@@ -326,6 +330,12 @@ struct sc_ctx {
   int eta_profile = 0;
   double eta_c = 0, eta_s = 0, eta_o = 0;
   std::vector<Op> plain_ops[2];  // per-box form: the schedule, run directly
+  // whole-state transfers: mode (SC_XFER_*) and the split timing of the last one
+  int xfer_mode = SC_XFER_AUTO;
+  cudaEvent_t xev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double xfer_copy_ms = 0, xfer_kernel_ms = 0;
+  size_t xfer_bytes = 0;
+  int xfer_direct = 0;
 
   void* dalloc(size_t bytes) {
     bytes = (bytes + 255) & ~(size_t)255;
@@ -1129,6 +1139,9 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       if (L.nphys) CU(launch_radiative_stage(a, L.phys, L.nphys, c->F, g, c->system, s));
       break;
     }
+    case OP_CHECK:
+      CU(launch_nonfinite_check(o.in, g.fs, c->F, L.tiles, L.ntiles, g.pitch, g.pitch * g.ext[1], c->status, s));
+      break;
     case OP_RESTRICT: {
       const Level& P = c->lev[o.level - 1];
       CU(launch_restrict_blocks(o.out, P.g.fs, P.g.pitch, P.g.pitch * P.g.ext[1], o.in, g.fs, g.pitch,
@@ -1158,6 +1171,14 @@ sc_status build_schedule(sc_ctx* c, int p) {
   em.par.assign(c->nlev, 0);
   em.par[0] = p;
   em.coarse_step();
+  if (c->finite_check)
+    for (int l = 0; l < c->nlev; ++l) {
+      Op o{};
+      o.kind = OP_CHECK;
+      o.level = l;
+      o.in = c->lev[l].S[em.par[l]];
+      em.ops.push_back(o);
+    }
   if (c->exec_mode == SC_EXEC_PER_BOX) {
     c->plain_ops[p] = em.ops;
     long n = 0;
@@ -1171,6 +1192,8 @@ sc_status build_schedule(sc_ctx* c, int p) {
         n += (o.level > 0 && L.namr && !o.no_amr ? 1 : 0) + (L.nperiodic ? 1 : 0);
       else if (o.kind == OP_PROLONG_DIRECT)
         n += (L.nblocks ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0) + (L.namr ? 1 : 0);
+      else if (o.kind == OP_CHECK)
+        n += L.ntiles ? 1 : 0;
       else
         n += (L.nrestr ? 1 : 0) + (L.nrblocks ? 1 : 0);
     }
@@ -1673,6 +1696,8 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
   c->eta_c = d->eta_c;
   c->eta_s = d->eta_s;
   c->eta_o = d->eta_o;
+  c->finite_check = d->finite_check ? 1 : 0;
+  cudaError_t e0 = cudaSuccess;
   if (d->allocator && d->allocator->alloc && d->allocator->free) {
     c->alloc = *d->allocator;
     c->has_alloc = true;
@@ -1710,9 +1735,15 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
     }
   }
   c->flag = (int*)c->dalloc(sizeof(int));
-  if (!c->flag) {
+  c->status = (int*)c->dalloc(sizeof(int));
+  if (!c->flag || !c->status) {
     c->release();
     return fail(SC_ENOMEM, "flag allocation failed");
+  }
+  e0 = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if (e0 != cudaSuccess) {
+    c->release();
+    return fail(SC_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e0));
   }
   // lists are uploaded from pageable host vectors: finish before they go away
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -1735,6 +1766,8 @@ void sc_destroy(sc_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (int p = 0; p < 2; ++p)
     if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
+  for (auto& e : c->xev)
+    if (e) cudaEventDestroy(e);
   c->release();
   delete c;
 }
@@ -1785,28 +1818,56 @@ sc_status sc_get_field_device(sc_ctx* c, int l, int b, int f, double* dst) {
 
 namespace {
 
-// Packed whole-state transfer (sc_set_state / sc_get_state).
+// Packed whole-state transfer (sc_set_state / sc_get_state).  Direct form
+// (page-locked host memory, or SC_XFER_DIRECT): the pack/unpack kernels read
+// and write the host buffer through its device mapping, so the data crosses
+// the CPU-GPU link once, with no staging buffer.  Staged form: one DMA copy
+// between the host buffer and a device staging buffer, and the kernels work
+// on the staging buffer.  CUDA events on the context's stream split the time
+// into copy (DMA) and kernel parts.
 sc_status state_transfer(sc_ctx* c, double* host, int ghosted_level0, bool to_device) {
   if (!c || !host) return fail(SC_EINVAL, "null argument");
   if (ghosted_level0 != 0 && ghosted_level0 != 1) return fail(SC_EINVAL, "ghosted_level0 must be 0 or 1");
   size_t bytes = 0;
   sc_status st = sc_state_bytes(c, ghosted_level0, &bytes);
   if (st) return st;
-  if ((st = ensure_staging(c, bytes))) return st;
-  if (to_device) CU(cudaMemcpyAsync(c->staging, host, bytes, cudaMemcpyHostToDevice, c->stream));
+  double* dhost = nullptr;
+  if (c->xfer_mode != SC_XFER_STAGED) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) cudaGetLastError();
+    else if (at.type == cudaMemoryTypeHost && at.devicePointer) dhost = static_cast<double*>(at.devicePointer);
+    if (c->xfer_mode == SC_XFER_DIRECT && !dhost)
+      return fail(SC_EINVAL, "direct state transfer needs page-locked (or registered) host memory");
+  }
+  if (!dhost && (st = ensure_staging(c, bytes))) return st;
+  for (auto& e : c->xev)
+    if (!e) CU(cudaEventCreate(&e));
+  double* buf = dhost ? dhost : c->staging;
+  CU(cudaEventRecord(c->xev[0], c->stream));
+  if (!dhost && to_device) CU(cudaMemcpyAsync(c->staging, host, bytes, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaEventRecord(c->xev[1], c->stream));
   size_t off = 0;
   for (int l = 0; l < c->nlev; ++l) {
     Level& L = c->lev[l];
     for (const sc_box& B : L.boxes) {
       int lo[3], n[3];
       box_region(B, (l == 0 && ghosted_level0) ? c->ghost : 0, lo, n);
-      CU(launch_pack_fields(L.S[L.parity], L.g.fs, c->F, L.g, lo, n, c->staging + off, to_device ? 1 : 0,
-                            c->stream));
+      CU(launch_pack_fields(L.S[L.parity], L.g.fs, c->F, L.g, lo, n, buf + off, to_device ? 1 : 0, c->stream));
       off += (size_t)n[0] * n[1] * n[2] * c->F;
     }
   }
-  if (!to_device) CU(cudaMemcpyAsync(host, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaEventRecord(c->xev[2], c->stream));
+  if (!dhost && !to_device) CU(cudaMemcpyAsync(host, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaEventRecord(c->xev[3], c->stream));
   CU(cudaStreamSynchronize(c->stream));
+  float t01 = 0, t12 = 0, t23 = 0;
+  CU(cudaEventElapsedTime(&t01, c->xev[0], c->xev[1]));
+  CU(cudaEventElapsedTime(&t12, c->xev[1], c->xev[2]));
+  CU(cudaEventElapsedTime(&t23, c->xev[2], c->xev[3]));
+  c->xfer_copy_ms = dhost ? 0.0 : (double)t01 + t23;
+  c->xfer_kernel_ms = t12;
+  c->xfer_bytes = bytes;
+  c->xfer_direct = dhost ? 1 : 0;
   return SC_OK;
 }
 
@@ -1832,6 +1893,23 @@ sc_status sc_set_state(sc_ctx* c, const double* src, int ghosted_level0) {
 
 sc_status sc_get_state(sc_ctx* c, double* dst, int ghosted_level0) {
   return state_transfer(c, dst, ghosted_level0, false);
+}
+
+sc_status sc_set_transfer_mode(sc_ctx* c, int mode) {
+  if (!c) return fail(SC_EINVAL, "null context");
+  if (mode != SC_XFER_AUTO && mode != SC_XFER_STAGED && mode != SC_XFER_DIRECT)
+    return fail(SC_EINVAL, "unknown transfer mode %d", mode);
+  c->xfer_mode = mode;
+  return SC_OK;
+}
+
+sc_status sc_transfer_stats(sc_ctx* c, double* copy_ms, double* kernel_ms, size_t* bytes, int* direct) {
+  if (!c || !copy_ms || !kernel_ms || !bytes || !direct) return fail(SC_EINVAL, "null argument");
+  *copy_ms = c->xfer_copy_ms;
+  *kernel_ms = c->xfer_kernel_ms;
+  *bytes = c->xfer_bytes;
+  *direct = c->xfer_direct;
+  return SC_OK;
 }
 
 sc_status sc_advance(sc_ctx* c, int n) {
@@ -1863,10 +1941,36 @@ sc_status sc_advance(sc_ctx* c, int n) {
   return SC_OK;
 }
 
+// Read and clear the device status word after the stream is idle.
+sc_status read_status(sc_ctx* c) {
+  int h = 0;
+  CU(cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (!h) return SC_OK;
+  CU(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (h & kStatusTimeout) return fail(SC_ETIMEOUT, "a grid barrier of the persistent coarse-step kernel timed out");
+  return fail(SC_ENONFINITE, "non-finite value in the evolved state after a coarse step");
+}
+
 sc_status sc_synchronize(sc_ctx* c) {
   if (!c) return fail(SC_EINVAL, "null context");
   CU(cudaStreamSynchronize(c->stream));
-  return SC_OK;
+  return read_status(c);
+}
+
+sc_status sc_synchronize_timeout(sc_ctx* c, double timeout_s) {
+  if (!c || !(timeout_s >= 0)) return fail(SC_EINVAL, "bad argument");
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(c->stream);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return fail(SC_ECUDA, "cudaStreamQuery: %s", cudaGetErrorString(e));
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >= timeout_s)
+      return fail(SC_ETIMEOUT, "the context's stream was still busy after %.3f s", timeout_s);
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  return read_status(c);
 }
 
 sc_status sc_get_constraints(sc_ctx* c, int level, int box, double* dst) {

@@ -144,6 +144,11 @@ __device__ __forceinline__ double fmul(double a, double b, const FmaK& K) { retu
 
 enum { kStageSingle = 0, kStageRk4 = 1, kStageTwo = 2, kStageNone = 3 };
 
+// Bits of a context's device status word (OR-ed by kernels, read and cleared
+// by sc_synchronize): a non-finite value after a coarse step, a grid barrier
+// of the persistent coarse-step kernel that gave up waiting.
+enum { kStatusNonFinite = 1, kStatusTimeout = 2 };
+
 struct Z4cParams {
   double kappa1, kappa2, eta, ko_sigma;
 };

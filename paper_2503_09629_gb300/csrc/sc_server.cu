@@ -17,6 +17,7 @@
 // synchronise the whole device.
 #include <chrono>
 #include <deque>
+#include <thread>
 #include <map>
 #include <memory>
 #include <string>
@@ -30,11 +31,14 @@ using Clock = std::chrono::steady_clock;
 
 struct PoolUser {
   cudaStream_t stream;
+  long* fail_countdown;  // server-wide fault injection: the allocation that takes it to 0 fails
 };
 
 void* pool_alloc(size_t bytes, void* user) {
+  PoolUser* u = static_cast<PoolUser*>(user);
+  if (*u->fail_countdown > 0 && --*u->fail_countdown == 0) return nullptr;
   void* p = nullptr;
-  if (cudaMallocAsync(&p, bytes, static_cast<PoolUser*>(user)->stream) != cudaSuccess) {
+  if (cudaMallocAsync(&p, bytes, u->stream) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -62,6 +66,7 @@ struct Request {
   int completed = 0;
   std::deque<cudaEvent_t> inflight;
   bool done = false;
+  sc_status status = SC_OK;  // SC_ENOMEM when admission could never allocate the request
   Clock::time_point t_submit, t_admit, t_done;
   double zu_finest = 0, zu_actual = 0;
 };
@@ -81,13 +86,14 @@ struct sc_server {
   unsigned long long next_ticket = 1;
   long launches = 0;
   double zu_finest_done = 0, zu_actual_done = 0;
+  long fail_countdown = 0;  // sc_server_inject_alloc_failure
 };
 
 namespace {
 
 sc_status admit(sc_server* S, Request* r, int slot) {
   r->slot = slot;
-  r->pool.reset(new PoolUser{S->streams[slot]});
+  r->pool.reset(new PoolUser{S->streams[slot], &S->fail_countdown});
   r->alloc.alloc = pool_alloc;
   r->alloc.free = pool_free;
   r->alloc.user = r->pool.get();
@@ -99,7 +105,11 @@ sc_status admit(sc_server* S, Request* r, int slot) {
   if (st != SC_OK) return st;
   st = sc_set_initial_data(r->ctx, r->id_kind, r->id_params.empty() ? nullptr : r->id_params.data(),
                            (int)r->id_params.size());
-  if (st != SC_OK) return st;
+  if (st != SC_OK) {
+    sc_destroy(r->ctx);
+    r->ctx = nullptr;
+    return st;
+  }
   S->slot_busy[slot] = true;
   S->in_use += r->footprint;
   r->t_admit = Clock::now();
@@ -192,6 +202,24 @@ sc_status sc_server_tick(sc_server* S, int* n_active, int* n_queued, int* n_laun
     if (slot < 0) break;
     S->queue.pop_front();
     sc_status st = admit(S, r, slot);
+    if (st == SC_ENOMEM) {
+      // sc_create released what it had allocated.  Retry once running
+      // requests have freed memory; with nothing running, no memory will
+      // come free, so the request fails (sc_server_poll reports SC_ENOMEM).
+      r->ctx = nullptr;
+      r->slot = -1;
+      bool any_active = false;
+      for (auto& kv : S->all)
+        if (kv.second->ctx && !kv.second->done) any_active = true;
+      if (any_active) {
+        S->queue.push_front(r);
+        break;
+      }
+      r->done = true;
+      r->status = SC_ENOMEM;
+      r->t_done = Clock::now();
+      continue;
+    }
     if (st != SC_OK) return st;
     if (r->steps == 0) finish(S, r);
   }
@@ -230,6 +258,27 @@ sc_status sc_server_poll(sc_server* S, unsigned long long ticket, int* done, dou
   Request* r = it->second.get();
   *done = r->done ? 1 : 0;
   if (latency_s) *latency_s = r->done ? std::chrono::duration<double>(r->t_done - r->t_submit).count() : -1.0;
+  return r->status;
+}
+
+sc_status sc_server_wait(sc_server* S, unsigned long long ticket, double timeout_s, double* latency_s) {
+  if (!S || !(timeout_s >= 0)) return err(SC_EINVAL, "bad wait arguments");
+  const auto t0 = Clock::now();
+  for (;;) {
+    sc_status st = sc_server_tick(S, nullptr, nullptr, nullptr);
+    if (st != SC_OK) return st;
+    int done = 0;
+    st = sc_server_poll(S, ticket, &done, latency_s);
+    if (done || st != SC_OK) return st;
+    if (std::chrono::duration<double>(Clock::now() - t0).count() >= timeout_s)
+      return err(SC_ETIMEOUT, "request not finished within the wait's time limit");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+sc_status sc_server_inject_alloc_failure(sc_server* S, long k) {
+  if (!S || k < 0) return err(SC_EINVAL, "bad fault-injection arguments");
+  S->fail_countdown = k;
   return SC_OK;
 }
 
@@ -246,7 +295,9 @@ sc_status sc_server_release(sc_server* S, unsigned long long ticket) {
   if (it == S->all.end()) return err(SC_EINVAL, "unknown ticket");
   Request* r = it->second.get();
   if (r->ctx && !r->done) return err(SC_EINVAL, "request still running");
-  if (r->ctx) {
+  if (r->status != SC_OK) {
+    // failed at admission: neither queued nor holding memory
+  } else if (r->ctx) {
     sc_destroy(r->ctx);
     S->in_use -= r->footprint;
   } else {

@@ -61,6 +61,43 @@ def test_state_through_pinned_buffers_and_uneven_boxes(sc):
     ctx.close()
 
 
+def test_direct_and_staged_transfers_agree(sc):
+    """Both transfer forms move the same bytes: the direct form (kernels read
+    and write page-locked host memory through its device mapping, no DMA) and
+    the staged form (one DMA to a device staging buffer plus kernels); the
+    event-timed split of each is reported, and the direct form refuses
+    pageable memory."""
+    torch = pytest.importorskip("torch")
+    h = W.bl_3level(20)
+    ctx = sc.Context(h)
+    ctx.sc_set_initial_data(h.id_kind, h.id_params)
+    ctx.sc_advance(1)
+    ref = ctx.sc_get_state(ghosted_level0=True)  # numpy (pageable): staged
+    st = ctx.sc_transfer_stats()
+    assert not st["direct"] and st["bytes"] == ref.nbytes and st["copy_ms"] > 0
+    pinned_ref = torch.from_numpy(ref).pin_memory()
+    buf = torch.empty(ref.size, dtype=torch.float64).pin_memory()
+    for mode, direct in ((sc.SC_XFER_AUTO, True), (sc.SC_XFER_STAGED, False), (sc.SC_XFER_DIRECT, True)):
+        ctx.sc_set_transfer_mode(mode)
+        buf.zero_()
+        ctx.sc_get_state(buf.data_ptr(), ghosted_level0=True)
+        st = ctx.sc_transfer_stats()
+        assert st["direct"] == direct and st["bytes"] == ref.nbytes, (mode, st)
+        assert (st["copy_ms"] == 0.0) == direct and st["kernel_ms"] > 0, (mode, st)
+        assert np.array_equal(buf.numpy(), ref), mode
+        buf.mul_(3.0)
+        ctx.sc_set_state(buf.data_ptr(), ghosted_level0=True)
+        assert ctx.sc_transfer_stats()["direct"] == direct
+        buf.zero_()
+        ctx.sc_get_state(buf.data_ptr(), ghosted_level0=True)
+        assert np.array_equal(buf.numpy(), 3.0 * ref), mode
+        ctx.sc_set_state(pinned_ref.data_ptr(), ghosted_level0=True)
+    with pytest.raises(sc.SubcycError) as e:
+        ctx.sc_get_state(np.empty_like(ref), ghosted_level0=True)  # pageable memory in the direct form
+    assert e.value.code == sc.SC_EINVAL
+    ctx.close()
+
+
 @pytest.mark.parametrize("make", [lambda: W.bl_3level(20), lambda: W.gaussian_3level(64, 2)])
 def test_checkpoint_restart_continues_bitwise(sc, make):
     """Checkpoint/restart through the public API: the whole state read after
