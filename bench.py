@@ -33,9 +33,10 @@ if ROOT not in sys.path:
 
 METRIC = "subcycled Z4c zone-updates/s on 1 GB300, % roofline; ensemble p50/p99 latency"
 UNIT = "zone-updates/s (finest-equivalent)"
-# FP64 peak derived from the unit counts and clocks: 152 SMs x 2070 MHz x
-# 2 DFMA lanes per SM per clock x 2 flops per DFMA.
-FP64_PEAK_GFLOPS = 152 * 2.070 * 2 * 2
+# The FP64 roofline denominators are read from the device at run time
+# (sc_measure_fp64_peak): the nominal rate (SMs x maximum SM clock x 2 DFMA
+# per SM per clock x 2 flops) and the measured issue rates of a general DFMA
+# and of a DADD (a DFMA with a unit multiplier issues at the DADD rate).
 
 
 def _measured_hbm_gbs() -> float:
@@ -63,12 +64,12 @@ FLOPS_PER_CELL = {"z4c_derivs": 1180.0, "z4c_stage": 1971.0}
 DRAM_BYTES_PER_CELL = {"z4c_derivs": None,
                        "z4c_stage": (514.633984e6 + 278.21952e6) / 262144}
 # FP64 instructions (DFMA + DMUL + DADD, thread-level / cell) per interior
-# cell of the derivative pass (D_x/D_y row pass + per-cell pass), counted by
-# ncu on the 3-level 64^3 case (profiles/z4c_kernels_bl3level64_ncu.md,
-# profiles/z4c_derivs_fd8_bl3level64_ncu.md).  The pass issues its additions
-# as DFMAs, so its bound is the DFMA issue rate: 152 SMs x 2070 MHz x 2.
-FP64_INSTR_PER_CELL = {4: {"z4c_derivs": 103.0 + 807.0}, 8: {"z4c_derivs": 242.0 + 1324.0}}
-FP64_ISSUE_PEAK_G = 152 * 2.070 * 2
+# cell of each pass, counted by ncu on the 3-level 64^3 case
+# (profiles/z4c_kernels_bl3level64_ncu.md, profiles/z4c_derivs_fd8_bl3level64_ncu.md).
+# The derivative pass is stencil additions and unit-multiplier FMAs (issued
+# at the DADD rate); the stage kernel is mostly general FMAs.
+FP64_INSTR_PER_CELL = {4: {"z4c_derivs": 103.0 + 807.0, "z4c_stage": 1132.0},
+                       8: {"z4c_derivs": 242.0 + 1324.0, "z4c_stage": 1132.0}}
 # Kernel with the largest share of a coarse step in the ncu launch list
 # (profiles/z4c_bl_7level_launch_list.md).
 DOMINANT = "z4c_stage"
@@ -106,6 +107,42 @@ def oracle_step_rate(h, steps: int, warmup: int):
     dt = time.perf_counter() - t0
     fin, _ = h.zone_updates_per_coarse_step()
     return fin * steps / dt, dt
+
+
+def _oracle_worker(job):
+    """One oracle process of the aggregate CPU baseline: (kind, coarse steps)
+    -> finest-equivalent zone-updates/s of that process."""
+    kind, steps = job
+    from paper_2503_09629_gb300 import workloads as W
+    if kind == "z4c":
+        return oracle_step_rate(sample_hierarchy(), steps, 0)[0]
+    import oracle
+    h = W.standing_wave_2level(32)
+    o = oracle.Oracle(h.system, h.boxes, h.ncells0, h.origin, h.h0, **h.kwargs())
+    for l in range(h.nlevels):
+        a = W.initial_fields(h, l, 0)
+        for f in range(2):
+            o.set_field(l, 0, f, a[f])
+    t0 = time.perf_counter()
+    o.advance(steps)
+    fin, _ = h.zone_updates_per_coarse_step()
+    return fin * steps / (time.perf_counter() - t0)
+
+
+def cpu_aggregate(cores: int):
+    """The oracle on every host core at once (one process per core, started
+    with spawn): aggregate zone-updates/s = the sum of the concurrent
+    processes' rates, for the Z4c sample and for the 2-level standing wave."""
+    import multiprocessing as mp
+    out = {}
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for kind, steps, label in (("z4c", 1, "z4c BL 5-level 20^3 sample, 1 coarse step per process"),
+                                   ("wave", 32, "standing wave 2-level 32^3, 32 coarse steps per process")):
+            t0 = time.perf_counter()
+            rates = pool.map(_oracle_worker, [(kind, steps)] * cores)
+            out[kind] = {"value": sum(rates), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": label,
+                         "per_process_mean": sum(rates) / cores, "wall_s": time.perf_counter() - t0}
+    return out
 
 
 class ClockSampler:
@@ -172,17 +209,23 @@ def whole_job_rate(world: int, units_per_step_per_rank: float, steps: int, t_max
     return world * units_per_step_per_rank * steps / (t_max_ms * 1e-3)
 
 
-def run_ensemble(sc, W, n: int, seed: int, burst: bool, mean_interarrival: float, served: bool,
+def run_ensemble(sc, W, n: int, seed: int, burst: bool, mean_interarrival: float, arm: str,
                  budget: int = 48 << 30, max_active: int = 32):
-    """Serve the seeded request ensemble; returns latency and throughput.
+    """Serve the seeded request ensemble in one arm; returns latency and throughput.
 
-    served=True: continuous batching (max_active slots, one stream each, CUDA
-    graph per coarse step); served=False: the plain per-box form, one request
-    at a time in arrival order, kernels launched box by box without graphs."""
+    arms: "plain_per_box" -- one request at a time in arrival order, kernels
+    launched box by box without graphs; "plain_graph" -- one request at a
+    time, one CUDA graph per coarse step; "served_streams" -- continuous
+    batching, max_active slots with one stream and one graph per request;
+    "served_merged" -- continuous batching with the scalar-wave requests of a
+    tick merged into one persistent cooperative launch (Z4c requests keep
+    their graphs on their own streams)."""
     reqs = sorted(W.serving_requests(n, seed, burst=burst, mean_interarrival=mean_interarrival), key=lambda r: r[0])
+    served = arm.startswith("served")
     srv = sc.Server(budget, max_active if served else 1, 2)
-    mode = sc.SC_EXEC_GRAPH if served else sc.SC_EXEC_PER_BOX
-    tickets, lat = [], []
+    srv.sc_server_set_merge(arm == "served_merged")
+    mode = sc.SC_EXEC_PER_BOX if arm == "plain_per_box" else sc.SC_EXEC_GRAPH
+    lat = []
     nxt = 0
     t0 = time.perf_counter()
     unfinished = []
@@ -210,10 +253,66 @@ def run_ensemble(sc, W, n: int, seed: int, burst: bool, mean_interarrival: float
     lat.sort()
     pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
     return {"requests": n, "arrivals": "burst" if burst else f"poisson mean {mean_interarrival * 1e3:.1f} ms",
-            "form": "served (continuous batching, graphs)" if served else "plain (FIFO, per-box launches)",
+            "arm": arm, "max_active": max_active if served else 1,
             "p50_s": pct(0.5), "p99_s": pct(0.99), "wall_s": wall,
             "zone_updates_per_s": st["zu_finest"] / wall, "actual_zone_updates_per_s": st["zu_actual"] / wall,
             "gpu_launches": st["launches"]}
+
+
+def run_serving_arms(sc, W, n: int, max_active: int = 32):
+    """The seeded ensemble (60% wave, 40% Z4c requests) in every arm, burst
+    arrivals and Poisson arrivals at 0.9 of the plain per-box service rate."""
+    import torch
+    torch.cuda.empty_cache()
+    burst = {arm: run_ensemble(sc, W, n, 0, True, 0.0, arm, max_active=max_active)
+             for arm in ("plain_per_box", "plain_graph", "served_streams", "served_merged")}
+    ia = burst["plain_per_box"]["wall_s"] / n / 0.9
+    poisson = {arm: run_ensemble(sc, W, n, 0, False, ia, arm, max_active=max_active)
+               for arm in ("plain_per_box", "plain_graph", "served_merged")}
+    return {"requests": n, "burst": burst, "poisson_load_0.9_of_plain_per_box": poisson}
+
+
+def time_form(sc, h, mode, steps, warm=2):
+    """Zone-updates/s of one hierarchy in one execution form, CUDA events on
+    the context's stream over `steps` coarse steps after `warm` untimed ones."""
+    import torch
+    ctx = sc.Context(h, exec_mode=mode)
+    ctx.sc_set_initial_data(h.id_kind, h.id_params)
+    ctx.sc_advance(warm)
+    ctx.sc_synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.sc_advance(steps)
+    e1.record(stream)
+    ctx.sc_synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = ctx.sc_launches_per_step()
+    ctx.close()
+    fin, _act = h.zone_updates_per_coarse_step()
+    return {"ms_per_coarse_step": ms, "zone_updates_per_s": fin / (ms * 1e-3), "launches_per_coarse_step": launches}
+
+
+def run_wave_forms(sc, W, scale: float = 1.0):
+    """The scalar-wave workloads in the three execution forms: plain per-box
+    launches, one CUDA graph per coarse step (one launch per level and phase
+    over all boxes), and the persistent cooperative kernel (one launch per
+    coarse step, grid barriers between phases)."""
+    cases = [("standing wave 2-level 32^3 (state 10 MB, L2-resident)", W.standing_wave_2level(32), 200),
+             ("gaussian 3-level 64^3, seeded uneven boxes", W.gaussian_3level(64, 0), 100),
+             ("gaussian 3-level 128^3, seeded uneven boxes", W.gaussian_3level(128, 0), 40)]
+    out = {}
+    for name, h, steps in cases:
+        steps = max(4, int(steps * scale))
+        r = {"plain_per_box": time_form(sc, h, sc.SC_EXEC_PER_BOX, steps),
+             "graph": time_form(sc, h, sc.SC_EXEC_GRAPH, steps),
+             "persistent": time_form(sc, h, sc.SC_EXEC_PERSISTENT, steps)}
+        base = r["plain_per_box"]["zone_updates_per_s"]
+        for k in ("graph", "persistent"):
+            r[k]["speedup_vs_plain"] = r[k]["zone_updates_per_s"] / base
+        r["steps"] = steps
+        out[name] = r
+    return out
 
 
 def run_serving(args):
@@ -223,16 +322,81 @@ def run_serving(args):
     from paper_2503_09629_gb300 import workloads as W
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     sc.build()
-    n = args.requests
-    plain_burst = run_ensemble(sc, W, n, 0, True, 0.0, served=False)
-    served_burst = run_ensemble(sc, W, n, 0, True, 0.0, served=True)
-    mean_service = plain_burst["wall_s"] / n
-    ia = mean_service / 0.9  # arrival rate 0.9 / mean plain service time
-    plain_poisson = run_ensemble(sc, W, n, 0, False, ia, served=False)
-    served_poisson = run_ensemble(sc, W, n, 0, False, ia, served=True)
-    return {"burst": {"served": served_burst, "plain": plain_burst},
-            "poisson": {"served": served_poisson, "plain": plain_poisson,
-                        "mean_plain_service_s": mean_service}}
+    return run_serving_arms(sc, W, args.requests, args.max_active)
+
+
+def study_moving(sc, W, steps: int):
+    """Moving-box run of the 9-level binary-black-hole layout: each coarse
+    step interpolates the shift at the punctures, moves them along dx/dt =
+    -beta (forward Euler over the coarse step), regrids levels 3-8 around
+    them and advances one coarse step."""
+    import torch
+    h, pos, radii, fm = W.moving_9level(32)
+    ctx = sc.Context(h)
+    ctx.sc_autotune()
+    ctx.sc_set_initial_data(h.id_kind, h.id_params)
+    dt0 = h.cfl * h.h0
+    t_regrid = t_step = fin = 0.0
+    track, cells = [pos], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        pos = W.track_punctures(ctx, pos, dt0)
+        ctx.sc_regrid(W.moving_layout(ctx.h, pos, radii, fm))
+        t1 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.sc_advance(1)
+        e1.record()
+        torch.cuda.synchronize()
+        t_regrid += t1 - t0
+        t_step += e0.elapsed_time(e1) * 1e-3
+        fin += ctx.h.zone_updates_per_coarse_step()[0]
+        track.append(pos)
+        cells.append(sum(ctx.h.interior_cells(l) for l in range(ctx.h.nlevels)))
+    out = {"workload": h.name, "coarse_steps": steps, "zone_updates_per_s_incl_regrid": fin / (t_step + t_regrid),
+           "zone_updates_per_s_step_only": fin / t_step, "regrid_share": t_regrid / (t_step + t_regrid),
+           "mean_step_ms": t_step / steps * 1e3, "mean_regrid_ms": t_regrid / steps * 1e3,
+           "interior_cells_first_last": [cells[0], cells[-1]],
+           "puncture_x_first_last": [track[0][1][0], track[-1][1][0]], "state_finite": bool(ctx.sc_check_finite()),
+           "final_boxes_per_level": [len(b) for b in ctx.h.boxes]}
+    ctx.close()
+    return out
+
+
+def study_wavekernel(sc, W, n: int = 256):
+    """The scalar-wave stage kernel alone on one periodic n^3 level: CUDA-event
+    time per launch against the FP64-issue and HBM bounds (15 FP64
+    instructions and 64 algorithmic bytes per cell: u, Pi and y_n read, k and
+    the next stage input written)."""
+    h = W.Hierarchy(system=W.WAVE, boxes=[[W.cube(0, n)]], ncells0=(n, n, n), origin=(0.0, 0.0, 0.0), h0=1.0 / n,
+                    id_kind=W.ID_STANDING_WAVE, id_params=[1.0, 1.0, 1.0, 1.0], name=f"wave 1-level {n}^3")
+    ctx = sc.Context(h)
+    ctx.sc_autotune()
+    ctx.sc_set_initial_data(h.id_kind, h.id_params)
+    ms, _ = ctx.sc_time_stage_kernels(0, 20)
+    ctx.close()
+    pk = sc.sc_measure_fp64_peak()
+    cells, ipc, bpc = n ** 3, 15, 64
+    issue = cells * ipc / (ms * 1e-3) / 1e9
+    return {"workload": h.name, "ms_per_launch": ms, "cells": cells, "fp64_issue_g_per_s": issue,
+            "frac_of_measured_dfma_issue": issue / pk["dfma_g_per_s"],
+            "frac_of_measured_dadd_issue": issue / pk["dadd_g_per_s"],
+            "algorithmic_gb_per_s": cells * bpc / (ms * 1e-3) / 1e9,
+            "hbm_frac": cells * bpc / (ms * 1e-3) / 1e9 / HBM_GBS, "peaks": pk}
+
+
+def run_study(args):
+    import torch
+
+    import paper_2503_09629_gb300 as sc
+    from paper_2503_09629_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    sc.build()
+    if args.study == "moving":
+        return study_moving(sc, W, args.study_steps)
+    if args.study == "wavekernel":
+        return study_wavekernel(sc, W)
+    return sc.sc_measure_fp64_peak()
 
 
 def run_reference(args, rank: int, world: int):
@@ -300,44 +464,66 @@ def run_gpu(args, rank: int, world: int):
     state_finite = ctx.sc_check_finite()
 
     # Roofline of the dominant kernels: FP64-ALU bound.  Per-launch durations
-    # from CUDA events on the library's stream, on the finest level.
+    # from CUDA events on the library's stream, on the finest level; peaks
+    # read from this device (nominal from its SM count and clock, and the
+    # measured DFMA and DADD issue rates).
+    pk = sc.sc_measure_fp64_peak(stream.cuda_stream)
+    nominal_tflops = pk["sms"] * pk["sm_clock_mhz"] * 4 / 1e6
+    dfma_tflops = 2 * pk["dfma_g_per_s"] / 1e3
     fin_level = h.nlevels - 1
     cells = h.interior_cells(fin_level)
     t_der, t_stage = ctx.sc_time_stage_kernels(fin_level, 5)
     roof = {}
     for name, t in (("z4c_derivs", t_der), ("z4c_stage", t_stage)):
         fpc = FLOPS_PER_CELL[name] if (h.fd_order == 4 or name == "z4c_stage") else None
-        if fpc is None:
-            roof[name] = {"ms_per_launch": t, "cells_per_launch": cells, "flops_per_cell": None}
-            continue
-        ach = cells * fpc / (t * 1e-3) / 1e12
-        tb = DRAM_BYTES_PER_CELL.get(name) if h.fd_order == 4 else None
-        roof[name] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                      "frac": ach * 1e3 / FP64_PEAK_GFLOPS, "traffic": (tb * cells if tb else None),
-                      "ms_per_launch": t, "cells_per_launch": cells, "flops_per_cell": fpc}
-    ipc = FP64_INSTR_PER_CELL[h.fd_order]["z4c_derivs"]
-    issue = cells * ipc / (t_der * 1e-3) / 1e9
-    roof["z4c_derivs"]["fp64_issue"] = {"achieved": issue, "peak": FP64_ISSUE_PEAK_G, "unit": "G FP64 instr/s",
-                                        "frac": issue / FP64_ISSUE_PEAK_G, "instr_per_cell": ipc}
-    # Refinement-boundary ghost fill on the finest level: the separable
-    # prolongation (FP64: 42 FMAs per fine position of a 4x4x4 block and
-    # vector-field, 2688 FMAs per block and vector-field) and the
-    # dense-output apply (HBM: 5 reads + 1 write per ghost value, plus the
-    # 12-byte cell record per ghost cell).
-    t_pro, t_app, (n_amr, n_blk, n_slow) = ctx.sc_time_ghost_kernels(fin_level, 5)
+        ipc = FP64_INSTR_PER_CELL[h.fd_order][name]
+        issue = cells * ipc / (t * 1e-3) / 1e9
+        r = {"ms_per_launch": t, "cells_per_launch": cells, "flops_per_cell": fpc,
+             "fp64_issue": {"achieved_g_instr_per_s": issue, "instr_per_cell": ipc,
+                            "frac_of_nominal_dfma_issue": issue / (nominal_tflops * 1e3 / 2),
+                            "frac_of_measured_dfma_issue": issue / pk["dfma_g_per_s"],
+                            "frac_of_measured_dadd_issue": issue / pk["dadd_g_per_s"]}}
+        if fpc is not None:
+            ach = cells * fpc / (t * 1e-3) / 1e12
+            tb = DRAM_BYTES_PER_CELL.get(name) if h.fd_order == 4 else None
+            r.update({"bound": "alu", "achieved": ach, "peak": nominal_tflops, "unit": "TFLOP/s",
+                      "frac": ach / nominal_tflops, "frac_of_measured_dfma": ach / dfma_tflops,
+                      "traffic": (tb * cells if tb else None)})
+        roof[name] = r
+    # Refinement-boundary ghost fill on the finest level: the tile-separable
+    # prolongation (FP64: the FMAs its tiles execute, counted by the library)
+    # and the dense-output apply (HBM: 5 reads + 1 write per ghost value, plus
+    # the 12-byte cell record per ghost cell).
+    t_pro, t_app, (n_amr, n_tiles, n_slow, tile_fmas) = ctx.sc_time_ghost_kernels(fin_level, 5)
     F = 22
-    pro_flops = n_blk * 5 * F * 2688 * 2 + n_slow * 5 * F * 258 * 2
+    nvec = 5
+    pro_flops = 2 * nvec * F * (tile_fmas + n_slow * 258)
+    pro_ach = pro_flops / (t_pro * 1e-3) / 1e12
+    roof["amr_prolong"] = {"bound": "alu", "achieved": pro_ach, "peak": nominal_tflops, "unit": "TFLOP/s",
+                           "frac": pro_ach / nominal_tflops, "frac_of_measured_dfma": pro_ach / dfma_tflops,
+                           "ms_per_launch": t_pro, "ghost_cells": n_amr, "tiles": n_tiles, "fallback_cells": n_slow,
+                           "fmas_per_ghost_value": (tile_fmas + n_slow * 258) / max(n_amr, 1),
+                           "ghost_values_per_s": n_amr * nvec * F / (t_pro * 1e-3),
+                           "frac_at_42_fma_per_value": 2 * 42 * n_amr * nvec * F / (t_pro * 1e-3) / 1e12 / nominal_tflops}
     app_bytes = n_amr * F * 6 * 8 + n_amr * 12
-    roof["amr_prolong"] = {"bound": "alu", "achieved": pro_flops / (t_pro * 1e-3) / 1e12,
-                           "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                           "frac": pro_flops / (t_pro * 1e-3) / 1e9 / FP64_PEAK_GFLOPS, "ms_per_launch": t_pro,
-                           "ghost_cells": n_amr, "blocks": n_blk, "fallback_cells": n_slow}
     roof["amr_apply"] = {"bound": "hbm", "achieved": app_bytes / (t_app * 1e-3) / 1e9, "peak": HBM_GBS,
                          "unit": "GB/s", "frac": app_bytes / (t_app * 1e-3) / 1e9 / HBM_GBS, "ms_per_launch": t_app}
     dominant = DOMINANT
     roofline = dict(roof[dominant])
     roofline["kernel"] = dominant
-    roofline["peak_source"] = "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (nominal 1.25 TFLOP/s)"
+    roofline["peak_source"] = (f"nominal from this device: {pk['sms']} SMs x {pk['sm_clock_mhz']:.0f} MHz x 4 FP64 "
+                               f"flop/clk/SM; measured issue rates: DFMA {pk['dfma_g_per_s']:.1f} G/s, "
+                               f"DADD {pk['dadd_g_per_s']:.1f} G/s (sc_measure_fp64_peak)")
+    roofline["measured_peaks"] = {"dfma_tflops": dfma_tflops, "dadd_g_instr_per_s": pk["dadd_g_per_s"],
+                                  "dfma_g_instr_per_s": pk["dfma_g_per_s"], "nominal_tflops": nominal_tflops}
+    # the whole coarse step against the FP64 peak: RHS flops of both Z4c
+    # passes per cell and stage, over every actual cell update
+    if h.fd_order == 4:
+        step_tflops = (FLOPS_PER_CELL["z4c_derivs"] + FLOPS_PER_CELL["z4c_stage"]) * 4 * act_per_step / (
+            ms_per_step * 1e-3) / 1e12
+        roofline["step_level"] = {"achieved": step_tflops, "unit": "TFLOP/s", "frac": step_tflops / nominal_tflops,
+                                  "frac_of_measured_dfma": step_tflops / dfma_tflops,
+                                  "flops_per_cell_stage": FLOPS_PER_CELL["z4c_derivs"] + FLOPS_PER_CELL["z4c_stage"]}
     roofline["other_kernels"] = {k: v for k, v in roof.items() if k != dominant}
 
     # End to end through the public API with host buffers: each step uploads
@@ -451,20 +637,17 @@ def run_gpu(args, rank: int, world: int):
                    "steps": args.per_box_steps}
         cp.close()
 
+    # The scalar-wave workloads in the plain, graph and persistent forms.
+    wave_forms = None
+    if rank == 0 and args.wave_forms:
+        wave_forms = run_wave_forms(sc, W)
+
     # Served form vs plain per-box form on a seeded ensemble (60% wave, 40% Z4c requests).
     serving = None
     if rank == 0 and args.serving_requests > 0:
         ctx.close()
         ctx = None
-        torch.cuda.empty_cache()
-        n = args.serving_requests
-        plain = run_ensemble(sc, W, n, 0, True, 0.0, served=False)
-        served = run_ensemble(sc, W, n, 0, True, 0.0, served=True)
-        ia = plain["wall_s"] / n / 0.9
-        plain_p = run_ensemble(sc, W, n, 0, False, ia, served=False)
-        served_p = run_ensemble(sc, W, n, 0, False, ia, served=True)
-        serving = {"requests": n, "burst": {"served": served, "plain": plain},
-                   "poisson_load_0.9": {"served": served_p, "plain": plain_p}}
+        serving = run_serving_arms(sc, W, args.serving_requests, args.max_active)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -472,6 +655,8 @@ def run_gpu(args, rank: int, world: int):
         v, dt = oracle_step_rate(hs, 1, 0)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"1 coarse step of {hs.name} ({dt:.1f} s)"}
+        if args.cpu_aggregate:
+            cpu["aggregate_all_cores"] = cpu_aggregate(os.cpu_count() or 1)
     if ctx is not None:
         ctx.close()
     if rank == 0:
@@ -495,7 +680,7 @@ def run_gpu(args, rank: int, world: int):
                         "transfer_form": "direct (kernels access page-locked host memory)" if direct else "staged",
                         "transfer_split": split, "staged_form_once": staged},
                 "gpu_launches": launches, "clocks": clk, "serving": serving, "uniform_step_mode": uniform,
-                "per_box_form": per_box}
+                "per_box_form": per_box, "wave_forms": wave_forms}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -515,9 +700,21 @@ def main():
                     help="coarse steps of the same hierarchy in the plain per-box form, no graph (0: skip)")
     ap.add_argument("--fd-order", type=int, default=4, choices=[4, 8],
                     help="finite-difference order of the Z4c right-hand side (8: the paper's production setting)")
-    ap.add_argument("--serving-requests", type=int, default=64,
+    ap.add_argument("--cpu-aggregate", type=int, default=1,
+                    help="1: also time the oracle on every host core at once (aggregate CPU baseline)")
+    ap.add_argument("--study", choices=["moving", "wavekernel", "fp64"],
+                    help="one study instead of the benchmark (moving: 9-level moving boxes; wavekernel: the wave "
+                         "stage kernel on one 256^3 level; fp64: the measured FP64 issue rates)")
+    ap.add_argument("--study-steps", type=int, default=32)
+    ap.add_argument("--wave-forms", type=int, default=1,
+                    help="1: time the scalar-wave workloads in the plain, graph and persistent forms")
+    ap.add_argument("--serving-requests", type=int, default=256,
                     help="requests of the served-vs-plain ensemble embedded in the default line (0: skip)")
+    ap.add_argument("--max-active", type=int, default=32, help="slots of the served arms")
     args = ap.parse_args()
+    if args.study:
+        print(json.dumps(run_study(args)), flush=True)
+        return
     if args.serving:
         res = run_serving(args)
         print(json.dumps({"metric": "ensemble p50/p99 latency and zone-updates/s (served vs plain per-box form)",

@@ -106,7 +106,11 @@ typedef struct {
   const sc_allocator* allocator;
   int exec_mode;  /* SC_EXEC_GRAPH (0, default): one CUDA graph per coarse step, one launch per
                      level and phase covering all boxes; SC_EXEC_PER_BOX (1): the plain form, stage
-                     kernels launched box by box directly on the stream, no graph (for comparison) */
+                     kernels launched box by box directly on the stream, no graph (for comparison);
+                     SC_EXEC_PERSISTENT (2, scalar wave only): one cooperative launch per coarse
+                     step runs every phase of Sec. II steps 1-7 on all levels (all stages of every
+                     substep, ghost fills, prolongation, restriction) with grid-wide barriers
+                     between dependent phases; bitwise the same fields as the graph form */
   int autotune;   /* 1: run sc_autotune at creation (cached per system and level shapes) */
   int eta_profile; /* Z4c: 0 = constant eta; 1 = eta(r) = (eta_c - eta_o) exp(-(r/eta_s)^4) + eta_o
                       with r the coordinate radius (Sec. III.A) */
@@ -131,7 +135,7 @@ typedef struct {
                        synchronisation); the next sc_synchronize reports SC_ENONFINITE */
 } sc_desc;
 
-enum { SC_EXEC_GRAPH = 0, SC_EXEC_PER_BOX = 1 };
+enum { SC_EXEC_GRAPH = 0, SC_EXEC_PER_BOX = 1, SC_EXEC_PERSISTENT = 2 };
 
 /* Build the hierarchy of Sec. II: nested levels with h^(l) / h^(l+1) = 2,
  * each a set of boxes.  Validates nesting and alignment, allocates every
@@ -358,6 +362,14 @@ sc_status sc_server_poll(sc_server* srv, unsigned long long ticket, int* done, d
 /* Tick and poll until the request is done or timeout_s seconds have passed
  * (SC_ETIMEOUT; the request keeps running).  Host-side wait, bounded. */
 sc_status sc_server_wait(sc_server* srv, unsigned long long ticket, double timeout_s, double* latency_s);
+/* Merged form (on = 1, the default): scalar-wave requests run in the
+ * persistent coarse-step form (SC_EXEC_PERSISTENT) and each tick launches the
+ * next coarse step of all of them as one cooperative kernel on the server's
+ * batch stream (phase i of every request between the same two grid
+ * barriers); Z4c requests keep one graph per step on their own stream.
+ * on = 0: every request runs its own graph on its own stream.  Applies to
+ * requests admitted afterwards; results are bitwise the same either way. */
+sc_status sc_server_set_merge(sc_server* srv, int on);
 /* Host-side fault injection for tests of the admission path: the k-th device
  * allocation the server makes from now on fails as if the pool were
  * exhausted (k = 0 disables).  A request whose allocation fails is retried
@@ -382,12 +394,23 @@ sc_status sc_debug_get_vector(sc_ctx* ctx, int level, int box, int vec, int fiel
  * graph, with CUDA events on the context's stream, averaged over nrep:
  * ms[0] = prolongation of the parent's y_n and the stage vectors its dense
  * output uses (k1..k4 for RK4) to the level's ghost cells
- * (block-separable kernel plus per-cell fallback), ms[1] = one dense-output
- * ghost fill.  counts[0] = ghost cells, counts[1] = 4x4x4 blocks of the
- * separable kernel, counts[2] = ghost cells on the per-cell fallback.
+ * (tile-separable kernel plus per-cell fallback), ms[1] = one dense-output
+ * ghost fill.  counts (4 longs): [0] ghost cells, [1] slab tiles of the
+ * separable kernel, [2] ghost cells on the per-cell fallback, [3] FMAs the
+ * separable kernel executes per (vector, field) over all its tiles.
  * Writes only the level's ghost store and second stage buffer; call between
  * sc_advance calls.  Synchronises. */
 sc_status sc_time_ghost_kernels(sc_ctx* ctx, int level, int nrep, double* ms, long* counts);
+
+/* Measurement (no counterpart in the paper; every kernel of this library is
+ * bound by the FP64 pipe, whose rate depends on the operands).  Measures, on
+ * the current device with CUDA events on cuda_stream, the issue rates of a
+ * general FP64 fused multiply-add and of an FP64 addition (G instructions per
+ * second, 8 independent chains per thread, 8 blocks of 256 threads per SM),
+ * and reports the SM count and the maximum SM clock.  Allocates and frees a
+ * small output buffer; synchronises.  Errors: SC_EINVAL, SC_ENOMEM, SC_ECUDA. */
+sc_status sc_measure_fp64_peak(void* cuda_stream, double* dfma_g_per_s, double* dadd_g_per_s, int* sms,
+                               double* sm_clock_mhz);
 
 const char* sc_last_error(void);
 

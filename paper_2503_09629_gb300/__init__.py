@@ -27,7 +27,7 @@ LIB_PATH = os.path.join(HERE, "libsubcyc.so")
 SC_OK, SC_EINVAL, SC_ENOMEM, SC_ECUDA, SC_ENESTING, SC_ENONFINITE, SC_ETIMEOUT, SC_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 SC_WAVE, SC_Z4C = 0, 1
 SC_BC_PERIODIC, SC_BC_RADIATIVE = 0, 1
-SC_EXEC_GRAPH, SC_EXEC_PER_BOX = 0, 1
+SC_EXEC_GRAPH, SC_EXEC_PER_BOX, SC_EXEC_PERSISTENT = 0, 1, 2
 SC_XFER_AUTO, SC_XFER_STAGED, SC_XFER_DIRECT = 0, 1, 2
 GHOST = 3
 NCONSTRAINTS = 7
@@ -130,6 +130,7 @@ def lib():
     L.sc_set_transfer_mode.argtypes = [P, I]
     L.sc_transfer_stats.argtypes = [P, DP, DP, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int)]
     L.sc_z4c_constraints_noalloc.argtypes = [P, P, ctypes.POINTER(ctypes.c_int), D, P]
+    L.sc_measure_fp64_peak.argtypes = [P, DP, DP, ctypes.POINTER(ctypes.c_int), DP]
     IP = ctypes.POINTER(ctypes.c_int)
     U64 = ctypes.c_ulonglong
     L.sc_server_create.argtypes = [ctypes.c_size_t, I, I, ctypes.POINTER(P)]
@@ -138,6 +139,7 @@ def lib():
     L.sc_server_poll.argtypes = [P, U64, IP, DP]
     L.sc_server_wait.argtypes = [P, U64, D, DP]
     L.sc_server_inject_alloc_failure.argtypes = [P, ctypes.c_long]
+    L.sc_server_set_merge.argtypes = [P, I]
     L.sc_server_read.argtypes = [P, U64, I, I, I, DP]
     L.sc_server_release.argtypes = [P, U64]
     L.sc_server_stats.argtypes = [P, DP, DP, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_size_t)]
@@ -223,6 +225,16 @@ def sc_z4c_constraints_noalloc(dev_state: int, dev_out: int, n: Sequence[int], h
     nn = (ctypes.c_int * 3)(*[int(v) for v in n])
     _check(lib().sc_z4c_constraints_noalloc(ctypes.c_void_p(dev_state), ctypes.c_void_p(dev_out), nn, float(h),
                                             ctypes.c_void_p(stream) if stream else None))
+
+
+def sc_measure_fp64_peak(stream: Optional[int] = None) -> dict:
+    """Measured FP64 issue rates of the current GPU (G instr/s) with its SM
+    count and maximum SM clock."""
+    a, b, mhz = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_int()
+    _check(lib().sc_measure_fp64_peak(ctypes.c_void_p(stream) if stream else None, ctypes.byref(a), ctypes.byref(b),
+                                      ctypes.byref(n), ctypes.byref(mhz)))
+    return {"dfma_g_per_s": a.value, "dadd_g_per_s": b.value, "sms": n.value, "sm_clock_mhz": mhz.value}
 
 
 def sc_footprint_estimate(h) -> int:
@@ -437,9 +449,9 @@ class Context:
 
     def sc_time_ghost_kernels(self, level: int, nrep: int = 5):
         ms = np.zeros(2)
-        cnt = (ctypes.c_long * 3)()
+        cnt = (ctypes.c_long * 4)()
         _check(lib().sc_time_ghost_kernels(self.ctx, level, nrep, _dp(ms), cnt))
-        return float(ms[0]), float(ms[1]), (cnt[0], cnt[1], cnt[2])
+        return float(ms[0]), float(ms[1]), (cnt[0], cnt[1], cnt[2], cnt[3])
 
     def sc_time_stage_kernels(self, level: int, nrep: int = 5) -> Tuple[float, float]:
         ms = np.zeros(2)
@@ -513,6 +525,10 @@ class Server:
         lat = ctypes.c_double()
         _check(lib().sc_server_wait(self.srv, ticket, float(timeout_s), ctypes.byref(lat)))
         return lat.value
+
+    def sc_server_set_merge(self, on: bool):
+        """Merge scalar-wave requests into one persistent launch per tick (default on)."""
+        _check(lib().sc_server_set_merge(self.srv, 1 if on else 0))
 
     def sc_server_inject_alloc_failure(self, k: int):
         _check(lib().sc_server_inject_alloc_failure(self.srv, int(k)))

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsubcyc.so")
-SOURCES = ["sc_host.cu", "sc_amr.cu", "sc_wave.cu", "sc_z4c.cu", "sc_noalloc.cu", "sc_server.cu"]
+SOURCES = ["sc_host.cu", "sc_amr.cu", "sc_wave.cu", "sc_z4c.cu", "sc_persist.cu", "sc_measure.cu", "sc_noalloc.cu", "sc_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", SRC]
@@ -38,7 +38,7 @@ def _stale(target: str, deps) -> bool:
 
 def build(verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    headers = [os.path.join(SRC, "sc_internal.h"), os.path.join(ROOT, "include", "subcyc.h")]
+    headers = [os.path.join(SRC, h) for h in ("sc_internal.h", "sc_device.cuh", "sc_persist.h")] + [os.path.join(ROOT, "include", "subcyc.h")]
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(SRC, s))]
     objs = []
     jobs = []

@@ -6,7 +6,7 @@
 // x fastest) through precomputed int32 offset lists.
 #include <math.h>
 
-#include "sc_internal.h"
+#include "sc_device.cuh"
 
 namespace sc {
 namespace {
@@ -20,241 +20,54 @@ inline int grid_for(long work, int threads) {
   return (int)b;
 }
 
-// Sec. II step 2: prolong y_n and the stage vectors the dense output reads
-// (k1..k4 for RK4; the pointers k1..k4 are the first nvec - 1 of them) of the
-// parent step to every refinement-boundary ghost cell of the fine level: tensor-product quintic
-// Lagrange interpolation from 6x6x6 parent cells.  One thread per
-// (ghost cell, field); results go to store[(v * F + f) * ncells + cell].
+// Stand-alone kernels over the device-function bodies of sc_device.cuh
+// (one launch covers a whole work list; the persistent coarse-step kernel
+// runs the same bodies phase by phase).
 __global__ void __launch_bounds__(kThreads) amr_prolong_kernel(
     const double* __restrict__ yn, const double* __restrict__ k1, const double* __restrict__ k2,
     const double* __restrict__ k3, const double* __restrict__ k4, long pfs, int psy, int psz,
     const AmrCell* __restrict__ cells, int first, int ncells, double* __restrict__ store, int F, Weights w, int nvec) {
-  const int nc = ncells - first;
-  const long total = (long)nc * F;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int a = first + (int)(idx % nc);
-    const int f = (int)(idx / nc);
-    const AmrCell c = cells[a];
-    const double* wx = w.prolong[c.parity & 1];
-    const double* wy = w.prolong[(c.parity >> 1) & 1];
-    const double* wz = w.prolong[(c.parity >> 2) & 1];
-    const double* src[5] = {yn, k1, k2, k3, k4};
-#pragma unroll 1
-    for (int v = 0; v < nvec; ++v) {
-      const double* p = src[v] + (long)f * pfs + c.pbase;
-      double sz = 0.0;
-#pragma unroll
-      for (int kz = 0; kz < kPN; ++kz) {
-        double sy = 0.0;
-#pragma unroll
-        for (int ky = 0; ky < kPN; ++ky) {
-          const double* row = p + (long)kz * psz + (long)ky * psy;
-          double sx = 0.0;
-#pragma unroll
-          for (int kx = 0; kx < kPN; ++kx) sx = fma(wx[kx], __ldg(row + kx), sx);
-          sy = fma(wy[ky], sx, sy);
-        }
-        sz = fma(wz[kz], sy, sz);
-      }
-      store[((long)v * F + f) * ncells + a] = sz;
-    }
-  }
+  amr_prolong_cells_body(yn, k1, k2, k3, k4, pfs, psy, psz, cells, first, ncells, store, F, w, nvec, blockIdx.x,
+                         gridDim.x);
 }
 
-
-// Separable form of the same interpolation for 4x4x4 fine blocks: one group
-// of 64 threads per (block, vector, field) stages the 8x8x8 parent region in
-// shared memory and interpolates along x, then y, then z (42 FMAs per fine
-// position instead of 258).  The order of operations per fine position is
-// the same as in amr_prolong_kernel (x sums, then y, then z), so both paths
-// give identical results.
-__global__ void __launch_bounds__(256) amr_prolong_block_kernel(
+__global__ void __launch_bounds__(256) amr_prolong_tile_kernel(
     const double* __restrict__ yn, const double* __restrict__ k1, const double* __restrict__ k2,
     const double* __restrict__ k3, const double* __restrict__ k4, long pfs, int psy, int psz,
-    const AmrBlock* __restrict__ blocks, int nblocks, int ncells, double* __restrict__ store, int F, Weights w,
-    int nvec) {
-  __shared__ double sP[4][512];
-  __shared__ double sX[4][256];
-  __shared__ double sY[4][128];
-  const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
-  const int combos = nvec * F;
-  const int ngroups = (combos + 3) / 4;
-  const long items = (long)nblocks * ngroups;
-  for (long item = blockIdx.x; item < items; item += gridDim.x) {
-    const int b = (int)(item / ngroups);
-    const int combo = (int)(item % ngroups) * 4 + grp;
-    const bool active = combo < combos;
-    const AmrBlock B = blocks[b];
-    const int v = active ? combo / F : 0, f = active ? combo % F : 0;
-    if (active) {
-      const double* base = (v == 0 ? yn : v == 1 ? k1 : v == 2 ? k2 : v == 3 ? k3 : k4) + (long)f * pfs + B.pbase;
-#pragma unroll
-      for (int q = t; q < 512; q += 64) sP[grp][q] = __ldg(base + (long)(q >> 6) * psz + (long)((q >> 3) & 7) * psy + (q & 7));
-    }
-    __syncthreads();
-    if (active) {  // x: row (y, z) = (t & 7, t >> 3), 4 fine x positions
-      const double* row = &sP[grp][t * 8];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int p = i & 1, o = (i >> 1) + p;
-        double s = 0.0;
-#pragma unroll
-        for (int m = 0; m < kPN; ++m) s = fma(w.prolong[p][m], row[o + m], s);
-        sX[grp][t * 4 + i] = s;  // [z][y][fx]
-      }
-    }
-    __syncthreads();
-    if (active) {  // y: z node = t >> 3, fx = t & 3, fine y pair (t >> 2) & 1
-      const int z = t >> 3, fx = t & 3, jp = (t >> 2) & 1;
-#pragma unroll
-      for (int jj = 0; jj < 2; ++jj) {
-        const int j = 2 * jp + jj, p = j & 1, o = (j >> 1) + p;
-        double s = 0.0;
-#pragma unroll
-        for (int m = 0; m < kPN; ++m) s = fma(w.prolong[p][m], sX[grp][(z * 8 + o + m) * 4 + fx], s);
-        sY[grp][(z * 4 + j) * 4 + fx] = s;  // [z][fy][fx]
-      }
-    }
-    __syncthreads();
-    if (active && ((B.mask >> t) & 1ull)) {  // z: fine position t = fx + 4 fy + 16 fz
-      const int fx = t & 3, fy = (t >> 2) & 3, fz = t >> 4, p = fz & 1, o = (fz >> 1) + p;
-      double s = 0.0;
-#pragma unroll
-      for (int m = 0; m < kPN; ++m) s = fma(w.prolong[p][m], sY[grp][((o + m) * 4 + fy) * 4 + fx], s);
-      const int slot = B.slot0 + __popcll(B.mask & ((1ull << t) - 1ull));
-      store[((long)v * F + f) * ncells + slot] = s;
-    }
-    __syncthreads();
-  }
+    const AmrTile* __restrict__ tiles, int ntiles, const int32_t* __restrict__ slots, int ncells,
+    double* __restrict__ store, int F, Weights w, int nvec) {
+  __shared__ double sm[2 * kProlongSmemPerGroup];
+  amr_prolong_tiles_body(yn, k1, k2, k3, k4, pfs, psy, psz, tiles, ntiles, slots, ncells, store, F, w, nvec,
+                         blockIdx.x, gridDim.x, sm, 2);
 }
 
-// Sec. II steps 3/5: ghost value = P[y_n] + sum_j c_j P[k_j] over the nk
-// prolonged stage vectors in the store (4 for RK4, 3 for RK3, 2 for RK2, 0
-// for a plain prolonged value); the coefficients encode dense output (Eqs.
-// denseoutput1/2) and the Taylor stage formulas (Eqs. Y1-Y4) for one stage of
-// one fine substep.
 __global__ void __launch_bounds__(kThreads) amr_apply_kernel(double* __restrict__ vec, long fs, int F,
                                                             const AmrCell* __restrict__ cells, int ncells,
                                                             const double* __restrict__ store, double c1,
                                                             double c2, double c3, double c4, int nk) {
-  const long total = (long)ncells * F;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int a = (int)(idx % ncells);
-    const int f = (int)(idx / ncells);
-    const long n = ncells;
-    const double* s = store + (long)f * n + a;
-    const long vs = (long)F * n;
-    double v = s[0];
-    if (nk > 0) v = fma(c1, s[vs], v);
-    if (nk > 1) v = fma(c2, s[2 * vs], v);
-    if (nk > 2) v = fma(c3, s[3 * vs], v);
-    if (nk > 3) v = fma(c4, s[4 * vs], v);
-    vec[(long)f * fs + cells[a].dst] = v;
-  }
+  amr_apply_body(vec, fs, F, cells, ncells, store, c1, c2, c3, c4, nk, blockIdx.x, gridDim.x);
 }
 
-// Sec. II step 7: every parent cell whose eight children are fine interior
-// cells takes the tensor-product quintic interpolant of the 6x6x6 fine cells
-// centred on it.
 __global__ void __launch_bounds__(kThreads) restrict_kernel(double* __restrict__ parent, long pfs,
                                                            const double* __restrict__ fine, long ffs, int fsy,
                                                            int fsz, const RestrictCell* __restrict__ cells,
                                                            int ncells, int F, Weights w) {
-  const long total = (long)ncells * F;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int a = (int)(idx % ncells);
-    const int f = (int)(idx / ncells);
-    const RestrictCell c = cells[a];
-    const double* p = fine + (long)f * ffs + c.fbase;
-    double sz = 0.0;
-#pragma unroll
-    for (int kz = 0; kz < kRN; ++kz) {
-      double sy = 0.0;
-#pragma unroll
-      for (int ky = 0; ky < kRN; ++ky) {
-        const double* row = p + (long)kz * fsz + (long)ky * fsy;
-        double sx = 0.0;
-#pragma unroll
-        for (int kx = 0; kx < kRN; ++kx) sx = fma(w.restrict_w[kx], __ldg(row + kx), sx);
-        sy = fma(w.restrict_w[ky], sx, sy);
-      }
-      sz = fma(w.restrict_w[kz], sy, sz);
-    }
-    parent[(long)f * pfs + c.dst] = sz;
-  }
+  restrict_cells_body(parent, pfs, fine, ffs, fsy, fsz, cells, ncells, F, w, blockIdx.x, gridDim.x);
 }
 
-// Separable form of the same restriction for 4x4x4 parent blocks: one group
-// of 64 threads per (block, field) stages the 12x12x12 fine region in shared
-// memory and sums along x, then y, then z (78 FMAs per parent cell instead of
-// 216).  Each parent value is the same chain of fused multiply-adds as in
-// restrict_kernel (x sums, then y, then z, each from zero in stencil order),
-// so both give identical results.
 __global__ void __launch_bounds__(128) restrict_block_kernel(double* __restrict__ parent, long pfs, int psy,
                                                             int psz, const double* __restrict__ fine, long ffs,
                                                             int fsy, int fsz,
                                                             const RestrictBlock* __restrict__ blocks, int nblocks,
                                                             int F, Weights w) {
-  __shared__ double sF[2][1728];
-  __shared__ double sX[2][576];
-  __shared__ double sY[2][192];
-  const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
-  const long items = (long)nblocks * F;
-  const long pairs = (items + 1) / 2;
-  for (long it = blockIdx.x; it < pairs; it += gridDim.x) {
-    const long item = it * 2 + grp;
-    const bool active = item < items;
-    const int b = active ? (int)(item / F) : 0, f = active ? (int)(item % F) : 0;
-    const RestrictBlock B = blocks[b];
-    if (active) {
-      const double* src = fine + (long)f * ffs + B.fbase;
-      for (int q = t; q < 1728; q += 64) {
-        const int z = q / 144, y = (q / 12) % 12, x = q % 12;
-        sF[grp][q] = __ldg(src + (long)z * fsz + (long)y * fsy + x);
-      }
-    }
-    __syncthreads();
-    if (active) {  // x: row (z, y) of the fine region, parent px
-      for (int q = t; q < 576; q += 64) {
-        const int z = q / 48, y = (q / 4) % 12, px = q % 4;
-        const double* row = &sF[grp][(z * 12 + y) * 12 + 2 * px];
-        double sx = 0.0;
-#pragma unroll
-        for (int m = 0; m < kRN; ++m) sx = fma(w.restrict_w[m], row[m], sx);
-        sX[grp][q] = sx;  // [z][y][px]
-      }
-    }
-    __syncthreads();
-    if (active) {  // y: fine z, parent (py, px)
-      for (int q = t; q < 192; q += 64) {
-        const int z = q / 16, py = (q / 4) % 4, px = q % 4;
-        double sy = 0.0;
-#pragma unroll
-        for (int m = 0; m < kRN; ++m) sy = fma(w.restrict_w[m], sX[grp][(z * 12 + 2 * py + m) * 4 + px], sy);
-        sY[grp][q] = sy;  // [z][py][px]
-      }
-    }
-    __syncthreads();
-    if (active && ((B.mask >> t) & 1ull)) {  // z: parent cell t = px + 4 py + 16 pz
-      const int pz = t >> 4, py = (t >> 2) & 3, px = t & 3;
-      double sz = 0.0;
-#pragma unroll
-      for (int m = 0; m < kRN; ++m) sz = fma(w.restrict_w[m], sY[grp][((2 * pz + m) * 4 + py) * 4 + px], sz);
-      parent[(long)f * pfs + B.pbase + (long)pz * psz + (long)py * psy + px] = sz;
-    }
-    __syncthreads();
-  }
+  __shared__ double sm[2 * kRestrictSmemPerGroup];
+  restrict_blocks_body(parent, pfs, psy, psz, fine, ffs, fsy, fsz, blocks, nblocks, F, w, blockIdx.x, gridDim.x, sm,
+                       2);
 }
 
 __global__ void __launch_bounds__(kThreads) periodic_copy_kernel(double* __restrict__ vec, long fs, int F,
                                                                 const int2* __restrict__ pairs, int npairs) {
-  const long total = (long)npairs * F;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int a = (int)(idx % npairs);
-    const int f = (int)(idx / npairs);
-    const int2 p = pairs[a];
-    vec[(long)f * fs + p.x] = vec[(long)f * fs + p.y];
-  }
+  periodic_copy_body(vec, fs, F, pairs, npairs, blockIdx.x, gridDim.x);
 }
 
 struct IdParams {
@@ -440,16 +253,7 @@ __global__ void __launch_bounds__(kThreads) pack_fields_kernel(double* __restric
 __global__ void __launch_bounds__(kThreads) nonfinite_kernel(const double* __restrict__ vec, long fs, int F,
                                                             const Tile* __restrict__ tiles, int ntiles,
                                                             int sy, int sz, int* flag) {
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const Tile T = tiles[t];
-    const int n = T.nx * T.ny * T.nz;
-    for (int q = threadIdx.x; q < n * F; q += blockDim.x) {
-      const int f = q / n, c = q % n;
-      const int i = c % T.nx, j = (c / T.nx) % T.ny, k = c / (T.nx * T.ny);
-      const double v = vec[(long)f * fs + (long)(T.z0 + k) * sz + (long)(T.y0 + j) * sy + T.x0 + i];
-      if (!isfinite(v)) atomicOr(flag, 1);
-    }
-  }
+  nonfinite_body(vec, fs, F, tiles, ntiles, sy, sz, flag, blockIdx.x, gridDim.x);
 }
 
 }  // namespace
@@ -463,15 +267,15 @@ cudaError_t launch_amr_prolong(const double* yn, const double* k1, const double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_amr_prolong_blocks(const double* yn, const double* k1, const double* k2, const double* k3,
-                                      const double* k4, long pfs, int psy, int psz, const AmrBlock* blocks,
-                                      int nblocks, int ncells, double* store, int F, const Weights& w,
-                                      cudaStream_t s, int nvec) {
-  if (nblocks == 0) return cudaSuccess;
-  const long items = (long)nblocks * ((nvec * F + 3) / 4);
-  const int grid = (int)(items < 152L * 8 * 16 ? items : 152L * 8 * 16);
-  amr_prolong_block_kernel<<<grid, 256, 0, s>>>(yn, k1, k2, k3, k4, pfs, psy, psz, blocks, nblocks, ncells, store, F,
-                                                w, nvec);
+cudaError_t launch_amr_prolong_tiles(const double* yn, const double* k1, const double* k2, const double* k3,
+                                     const double* k4, long pfs, int psy, int psz, const AmrTile* tiles, int ntiles,
+                                     const int32_t* slots, int ncells, double* store, int F, const Weights& w,
+                                     cudaStream_t s, int nvec) {
+  if (ntiles == 0) return cudaSuccess;
+  const long items = (long)ntiles * ((nvec * F + 1) / 2);
+  const int grid = (int)(items < 152L * 6 * 8 ? items : 152L * 6 * 8);
+  amr_prolong_tile_kernel<<<grid, 256, 0, s>>>(yn, k1, k2, k3, k4, pfs, psy, psz, tiles, ntiles, slots, ncells, store,
+                                               F, w, nvec);
   return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "sc_internal.h"
+#include "sc_persist.h"
 
 using namespace sc;
 
@@ -259,8 +260,10 @@ struct Level {
   std::vector<int> box_ptile_begin;
   AmrCell* amr = nullptr;
   int namr = 0;
-  AmrBlock* blocks = nullptr;
-  int nblocks = 0;
+  AmrTile* atiles = nullptr;  // separable-prolongation tiles and their position -> AMR index map
+  int natiles = 0;
+  int32_t* aslots = nullptr;
+  long tile_fmas = 0;
   RowSeg* dxy = nullptr;
   int ndxy = 0;
   double* eta = nullptr;  // per-element eta(r) (Z4c with the Sec. III.A profile), else null
@@ -330,6 +333,12 @@ struct sc_ctx {
   int eta_profile = 0;
   double eta_c = 0, eta_s = 0, eta_o = 0;
   std::vector<Op> plain_ops[2];  // per-box form: the schedule, run directly
+  // persistent form (scalar wave): the phase table of each parity (device and
+  // host copies), the grid it needs and the barrier of its launches
+  POp* pops[2] = {nullptr, nullptr};
+  std::vector<POp> host_pops[2];
+  long pwork[2] = {0, 0};
+  GridBarrier* bar = nullptr;
   // whole-state transfers: mode (SC_XFER_*) and the split timing of the last one
   int xfer_mode = SC_XFER_AUTO;
   cudaEvent_t xev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -410,6 +419,10 @@ sc_status validate(const sc_desc* d) {
     if (d->ncells0[q] < 1) return fail(SC_EINVAL, "ncells0 must be positive");
   if (d->outer_bc == SC_BC_RADIATIVE && d->nboxes[0] != 1) return fail(SC_EINVAL, "radiative boundary needs one level-0 box");
   if (d->eta_profile && !(d->eta_s > 0)) return fail(SC_EINVAL, "eta_s must be positive");
+  if (d->exec_mode != SC_EXEC_GRAPH && d->exec_mode != SC_EXEC_PER_BOX && d->exec_mode != SC_EXEC_PERSISTENT)
+    return fail(SC_EINVAL, "unknown exec_mode %d", d->exec_mode);
+  if (d->exec_mode == SC_EXEC_PERSISTENT && d->system != SC_WAVE)
+    return fail(SC_EINVAL, "the persistent coarse-step kernel is built for the scalar wave");
   int bi = 0;
   for (int l = 0; l < d->nlevels; ++l) {
     if (d->nboxes[l] < 1) return fail(SC_EINVAL, "level %d has no boxes", l);
@@ -433,9 +446,11 @@ struct HostLists {
   std::vector<Tile> ptiles;
   std::vector<AmrCell> amr;
   std::vector<int> amr_gi, amr_gw;  // unwrapped / wrapped global fine index per AMR cell
-  std::vector<AmrBlock> blocks;     // 4x4x4 fine blocks served by the separable kernel
+  std::vector<AmrTile> atiles;      // slab tiles served by the separable kernel
+  std::vector<int32_t> aslots;      // per tile position: AMR list index or -1
+  long tile_fmas = 0;               // FMAs of the tile kernel per (vector, field)
   std::vector<RowSeg> dxy;          // rows where D_x / D_y of the Hessian fields are stored
-  int namr_blocked = 0;             // AMR cells [0, namr_blocked) belong to blocks
+  int namr_blocked = 0;             // AMR cells [0, namr_blocked) belong to tiles
   std::vector<int2> periodic;
   std::vector<int32_t> phys;
   std::vector<RestrictCell> restr;   // restricted parent cells outside blocks
@@ -523,92 +538,109 @@ struct InteriorCount {
   }
 };
 
-// Group the refinement-boundary ghost cells of level l into 4x4x4 fine blocks
-// (aligned to multiples of 4 in the level's unwrapped index space) for the
-// separable prolongation kernel.  A block qualifies when all its ghost cells
-// wrap by the same periodic shift and the 8x8x8 parent region that covers the
-// stencils of all 64 fine positions lies inside the parent array.  Ghost
-// cells of qualifying blocks are reordered block by block (bit order
-// x + 4y + 16z inside a block); the remaining cells follow and use the
-// per-cell kernel.
-void group_amr_blocks(sc_ctx* c, int l, HostLists& hl) {
+// Tile the refinement-boundary ghost cells of level l for the separable
+// prolongation.  The ghost shell of every box is cut into six slabs -- the
+// low and high z slabs span the whole shell in x and y, the y slabs the
+// shell in x and the box in z, the x slabs the box in y and z -- and each
+// slab into tiles of at most 8 cells along its two long axes and the ghost
+// width along its thin axis.  A tile claims the ghost cells in it that no
+// earlier tile claimed and that wrap by the same periodic shift as its first
+// one; the kernel computes every position of the tile (its parent region must
+// lie in the parent array) and stores the claimed ones.  Claimed cells are
+// reordered tile by tile (x fastest within a tile); the others follow and use
+// the per-cell kernel.
+void build_amr_tiles(sc_ctx* c, int l, HostLists& hl) {
+  const Level& L = c->lev[l];
   const Level& P = c->lev[l - 1];
+  const Geom& g = L.g;
   const size_t n = hl.amr.size();
-  struct Key {
-    int b[3];
-    bool operator<(const Key& o) const {
-      if (b[2] != o.b[2]) return b[2] < o.b[2];
-      if (b[1] != o.b[1]) return b[1] < o.b[1];
-      return b[0] < o.b[0];
-    }
-  };
-  auto fdiv4 = [](int v) { return v >= 0 ? v / 4 : -((-v + 3) / 4); };
-  std::vector<std::pair<Key, size_t>> order(n);
+  std::vector<int32_t> at((size_t)g.ext[0] * g.ext[1] * g.ext[2], -1);  // AMR index of each array element
   for (size_t a = 0; a < n; ++a) {
-    Key k;
-    for (int q = 0; q < 3; ++q) k.b[q] = fdiv4(hl.amr_gi[3 * a + q]);
-    order[a] = {k, a};
+    const int gi[3] = {hl.amr_gi[3 * a], hl.amr_gi[3 * a + 1], hl.amr_gi[3 * a + 2]};
+    at[elem_index(g, gi)] = (int32_t)a;
   }
-  std::stable_sort(order.begin(), order.end(),
-                   [](const std::pair<Key, size_t>& x, const std::pair<Key, size_t>& y) { return x.first < y.first; });
-  std::vector<AmrCell> fast, slow;
-  std::vector<AmrBlock> blocks;
-  size_t i = 0;
-  while (i < n) {
-    size_t j = i;
-    while (j < n && !(order[i].first < order[j].first) && !(order[j].first < order[i].first)) ++j;
-    const size_t a0 = order[i].second;
-    int shift[3], borg[3];
-    bool ok = true;
-    for (int q = 0; q < 3; ++q) {
-      shift[q] = hl.amr_gw[3 * a0 + q] - hl.amr_gi[3 * a0 + q];
-      borg[q] = 4 * order[i].first.b[q] + shift[q];  // wrapped fine index of the block origin
-      if (borg[q] & 1) ok = false;
-    }
-    uint64_t mask = 0;
-    for (size_t t = i; t < j && ok; ++t) {
-      const size_t a = order[t].second;
-      int bit = 0, mul = 1;
+  auto shift_of = [&](size_t a, int q) { return hl.amr_gw[3 * a + q] - hl.amr_gi[3 * a + q]; };
+  std::vector<char> claimed(n, 0);
+  std::vector<AmrCell> fast;
+  fast.reserve(n);
+  hl.atiles.clear();
+  hl.aslots.clear();
+  const int G = c->ghost;
+  for (const sc_box& B : L.boxes) {
+    for (int sl = 0; sl < 6; ++sl) {
+      const int ax = 2 - sl / 2;  // thin axis: z, z, y, y, x, x
+      const bool high = sl & 1;
+      int lo[3], hi[3];
       for (int q = 0; q < 3; ++q) {
-        if (hl.amr_gw[3 * a + q] - hl.amr_gi[3 * a + q] != shift[q]) ok = false;
-        bit += (hl.amr_gi[3 * a + q] - 4 * order[i].first.b[q]) * mul;
-        mul *= 4;
+        // long axes below the thin one (x for the y slabs, x and y for the z
+        // slabs) span the shell, those above it span the box, so the six
+        // slabs partition the shell
+        const bool span_shell = q < ax;
+        lo[q] = span_shell ? B.lo[q] - G : B.lo[q];
+        hi[q] = span_shell ? B.hi[q] + G : B.hi[q];
       }
-      mask |= 1ull << bit;
+      lo[ax] = high ? B.hi[ax] + 1 : B.lo[ax] - G;
+      hi[ax] = high ? B.hi[ax] + G : B.lo[ax] - 1;
+      for (int z0 = lo[2]; z0 <= hi[2]; z0 += (ax == 2 ? G : 8))
+        for (int y0 = lo[1]; y0 <= hi[1]; y0 += (ax == 1 ? G : 8))
+          for (int x0 = lo[0]; x0 <= hi[0]; x0 += (ax == 0 ? G : 8)) {
+            const int t0[3] = {x0, y0, z0};
+            int ext[3];
+            for (int q = 0; q < 3; ++q) ext[q] = std::min(q == ax ? G : 8, hi[q] - t0[q] + 1);
+            // first unclaimed ghost cell of the tile fixes its periodic shift
+            long first = -1;
+            for (int k = 0; k < ext[2] && first < 0; ++k)
+              for (int j = 0; j < ext[1] && first < 0; ++j)
+                for (int i = 0; i < ext[0] && first < 0; ++i) {
+                  const int gi[3] = {x0 + i, y0 + j, z0 + k};
+                  const int32_t a = in_array(g, gi) ? at[elem_index(g, gi)] : -1;
+                  if (a >= 0 && !claimed[a]) first = a;
+                }
+            if (first < 0) continue;
+            int shift[3], par = 0, r0[3], r1[3];
+            for (int q = 0; q < 3; ++q) {
+              shift[q] = shift_of(first, q);
+              const int wo = t0[q] + shift[q];  // wrapped fine origin
+              const int p0 = wo & 1;
+              par |= p0 << q;
+              r0[q] = (wo >> 1) - 3 + p0;  // first parent node of the region
+              const int i = ext[q] - 1;
+              r1[q] = r0[q] + ((p0 + i) >> 1) + ((p0 + i) & 1) - p0 + kPN - 1;  // last node
+            }
+            if (!in_array(P.g, r0) || !in_array(P.g, r1)) continue;
+            // the kernel's shared-memory bounds (always met by slabs of
+            // extents <= 8 x 8 x 4; checked so that no tile can exceed them)
+            const long N[3] = {r1[0] - r0[0] + 1L, r1[1] - r0[1] + 1L, r1[2] - r0[2] + 1L};
+            if (N[0] * N[1] * N[2] > 800 || ext[0] * N[1] * N[2] > 640 || (long)ext[0] * ext[1] * N[2] > 512) continue;
+            hl.tile_fmas += 6 * (ext[0] * N[1] * N[2] + (long)ext[0] * ext[1] * N[2] + (long)ext[0] * ext[1] * ext[2]);
+            AmrTile T;
+            T.pbase = (int32_t)P.g.off(r0[0], r0[1], r0[2]);
+            T.slot_base = (int32_t)hl.aslots.size();
+            for (int q = 0; q < 3; ++q) T.ext[q] = (int8_t)ext[q];
+            T.par = (int8_t)par;
+            for (int k = 0; k < ext[2]; ++k)
+              for (int j = 0; j < ext[1]; ++j)
+                for (int i = 0; i < ext[0]; ++i) {
+                  const int gi[3] = {x0 + i, y0 + j, z0 + k};
+                  const int32_t a = in_array(g, gi) ? at[elem_index(g, gi)] : -1;
+                  bool take = a >= 0 && !claimed[a];
+                  for (int q = 0; q < 3 && take; ++q) take = shift_of(a, q) == shift[q];
+                  if (take) {
+                    claimed[a] = 1;
+                    hl.aslots.push_back((int32_t)fast.size());
+                    fast.push_back(hl.amr[a]);
+                  } else {
+                    hl.aslots.push_back(-1);
+                  }
+                }
+            hl.atiles.push_back(T);
+          }
     }
-    int lo[3], hi[3];
-    for (int q = 0; q < 3; ++q) {
-      lo[q] = borg[q] / 2 - 3;  // parent region [c0 - 3, c0 + 4]
-      hi[q] = borg[q] / 2 + 4;
-    }
-    if (ok && in_array(P.g, lo) && in_array(P.g, hi)) {
-      AmrBlock B;
-      B.pbase = (int32_t)P.g.off(lo[0], lo[1], lo[2]);
-      B.slot0 = (int32_t)fast.size();
-      B.mask = mask;
-      // cells in bit order
-      std::vector<std::pair<int, size_t>> bits;
-      for (size_t t = i; t < j; ++t) {
-        const size_t a = order[t].second;
-        int bit = 0, mul = 1;
-        for (int q = 0; q < 3; ++q) {
-          bit += (hl.amr_gi[3 * a + q] - 4 * order[i].first.b[q]) * mul;
-          mul *= 4;
-        }
-        bits.push_back({bit, a});
-      }
-      std::sort(bits.begin(), bits.end());
-      for (auto& pr : bits) fast.push_back(hl.amr[pr.second]);
-      blocks.push_back(B);
-    } else {
-      for (size_t t = i; t < j; ++t) slow.push_back(hl.amr[order[t].second]);
-    }
-    i = j;
   }
   hl.namr_blocked = (int)fast.size();
-  fast.insert(fast.end(), slow.begin(), slow.end());
+  for (size_t a = 0; a < n; ++a)
+    if (!claimed[a]) fast.push_back(hl.amr[a]);
   hl.amr.swap(fast);
-  hl.blocks.swap(blocks);
 }
 
 // Interior tiles of the stencil kernels: per box, tiles of shape tile[0..2]
@@ -720,7 +752,7 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
           }
         }
       }
-  if (l > 0 && !hl.amr.empty()) group_amr_blocks(c, l, hl);
+  if (l > 0 && !hl.amr.empty()) build_amr_tiles(c, l, hl);
   build_stencil_tiles(L, c->tile, hl.tiles);
   L.box_ptile_begin.clear();
   for (const sc_box& B : L.boxes) {
@@ -879,12 +911,13 @@ sc_status setup_level_device(sc_ctx* c, int l, HostLists& hl) {
   if ((st = level_upload(c, L, hl.tiles, &L.tiles)) || (st = level_upload(c, L, hl.amr, &L.amr)) ||
       (st = level_upload(c, L, hl.periodic, &L.periodic)) || (st = level_upload(c, L, hl.phys, &L.phys)) ||
       (st = level_upload(c, L, hl.restr, &L.restr)) || (st = level_upload(c, L, hl.rblocks, &L.rblocks)) ||
-      (st = level_upload(c, L, hl.blocks, &L.blocks)) ||
+      (st = level_upload(c, L, hl.atiles, &L.atiles)) || (st = level_upload(c, L, hl.aslots, &L.aslots)) ||
       (st = level_upload(c, L, hl.dxy, &L.dxy)) || (st = level_upload(c, L, hl.ptiles, &L.ptiles)))
     return st;
   L.ntiles = (int)hl.tiles.size();
   L.namr = (int)hl.amr.size();
-  L.nblocks = (int)hl.blocks.size();
+  L.natiles = (int)hl.atiles.size();
+  L.tile_fmas = hl.tile_fmas;
   L.nptiles = (int)hl.ptiles.size();
   L.ndxy = (int)hl.dxy.size();
   L.namr_blocked = hl.namr_blocked;
@@ -1070,7 +1103,8 @@ cudaError_t prolong_parent(sc_ctx* c, int l, const double* yn, cudaStream_t s) {
   const double* v[4] = {yn, yn, yn, yn};
   for (int j = 0; j < nk; ++j) v[j] = P.K[idx[j]];
   const int psy = P.g.pitch, psz = P.g.pitch * P.g.ext[1];
-  cudaError_t e = launch_amr_prolong_blocks(yn, v[0], v[1], v[2], v[3], P.g.fs, psy, psz, L.blocks, L.nblocks, L.namr,
+  cudaError_t e = launch_amr_prolong_tiles(yn, v[0], v[1], v[2], v[3], P.g.fs, psy, psz, L.atiles, L.natiles, L.aslots,
+                                           L.namr,
                                             L.amr_store, c->F, c->w, s, 1 + nk);
   if (e != cudaSuccess) return e;
   return launch_amr_prolong(yn, v[0], v[1], v[2], v[3], P.g.fs, psy, psz, L.amr, L.namr_blocked, L.namr, L.amr_store,
@@ -1089,7 +1123,7 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       // then an apply with zero k coefficients (exactly the prolonged value)
       const Level& P = c->lev[o.level - 1];
       const int psy = P.g.pitch, psz = P.g.pitch * P.g.ext[1];
-      CU(launch_amr_prolong_blocks(o.in, o.in, o.in, o.in, o.in, P.g.fs, psy, psz, L.blocks, L.nblocks, L.namr,
+      CU(launch_amr_prolong_tiles(o.in, o.in, o.in, o.in, o.in, P.g.fs, psy, psz, L.atiles, L.natiles, L.aslots, L.namr,
                                    L.amr_store, c->F, c->w, s, 1));
       CU(launch_amr_prolong(o.in, o.in, o.in, o.in, o.in, P.g.fs, psy, psz, L.amr, L.namr_blocked, L.namr, L.amr_store,
                             c->F, c->w, s, 1));
@@ -1160,8 +1194,154 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
 
 namespace {
 
+// Phase table of the persistent coarse-step kernel from the op list: each op
+// becomes the phase(s) that do what run_op launches for it.
+void persistent_phases(sc_ctx* c, const std::vector<Op>& ops, std::vector<POp>& out) {
+  out.clear();
+  int idx[4];
+  const int nk = dense_vectors(c->rk, idx);
+  for (const Op& o : ops) {
+    Level& L = c->lev[o.level];
+    const Geom& g = L.g;
+    POp p{};
+    p.F = c->F;
+    p.nk = -1;
+    switch (o.kind) {
+      case OP_PROLONG:
+      case OP_PROLONG_DIRECT: {
+        const Level& P = c->lev[o.level - 1];
+        p.kind = kPhaseProlong;
+        const double* v0 = o.kind == OP_PROLONG ? o.yn : o.in;
+        for (int j = 0; j < 5; ++j) p.pv[j] = v0;
+        if (o.kind == OP_PROLONG)
+          for (int j = 0; j < nk; ++j) p.pv[1 + j] = P.K[idx[j]];
+        p.nvec = o.kind == OP_PROLONG ? 1 + nk : 1;
+        p.pfs = P.g.fs;
+        p.psy = P.g.pitch;
+        p.psz = P.g.pitch * P.g.ext[1];
+        p.atiles = L.atiles;
+        p.natiles = L.natiles;
+        p.aslots = L.aslots;
+        p.amr = L.amr;
+        p.namr = L.namr;
+        p.namr_blocked = L.namr_blocked;
+        p.store = L.amr_store;
+        out.push_back(p);
+        if (o.kind == OP_PROLONG_DIRECT) {  // then the prolonged value itself (zero k coefficients)
+          POp q{};
+          q.kind = kPhaseFill;
+          q.F = c->F;
+          q.vec = o.out;
+          q.fs = g.fs;
+          q.amr = L.amr;
+          q.namr = L.namr;
+          q.store = L.amr_store;
+          q.nk = 0;
+          out.push_back(q);
+        }
+        break;
+      }
+      case OP_FILL:
+        p.kind = kPhaseFill;
+        p.vec = o.in;
+        p.fs = g.fs;
+        if (o.level > 0 && !o.no_amr) {
+          p.amr = L.amr;
+          p.namr = L.namr;
+          p.store = L.amr_store;
+          for (int j = 0; j < 4; ++j) p.c[j] = o.c[j];
+          p.nk = nk;
+        }
+        p.periodic = L.periodic;
+        p.nperiodic = L.nperiodic;
+        out.push_back(p);
+        break;
+      case OP_STAGE:
+        p.kind = kPhaseStage;
+        p.a.Y = o.in;
+        p.a.yn = o.yn;
+        p.a.k = L.K[o.stage - 1];
+        p.a.out = o.out;
+        p.a.k1 = L.K[0];
+        p.a.k2 = L.K[1];
+        p.a.k3 = L.K[2];
+        p.a.cdt = o.cdt;
+        p.a.c1dt = o.c1dt;
+        p.a.form = o.form;
+        p.a.stage = o.stage;
+        p.a.fs = g.fs;
+        p.a.sy = g.pitch;
+        p.a.sz = g.pitch * g.ext[1];
+        p.a.h = g.h;
+        p.a.eta = L.eta;
+        p.tiles = L.tiles;
+        p.ntiles = L.ntiles;
+        p.order = c->order;
+        p.phys = L.phys;
+        p.nphys = L.nphys;
+        p.system = c->system;
+        p.g = g;
+        out.push_back(p);
+        break;
+      case OP_RESTRICT: {
+        const Level& P = c->lev[o.level - 1];
+        p.kind = kPhaseRestrict;
+        p.parent = o.out;
+        p.ppfs = P.g.fs;
+        p.ppsy = P.g.pitch;
+        p.ppsz = P.g.pitch * P.g.ext[1];
+        p.fine = o.in;
+        p.ffs = g.fs;
+        p.fsy = g.pitch;
+        p.fsz = g.pitch * g.ext[1];
+        p.rblocks = L.rblocks;
+        p.nrblocks = L.nrblocks;
+        p.rcells = L.restr;
+        p.nrcells = L.nrestr;
+        out.push_back(p);
+        break;
+      }
+      case OP_CHECK:
+        p.kind = kPhaseCheck;
+        p.vec = o.in;
+        p.fs = g.fs;
+        p.tiles = L.tiles;
+        p.ntiles = L.ntiles;
+        p.a.sy = g.pitch;
+        p.a.sz = g.pitch * g.ext[1];
+        p.status = c->status;
+        out.push_back(p);
+        break;
+    }
+  }
+  // Fold a pure refinement-boundary fill (no periodic images) into the stage
+  // phase before it when the fill's buffer is not the stage's input: the
+  // fill writes ghost cells of the next stage input (or of the new state),
+  // which the stage neither reads nor writes, and reads only the ghost store
+  // an earlier phase prolonged.  One grid barrier fewer per stage.
+  std::vector<POp> merged;
+  for (const POp& q : out) {
+    if (q.kind == kPhaseFill && q.nk >= 0 && q.nperiodic == 0 && !merged.empty() &&
+        merged.back().kind == kPhaseStage && merged.back().nk < 0 && merged.back().a.Y != q.vec &&
+        merged.back().a.yn != q.vec) {
+      POp& st = merged.back();
+      st.vec = q.vec;
+      st.fs = q.fs;
+      st.amr = q.amr;
+      st.namr = q.namr;
+      st.store = q.store;
+      for (int j = 0; j < 4; ++j) st.c[j] = q.c[j];
+      st.nk = q.nk;
+      continue;
+    }
+    merged.push_back(q);
+  }
+  out.swap(merged);
+}
+
 // Build (or refresh) the coarse-step schedule of level-0 parity p: the op
-// list for the per-box form, else one CUDA graph captured from it.  An
+// list for the per-box form, the phase table for the persistent form, else
+// one CUDA graph captured from the op list.  An
 // existing executable graph is updated in place when the new capture has the
 // same topology (the usual case after a regrid: same levels, same phases,
 // new work lists and sizes), which is much cheaper than instantiating.
@@ -1179,6 +1359,21 @@ sc_status build_schedule(sc_ctx* c, int p) {
       o.in = c->lev[l].S[em.par[l]];
       em.ops.push_back(o);
     }
+  if (c->exec_mode == SC_EXEC_PERSISTENT) {
+    std::vector<POp>& ph = c->host_pops[p];
+    persistent_phases(c, em.ops, ph);
+    if (c->pops[p]) c->dfree(c->pops[p]);
+    c->pops[p] = (POp*)c->dalloc(sizeof(POp) * ph.size());
+    if (!c->pops[p]) return fail(SC_ENOMEM, "phase table allocation failed");
+    CU(cudaMemcpyAsync(c->pops[p], ph.data(), sizeof(POp) * ph.size(), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));  // the host vector stays, but keep uploads ordered before use
+    long work = 1;
+    for (const POp& q : ph) work = std::max(work, phase_work_blocks(q));
+    c->pwork[p] = work;
+    c->launches_per_step = 1;
+    c->graph_stale[p] = false;
+    return SC_OK;
+  }
   if (c->exec_mode == SC_EXEC_PER_BOX) {
     c->plain_ops[p] = em.ops;
     long n = 0;
@@ -1187,11 +1382,11 @@ sc_status build_schedule(sc_ctx* c, int p) {
       if (o.kind == OP_STAGE)
         n += (long)L.boxes.size() * (c->system == SC_Z4C ? 2 : 1) + (c->system == SC_Z4C ? 1 : 0) + (L.nphys ? 1 : 0);
       else if (o.kind == OP_PROLONG)
-        n += (L.nblocks ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0);
+        n += (L.natiles ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0);
       else if (o.kind == OP_FILL)
         n += (o.level > 0 && L.namr && !o.no_amr ? 1 : 0) + (L.nperiodic ? 1 : 0);
       else if (o.kind == OP_PROLONG_DIRECT)
-        n += (L.nblocks ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0) + (L.namr ? 1 : 0);
+        n += (L.natiles ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0) + (L.namr ? 1 : 0);
       else if (o.kind == OP_CHECK)
         n += L.ntiles ? 1 : 0;
       else
@@ -1687,7 +1882,7 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
   c->cfl = d->cfl;
   c->zp = Z4cParams{d->kappa1, d->kappa2, d->eta, d->ko_sigma};
   c->stream = (cudaStream_t)d->cuda_stream;
-  c->exec_mode = d->exec_mode == SC_EXEC_PER_BOX ? SC_EXEC_PER_BOX : SC_EXEC_GRAPH;
+  c->exec_mode = d->exec_mode;
   c->subcycle = d->subcycle;
   c->order = d->fd_order == 8 ? 8 : 4;
   c->ghost = c->order == 8 ? 4 : 3;
@@ -1736,11 +1931,13 @@ sc_status sc_create(const sc_desc* d, sc_ctx** out) {
   }
   c->flag = (int*)c->dalloc(sizeof(int));
   c->status = (int*)c->dalloc(sizeof(int));
-  if (!c->flag || !c->status) {
+  c->bar = (GridBarrier*)c->dalloc(sizeof(GridBarrier));
+  if (!c->flag || !c->status || !c->bar) {
     c->release();
     return fail(SC_ENOMEM, "flag allocation failed");
   }
   e0 = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if (e0 == cudaSuccess) e0 = cudaMemsetAsync(c->bar, 0, sizeof(GridBarrier), c->stream);
   if (e0 != cudaSuccess) {
     c->release();
     return fail(SC_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e0));
@@ -1915,14 +2112,25 @@ sc_status sc_transfer_stats(sc_ctx* c, double* copy_ms, double* kernel_ms, size_
 sc_status sc_advance(sc_ctx* c, int n) {
   if (!c) return fail(SC_EINVAL, "null context");
   if (n < 0) return fail(SC_EINVAL, "negative step count");
-  const int L = c->nlev;
   for (int s = 0; s < n; ++s) {
     Level& L0 = c->lev[0];
     if (c->graph_stale[L0.parity]) {
       sc_status st = build_schedule(c, L0.parity);
       if (st != SC_OK) return st;
     }
-    if (c->exec_mode == SC_EXEC_PER_BOX) {
+    if (c->exec_mode == SC_EXEC_PERSISTENT) {
+      PBatch b{};
+      b.n = 1;
+      b.nops = (int)c->host_pops[L0.parity].size();
+      b.bar = c->bar;
+      b.w = c->w;
+      b.ops[0] = c->pops[L0.parity];
+      b.status[0] = c->status;
+      b.nops_r[0] = b.nops;
+      int maxb = 0;
+      CU(persistent_max_blocks(&maxb));
+      CU(launch_persistent_step(b, (int)std::min<long>(c->pwork[L0.parity], maxb), c->stream));
+    } else if (c->exec_mode == SC_EXEC_PER_BOX) {
       for (const Op& o : c->plain_ops[L0.parity]) {
         sc_status st = run_op(c, o, c->stream);
         if (st != SC_OK) return st;
@@ -1930,16 +2138,40 @@ sc_status sc_advance(sc_ctx* c, int n) {
     } else {
       CU(cudaGraphLaunch(c->graph[L0.parity], c->stream));
     }
-    // level 0 takes one step per coarse step when subcycling, 2^(L-1) otherwise
-    if (c->subcycle || L == 1) L0.parity ^= 1;
-    c->t += L0.dt;
-    for (int l = 0; l < L; ++l) {
-      c->zu_finest += (double)(1L << (L - 1)) * (double)c->lev[l].interior_cells;
-      c->zu_actual += (double)(c->subcycle ? (1L << l) : (1L << (L - 1))) * (double)c->lev[l].interior_cells;
-    }
+    sc::persistent_step_done(c);
   }
   return SC_OK;
 }
+
+}  // extern "C"
+
+void sc::persistent_step_done(sc_ctx* c) {
+  const int L = c->nlev;
+  Level& L0 = c->lev[0];
+  // level 0 takes one step per coarse step when subcycling, 2^(L-1) otherwise
+  if (c->subcycle || L == 1) L0.parity ^= 1;
+  c->t += L0.dt;
+  for (int l = 0; l < L; ++l) {
+    c->zu_finest += (double)(1L << (L - 1)) * (double)c->lev[l].interior_cells;
+    c->zu_actual += (double)(c->subcycle ? (1L << l) : (1L << (L - 1))) * (double)c->lev[l].interior_cells;
+  }
+}
+
+sc_status sc::persistent_view(sc_ctx* c, PersistView* v) {
+  if (!c || !v || c->exec_mode != SC_EXEC_PERSISTENT) return fail(SC_EINVAL, "not a persistent-form context");
+  const int p = c->lev[0].parity;
+  if (c->graph_stale[p]) {
+    sc_status st = build_schedule(c, p);
+    if (st != SC_OK) return st;
+  }
+  v->ops = c->pops[p];
+  v->host = &c->host_pops[p];
+  v->status = c->status;
+  v->w = c->w;
+  return SC_OK;
+}
+
+extern "C" {
 
 // Read and clear the device status word after the stream is idle.
 sc_status read_status(sc_ctx* c) {
@@ -2138,8 +2370,9 @@ sc_status sc_time_ghost_kernels(sc_ctx* c, int level, int nrep, double* ms, long
   ms[0] = t0 / nrep;
   ms[1] = t1 / nrep;
   counts[0] = L.namr;
-  counts[1] = L.nblocks;
+  counts[1] = L.natiles;
   counts[2] = L.namr - L.namr_blocked;
+  counts[3] = L.tile_fmas;
   return SC_OK;
 }
 

@@ -50,16 +50,18 @@ struct AmrCell {
   int32_t parity;
 };
 
-// A 4x4x4 block of fine cells (first fine index even, aligned to 4 in the
-// unwrapped index space) whose refinement-boundary ghost cells are prolonged
-// together: pbase = offset of the first cell of the 8x8x8 parent region
-// [c0-3, c0+4]^3 in the parent array (c0 = parent of the block's first cell),
-// slot0 = store slot of the block's first ghost cell, mask bit x + 4y + 16z
-// set for each fine position that is a ghost cell (slots follow bit order).
-struct AmrBlock {
+// A tile of refinement-boundary ghost positions prolonged together by the
+// separable kernel: extents ext[3] (at most 8 per axis, at most 4 along its
+// thin axis), bit d of par = parity of the wrapped fine index of its first
+// position along axis d, pbase = offset of the first parent node of the
+// region its stencils cover, and slots[slot_base + (k * ext[1] + j) * ext[0]
+// + i] = the store slot (AMR list index) of position (i, j, k), or -1 for a
+// position that is computed but not stored.
+struct AmrTile {
   int32_t pbase;
-  int32_t slot0;
-  unsigned long long mask;
+  int32_t slot_base;
+  int8_t ext[3];
+  int8_t par;
 };
 
 // Restricted parent cell: its offset in the parent array and the offset of
@@ -186,11 +188,11 @@ cudaError_t launch_periodic_copy(double* vec, long fs, int F, const int2* pairs,
 cudaError_t launch_amr_prolong(const double* yn, const double* k1, const double* k2, const double* k3,
                                const double* k4, long pfs, int psy, int psz, const AmrCell* cells, int first,
                                int ncells, double* store, int F, const Weights& w, cudaStream_t s, int nvec = 5);
-// block-separable prolongation of the ghost cells grouped in 4x4x4 blocks
-cudaError_t launch_amr_prolong_blocks(const double* yn, const double* k1, const double* k2, const double* k3,
-                                      const double* k4, long pfs, int psy, int psz, const AmrBlock* blocks,
-                                      int nblocks, int ncells, double* store, int F, const Weights& w,
-                                      cudaStream_t s, int nvec = 5);
+// separable prolongation of the ghost cells grouped in slab tiles
+cudaError_t launch_amr_prolong_tiles(const double* yn, const double* k1, const double* k2, const double* k3,
+                                     const double* k4, long pfs, int psy, int psz, const AmrTile* tiles, int ntiles,
+                                     const int32_t* slots, int ncells, double* store, int F, const Weights& w,
+                                     cudaStream_t s, int nvec = 5);
 cudaError_t launch_amr_apply(double* vec, long fs, int F, const AmrCell* cells, int ncells,
                              const double* store, const double* c4, cudaStream_t s, int nk = 4);
 cudaError_t launch_restrict(double* parent, long pfs, const double* fine, long ffs, int fsy, int fsz,

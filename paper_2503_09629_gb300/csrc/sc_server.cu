@@ -15,6 +15,16 @@
 // Device memory of requests comes from a stream-ordered pool
 // (cudaMallocAsync on the request's stream), so admission and release never
 // synchronise the whole device.
+//
+// Merged form (the default for scalar-wave requests): wave requests run in
+// the persistent coarse-step form, and each tick launches the next coarse
+// step of all of them together as one cooperative kernel on the server's
+// batch stream (phase i of every request between the same two grid
+// barriers), instead of one graph per request.  Z4c requests keep their
+// graphs on their own streams and overlap with the merged launches.  The
+// arithmetic of every request is unchanged (same device-function bodies), so
+// results stay bitwise those of the request running alone.
+#include <algorithm>
 #include <chrono>
 #include <deque>
 #include <thread>
@@ -24,6 +34,7 @@
 #include <vector>
 
 #include "sc_internal.h"
+#include "sc_persist.h"
 
 namespace {
 
@@ -87,6 +98,9 @@ struct sc_server {
   long launches = 0;
   double zu_finest_done = 0, zu_actual_done = 0;
   long fail_countdown = 0;  // sc_server_inject_alloc_failure
+  int merge = 1;            // merge scalar-wave requests into one persistent launch per tick
+  cudaStream_t batch_stream = nullptr;
+  sc::GridBarrier* bar = nullptr;
 };
 
 namespace {
@@ -101,6 +115,7 @@ sc_status admit(sc_server* S, Request* r, int slot) {
   r->desc.boxes = r->boxes.data();
   r->desc.cuda_stream = S->streams[slot];
   r->desc.allocator = &r->alloc;
+  if (S->merge && r->desc.system == SC_WAVE) r->desc.exec_mode = SC_EXEC_PERSISTENT;
   sc_status st = sc_create(&r->desc, &r->ctx);
   if (st != SC_OK) return st;
   st = sc_set_initial_data(r->ctx, r->id_kind, r->id_params.empty() ? nullptr : r->id_params.data(),
@@ -143,6 +158,10 @@ sc_status sc_server_create(size_t hbm_budget_bytes, int max_active, int depth, s
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e != cudaSuccess) return err(SC_ECUDA, cudaGetErrorString(e));
   }
+  cudaError_t e = cudaStreamCreateWithFlags(&S->batch_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&S->bar, sizeof(sc::GridBarrier));
+  if (e == cudaSuccess) e = cudaMemset(S->bar, 0, sizeof(sc::GridBarrier));
+  if (e != cudaSuccess) return err(SC_ECUDA, cudaGetErrorString(e));
   *out = S.release();
   return SC_OK;
 }
@@ -223,25 +242,69 @@ sc_status sc_server_tick(sc_server* S, int* n_active, int* n_queued, int* n_laun
     if (st != SC_OK) return st;
     if (r->steps == 0) finish(S, r);
   }
-  // 3. launch the next coarse step of every active request
+  // 3. launch the next coarse step of every active request: one graph per
+  // graph-form request on its stream, one merged launch for the
+  // persistent-form requests on the batch stream
   int active = 0;
+  std::vector<Request*> merged;
   for (auto& kv : S->all) {
     Request* r = kv.second.get();
     if (!r->ctx || r->done) continue;
     ++active;
-    if (r->launched < r->steps && (int)r->inflight.size() < S->depth) {
-      sc_status st = sc_advance(r->ctx, 1);
+    if (r->launched >= r->steps || (int)r->inflight.size() >= S->depth) continue;
+    if (r->desc.exec_mode == SC_EXEC_PERSISTENT) {
+      merged.push_back(r);
+      continue;
+    }
+    sc_status st = sc_advance(r->ctx, 1);
+    if (st != SC_OK) return st;
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return err(SC_ECUDA, cudaGetErrorString(e));
+    e = cudaEventRecord(ev, S->streams[r->slot]);
+    if (e != cudaSuccess) return err(SC_ECUDA, cudaGetErrorString(e));
+    r->inflight.push_back(ev);
+    ++r->launched;
+    long per = 0;
+    sc_launches_per_step(r->ctx, &per);
+    S->launches += per;
+    ++launched;
+  }
+  for (size_t first = 0; first < merged.size(); first += sc::kMaxBatch) {
+    const size_t n = std::min(merged.size() - first, (size_t)sc::kMaxBatch);
+    sc::PBatch b{};
+    b.n = (int)n;
+    b.bar = S->bar;
+    std::vector<long> work;
+    for (size_t q = 0; q < n; ++q) {
+      Request* r = merged[first + q];
+      sc::PersistView v{};
+      sc_status st = sc::persistent_view(r->ctx, &v);
       if (st != SC_OK) return st;
+      b.ops[q] = v.ops;
+      b.status[q] = v.status;
+      b.w = v.w;
+      b.nops_r[q] = (int)v.host->size();
+      b.nops = std::max(b.nops, b.nops_r[q]);
+      if (work.size() < v.host->size()) work.resize(v.host->size(), 0);
+      for (size_t i = 0; i < v.host->size(); ++i) work[i] += sc::phase_work_blocks((*v.host)[i]);
+    }
+    long need = 1;
+    for (long w : work) need = std::max(need, w);
+    int maxb = 0;
+    cudaError_t e = sc::persistent_max_blocks(&maxb);
+    if (e == cudaSuccess) e = sc::launch_persistent_step(b, (int)std::min<long>(need, maxb), S->batch_stream);
+    if (e != cudaSuccess) return err(SC_ECUDA, cudaGetErrorString(e));
+    S->launches += 1;
+    for (size_t q = 0; q < n; ++q) {
+      Request* r = merged[first + q];
+      sc::persistent_step_done(r->ctx);
       cudaEvent_t ev;
-      cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-      if (e != cudaSuccess) return err(SC_ECUDA, cudaGetErrorString(e));
-      e = cudaEventRecord(ev, S->streams[r->slot]);
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(ev, S->batch_stream);
       if (e != cudaSuccess) return err(SC_ECUDA, cudaGetErrorString(e));
       r->inflight.push_back(ev);
       ++r->launched;
-      long per = 0;
-      sc_launches_per_step(r->ctx, &per);
-      S->launches += per;
       ++launched;
     }
   }
@@ -274,6 +337,12 @@ sc_status sc_server_wait(sc_server* S, unsigned long long ticket, double timeout
       return err(SC_ETIMEOUT, "request not finished within the wait's time limit");
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
+}
+
+sc_status sc_server_set_merge(sc_server* S, int on) {
+  if (!S || (on != 0 && on != 1)) return err(SC_EINVAL, "bad merge argument");
+  S->merge = on;
+  return SC_OK;
 }
 
 sc_status sc_server_inject_alloc_failure(sc_server* S, long k) {
@@ -324,6 +393,7 @@ sc_status sc_server_stats(sc_server* S, double* zu_finest_done, double* zu_actua
 sc_status sc_server_destroy(sc_server* S) {
   if (!S) return SC_OK;
   for (auto& s : S->streams) cudaStreamSynchronize(s);
+  if (S->batch_stream) cudaStreamSynchronize(S->batch_stream);
   for (auto& kv : S->all) {
     Request* r = kv.second.get();
     for (auto ev : r->inflight) cudaEventDestroy(ev);
@@ -331,6 +401,8 @@ sc_status sc_server_destroy(sc_server* S) {
   }
   S->all.clear();
   for (auto& s : S->streams) cudaStreamDestroy(s);
+  if (S->batch_stream) cudaStreamDestroy(S->batch_stream);
+  if (S->bar) cudaFree(S->bar);
   delete S;
   return SC_OK;
 }

@@ -93,3 +93,31 @@ def test_per_box_form_equals_graph_form(sc, system):
         c.close()
     for a, b in zip(*res):
         assert np.array_equal(a, b)
+
+
+def test_merged_launches_equal_per_request_graphs(sc):
+    """Merged form (scalar-wave requests of a tick in one persistent launch)
+    against one graph per request on its own stream: bitwise the same
+    fields for every request of the mix; the merged server launches fewer
+    kernels."""
+    mix = _mix()
+    res, launches = {}, {}
+    for merge in (False, True):
+        srv = sc.Server(hbm_budget_bytes=64 << 30, max_active=8)
+        srv.sc_server_set_merge(merge)
+        tickets = [srv.sc_server_submit(h, s) for h, s in mix]
+        got = {}
+
+        def on_done(t, srv=srv, got=got, tickets=tickets):
+            h = mix[tickets.index(t)][0]
+            got[t] = _fields(lambda l, b, f: srv.sc_server_read(t, l, b, f), h)
+            srv.sc_server_release(t)
+
+        srv.run_until_done(tickets, timeout_s=300.0, on_done=on_done)
+        res[merge] = [got[t] for t in tickets]
+        launches[merge] = srv.sc_server_stats()["launches"]
+        srv.close()
+    for a, b in zip(res[False], res[True]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert launches[True] < launches[False]

@@ -1,0 +1,102 @@
+"""Z4c parity at full size against stored oracle values.
+
+The expected values were written by tests/golden/make_z4c_golden.py, which
+runs only the CPU oracle from the shared seeded inputs: sampled 8^3 blocks of
+all 22 fields of every level, taken from the ghosted box arrays (a corner and
+a face of every box with its ghost layers -- refinement-boundary ghosts filled
+by the dense output on refined levels, the evolved radiative shell on level
+0 --, the restricted centre of every level with a finer level, and the
+punctures on the finest level).  Cases: the 7-level benchmark hierarchy after
+2 coarse steps, and 3 levels of 48^3 after 16 coarse steps (the size of the
+largest Z4c requests of the serving ensemble).
+
+Tolerance: the Z4c bar, 1e-10 of the largest value of the field over the
+sampled blocks (floor 1e-14), element by element.
+
+A second test checks one refinement-boundary fill of the finest level of the
+benchmark hierarchy element by element: the oracle prolongs the GPU's own
+parent vectors (y_n, k1..k4 of the parent's last step) and applies the dense
+output and the Taylor stage formula of the first stage of the second substep
+(theta0 = 1/2, Sec. II Eqs. denseoutput1-Y4); the GPU's ghost values of that
+stage must match."""
+import os
+
+import numpy as np
+import pytest
+
+from helpers import init_arrays, load
+from paper_2503_09629_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def sc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2503_09629_gb300 as m
+    m.build()
+    return m
+
+
+def _case(name):
+    if name == "bl7_2steps":
+        return W.bl_7level()
+    return W.bl_3level(48)
+
+
+@pytest.mark.parametrize("name", ["bl3_48_16", "bl7_2steps"])
+def test_sampled_blocks_match_oracle(sc, name):
+    g = np.load(os.path.join(GOLDEN, f"z4c_{name}.npz"))
+    h = _case(name)
+    ctx = sc.Context(h)
+    load(ctx, h, init_arrays(h))
+    ctx.sc_advance(int(g["steps"]))
+    fin, act = ctx.sc_zone_updates()
+    assert np.array_equal([fin, act], g["zone_updates"])  # the same count of cell updates
+    meta, ref = g["meta"], g["blocks"]
+    scale = np.maximum(np.abs(ref).max(axis=(0, 2, 3, 4)), 1e-14)  # per field over all blocks
+    cache = {}
+    worst = 0.0
+    for (l, b, z, y, x), want in zip(meta, ref):
+        if (l, b) not in cache:
+            cache[(l, b)] = np.stack([ctx.sc_get_field(int(l), int(b), f, ghosted=True) for f in range(22)])
+        got = cache[(l, b)][:, z:z + 8, y:y + 8, x:x + 8]
+        rel = (np.abs(got - want).max(axis=(1, 2, 3)) / scale).max()
+        worst = max(worst, rel)
+        assert rel <= TOL, (name, int(l), int(b), (int(z), int(y), int(x)), rel)
+    ctx.close()
+    print(f"{name}: worst relative difference {worst:.3e} over {len(meta)} blocks")
+
+
+def test_finest_refinement_boundary_fill_matches_oracle(sc, orc):
+    h = W.bl_7level()
+    ctx = sc.Context(h)
+    ctx.sc_set_initial_data(h.id_kind, h.id_params)
+    ctx.sc_advance(1)
+    kw = h.kwargs()
+    o = orc.Oracle(h.system, h.boxes, h.ncells0, h.origin, h.h0, **kw)
+    P, F = 5, 6  # parent and fine level
+    # the parent's y_n (start of its last step) and k1..k4 of that step
+    for f in range(22):
+        o.set_vector(P, 0, orc.V_YOLD, f, ctx.sc_debug_get_vector(P, 0, 1, f, ghosted=True))
+        for j in range(4):
+            o.set_vector(P, 0, orc.V_K1 + j, f, ctx.sc_debug_get_vector(P, 0, 4 + j, f, ghosted=True))
+    o.prolong(F)
+    o.fill_amr(F, orc.V_Y, 0.5, 1)
+    g = h.ghost
+    for b in range(len(h.boxes[F])):
+        ghost = np.ones(o.shape(F, b, True), dtype=bool)
+        ghost[g:-g, g:-g, g:-g] = False  # every ghost cell of these boxes is a refinement-boundary ghost
+        for f in range(22):
+            want = o.get_vector(F, b, orc.V_Y, f)[ghost]
+            # GPU: the first stage of the level's last step read its ghosts from the state
+            # buffer that holds y_n of that step (vector 1 after the step)
+            got = ctx.sc_debug_get_vector(F, b, 1, f, ghosted=True)[ghost]
+            scale = max(np.abs(want).max(), 1e-14)
+            assert np.abs(got - want).max() <= TOL * scale, (b, f, np.abs(got - want).max() / scale)
+    ctx.close()
