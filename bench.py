@@ -268,7 +268,7 @@ def run_serving_arms(sc, W, n: int, max_active: int = 32):
              for arm in ("plain_per_box", "plain_graph", "served_streams", "served_merged")}
     ia = burst["plain_per_box"]["wall_s"] / n / 0.9
     poisson = {arm: run_ensemble(sc, W, n, 0, False, ia, arm, max_active=max_active)
-               for arm in ("plain_per_box", "plain_graph", "served_merged")}
+               for arm in ("plain_per_box", "plain_graph", "served_streams")}
     return {"requests": n, "burst": burst, "poisson_load_0.9_of_plain_per_box": poisson}
 
 
@@ -385,6 +385,27 @@ def study_wavekernel(sc, W, n: int = 256):
             "hbm_frac": cells * bpc / (ms * 1e-3) / 1e9 / HBM_GBS, "peaks": pk}
 
 
+def study_z4c3level(sc, W, steps: int, n: int = 64):
+    """Brill-Lindquist head-on on 3 nested levels of n^3 (n = 64: about 1.3 GB
+    of device state, more than L2): the small case the ncu captures of the
+    Z4c and refinement-boundary kernels run on."""
+    import torch
+    h = W.bl_3level(n)
+    ctx = sc.Context(h)
+    ctx.sc_set_initial_data(h.id_kind, h.id_params)
+    ctx.sc_advance(1)
+    ctx.sc_synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.sc_advance(steps)
+    e1.record()
+    ctx.sc_synchronize()
+    out = {"workload": h.name, "coarse_steps": steps, "ms_per_coarse_step": e0.elapsed_time(e1) / max(steps, 1),
+           "launches_per_coarse_step": ctx.sc_launches_per_step()}
+    ctx.close()
+    return out
+
+
 def run_study(args):
     import torch
 
@@ -396,6 +417,8 @@ def run_study(args):
         return study_moving(sc, W, args.study_steps)
     if args.study == "wavekernel":
         return study_wavekernel(sc, W)
+    if args.study == "z4c3level":
+        return study_z4c3level(sc, W, args.study_steps)
     return sc.sc_measure_fp64_peak()
 
 
@@ -702,9 +725,10 @@ def main():
                     help="finite-difference order of the Z4c right-hand side (8: the paper's production setting)")
     ap.add_argument("--cpu-aggregate", type=int, default=1,
                     help="1: also time the oracle on every host core at once (aggregate CPU baseline)")
-    ap.add_argument("--study", choices=["moving", "wavekernel", "fp64"],
+    ap.add_argument("--study", choices=["moving", "wavekernel", "fp64", "z4c3level"],
                     help="one study instead of the benchmark (moving: 9-level moving boxes; wavekernel: the wave "
-                         "stage kernel on one 256^3 level; fp64: the measured FP64 issue rates)")
+                         "stage kernel on one 256^3 level; fp64: the measured FP64 issue rates; z4c3level: "
+                         "3-level 64^3 Brill-Lindquist, the small case of the ncu captures)")
     ap.add_argument("--study-steps", type=int, default=32)
     ap.add_argument("--wave-forms", type=int, default=1,
                     help="1: time the scalar-wave workloads in the plain, graph and persistent forms")

@@ -527,7 +527,7 @@ class Server:
         return lat.value
 
     def sc_server_set_merge(self, on: bool):
-        """Merge scalar-wave requests into one persistent launch per tick (default on)."""
+        """Merge scalar-wave requests into one persistent launch per tick (default off)."""
         _check(lib().sc_server_set_merge(self.srv, 1 if on else 0))
 
     def sc_server_inject_alloc_failure(self, k: int):

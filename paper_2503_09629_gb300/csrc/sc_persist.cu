@@ -55,6 +55,7 @@ __device__ bool grid_barrier(GridBarrier* bar, unsigned nblocks) {
           good = 0;
           break;
         }
+        __nanosleep(20);
       }
     }
     __threadfence();

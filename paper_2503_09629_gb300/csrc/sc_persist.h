@@ -59,9 +59,14 @@ struct POp {
   int* status;
 };
 
+// Arrival count and generation of the grid barrier, on separate 128-byte
+// lines so that the waiting blocks' polls of the generation do not queue
+// behind the arrivals' atomics on the same line.
 struct GridBarrier {
   unsigned count;
+  unsigned pad0[31];
   unsigned gen;
+  unsigned pad1[31];
 };
 
 constexpr int kMaxBatch = 128;

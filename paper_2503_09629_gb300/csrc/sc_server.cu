@@ -16,7 +16,8 @@
 // (cudaMallocAsync on the request's stream), so admission and release never
 // synchronise the whole device.
 //
-// Merged form (the default for scalar-wave requests): wave requests run in
+// Merged form (sc_server_set_merge; off by default, because one graph per
+// request on its own stream measured faster on GB300): wave requests run in
 // the persistent coarse-step form, and each tick launches the next coarse
 // step of all of them together as one cooperative kernel on the server's
 // batch stream (phase i of every request between the same two grid
@@ -98,7 +99,7 @@ struct sc_server {
   long launches = 0;
   double zu_finest_done = 0, zu_actual_done = 0;
   long fail_countdown = 0;  // sc_server_inject_alloc_failure
-  int merge = 1;            // merge scalar-wave requests into one persistent launch per tick
+  int merge = 0;            // merge scalar-wave requests into one persistent launch per tick
   cudaStream_t batch_stream = nullptr;
   sc::GridBarrier* bar = nullptr;
 };
