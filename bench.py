@@ -385,12 +385,14 @@ def study_wavekernel(sc, W, n: int = 256):
             "hbm_frac": cells * bpc / (ms * 1e-3) / 1e9 / HBM_GBS, "peaks": pk}
 
 
-def study_z4c3level(sc, W, steps: int, n: int = 64):
+def study_z4c3level(sc, W, steps: int, n: int = 64, fd_order: int = 4):
     """Brill-Lindquist head-on on 3 nested levels of n^3 (n = 64: about 1.3 GB
     of device state, more than L2): the small case the ncu captures of the
-    Z4c and refinement-boundary kernels run on."""
+    Z4c and refinement-boundary kernels run on.  One untimed coarse step,
+    then `steps` timed ones."""
     import torch
     h = W.bl_3level(n)
+    h.fd_order = fd_order
     ctx = sc.Context(h)
     ctx.sc_set_initial_data(h.id_kind, h.id_params)
     ctx.sc_advance(1)
@@ -418,7 +420,7 @@ def run_study(args):
     if args.study == "wavekernel":
         return study_wavekernel(sc, W)
     if args.study == "z4c3level":
-        return study_z4c3level(sc, W, args.study_steps)
+        return study_z4c3level(sc, W, args.study_steps, fd_order=args.fd_order)
     return sc.sc_measure_fp64_peak()
 
 

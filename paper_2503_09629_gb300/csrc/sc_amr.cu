@@ -16,7 +16,7 @@ constexpr int kThreads = 256;
 inline int grid_for(long work, int threads) {
   long b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
-  if (b > 152L * 64) b = 152L * 64;  // grid-stride beyond 64 blocks per SM
+  if (b > sm_count() * 64L) b = sm_count() * 64L;  // grid-stride beyond 64 blocks per SM
   return (int)b;
 }
 
@@ -256,7 +256,17 @@ __global__ void __launch_bounds__(kThreads) nonfinite_kernel(const double* __res
   nonfinite_body(vec, fs, F, tiles, ntiles, sy, sz, flag, blockIdx.x, gridDim.x);
 }
 
+int g_sm_count[64];  // per device; 0 = not queried yet
+
 }  // namespace
+
+int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  int& n = g_sm_count[dev & 63];
+  if (n == 0 && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 152;
+  return n;
+}
 
 cudaError_t launch_amr_prolong(const double* yn, const double* k1, const double* k2, const double* k3,
                                const double* k4, long pfs, int psy, int psz, const AmrCell* cells, int first,
@@ -273,7 +283,8 @@ cudaError_t launch_amr_prolong_tiles(const double* yn, const double* k1, const d
                                      cudaStream_t s, int nvec) {
   if (ntiles == 0) return cudaSuccess;
   const long items = (long)ntiles * ((nvec * F + 1) / 2);
-  const int grid = (int)(items < 152L * 6 * 8 ? items : 152L * 6 * 8);
+  const long cap = sm_count() * 6L * 8;
+  const int grid = (int)(items < cap ? items : cap);
   amr_prolong_tile_kernel<<<grid, 256, 0, s>>>(yn, k1, k2, k3, k4, pfs, psy, psz, tiles, ntiles, slots, ncells, store,
                                                F, w, nvec);
   return cudaGetLastError();
@@ -300,7 +311,8 @@ cudaError_t launch_restrict_blocks(double* parent, long pfs, int psy, int psz, c
                                    cudaStream_t s) {
   if (nblocks == 0) return cudaSuccess;
   const long pairs = ((long)nblocks * F + 1) / 2;
-  const int grid = (int)(pairs < 152L * 10 ? pairs : 152L * 10);
+  const long cap = sm_count() * 10L;
+  const int grid = (int)(pairs < cap ? pairs : cap);
   restrict_block_kernel<<<grid, 128, 0, s>>>(parent, pfs, psy, psz, fine, ffs, fsy, fsz, blocks, nblocks, F, w);
   return cudaGetLastError();
 }
@@ -369,7 +381,7 @@ cudaError_t launch_pack_fields(double* vec, long fs, int F, const Geom& g, const
   if (rows == 0 || n[0] == 0) return cudaSuccess;
   const long warps_per_block = kThreads / 32;
   long blocks = (rows + warps_per_block - 1) / warps_per_block;
-  if (blocks > 152L * 16) blocks = 152L * 16;
+  if (blocks > sm_count() * 16L) blocks = sm_count() * 16L;
   pack_fields_kernel<<<(int)blocks, kThreads, 0, s>>>(vec, fs, F, g.pitch, g.ext[1], lo[0] - g.org[0], lo[1] - g.org[1],
                                                       lo[2] - g.org[2], n[0], n[1], n[2], buf, unpack);
   return cudaGetLastError();
@@ -378,7 +390,7 @@ cudaError_t launch_pack_fields(double* vec, long fs, int F, const Geom& g, const
 cudaError_t launch_nonfinite_check(const double* vec, long fs, int F, const Tile* tiles, int ntiles, int sy, int sz,
                                    int* flag, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
-  nonfinite_kernel<<<ntiles < 152 * 8 ? ntiles : 152 * 8, kThreads, 0, s>>>(vec, fs, F, tiles, ntiles, sy, sz, flag);
+  nonfinite_kernel<<<ntiles < sm_count() * 8 ? ntiles : sm_count() * 8, kThreads, 0, s>>>(vec, fs, F, tiles, ntiles, sy, sz, flag);
   return cudaGetLastError();
 }
 

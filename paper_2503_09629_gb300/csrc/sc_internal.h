@@ -158,6 +158,11 @@ struct Z4cParams {
 // Record a message for sc_last_error() and return code (defined in sc_host.cu).
 sc_status set_last_error(sc_status code, const char* msg);
 
+// Streaming multiprocessors of the current device (queried once per device;
+// the grid caps of the grid-stride and persistent launches are multiples of
+// it).  Defined in sc_amr.cu.
+int sm_count();
+
 // ---- kernel launchers (defined in the .cu files) -------------------------
 cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s, int order = 4);
 

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kThreads) radiative_stage_kernel(StageArgs a, 
 
 cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s, int order) {
   if (ntiles == 0) return cudaSuccess;
-  const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
+  const int grid = ntiles < sm_count() * 16 ? ntiles : sm_count() * 16;
   const FmaK K{1.0, -1.0, -0.0};
   if (order == 8) wave_stage_kernel<8><<<grid, kThreads, 0, s>>>(a, tiles, ntiles, K);
   else wave_stage_kernel<4><<<grid, kThreads, 0, s>>>(a, tiles, ntiles, K);
@@ -42,7 +42,7 @@ cudaError_t launch_radiative_stage(const StageArgs& a, const int32_t* cells, int
   if (ncells == 0) return cudaSuccess;
   const long work = (long)ncells * F;
   long grid = (work + kThreads - 1) / kThreads;
-  if (grid > 152 * 32) grid = 152 * 32;
+  if (grid > sm_count() * 32L) grid = sm_count() * 32L;
   radiative_stage_kernel<<<(int)grid, kThreads, 0, s>>>(a, cells, ncells, F, g, system);
   return cudaGetLastError();
 }

@@ -735,7 +735,7 @@ cudaError_t z4c_init_launch_config() {
 cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy, int sz, double h, const Tile* tiles,
                               int ntiles, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
-  const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
+  const int grid = ntiles < sm_count() * 16 ? ntiles : sm_count() * 16;
   z4c_derivs_kernel<<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles);
   return cudaGetLastError();
 }
@@ -779,7 +779,7 @@ cudaError_t launch_z4c_constraints(const double* Y, const double* scratch, doubl
                                    const Z4cParams& p, const Tile* tiles, int ntiles, long out_stride,
                                    const int* box_lo, const int* box_n, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
-  const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
+  const int grid = ntiles < sm_count() * 16 ? ntiles : sm_count() * 16;
   z4c_constraints_kernel<<<grid, 128, 0, s>>>(Y, scratch, out, fs, sy, sz, p, tiles, ntiles, out_stride, box_lo[0],
                                               box_lo[1], box_lo[2], box_n[0], box_n[1], FmaK{1.0, -1.0, -0.0});
   return cudaGetLastError();

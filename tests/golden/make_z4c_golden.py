@@ -18,7 +18,10 @@ ghosted box arrays, so that the samples cover
 Cases (names used by tests/test_gpu_z4c_fullsize.py):
   bl7_2steps   the 7-level benchmark hierarchy (64^3 base over [-32,32]^3,
                finest h = 1/64), 2 coarse steps: about an hour single-threaded;
-  bl3_48_16    3 levels of 48^3 over [-8,8]^3, 16 coarse steps: a few minutes.
+  bl3_48_16    3 levels of 48^3 over [-8,8]^3, 16 coarse steps: a few minutes;
+  bl3_32_16_unequal  3 levels of 32^3 over [-8,8]^3, masses 0.3 and 0.7 at
+               separation 6 (the smallest and most asymmetric Z4c requests of
+               the serving ensemble), 16 coarse steps: about two minutes.
 
 Usage: python tests/golden/make_z4c_golden.py [bl7_2steps|bl3_48_16 ...]
 Output: tests/golden/z4c_<case>.npz (block origins, fields, oracle time and
@@ -85,6 +88,8 @@ def case_hierarchy(name: str):
         return W.bl_7level(), 2
     if name == "bl3_48_16":
         return W.bl_3level(48), 16
+    if name == "bl3_32_16_unequal":
+        return W.bl_3level(32, 0.3, 0.7, 6.0), 16
     raise ValueError(name)
 
 
@@ -112,5 +117,5 @@ def make(name: str) -> str:
 
 
 if __name__ == "__main__":
-    for n in sys.argv[1:] or ["bl3_48_16", "bl7_2steps"]:
+    for n in sys.argv[1:] or ["bl3_48_16", "bl3_32_16_unequal", "bl7_2steps"]:
         make(n)

@@ -7,8 +7,9 @@ a face of every box with its ghost layers -- refinement-boundary ghosts filled
 by the dense output on refined levels, the evolved radiative shell on level
 0 --, the restricted centre of every level with a finer level, and the
 punctures on the finest level).  Cases: the 7-level benchmark hierarchy after
-2 coarse steps, and 3 levels of 48^3 after 16 coarse steps (the size of the
-largest Z4c requests of the serving ensemble).
+2 coarse steps, 3 levels of 48^3 after 16 coarse steps (the largest Z4c
+requests of the serving ensemble) and 3 levels of 32^3 with masses 0.3 and 0.7
+at separation 6 after 16 coarse steps (the smallest and most asymmetric).
 
 Tolerance: the Z4c bar, 1e-10 of the largest value of the field over the
 sampled blocks (floor 1e-14), element by element.
@@ -46,10 +47,12 @@ def sc():
 def _case(name):
     if name == "bl7_2steps":
         return W.bl_7level()
+    if name == "bl3_32_16_unequal":
+        return W.bl_3level(32, 0.3, 0.7, 6.0)
     return W.bl_3level(48)
 
 
-@pytest.mark.parametrize("name", ["bl3_48_16", "bl7_2steps"])
+@pytest.mark.parametrize("name", ["bl3_48_16", "bl3_32_16_unequal", "bl7_2steps"])
 def test_sampled_blocks_match_oracle(sc, name):
     g = np.load(os.path.join(GOLDEN, f"z4c_{name}.npz"))
     h = _case(name)
