@@ -407,7 +407,8 @@ sc_status sc_time_ghost_kernels(sc_ctx* ctx, int level, int nrep, double* ms, lo
  * bound by the FP64 pipe, whose rate depends on the operands).  Measures, on
  * the current device with CUDA events on cuda_stream, the issue rates of a
  * general FP64 fused multiply-add and of an FP64 addition (G instructions per
- * second, 8 independent chains per thread, 8 blocks of 256 threads per SM),
+ * second, 8 independent chains per thread, 8 blocks of 256 threads per SM,
+ * the best of three timed launches after an untimed one),
  * and reports the SM count and the maximum SM clock.  Allocates and frees a
  * small output buffer; synchronises.  Errors: SC_EINVAL, SC_ENOMEM, SC_ECUDA. */
 sc_status sc_measure_fp64_peak(void* cuda_stream, double* dfma_g_per_s, double* dadd_g_per_s, int* sms,
