@@ -459,6 +459,7 @@ def run_gpu(args, rank: int, world: int):
     fin_per_step, act_per_step = h.zone_updates_per_coarse_step()
     ctx = sc.Context(h)
     tile, _tune_ms = ctx.sc_autotune()
+    tuning = ctx.sc_get_tuning()
     ctx.sc_set_initial_data(h.id_kind, h.id_params)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -695,7 +696,7 @@ def run_gpu(args, rank: int, world: int):
                            "actual_zone_updates_per_step": act_per_step,
                            "actual_zone_updates_per_s": world * act_per_step / (ms_per_step * 1e-3),
                            "l2": "state ~5 GB per replica > 129 MB L2: inputs larger than L2, no flush",
-                           "stencil_tile": list(tile),
+                           "stencil_tile": list(tile), "tuning": tuning,
                            "state_finite_after_timed_steps": state_finite,
                            "parallelism": f"replicas{world}"},
                 "roofline": roofline, "cpu_baseline": cpu,

@@ -326,14 +326,28 @@ sc_status sc_regrid(sc_ctx* ctx, const int* nboxes, const sc_box* boxes);
  * no level holds it.  out: npts doubles (host).  Synchronises. */
 sc_status sc_interpolate(sc_ctx* ctx, int npts, const double* xyz, int field, double* out);
 
-/* Autotuner: time candidate tile shapes of the stencil kernel (Z4c
- * derivative pass, or the fused wave stage) on the context's largest level
- * with CUDA events on its stream, keep the fastest, rebuild the tile lists
- * and the coarse-step graphs.  The choice is cached for the process per
+/* Autotuner (no counterpart in the paper): on the context's largest level,
+ * with CUDA events on its stream, time the candidate tile shapes of the
+ * stencil kernel (the fused wave stage, or the Z4c derivative pass in its
+ * two-kernel form), the one-kernel Z4c derivative pass (4th order) and the
+ * Z4c stage kernel built for 2 and for 3 blocks per SM; keep the fastest
+ * derivative configuration and stage build, rebuild the tile lists and the
+ * coarse-step graphs.  The choice is cached for the process per
  * (system, box shapes of every level); a cached context skips the timing
  * (*ms_out = -1).  Overwrites only stage/scratch buffers that every coarse
  * step recomputes; call between sc_advance calls.  tile_out: 3 ints or NULL. */
 sc_status sc_autotune(sc_ctx* ctx, int* tile_out, double* ms_out);
+/* The tuning in effect (no counterpart in the paper): tile = 3 ints (tile
+ * shape of the stencil kernels), deriv_form = 0 (Z4c derivative pass as two
+ * kernels: D_x/D_y of the Hessian fields on rows, then the per-column pass
+ * that differentiates them for the mixed derivatives) or 1 (one kernel per
+ * cell and field with direct 16-point mixed stencils; Z4c at 4th order
+ * only), stage_blocks_per_sm = 2 or 3 (the Z4c stage kernel's build: 128-
+ * thread blocks per SM it is constrained to).  sc_set_tuning applies a
+ * choice made elsewhere (rebuilds the tile lists and graphs; call between
+ * sc_advance calls); SC_EINVAL for values outside those ranges. */
+sc_status sc_get_tuning(sc_ctx* ctx, int* tile, int* deriv_form, int* stage_blocks_per_sm);
+sc_status sc_set_tuning(sc_ctx* ctx, const int* tile, int deriv_form, int stage_blocks_per_sm);
 
 /* ---- serving: continuous batching of independent evolutions ---------------
  * The paper has no counterpart: this is the serving form of the method, many

@@ -119,6 +119,9 @@ def lib():
     L.sc_footprint_estimate.argtypes = [ctypes.POINTER(sc_desc), ctypes.POINTER(ctypes.c_size_t)]
     L.sc_time_stage_kernels.argtypes = [P, I, I, DP]
     L.sc_autotune.argtypes = [P, ctypes.POINTER(ctypes.c_int), DP]
+    L.sc_get_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int)]
+    L.sc_set_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int), I, I]
     L.sc_time_ghost_kernels.argtypes = [P, I, I, DP, ctypes.POINTER(ctypes.c_long)]
     L.sc_debug_get_vector.argtypes = [P, I, I, I, I, I, DP]
     L.sc_regrid.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(sc_box)]
@@ -403,6 +406,17 @@ class Context:
         ms = ctypes.c_double()
         _check(lib().sc_autotune(self.ctx, t, ctypes.byref(ms)))
         return (t[0], t[1], t[2]), ms.value
+
+    def sc_get_tuning(self) -> dict:
+        """Tile shape, Z4c derivative form (0 two kernels, 1 one kernel) and stage blocks per SM in effect."""
+        t = (ctypes.c_int * 3)()
+        f, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().sc_get_tuning(self.ctx, t, ctypes.byref(f), ctypes.byref(b)))
+        return {"tile": (t[0], t[1], t[2]), "deriv_form": f.value, "stage_blocks_per_sm": b.value}
+
+    def sc_set_tuning(self, tile, deriv_form: int = 0, stage_blocks_per_sm: int = 3):
+        t = (ctypes.c_int * 3)(*[int(v) for v in tile])
+        _check(lib().sc_set_tuning(self.ctx, t, int(deriv_form), int(stage_blocks_per_sm)))
 
     def sc_check_finite(self) -> bool:
         """True if the evolved state is finite everywhere (device scan)."""

@@ -330,6 +330,12 @@ struct sc_ctx {
   int rk = 4;      // Runge-Kutta method: stages = order = 4, 3 or 2
   int ghost = 3;   // ghost layers per box: 3 for 4th order, 4 for 8th
   int tile[3] = {32, 4, 2};  // stencil-kernel tile shape (autotuned on request)
+  // Z4c derivative pass: 0 = two kernels (D_x/D_y row pass, then the per-column
+  // pass that differentiates them for the mixed derivatives), 1 = one kernel
+  // per (cell, field) with direct 16-point mixed stencils (4th order only);
+  // stage kernel build: 2 or 3 blocks of 128 threads per SM (autotuned)
+  int deriv_form = 0;
+  int stage_bps = 3;
   int eta_profile = 0;
   double eta_c = 0, eta_s = 0, eta_o = 0;
   std::vector<Op> plain_ops[2];  // per-box form: the schedule, run directly
@@ -1156,7 +1162,9 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       a.eta = L.eta;
       // graph form: one launch over the tiles of all boxes; per-box form: one per box
       const int nparts = c->exec_mode == SC_EXEC_PER_BOX ? (int)L.boxes.size() : 1;
-      if (c->system == SC_Z4C) CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, s, c->order));
+      const bool one_pass = c->deriv_form == 1 && c->order == 4;
+      if (c->system == SC_Z4C && !one_pass)
+        CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, s, c->order));
       for (int b = 0; b < nparts; ++b) {
         const int t0 = nparts == 1 ? 0 : L.box_tile_begin[b];
         const int nt = nparts == 1 ? L.ntiles : L.box_tile_begin[b + 1] - t0;
@@ -1165,9 +1173,11 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
         } else {
           const int p0 = nparts == 1 ? 0 : L.box_ptile_begin[b];
           const int np = nparts == 1 ? L.nptiles : L.box_ptile_begin[b + 1] - p0;
-          CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles + t0, nt, s, c->order,
-                                     L.tile_cols));
-          CU(launch_z4c_stage(a, c->scratch, c->zp, L.ptiles + p0, np, s));
+          if (one_pass) CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles + t0, nt, s));
+          else
+            CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles + t0, nt, s, c->order,
+                                       L.tile_cols));
+          CU(launch_z4c_stage(a, c->scratch, c->zp, L.ptiles + p0, np, s, c->stage_bps));
         }
       }
       if (L.nphys) CU(launch_radiative_stage(a, L.phys, L.nphys, c->F, g, c->system, s));
@@ -1380,7 +1390,8 @@ sc_status build_schedule(sc_ctx* c, int p) {
     for (const Op& o : em.ops) {
       const Level& L = c->lev[o.level];
       if (o.kind == OP_STAGE)
-        n += (long)L.boxes.size() * (c->system == SC_Z4C ? 2 : 1) + (c->system == SC_Z4C ? 1 : 0) + (L.nphys ? 1 : 0);
+        n += (long)L.boxes.size() * (c->system == SC_Z4C ? 2 : 1) +
+             (c->system == SC_Z4C && !(c->deriv_form == 1 && c->order == 4) ? 1 : 0) + (L.nphys ? 1 : 0);
       else if (o.kind == OP_PROLONG)
         n += (L.natiles ? 1 : 0) + (L.namr > L.namr_blocked ? 1 : 0);
       else if (o.kind == OP_FILL)
@@ -1519,10 +1530,11 @@ sc_status sc::set_last_error(sc_status code, const char* msg) { return fail(code
 namespace {
 
 std::mutex g_tune_mutex;
-std::map<std::string, std::array<int, 3>> g_tune_cache;
+// per (system, level shapes): tile shape, derivative form, stage blocks per SM
+std::map<std::string, std::array<int, 5>> g_tune_cache;
 
 std::string tune_key(const sc_ctx* c) {
-  std::string k = std::to_string(c->system);
+  std::string k = std::to_string(c->system) + "/" + std::to_string(c->order);
   for (const Level& L : c->lev) {
     std::vector<std::array<int, 3>> ext;
     for (const sc_box& B : L.boxes) ext.push_back({B.hi[0] - B.lo[0] + 1, B.hi[1] - B.lo[1] + 1, B.hi[2] - B.lo[2] + 1});
@@ -1533,8 +1545,7 @@ std::string tune_key(const sc_ctx* c) {
   return k;
 }
 
-// Time the stencil kernel of one level with the given tiles (device array).
-sc_status time_stencil(sc_ctx* c, Level& L, const Tile* tiles, int ntiles, int cols, int reps, double* ms) {
+StageArgs tuning_stage_args(const Level& L) {
   const Geom& g = L.g;
   StageArgs a{};
   a.Y = L.A;
@@ -1551,14 +1562,33 @@ sc_status time_stencil(sc_ctx* c, Level& L, const Tile* tiles, int ntiles, int c
   a.sy = g.pitch;
   a.sz = g.pitch * g.ext[1];
   a.h = g.h;
+  a.eta = L.eta;
+  return a;
+}
+
+// Time one candidate on one level with CUDA events on the context's stream
+// (one untimed launch first, then reps): kind 0 = the stencil kernel with the
+// given tiles (the wave's fused stage, or the Z4c derivative pass in the form
+// deriv_form), kind 1 = the Z4c stage kernel built for bps blocks per SM.
+sc_status time_candidate(sc_ctx* c, Level& L, int kind, const Tile* tiles, int ntiles, int cols, int deriv_form,
+                         int bps, int reps, double* ms) {
+  const Geom& g = L.g;
+  const StageArgs a = tuning_stage_args(L);
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
-  for (int r = -1; r < reps; ++r) {  // one untimed launch first
+  for (int r = -1; r < reps; ++r) {
     if (r == 0) CU(cudaEventRecord(e0, c->stream));
-    if (c->system == SC_WAVE) CU(launch_wave_stage(a, tiles, ntiles, c->stream, c->order));
-    else
+    if (kind == 1) {
+      CU(launch_z4c_stage(a, c->scratch, c->zp, L.ptiles, L.nptiles, c->stream, bps));
+    } else if (c->system == SC_WAVE) {
+      CU(launch_wave_stage(a, tiles, ntiles, c->stream, c->order));
+    } else if (deriv_form == 1) {
+      CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, tiles, ntiles, c->stream));
+    } else {
+      CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, c->stream, c->order));
       CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, tiles, ntiles, c->stream, c->order, cols));
+    }
   }
   CU(cudaEventRecord(e1, c->stream));
   CU(cudaEventSynchronize(e1));
@@ -1570,16 +1600,24 @@ sc_status time_stencil(sc_ctx* c, Level& L, const Tile* tiles, int ntiles, int c
   return SC_OK;
 }
 
-sc_status apply_tile_shape(sc_ctx* c, const int* shape) {
+sc_status apply_tuning(sc_ctx* c, const int* shape, int deriv_form, int bps) {
   for (int q = 0; q < 3; ++q) c->tile[q] = shape[q];
+  c->deriv_form = deriv_form;
+  c->stage_bps = bps;
   for (Level& L : c->lev) {
     std::vector<Tile> t;
     build_stencil_tiles(L, c->tile, t);
     Tile* d = nullptr;
-    sc_status st = upload(c, t, &d);
+    CU(cudaStreamSynchronize(c->stream));  // the old list may still be read by queued work
+    sc_status st = level_upload(c, L, t, &d);
     if (st) return st;
+    if (L.tiles) {
+      c->dfree(L.tiles);
+      L.allocs.erase(std::find(L.allocs.begin(), L.allocs.end(), (void*)L.tiles));
+    }
     L.tiles = d;
     L.ntiles = (int)t.size();
+    L.tile_cols = max_tile_cols(t);
   }
   CU(cudaStreamSynchronize(c->stream));
   return build_graphs(c, false);
@@ -1587,10 +1625,18 @@ sc_status apply_tile_shape(sc_ctx* c, const int* shape) {
 
 }  // namespace
 
+// Autotuner (the search space: tile shape x derivative-pass split x stage
+// kernel blocks per SM).  On the context's largest level it times every tile
+// shape of the stencil kernel (the wave's fused stage, or the Z4c derivative
+// pass in its two-kernel form), the one-kernel Z4c derivative pass (4th
+// order, default tiles), and the Z4c stage kernel built for 2 and for 3 blocks
+// per SM; it keeps the fastest derivative configuration and the faster stage
+// build.  All forms compute the same derivatives (the one-kernel form sums the
+// mixed stencils in another order, so its results differ by rounding).
 extern "C" sc_status sc_autotune(sc_ctx* c, int* tile_out, double* ms_out) {
   if (!c) return fail(SC_EINVAL, "null context");
   const std::string key = tune_key(c);
-  std::array<int, 3> best{c->tile[0], c->tile[1], c->tile[2]};
+  std::array<int, 5> best{c->tile[0], c->tile[1], c->tile[2], c->deriv_form, c->stage_bps};
   double best_ms = -1.0;
   bool cached = false;
   {
@@ -1608,35 +1654,68 @@ extern "C" sc_status sc_autotune(sc_ctx* c, int* tile_out, double* ms_out) {
     Level& L = c->lev[big];
     static const int cand[][3] = {{32, 4, 2}, {32, 2, 4}, {32, 1, 8}, {32, 4, 4}, {32, 2, 8}, {32, 1, 16},
                                   {16, 4, 8}, {64, 1, 8}, {16, 2, 16}, {32, 1, 32}};
+    const int nform = (c->system == SC_Z4C && c->order == 4) ? 2 : 1;
     std::vector<Tile> t;
     Tile* d = nullptr;
     size_t cap = 0;
-    for (const auto& cd : cand) {
-      build_stencil_tiles(L, cd, t);
-      if (t.size() > cap) {
-        cap = t.size() * 2;
-        d = (Tile*)c->dalloc(cap * sizeof(Tile));
-        if (!d) return fail(SC_ENOMEM, "autotune tile buffer");
+    std::vector<void*> scratch_lists;
+    for (int form = 0; form < nform; ++form)
+      for (const auto& cd : cand) {
+        if (form == 1 && (cd[0] != 32 || cd[1] != 4 || cd[2] != 2)) continue;  // one-kernel form: default tiles
+        build_stencil_tiles(L, cd, t);
+        if (t.size() > cap) {
+          cap = t.size() * 2;
+          d = (Tile*)c->dalloc(cap * sizeof(Tile));
+          if (!d) return fail(SC_ENOMEM, "autotune tile buffer");
+          scratch_lists.push_back(d);
+        }
+        CU(cudaMemcpyAsync(d, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
+        double ms = 0;
+        sc_status st = time_candidate(c, L, 0, d, (int)t.size(), max_tile_cols(t), form, 0, 3, &ms);
+        if (st) return st;
+        if (best_ms < 0 || ms < best_ms) {
+          best_ms = ms;
+          best = {cd[0], cd[1], cd[2], form, best[4]};
+        }
       }
-      CU(cudaMemcpyAsync(d, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
-      double ms = 0;
-      sc_status st = time_stencil(c, L, d, (int)t.size(), max_tile_cols(t), 3, &ms);
+    if (c->system == SC_Z4C) {
+      double ms2 = 0, ms3 = 0;
+      sc_status st = time_candidate(c, L, 1, nullptr, 0, 0, 0, 2, 3, &ms2);
+      if (!st) st = time_candidate(c, L, 1, nullptr, 0, 0, 0, 3, 3, &ms3);
       if (st) return st;
-      if (best_ms < 0 || ms < best_ms) {
-        best_ms = ms;
-        best = {cd[0], cd[1], cd[2]};
-      }
+      best[4] = ms2 < ms3 ? 2 : 3;
     }
-    // restore the level's box ranges for the current shape before rebuilding
+    CU(cudaStreamSynchronize(c->stream));
+    for (void* p : scratch_lists) c->dfree(p);
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tune_cache[key] = best;
   }
-  sc_status st = apply_tile_shape(c, best.data());
+  sc_status st = apply_tuning(c, best.data(), best[3], best[4]);
   if (st) return st;
   if (tile_out)
     for (int q = 0; q < 3; ++q) tile_out[q] = best[q];
   if (ms_out) *ms_out = best_ms;
   return SC_OK;
+}
+
+extern "C" sc_status sc_get_tuning(sc_ctx* c, int* tile, int* deriv_form, int* stage_blocks_per_sm) {
+  if (!c || !tile || !deriv_form || !stage_blocks_per_sm) return fail(SC_EINVAL, "null argument");
+  for (int q = 0; q < 3; ++q) tile[q] = c->tile[q];
+  *deriv_form = c->deriv_form;
+  *stage_blocks_per_sm = c->stage_bps;
+  return SC_OK;
+}
+
+extern "C" sc_status sc_set_tuning(sc_ctx* c, const int* tile, int deriv_form, int stage_blocks_per_sm) {
+  if (!c || !tile) return fail(SC_EINVAL, "null argument");
+  for (int q = 0; q < 3; ++q)
+    if (tile[q] < 1 || tile[q] > 64) return fail(SC_EINVAL, "tile extents must be 1..64");
+  if ((long)tile[0] * tile[1] > 1024) return fail(SC_EINVAL, "tile columns must be at most 1024");
+  if (deriv_form != 0 && deriv_form != 1) return fail(SC_EINVAL, "derivative form must be 0 or 1");
+  if (deriv_form == 1 && (c->system != SC_Z4C || c->order != 4))
+    return fail(SC_EINVAL, "the one-kernel derivative pass exists for Z4c at 4th order");
+  if (stage_blocks_per_sm != 2 && stage_blocks_per_sm != 3) return fail(SC_EINVAL, "stage blocks per SM must be 2 or 3");
+  return apply_tuning(c, tile, deriv_form, stage_blocks_per_sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -2298,6 +2377,8 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   CU(cudaEventRecord(e[0], c->stream));
   for (int r = 0; r < nrep; ++r) {
     if (c->system == SC_WAVE) CU(launch_wave_stage(a, L.tiles, L.ntiles, c->stream, c->order));
+    else if (c->deriv_form == 1 && c->order == 4)
+      CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, c->stream));
     else {
       CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, c->stream, c->order));
       CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, c->stream, c->order,
@@ -2306,7 +2387,8 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   }
   CU(cudaEventRecord(e[1], c->stream));
   if (c->system == SC_Z4C)
-    for (int r = 0; r < nrep; ++r) CU(launch_z4c_stage(a, c->scratch, c->zp, L.ptiles, L.nptiles, c->stream));
+    for (int r = 0; r < nrep; ++r)
+      CU(launch_z4c_stage(a, c->scratch, c->zp, L.ptiles, L.nptiles, c->stream, c->stage_bps));
   CU(cudaEventRecord(e[2], c->stream));
   CU(cudaEventSynchronize(e[2]));
   CU(cudaEventElapsedTime(&t0, e[0], e[1]));

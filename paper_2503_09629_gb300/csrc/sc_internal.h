@@ -178,8 +178,10 @@ cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, do
 // chunks sized by it); cudaErrorInvalidValue if below 1.
 cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz, double h,
                                     const Tile* tiles, int ntiles, cudaStream_t s, int order, int max_cols);
+// bps: 128-thread blocks per SM of the stage kernel's build, 2 or 3 (a tuning
+// choice); cudaErrorInvalidValue otherwise.
 cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4cParams& p,
-                             const Tile* tiles, int ntiles, cudaStream_t s);
+                             const Tile* tiles, int ntiles, cudaStream_t s, int bps = 3);
 cudaError_t launch_radiative_stage(const StageArgs& a, const int32_t* cells, int ncells, int F,
                                    const Geom& g, int system, cudaStream_t s);
 cudaError_t launch_z4c_constraints(const double* Y, const double* scratch, double* out, long fs, int sy,

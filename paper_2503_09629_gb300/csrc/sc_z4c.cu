@@ -568,16 +568,16 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
 }
 
 // FORM: the stage update of StageArgs (kStageSingle, kStageRk4, kStageTwo,
-// kStageNone),
-// fixed at compile time so the update adds no registers to the RHS.
-// Three 128-thread blocks per SM (at most 168 registers): the RHS then spills
-// about 700 bytes per thread (written back to DRAM; the kernel is FP64-bound
-// and DRAM has room), but 3 warps per scheduler instead of 2 hide the FP64
-// dependency latency better; measured 5% faster than the unconstrained
-// 252-register build on the 524,288-cell benchmark level.
-template <int FORM>
-__global__ void __launch_bounds__(128, 3) z4c_stage_kernel(StageArgs a, const double* __restrict__ S, Z4cParams P,
-                                                          const Tile* __restrict__ tiles, int ntiles, FmaK K) {
+// kStageNone), fixed at compile time so the update adds no registers to the
+// RHS.  BPS: 128-thread blocks per SM the build is constrained to, a choice
+// of sc_autotune: 3 (at most 168 registers; the RHS then spills about 700
+// bytes per thread, written back to DRAM, which the FP64-bound kernel can
+// afford, while 3 warps per scheduler instead of 2 hide the FP64 dependency
+// latency better -- measured 5% faster on the 524,288-cell benchmark level)
+// or 2 (252 registers, no spills).
+template <int FORM, int BPS>
+__global__ void __launch_bounds__(128, BPS) z4c_stage_kernel(StageArgs a, const double* __restrict__ S, Z4cParams P,
+                                                            const Tile* __restrict__ tiles, int ntiles, FmaK K) {
   const double ko = P.ko_sigma / (64.0 * a.h);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile T = tiles[t];
@@ -701,7 +701,8 @@ __global__ void __launch_bounds__(128) z4c_constraints_kernel(const double* __re
 // evenly over the whole GPU instead of leaving a partial last wave.
 struct GridCaps {
   int ready = 0;
-  int stage = 304, derivs = 1216, dxy = 2432;
+  int stage[4] = {304, 304, 304, 456};  // by blocks per SM of the build (2 or 3)
+  int derivs = 1216, dxy = 2432;
 };
 GridCaps g_caps[64];
 
@@ -720,9 +721,14 @@ cudaError_t z4c_init_launch_config() {
   GridCaps& c = g_caps[dev & 63];
   if (c.ready) return cudaSuccess;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel<kStageSingle>, 128, 0)) != cudaSuccess)
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel<kStageSingle, 2>, 128, 0)) !=
+      cudaSuccess)
     return e;
-  c.stage = nsm * (occ > 0 ? occ : 1);
+  c.stage[2] = nsm * (occ > 0 ? occ : 1);
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel<kStageSingle, 3>, 128, 0)) !=
+      cudaSuccess)
+    return e;
+  c.stage[3] = nsm * (occ > 0 ? occ : 1);
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_derivs_split_kernel<8>, kThreads, 0)) != cudaSuccess)
     return e;
   c.derivs = nsm * (occ > 0 ? occ : 1);
@@ -763,15 +769,29 @@ cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, i
   return cudaGetLastError();
 }
 
+namespace {
+
+template <int BPS>
+void launch_stage_bps(const StageArgs& a, const double* scratch, const Z4cParams& p, const Tile* tiles, int ntiles,
+                      int grid, cudaStream_t s, const FmaK& K) {
+  if (a.form == kStageRk4) z4c_stage_kernel<kStageRk4, BPS><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+  else if (a.form == kStageTwo) z4c_stage_kernel<kStageTwo, BPS><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+  else if (a.form == kStageNone)
+    z4c_stage_kernel<kStageNone, BPS><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+  else z4c_stage_kernel<kStageSingle, BPS><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+}
+
+}  // namespace
+
 cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4cParams& p, const Tile* tiles,
-                             int ntiles, cudaStream_t s) {
+                             int ntiles, cudaStream_t s, int bps) {
   if (ntiles == 0) return cudaSuccess;
-  const int grid = ntiles < caps().stage ? ntiles : caps().stage;
+  if (bps != 2 && bps != 3) return cudaErrorInvalidValue;
+  const int cap = caps().stage[bps];
+  const int grid = ntiles < cap ? ntiles : cap;
   const FmaK K{1.0, -1.0, -0.0};
-  if (a.form == kStageRk4) z4c_stage_kernel<kStageRk4><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
-  else if (a.form == kStageTwo) z4c_stage_kernel<kStageTwo><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
-  else if (a.form == kStageNone) z4c_stage_kernel<kStageNone><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
-  else z4c_stage_kernel<kStageSingle><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+  if (bps == 2) launch_stage_bps<2>(a, scratch, p, tiles, ntiles, grid, s, K);
+  else launch_stage_bps<3>(a, scratch, p, tiles, ntiles, grid, s, K);
   return cudaGetLastError();
 }
 

@@ -24,8 +24,10 @@ Cases (names used by tests/test_gpu_z4c_fullsize.py):
                the serving ensemble), 16 coarse steps: about two minutes.
 
 Usage: python tests/golden/make_z4c_golden.py [bl7_2steps|bl3_48_16 ...]
-Output: tests/golden/z4c_<case>.npz (block origins, fields, oracle time and
-zone-update counts).
+Output: tests/golden/z4c_<case>.npz (block origins, fields, the largest
+|value| of each field over the interior cells of the whole hierarchy -- the
+scale of the max-relative-difference metric --, oracle time and zone-update
+counts).
 """
 from __future__ import annotations
 
@@ -101,9 +103,12 @@ def make(name: str) -> str:
     o.advance(nsteps)
     wall = time.perf_counter() - t0
     meta, blocks = [], []
+    field_max = np.zeros(22)  # max |value| of each field over the interior cells of the whole hierarchy
     for l in range(h.nlevels):
         for b in range(len(h.boxes[l])):
             full = np.stack([o.get_field(l, b, f, ghosted=True) for f in range(22)])
+            g = h.ghost
+            field_max = np.maximum(field_max, np.abs(full[:, g:-g, g:-g, g:-g]).max(axis=(1, 2, 3)))
             for (z, y, x) in sample_origins(h, l, b):
                 meta.append((l, b, z, y, x))
                 blocks.append(full[:, z:z + B, y:y + B, x:x + B].copy())
@@ -111,7 +116,7 @@ def make(name: str) -> str:
     path = os.path.join(HERE, f"z4c_{name}.npz")
     np.savez_compressed(path, meta=np.array(meta, dtype=np.int32), blocks=np.stack(blocks),
                         steps=np.int32(nsteps), time=np.float64(o.time), zone_updates=np.array([fin, act]),
-                        oracle_wall_s=np.float64(wall))
+                        field_max=field_max, oracle_wall_s=np.float64(wall))
     print(f"{name}: {nsteps} coarse steps in {wall:.0f} s, {len(meta)} blocks -> {path}", flush=True)
     return path
 

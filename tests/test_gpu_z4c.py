@@ -185,3 +185,39 @@ def test_uniform_step_mode_z4c_matches_oracle(sc, orc):
     h = W.bl_3level(20)
     h.subcycle = False
     assert _parity(sc, orc, h, 1) <= TOL
+
+
+@pytest.mark.parametrize("tile,form,bps", [((32, 4, 2), 0, 2), ((32, 4, 2), 1, 3), ((32, 2, 4), 0, 3),
+                                           ((16, 4, 8), 1, 2)])
+def test_tuning_choices_match_oracle(sc, orc, tile, form, bps):
+    """Every point of the autotuner's search space (tile shape x derivative
+    pass in one or two kernels x stage kernel built for 2 or 3 blocks per SM)
+    evolves the same Z4c state as the oracle within the Z4c tolerance."""
+    h = W.bl_3level(20)
+    arrays = init_arrays(h)
+    ctx = sc.Context(h)
+    ctx.sc_set_tuning(tile, form, bps)
+    assert ctx.sc_get_tuning() == {"tile": tile, "deriv_form": form, "stage_blocks_per_sm": bps}
+    o = make_oracle(orc, h)
+    load(ctx, h, arrays)
+    load(o, h, arrays)
+    ctx.sc_advance(4)
+    o.advance(4)
+    assert max_rel_diff(fetch(ctx, h), fetch(o, h)) <= TOL
+    ctx.close()
+
+
+def test_autotune_z4c_matches_oracle(sc, orc):
+    h = W.bl_3level(24, m1=0.3, m2=0.7, sep=3.0)
+    arrays = init_arrays(h)
+    ctx = sc.Context(h)
+    tile, _ms = ctx.sc_autotune()
+    t = ctx.sc_get_tuning()
+    assert t["tile"] == tile and t["deriv_form"] in (0, 1) and t["stage_blocks_per_sm"] in (2, 3)
+    o = make_oracle(orc, h)
+    load(ctx, h, arrays)
+    load(o, h, arrays)
+    ctx.sc_advance(3)
+    o.advance(3)
+    assert max_rel_diff(fetch(ctx, h), fetch(o, h)) <= TOL
+    ctx.close()

@@ -11,8 +11,10 @@ punctures on the finest level).  Cases: the 7-level benchmark hierarchy after
 requests of the serving ensemble) and 3 levels of 32^3 with masses 0.3 and 0.7
 at separation 6 after 16 coarse steps (the smallest and most asymmetric).
 
-Tolerance: the Z4c bar, 1e-10 of the largest value of the field over the
-sampled blocks (floor 1e-14), element by element.
+Tolerance: the Z4c bar, element by element: 1e-10 of the largest |value| of
+the field over the interior cells of the whole hierarchy (stored with the
+blocks; floor 1e-14), the max-relative-field-difference metric of the other
+parity tests.
 
 A second test checks one refinement-boundary fill of the finest level of the
 benchmark hierarchy element by element: the oracle prolongs the GPU's own
@@ -62,18 +64,28 @@ def test_sampled_blocks_match_oracle(sc, name):
     fin, act = ctx.sc_zone_updates()
     assert np.array_equal([fin, act], g["zone_updates"])  # the same count of cell updates
     meta, ref = g["meta"], g["blocks"]
-    scale = np.maximum(np.abs(ref).max(axis=(0, 2, 3, 4)), 1e-14)  # per field over all blocks
+    # the metric's scale: the oracle's largest |value| of each field over the
+    # interior cells of the whole hierarchy (floor 1e-14 for fields that vanish)
+    scale = np.maximum(g["field_max"], 1e-14)
     cache = {}
-    worst = 0.0
+    report = []
+    g0 = h.ghost
     for (l, b, z, y, x), want in zip(meta, ref):
         if (l, b) not in cache:
             cache[(l, b)] = np.stack([ctx.sc_get_field(int(l), int(b), f, ghosted=True) for f in range(22)])
-        got = cache[(l, b)][:, z:z + 8, y:y + 8, x:x + 8]
-        rel = (np.abs(got - want).max(axis=(1, 2, 3)) / scale).max()
-        worst = max(worst, rel)
-        assert rel <= TOL, (name, int(l), int(b), (int(z), int(y), int(x)), rel)
+        full = cache[(l, b)]
+        got = full[:, z:z + 8, y:y + 8, x:x + 8]
+        d = np.abs(got - want)
+        f = int(np.argmax(d.max(axis=(1, 2, 3)) / scale))
+        k, j, i = np.unravel_index(int(np.argmax(d[f])), d[f].shape)
+        ghost = not all(g0 <= c < n - g0 for c, n in zip((z + k, y + j, x + i), full.shape[1:]))
+        report.append((d.max(axis=(1, 2, 3))[f] / scale[f], int(l), int(b), (int(z), int(y), int(x)), f,
+                       float(d[f].max()), float(scale[f]), "ghost" if ghost else "interior"))
     ctx.close()
-    print(f"{name}: worst relative difference {worst:.3e} over {len(meta)} blocks")
+    report.sort(reverse=True)
+    for r in report[:5]:
+        print(name, "rel %.3e level %d box %d block %s field %d abs %.3e scale %.3e %s" % r)
+    assert report[0][0] <= TOL, report[0]
 
 
 def test_finest_refinement_boundary_fill_matches_oracle(sc, orc):
