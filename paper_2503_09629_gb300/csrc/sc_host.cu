@@ -296,6 +296,10 @@ struct Op {
   double c1dt;
   int form;
   bool no_amr;    // OP_FILL: periodic images only (uniform-step mode)
+  bool amr_folded;  // OP_FILL: its refinement-boundary part runs in the stage launch before it
+  bool fold_fill;   // OP_STAGE: also applies the next op's refinement-boundary fill
+  double* fold_vec;
+  double fold_c[4];
 };
 
 }  // namespace
@@ -1138,7 +1142,7 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       break;
     }
     case OP_FILL:
-      if (o.level > 0 && !o.no_amr)
+      if (o.level > 0 && !o.no_amr && !o.amr_folded)
         CU(launch_amr_apply(o.in, g.fs, c->F, L.amr, L.namr, L.amr_store, o.c, s, dense_count(c->rk)));
       CU(launch_periodic_copy(o.in, g.fs, c->F, L.periodic, L.nperiodic, s));
       break;
@@ -1162,6 +1166,18 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       a.eta = L.eta;
       // graph form: one launch over the tiles of all boxes; per-box form: one per box
       const int nparts = c->exec_mode == SC_EXEC_PER_BOX ? (int)L.boxes.size() : 1;
+      ApplyArgs fold{};
+      if (o.fold_fill) {
+        fold.vec = o.fold_vec;
+        fold.fs = g.fs;
+        fold.F = c->F;
+        fold.cells = L.amr;
+        fold.ncells = L.namr;
+        fold.store = L.amr_store;
+        for (int j = 0; j < 4; ++j) fold.c[j] = o.fold_c[j];
+        fold.nk = dense_count(c->rk);
+      }
+      const ApplyArgs* foldp = (o.fold_fill && nparts == 1) ? &fold : nullptr;
       const bool one_pass = c->deriv_form == 1 && c->order == 4;
       if (c->system == SC_Z4C && !one_pass)
         CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, s, c->order));
@@ -1169,7 +1185,7 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
         const int t0 = nparts == 1 ? 0 : L.box_tile_begin[b];
         const int nt = nparts == 1 ? L.ntiles : L.box_tile_begin[b + 1] - t0;
         if (c->system == SC_WAVE) {
-          CU(launch_wave_stage(a, L.tiles + t0, nt, s, c->order));
+          CU(launch_wave_stage(a, L.tiles + t0, nt, s, c->order, foldp));
         } else {
           const int p0 = nparts == 1 ? 0 : L.box_ptile_begin[b];
           const int np = nparts == 1 ? L.nptiles : L.box_ptile_begin[b + 1] - p0;
@@ -1406,6 +1422,23 @@ sc_status build_schedule(sc_ctx* c, int p) {
     c->launches_per_step = n;
     c->graph_stale[p] = false;
     return SC_OK;
+  }
+  // Graph form of the scalar wave: fold each refinement-boundary fill into
+  // the stage launch before it when the fill writes ghost cells of a buffer
+  // that stage neither reads nor writes (the next stage input, or the new
+  // state): one launch fewer per fine-level stage.  Not for Z4c, where the
+  // fill inside the register-heavy stage kernel ran slower than alone.
+  for (size_t i = 0; i + 1 < em.ops.size(); ++i) {
+    Op& st = em.ops[i];
+    Op& fl = em.ops[i + 1];
+    if (c->system == SC_WAVE && st.kind == OP_STAGE && fl.kind == OP_FILL && fl.level == st.level && fl.level > 0 &&
+        !fl.no_amr &&
+        c->lev[fl.level].namr > 0 && fl.in != st.in && fl.in != st.yn) {
+      st.fold_fill = true;
+      st.fold_vec = fl.in;
+      for (int j = 0; j < 4; ++j) st.fold_c[j] = fl.c[j];
+      fl.amr_folded = true;
+    }
   }
   cudaStream_t cs;
   CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));

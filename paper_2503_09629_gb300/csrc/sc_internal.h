@@ -146,6 +146,25 @@ __device__ __forceinline__ double fmul(double a, double b, const FmaK& K) { retu
 
 enum { kStageSingle = 0, kStageRk4 = 1, kStageTwo = 2, kStageNone = 3 };
 
+// A refinement-boundary ghost fill carried out by a stage launch (ncells = 0:
+// none): ghost value = store[0] + sum_j c_j store[j + 1] over nk prolonged
+// stage vectors, written to vec at the AMR cells.  The graph form of the
+// scalar wave folds the fill of the next stage input into the stage that
+// precedes it: the fill writes ghost cells of a buffer that stage neither
+// reads nor writes.  (Z4c keeps separate fill launches: inside its stage
+// kernel, at 12 warps per SM, the latency-bound fill ran slower than alone
+// and lengthened the step.)
+struct ApplyArgs {
+  double* vec;
+  long fs;
+  int F;
+  const AmrCell* cells;
+  int ncells;
+  const double* store;
+  double c[4];
+  int nk;
+};
+
 // Bits of a context's device status word (OR-ed by kernels, read and cleared
 // by sc_synchronize): a non-finite value after a coarse step, a grid barrier
 // of the persistent coarse-step kernel that gave up waiting.
@@ -164,7 +183,8 @@ sc_status set_last_error(sc_status code, const char* msg);
 int sm_count();
 
 // ---- kernel launchers (defined in the .cu files) -------------------------
-cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s, int order = 4);
+cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s, int order = 4,
+                              const ApplyArgs* fill = nullptr);
 
 cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy, int sz, double h,
                               const Tile* tiles, int ntiles, cudaStream_t s);

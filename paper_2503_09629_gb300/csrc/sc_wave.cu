@@ -17,8 +17,11 @@ constexpr int kThreads = 256;
 
 template <int ORD>
 __global__ void __launch_bounds__(kThreads) wave_stage_kernel(StageArgs a, const Tile* __restrict__ tiles,
-                                                             int ntiles, FmaK K) {
+                                                             int ntiles, FmaK K, ApplyArgs fill) {
   wave_stage_body<ORD>(a, tiles, ntiles, K, blockIdx.x, gridDim.x);
+  if (fill.ncells)
+    amr_apply_body(fill.vec, fill.fs, fill.F, fill.cells, fill.ncells, fill.store, fill.c[0], fill.c[1], fill.c[2],
+                   fill.c[3], fill.nk, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kThreads) radiative_stage_kernel(StageArgs a, const int32_t* __restrict__ cells,
@@ -28,12 +31,17 @@ __global__ void __launch_bounds__(kThreads) radiative_stage_kernel(StageArgs a, 
 
 }  // namespace
 
-cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s, int order) {
-  if (ntiles == 0) return cudaSuccess;
-  const int grid = ntiles < sm_count() * 16 ? ntiles : sm_count() * 16;
+cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s, int order,
+                              const ApplyArgs* fill) {
+  ApplyArgs f{};
+  if (fill) f = *fill;
+  const long fill_blocks = ((long)f.ncells * f.F + kThreads - 1) / kThreads;
+  long work = ntiles > fill_blocks ? ntiles : fill_blocks;
+  if (work == 0) return cudaSuccess;
+  const int grid = (int)(work < sm_count() * 16L ? work : sm_count() * 16L);
   const FmaK K{1.0, -1.0, -0.0};
-  if (order == 8) wave_stage_kernel<8><<<grid, kThreads, 0, s>>>(a, tiles, ntiles, K);
-  else wave_stage_kernel<4><<<grid, kThreads, 0, s>>>(a, tiles, ntiles, K);
+  if (order == 8) wave_stage_kernel<8><<<grid, kThreads, 0, s>>>(a, tiles, ntiles, K, f);
+  else wave_stage_kernel<4><<<grid, kThreads, 0, s>>>(a, tiles, ntiles, K, f);
   return cudaGetLastError();
 }
 
