@@ -14,7 +14,9 @@ at separation 6 after 16 coarse steps (the smallest and most asymmetric).
 Tolerance: the Z4c bar, element by element: 1e-10 of the largest |value| of
 the field over the interior cells of the whole hierarchy (stored with the
 blocks; floor 1e-14), the max-relative-field-difference metric of the other
-parity tests.
+parity tests; for Theta, the constraint variable that vanishes for exact
+solutions, 1e-10 of the largest field magnitude of the state (the reading is
+explained at the comparison).
 
 A second test checks one refinement-boundary fill of the finest level of the
 benchmark hierarchy element by element: the oracle prolongs the GPU's own
@@ -34,6 +36,7 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 TOL = 1e-10
+THETA = 17  # Z4c field index of Theta
 
 
 @pytest.fixture(scope="module")
@@ -65,8 +68,15 @@ def test_sampled_blocks_match_oracle(sc, name):
     assert np.array_equal([fin, act], g["zone_updates"])  # the same count of cell updates
     meta, ref = g["meta"], g["blocks"]
     # the metric's scale: the oracle's largest |value| of each field over the
-    # interior cells of the whole hierarchy (floor 1e-14 for fields that vanish)
+    # interior cells of the whole hierarchy (floor 1e-14 for fields that
+    # vanish) -- except Theta, which vanishes for exact solutions (Sec. III.A)
+    # and here holds only truncation error (3e-4 on the benchmark hierarchy
+    # after 2 coarse steps): it is compared on the scale of the state, the
+    # largest field magnitude, since two FP64 evaluations of its right-hand
+    # side (sums of O(1/h^2) Ricci terms of O(1) fields) differ by rounding on
+    # that scale, not on Theta's own.
     scale = np.maximum(g["field_max"], 1e-14)
+    scale[THETA] = max(scale[THETA], g["field_max"].max())
     cache = {}
     report = []
     g0 = h.ghost
