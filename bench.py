@@ -210,7 +210,7 @@ def whole_job_rate(world: int, units_per_step_per_rank: float, steps: int, t_max
 
 
 def run_ensemble(sc, W, n: int, seed: int, burst: bool, mean_interarrival: float, arm: str,
-                 budget: int = 48 << 30, max_active: int = 32):
+                 budget: int = 48 << 30, max_active: int = 8):
     """Serve the seeded request ensemble in one arm; returns latency and throughput.
 
     arms: "plain_per_box" -- one request at a time in arrival order, kernels
@@ -259,7 +259,7 @@ def run_ensemble(sc, W, n: int, seed: int, burst: bool, mean_interarrival: float
             "gpu_launches": st["launches"]}
 
 
-def run_serving_arms(sc, W, n: int, max_active: int = 32):
+def run_serving_arms(sc, W, n: int, max_active: int = 8):
     """The seeded ensemble (60% wave, 40% Z4c requests) in every arm, burst
     arrivals and Poisson arrivals at 0.9 of the plain per-box service rate."""
     import torch
@@ -737,7 +737,8 @@ def main():
                     help="1: time the scalar-wave workloads in the plain, graph and persistent forms")
     ap.add_argument("--serving-requests", type=int, default=256,
                     help="requests of the served-vs-plain ensemble embedded in the default line (0: skip)")
-    ap.add_argument("--max-active", type=int, default=32, help="slots of the served arms")
+    ap.add_argument("--max-active", type=int, default=8,
+                    help="slots of the served arms (8: best p50, p99 and throughput of 4/8/16/32/64 on this ensemble)")
     args = ap.parse_args()
     if args.study:
         print(json.dumps(run_study(args)), flush=True)
