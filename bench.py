@@ -12,6 +12,15 @@ Arms:
                      coarse step of a bounded sample of the same workload
                      (5 nested levels of 20^3, same physics and parameters).
 
+The default JSON line also carries: the roofline of the dominant kernel and
+of the others against FP64 peaks read and measured on the device; e2e through
+the C ABI with host buffers and the transfer split; the uniform-step mode and
+the plain per-box form of the same hierarchy; the scalar-wave workloads in the
+plain, graph and persistent forms; the 256-request serving ensemble in four
+arms; the CPU oracle on one core and on every core.  --study runs one study
+instead (moving boxes, the wave stage kernel, the FP64 issue rates, the small
+Z4c case of the ncu captures).
+
 Multi-GPU (torchrun): independent replicas, one per GPU ("weak" scaling);
 the path has no exchange step on one hierarchy per GPU.
 """

@@ -868,16 +868,6 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
   return SC_OK;
 }
 
-template <class T>
-sc_status upload(sc_ctx* c, const std::vector<T>& v, T** dst) {
-  *dst = nullptr;
-  if (v.empty()) return SC_OK;
-  *dst = (T*)c->dalloc(v.size() * sizeof(T));
-  if (!*dst) return fail(SC_ENOMEM, "device allocation of %zu bytes failed", v.size() * sizeof(T));
-  CU(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-  return SC_OK;
-}
-
 // Allocation owned by one level (released when the level is regridded).
 void* level_alloc(sc_ctx* c, Level& L, size_t bytes) {
   void* p = c->dalloc(bytes);
