@@ -1153,6 +1153,7 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       a.sy = g.pitch;
       a.sz = g.pitch * g.ext[1];
       a.h = g.h;
+      a.ds = deriv_scales(c->order, g.h);
       a.eta = L.eta;
       // graph form: one launch over the tiles of all boxes; per-box form: one per box
       const int nparts = c->exec_mode == SC_EXEC_PER_BOX ? (int)L.boxes.size() : 1;
@@ -1170,7 +1171,7 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
       const ApplyArgs* foldp = (o.fold_fill && nparts == 1) ? &fold : nullptr;
       const bool one_pass = c->deriv_form == 1 && c->order == 4;
       if (c->system == SC_Z4C && !one_pass)
-        CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, s, c->order));
+        CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, L.dxy, L.ndxy, s, c->order));
       for (int b = 0; b < nparts; ++b) {
         const int t0 = nparts == 1 ? 0 : L.box_tile_begin[b];
         const int nt = nparts == 1 ? L.ntiles : L.box_tile_begin[b + 1] - t0;
@@ -1179,9 +1180,9 @@ sc_status run_op(sc_ctx* c, const Op& o, cudaStream_t s) {
         } else {
           const int p0 = nparts == 1 ? 0 : L.box_ptile_begin[b];
           const int np = nparts == 1 ? L.nptiles : L.box_ptile_begin[b + 1] - p0;
-          if (one_pass) CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles + t0, nt, s));
+          if (one_pass) CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, L.tiles + t0, nt, s));
           else
-            CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles + t0, nt, s, c->order,
+            CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, L.tiles + t0, nt, s, c->order,
                                        L.tile_cols));
           CU(launch_z4c_stage(a, c->scratch, c->zp, L.ptiles + p0, np, s, c->stage_bps));
         }
@@ -1568,7 +1569,7 @@ std::string tune_key(const sc_ctx* c) {
   return k;
 }
 
-StageArgs tuning_stage_args(const Level& L) {
+StageArgs tuning_stage_args(const Level& L, int order) {
   const Geom& g = L.g;
   StageArgs a{};
   a.Y = L.A;
@@ -1585,6 +1586,7 @@ StageArgs tuning_stage_args(const Level& L) {
   a.sy = g.pitch;
   a.sz = g.pitch * g.ext[1];
   a.h = g.h;
+  a.ds = deriv_scales(order, g.h);
   a.eta = L.eta;
   return a;
 }
@@ -1596,7 +1598,7 @@ StageArgs tuning_stage_args(const Level& L) {
 sc_status time_candidate(sc_ctx* c, Level& L, int kind, const Tile* tiles, int ntiles, int cols, int deriv_form,
                          int bps, int reps, double* ms) {
   const Geom& g = L.g;
-  const StageArgs a = tuning_stage_args(L);
+  const StageArgs a = tuning_stage_args(L, c->order);
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
@@ -1607,10 +1609,10 @@ sc_status time_candidate(sc_ctx* c, Level& L, int kind, const Tile* tiles, int n
     } else if (c->system == SC_WAVE) {
       CU(launch_wave_stage(a, tiles, ntiles, c->stream, c->order));
     } else if (deriv_form == 1) {
-      CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, tiles, ntiles, c->stream));
+      CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, tiles, ntiles, c->stream));
     } else {
-      CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, c->stream, c->order));
-      CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, tiles, ntiles, c->stream, c->order, cols));
+      CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, L.dxy, L.ndxy, c->stream, c->order));
+      CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, tiles, ntiles, c->stream, c->order, cols));
     }
   }
   CU(cudaEventRecord(e1, c->stream));
@@ -2340,13 +2342,13 @@ sc_status sc_get_constraints(sc_ctx* c, int level, int box, double* dst) {
   const int sy = L.g.pitch, sz = L.g.pitch * L.g.ext[1];
   const int blo[3] = {B.lo[0] - L.g.org[0], B.lo[1] - L.g.org[1], B.lo[2] - L.g.org[2]};
   if (c->order == 4) {
-    CU(launch_z4c_derivs(Y, c->scratch, L.g.fs, sy, sz, L.g.h, dt, (int)tl.size(), c->stream));
+    CU(launch_z4c_derivs(Y, c->scratch, L.g.fs, sy, sz, dt, (int)tl.size(), c->stream));
   } else {
-    CU(launch_z4c_dxy(Y, c->scratch, L.g.fs, sy, L.g.h, L.dxy, L.ndxy, c->stream, c->order));
-    CU(launch_z4c_derivs_split(Y, c->scratch, L.g.fs, sy, sz, L.g.h, dt, (int)tl.size(), c->stream, c->order,
+    CU(launch_z4c_dxy(Y, c->scratch, L.g.fs, sy, L.dxy, L.ndxy, c->stream, c->order));
+    CU(launch_z4c_derivs_split(Y, c->scratch, L.g.fs, sy, sz, dt, (int)tl.size(), c->stream, c->order,
                                max_tile_cols(tl)));
   }
-  CU(launch_z4c_constraints(Y, c->scratch, c->staging, L.g.fs, sy, sz, c->zp, dt, (int)tl.size(), ncell, blo, n,
+  CU(launch_z4c_constraints(Y, c->scratch, c->staging, L.g.fs, sy, sz, c->zp, deriv_scales(c->order, L.g.h), dt, (int)tl.size(), ncell, blo, n,
                             c->stream));
   CU(cudaMemcpyAsync(dst, c->staging, bytes, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -2393,6 +2395,7 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   a.sy = g.pitch;
   a.sz = g.pitch * g.ext[1];
   a.h = g.h;
+  a.ds = deriv_scales(c->order, g.h);
   a.eta = L.eta;
   cudaEvent_t e[3];
   for (auto& x : e) CU(cudaEventCreate(&x));
@@ -2401,10 +2404,10 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   for (int r = 0; r < nrep; ++r) {
     if (c->system == SC_WAVE) CU(launch_wave_stage(a, L.tiles, L.ntiles, c->stream, c->order));
     else if (c->deriv_form == 1 && c->order == 4)
-      CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, c->stream));
+      CU(launch_z4c_derivs(a.Y, c->scratch, g.fs, a.sy, a.sz, L.tiles, L.ntiles, c->stream));
     else {
-      CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, g.h, L.dxy, L.ndxy, c->stream, c->order));
-      CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, g.h, L.tiles, L.ntiles, c->stream, c->order,
+      CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, L.dxy, L.ndxy, c->stream, c->order));
+      CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, L.tiles, L.ntiles, c->stream, c->order,
                                  L.tile_cols));
     }
   }

@@ -103,6 +103,30 @@ struct Weights {
   double restrict_w[kRN];
 };
 
+// Factors that turn the Z4c derivative pass's stored integer-weight stencil
+// sums into derivatives: first derivatives times s1, pure second derivatives
+// times s2p, mixed second derivatives times s2m (4th order: 1/(12h),
+// 1/(12h^2), 1/(144h^2); 8th order: 1/(840h), 1/(5040h^2), 1/(840h)^2).
+struct DerivScales {
+  double s1, s2p, s2m;  // first, pure second and mixed second derivative
+  double hs1, ts1;      // s1 / 2 and s1 / 3
+  double hs2p, ts2m;    // s2p / 2 and 2 s2m
+};
+// The products are formed on the host so that the kernels take every factor
+// as a kernel-parameter operand (no register, no extra instruction).
+inline DerivScales deriv_scales(int order, double h) {
+  const double w1 = order == 8 ? 840.0 : 12.0, w2 = order == 8 ? 5040.0 : 12.0;
+  DerivScales d;
+  d.s1 = 1.0 / (w1 * h);
+  d.s2p = 1.0 / (w2 * h * h);
+  d.s2m = 1.0 / (w1 * h * w1 * h);
+  d.hs1 = 0.5 * d.s1;
+  d.ts1 = d.s1 / 3.0;
+  d.hs2p = 0.5 * d.s2p;
+  d.ts2m = 2.0 * d.s2m;
+  return d;
+}
+
 // Arguments of one fused RK4 stage (right-hand side + stage update).
 struct StageArgs {
   const double* Y;   // stage input, ghosts valid
@@ -125,6 +149,7 @@ struct StageArgs {
   int sy, sz;        // strides of y and z in doubles
   double h;
   const double* eta; // Z4c: per-cell Gamma-driver damping eta(r), or null for the constant
+  DerivScales ds;    // Z4c: scales of the stored derivative sums
 };
 
 // Additions, subtractions and scalings that do not fuse are written as fused
@@ -186,17 +211,17 @@ int sm_count();
 cudaError_t launch_wave_stage(const StageArgs& a, const Tile* tiles, int ntiles, cudaStream_t s, int order = 4,
                               const ApplyArgs* fill = nullptr);
 
-cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy, int sz, double h,
+cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy, int sz,
                               const Tile* tiles, int ntiles, cudaStream_t s);
 // Occupancy-derived persistent grid sizes of the Z4c kernels (once per device,
 // before any graph capture).
 cudaError_t z4c_init_launch_config();
 // order: finite-difference order of the derivatives, 4 or 8 (Kreiss-Oliger stays r = 4)
-cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, double h, const RowSeg* segs, int nsegs,
+cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, const RowSeg* segs, int nsegs,
                            cudaStream_t s, int order = 4);
 // max_cols: the largest nx * ny of the tiles (work is dealt out per tile in
 // chunks sized by it); cudaErrorInvalidValue if below 1.
-cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz, double h,
+cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz,
                                     const Tile* tiles, int ntiles, cudaStream_t s, int order, int max_cols);
 // bps: 128-thread blocks per SM of the stage kernel's build, 2 or 3 (a tuning
 // choice); cudaErrorInvalidValue otherwise.
@@ -205,8 +230,8 @@ cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4
 cudaError_t launch_radiative_stage(const StageArgs& a, const int32_t* cells, int ncells, int F,
                                    const Geom& g, int system, cudaStream_t s);
 cudaError_t launch_z4c_constraints(const double* Y, const double* scratch, double* out, long fs, int sy,
-                                   int sz, const Z4cParams& p, const Tile* tiles, int ntiles, long out_stride,
-                                   const int* box_lo, const int* box_n, cudaStream_t s);
+                                   int sz, const Z4cParams& p, const DerivScales& ds, const Tile* tiles, int ntiles,
+                                   long out_stride, const int* box_lo, const int* box_n, cudaStream_t s);
 
 cudaError_t launch_periodic_copy(double* vec, long fs, int F, const int2* pairs, int npairs, cudaStream_t s);
 // per-cell prolongation of AMR cells [first, ncells) of the list (store has ncells slots per vector-field);

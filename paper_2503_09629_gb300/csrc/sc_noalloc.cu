@@ -129,11 +129,11 @@ extern "C" sc_status sc_z4c_constraints_noalloc(const double* dev_state, double*
   if (e != cudaSuccess) return noalloc_fail(SC_ECUDA, "tile kernel", e);
   const long fs = vol;  // state: field stride = ghosted box volume
   const int sy = (int)ext[0], sz = (int)(ext[0] * ext[1]);
-  e = sc::launch_z4c_derivs(dev_state, sym->scratch, fs, sy, sz, h, sym->tiles, (int)nt, s);
+  e = sc::launch_z4c_derivs(dev_state, sym->scratch, fs, sy, sz, sym->tiles, (int)nt, s);
   if (e != cudaSuccess) return noalloc_fail(SC_ECUDA, "derivative kernel", e);
   const int lo[3] = {sc::kGhost, sc::kGhost, sc::kGhost};
   const sc::Z4cParams p{0.0, 0.0, 0.0, 0.0};  // the constraints do not depend on the damping/gauge parameters
-  e = sc::launch_z4c_constraints(dev_state, sym->scratch, dev_out, fs, sy, sz, p, sym->tiles, (int)nt,
+  e = sc::launch_z4c_constraints(dev_state, sym->scratch, dev_out, fs, sy, sz, p, sc::deriv_scales(4, h), sym->tiles, (int)nt,
                                  (long)n[0] * n[1] * n[2], lo, n, s);
   if (e != cudaSuccess) return noalloc_fail(SC_ECUDA, "constraint kernel", e);
   return SC_OK;

@@ -3,11 +3,14 @@
 // RK4 stage update, plus the constraint evaluation.
 //
 // Two passes per stage, both over the interior tiles of a level:
-//   1. z4c_derivs_kernel: one thread per (cell, field) computes the 4th-order
-//      centred first derivatives of every field, the second derivatives of
-//      W, gt_ij, alpha and beta^i, and the KO sum sum_d delta_d^6 u, and
-//      stores them (already scaled by 1/h, 1/h^2) in a scratch array indexed
-//      like the level array: scratch[q * fs + cell].
+//   1. the derivative pass computes the centred first derivatives of every
+//      field, the second derivatives of W, gt_ij, alpha and beta^i, and the
+//      KO sum sum_d delta_d^6 u, and stores them in a scratch array indexed
+//      like the level array: scratch[q * fs + cell].  The stored values are
+//      the stencils' integer-weight sums, without their 1/h and 1/h^2
+//      factors (see DerivScales): a multiplication issues at the slower of
+//      the two FP64 rates, and the consumers fold the factors into FMA
+//      constants they evaluate anyway.
 //   2. z4c_stage_kernel: one thread per cell reads the 22 fields and their
 //      derivatives, evaluates the right-hand side, adds dissipation and
 //      performs the RK4 stage update.
@@ -37,12 +40,13 @@ __host__ __device__ inline int d2_slot(int f) {
   return -1;
 }
 
+// One-kernel form of the derivative pass (4th order): one thread per (cell,
+// field), mixed derivatives from the direct 16-point product stencil.
+// Stored scales as the two-kernel form: 12 h d_i u, 12 h^2 d_i^2 u,
+// 144 h^2 d_i d_j u, and the raw Kreiss-Oliger sum.
 __global__ void __launch_bounds__(kThreads) z4c_derivs_kernel(const double* __restrict__ Y, double* __restrict__ S,
-                                                             long fs, int sy_, int sz_, double h,
+                                                             long fs, int sy_, int sz_,
                                                              const Tile* __restrict__ tiles, int ntiles) {
-  const double i12h = 1.0 / (12.0 * h);
-  const double i12h2 = 1.0 / (12.0 * h * h);
-  const double i144h2 = 1.0 / (144.0 * h * h);
   const long st[3] = {1, (long)sy_, (long)sz_};
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile T = tiles[t];
@@ -64,8 +68,8 @@ __global__ void __launch_bounds__(kThreads) z4c_derivs_kernel(const double* __re
         p1[d] = a1 + b1;
         p2[d] = a2 + b2;
         P3 += u[-3 * s] + u[3 * s];
-        // (u_-2 - 8 u_-1 + 8 u_1 - u_2) / (12 h)
-        S[(long)(Q_D1 + 3 * f + d) * fs + o] = fma(8.0, b1 - a1, a2 - b2) * i12h;
+        // 12 h u' = u_-2 - 8 u_-1 + 8 u_1 - u_2
+        S[(long)(Q_D1 + 3 * f + d) * fs + o] = fma(8.0, b1 - a1, a2 - b2);
       }
       // Kreiss-Oliger: sum_d (u_-3 - 6 u_-2 + 15 u_-1 - 20 u_0 + 15 u_1 - 6 u_2 + u_3)
       const double P1 = p1[0] + p1[1] + p1[2], P2 = p2[0] + p2[1] + p2[2];
@@ -73,11 +77,11 @@ __global__ void __launch_bounds__(kThreads) z4c_derivs_kernel(const double* __re
       const int sl = d2_slot(f);
       if (sl < 0) continue;
       double* d2 = S + (long)(Q_D2 + 6 * sl) * fs + o;
-      // pure: (-u_-2 + 16 u_-1 - 30 u_0 + 16 u_1 - u_2) / (12 h^2)
-      d2[0 * fs] = fma(-30.0, u0, fma(16.0, p1[0], -p2[0])) * i12h2;
-      d2[3 * fs] = fma(-30.0, u0, fma(16.0, p1[1], -p2[1])) * i12h2;
-      d2[5 * fs] = fma(-30.0, u0, fma(16.0, p1[2], -p2[2])) * i12h2;
-      // mixed: product of the two first-derivative stencils / (144 h^2)
+      // pure: 12 h^2 u'' = -u_-2 + 16 u_-1 - 30 u_0 + 16 u_1 - u_2
+      d2[0 * fs] = fma(-30.0, u0, fma(16.0, p1[0], -p2[0]));
+      d2[3 * fs] = fma(-30.0, u0, fma(16.0, p1[1], -p2[1]));
+      d2[5 * fs] = fma(-30.0, u0, fma(16.0, p1[2], -p2[2]));
+      // mixed: 144 h^2 d_i d_j u, the product of the two first-derivative stencils
       const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2}, slot[3] = {1, 2, 4};
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
@@ -89,7 +93,7 @@ __global__ void __launch_bounds__(kThreads) z4c_derivs_kernel(const double* __re
           const double* v = u + offs[r] * sb;
           D[r] = fma(8.0, v[sa] - v[-sa], v[-2 * sa] - v[2 * sa]);
         }
-        d2[slot[m] * fs] = fma(8.0, D[2] - D[1], D[0] - D[3]) * i144h2;
+        d2[slot[m] * fs] = fma(8.0, D[2] - D[1], D[0] - D[3]);
       }
     }
   }
@@ -111,37 +115,26 @@ __global__ void __launch_bounds__(kThreads) z4c_derivs_kernel(const double* __re
 __device__ __forceinline__ int d2_field(int s) { return s <= 6 ? s : s + 11; }
 
 // Centred first derivative from the differences dm = v_m - v_-m, m = 1..R
-// (R = ORD/2): 4th order (8 d1 - d2) / (12 h), 8th order
-// (672 d1 - 168 d2 + 32 d3 - 3 d4) / (840 h); ih = 1/(12 h) or 1/(840 h).
+// (R = ORD/2), as the integer-weight sum: 4th order 8 d1 - d2 (= 12 h u'),
+// 8th order 672 d1 - 168 d2 + 32 d3 - 3 d4 (= 840 h u').
 template <int ORD>
-__device__ __forceinline__ double dfirst(const double* d, double ih, const FmaK& K) {
-  if (ORD == 4) return fmul(fma(8.0, d[0], -d[1]), ih, K);
-  return fmul(fma(672.0, d[0], fma(-168.0, d[1], fma(32.0, d[2], fmul(-3.0, d[3], K)))), ih, K);
+__device__ __forceinline__ double dfirst(const double* d, const FmaK& K) {
+  if (ORD == 4) return fma(8.0, d[0], -d[1]);
+  return fma(672.0, d[0], fma(-168.0, d[1], fma(32.0, d[2], fmul(-3.0, d[3], K))));
 }
-// Centred second derivative from the pair sums pm = v_m + v_-m:
-// 4th order (16 p1 - p2 - 30 u0) / (12 h^2), 8th order
-// (8064 p1 - 1008 p2 + 128 p3 - 9 p4 - 14350 u0) / (5040 h^2).
+// Centred second derivative from the pair sums pm = v_m + v_-m, as the
+// integer-weight sum: 4th order 16 p1 - p2 - 30 u0 (= 12 h^2 u''), 8th order
+// 8064 p1 - 1008 p2 + 128 p3 - 9 p4 - 14350 u0 (= 5040 h^2 u'').
 template <int ORD>
-__device__ __forceinline__ double dsecond(const double* p, double u0, double ih2, const FmaK& K) {
-  if (ORD == 4) return fmul(fma(-30.0, u0, fma(16.0, p[0], -p[1])), ih2, K);
-  return fmul(fma(-14350.0, u0, fma(8064.0, p[0], fma(-1008.0, p[1], fma(128.0, p[2], fmul(-9.0, p[3], K))))), ih2,
-              K);
-}
-template <int ORD>
-__device__ __forceinline__ double first_scale(double h) {
-  return ORD == 4 ? 1.0 / (12.0 * h) : 1.0 / (840.0 * h);
-}
-template <int ORD>
-__device__ __forceinline__ double second_scale(double h) {
-  return ORD == 4 ? 1.0 / (12.0 * h * h) : 1.0 / (5040.0 * h * h);
+__device__ __forceinline__ double dsecond(const double* p, double u0, const FmaK& K) {
+  if (ORD == 4) return fma(-30.0, u0, fma(16.0, p[0], -p[1]));
+  return fma(-14350.0, u0, fma(8064.0, p[0], fma(-1008.0, p[1], fma(128.0, p[2], fmul(-9.0, p[3], K)))));
 }
 
 template <int ORD>
 __global__ void __launch_bounds__(128) z4c_dxy_kernel(const double* __restrict__ Y, double* __restrict__ S, long fs,
-                                                     int sy_, const RowSeg* __restrict__ segs, int nsegs, double h,
-                                                     FmaK K) {
+                                                     int sy_, const RowSeg* __restrict__ segs, int nsegs, FmaK K) {
   constexpr int R = ORD / 2;
-  const double ih = first_scale<ORD>(h);
   const long sy = sy_;
   for (int sgi = blockIdx.x; sgi < nsegs; sgi += gridDim.x) {
     const RowSeg sg = segs[sgi];
@@ -154,12 +147,12 @@ __global__ void __launch_bounds__(128) z4c_dxy_kernel(const double* __restrict__
       if (sg.which & 1) {
 #pragma unroll
         for (int m = 1; m <= R; ++m) d[m - 1] = fsub(u[m], u[-m], K);
-        S[(long)(Q_D1 + 3 * f + 0) * fs + o] = dfirst<ORD>(d, ih, K);
+        S[(long)(Q_D1 + 3 * f + 0) * fs + o] = dfirst<ORD>(d, K);
       }
       if (sg.which & 2) {
 #pragma unroll
         for (int m = 1; m <= R; ++m) d[m - 1] = fsub(u[m * sy], u[-m * sy], K);
-        S[(long)(Q_D1 + 3 * f + 1) * fs + o] = dfirst<ORD>(d, ih, K);
+        S[(long)(Q_D1 + 3 * f + 1) * fs + o] = dfirst<ORD>(d, K);
       }
     }
   }
@@ -168,8 +161,7 @@ __global__ void __launch_bounds__(128) z4c_dxy_kernel(const double* __restrict__
 template <int ORD>
 __global__ void __launch_bounds__(kThreads, 2) z4c_derivs_split_kernel(const double* __restrict__ Y,
                                                                       double* __restrict__ S, long fs, int sy_,
-                                                                      int sz_, double h,
-                                                                      const Tile* __restrict__ tiles, int ntiles,
+                                                                      int sz_, const Tile* __restrict__ tiles, int ntiles,
                                                                       int max_cols, FmaK K) {
   // One thread per (x, y, field) column of a tile, walking z with sliding
   // windows: u at z-W..z+W (W = max(R, 3), R = ORD/2 the derivative radius,
@@ -182,8 +174,6 @@ __global__ void __launch_bounds__(kThreads, 2) z4c_derivs_split_kernel(const dou
   constexpr int WR = R > 3 ? R : 3;
   constexpr int NW = 2 * WR + 1;
   constexpr int ND = 2 * R + 1;
-  const double ih = first_scale<ORD>(h);
-  const double ih2 = second_scale<ORD>(h);
   const long sy = sy_, sz = sz_;
   const int U = (max_cols * kNZ4c + blockDim.x - 1) / blockDim.x;
   for (long u = blockIdx.x; u < (long)ntiles * U; u += gridDim.x) {
@@ -229,14 +219,14 @@ __global__ void __launch_bounds__(kThreads, 2) z4c_derivs_split_kernel(const dou
           if (sl < 0) {
 #pragma unroll
             for (int m = 1; m <= R; ++m) d[m - 1] = fsub(v[m * s], v[-m * s], K);
-            S[(long)(Q_D1 + 3 * f + dim) * fs + o] = dfirst<ORD>(d, ih, K);
+            S[(long)(Q_D1 + 3 * f + dim) * fs + o] = dfirst<ORD>(d, K);
           }
         }
 #pragma unroll
         for (int m = 1; m <= WR; ++m) p[2][m - 1] = fadd(w[WR - m], w[WR + m], K);
 #pragma unroll
         for (int m = 1; m <= R; ++m) d[m - 1] = fsub(w[WR + m], w[WR - m], K);
-        S[(long)(Q_D1 + 3 * f + 2) * fs + o] = dfirst<ORD>(d, ih, K);
+        S[(long)(Q_D1 + 3 * f + 2) * fs + o] = dfirst<ORD>(d, K);
         // Kreiss-Oliger (r = 4): sum_d (u_-3 - 6 u_-2 + 15 u_-1 - 20 u_0 + 15 u_1 - 6 u_2 + u_3)
         const double P1 = fadd(fadd(p[0][0], p[1][0], K), p[2][0], K);
         const double P2 = fadd(fadd(p[0][1], p[1][1], K), p[2][1], K);
@@ -244,19 +234,19 @@ __global__ void __launch_bounds__(kThreads, 2) z4c_derivs_split_kernel(const dou
         S[(long)(Q_KO + f) * fs + o] = fma(15.0, P1, fma(-6.0, P2, fma(-60.0, u0, P3)));
         if (sl >= 0) {
           double* d2 = S + (long)(Q_D2 + 6 * sl) * fs + o;
-          d2[0 * fs] = dsecond<ORD>(p[0], u0, ih2, K);
-          d2[3 * fs] = dsecond<ORD>(p[1], u0, ih2, K);
-          d2[5 * fs] = dsecond<ORD>(p[2], u0, ih2, K);
+          d2[0 * fs] = dsecond<ORD>(p[0], u0, K);
+          d2[3 * fs] = dsecond<ORD>(p[1], u0, K);
+          d2[5 * fs] = dsecond<ORD>(p[2], u0, K);
           const double* dxk = Dx + k * sz;
 #pragma unroll
           for (int m = 1; m <= R; ++m) d[m - 1] = fsub(dxk[m * sy], dxk[-m * sy], K);
-          d2[1 * fs] = dfirst<ORD>(d, ih, K);  // D_y D_x
+          d2[1 * fs] = dfirst<ORD>(d, K);  // D_y D_x
 #pragma unroll
           for (int m = 1; m <= R; ++m) d[m - 1] = fsub(wx[R + m], wx[R - m], K);
-          d2[2 * fs] = dfirst<ORD>(d, ih, K);  // D_z D_x
+          d2[2 * fs] = dfirst<ORD>(d, K);  // D_z D_x
 #pragma unroll
           for (int m = 1; m <= R; ++m) d[m - 1] = fsub(wy[R + m], wy[R - m], K);
-          d2[4 * fs] = dfirst<ORD>(d, ih, K);  // D_z D_y
+          d2[4 * fs] = dfirst<ORD>(d, K);  // D_z D_y
         }
         if (k + 1 < T.nz) {  // slide the windows one cell up in z
 #pragma unroll
@@ -291,10 +281,14 @@ struct Z4cPoint {
 // differences and products that do not fuse with a neighbour are written as
 // FMAs with the run-time unit constants of K (fadd, fsub, fmul; measured
 // faster than plain DADD/DMUL in this kernel, see FmaK).
+// The stored derivatives are stencil sums (DerivScales): first derivatives
+// enter through constants that carry s1 (the Christoffel 1/2, the 1/3 of the
+// Gamt equation) or are scaled once where several terms use them (W, alpha,
+// beta), second derivatives through the scale of their pure or mixed kind.
 template <bool kDiag>
 __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, const double* __restrict__ S, long fs,
-                                              long o, const Z4cParams& P, double eta, double* rhs, double* diag,
-                                              const FmaK& K) {
+                                              long o, const Z4cParams& P, double eta, const DerivScales& ds,
+                                              double* rhs, double* diag, const FmaK& K) {
 #define FLD(f) Y[(long)(f) * fs + o]
 #define D1(f, d) S[(long)(Q_D1 + 3 * (f) + (d)) * fs + o]
 #define D2(sl, p) S[(long)(Q_D2 + 6 * (sl) + (p)) * fs + o]
@@ -328,7 +322,7 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
 #pragma unroll
   for (int s = 0; s < 6; ++s) gw[s] = (s == 1 || s == 2 || s == 4) ? fmul(2.0, gu[s], K) : gu[s];
 
-  // first derivatives of the metric, Christoffel symbols
+  // first derivatives of the metric (stencil sums), Christoffel symbols
   double dg[6][3];
 #pragma unroll
   for (int s = 0; s < 6; ++s)
@@ -342,7 +336,7 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = i; j < 3; ++j)
-        Gl[k][sidx(i, j)] = fma(0.5, dg[sidx(j, k)][i], fma(0.5, dg[sidx(i, k)][j], fmul(-0.5, dg[sidx(i, j)][k], K)));
+        Gl[k][sidx(i, j)] = fma(ds.hs1, dg[sidx(j, k)][i], fma(ds.hs1, dg[sidx(i, k)][j], fmul(-ds.hs1, dg[sidx(i, j)][k], K)));
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
@@ -366,8 +360,8 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
         U[j][k][l] = fma(gu[sidx(l, 0)], Gl[j][sidx(k, 0)],
                          fma(gu[sidx(l, 1)], Gl[j][sidx(k, 1)], fmul(gu[sidx(l, 2)], Gl[j][sidx(k, 2)], K)));
 
-  const double dW[3] = {D1(ZW, 0), D1(ZW, 1), D1(ZW, 2)};
-  const double dal[3] = {D1(ZAL, 0), D1(ZAL, 1), D1(ZAL, 2)};
+  const double dW[3] = {fmul(D1(ZW, 0), ds.s1, K), fmul(D1(ZW, 1), ds.s1, K), fmul(D1(ZW, 2), ds.s1, K)};
+  const double dal[3] = {fmul(D1(ZAL, 0), ds.s1, K), fmul(D1(ZAL, 1), ds.s1, K), fmul(D1(ZAL, 2), ds.s1, K)};
   // gt^{kl} d_l W and |dW|^2, gt^{kl} d_l W d_k alpha
   double gudW[3];
 #pragma unroll
@@ -383,7 +377,8 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
     double trDDW = 0.0;
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
-      DDW[s] = fsub(D2(0, s), fma(Gu[0][s], dW[0], fma(Gu[1][s], dW[1], fmul(Gu[2][s], dW[2], K))), K);
+      const double s2 = (s == 0 || s == 3 || s == 5) ? ds.s2p : ds.s2m;
+      DDW[s] = fma(D2(0, s), s2, -fma(Gu[0][s], dW[0], fma(Gu[1][s], dW[1], fmul(Gu[2][s], dW[2], K))));
       trDDW = fma(gw[s], DDW[s], trDDW);
     }
     const double dGam[3][3] = {{D1(ZGAM, 0), D1(ZGAM, 1), D1(ZGAM, 2)},
@@ -408,14 +403,15 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
 #pragma unroll
       for (int j = i; j < 3; ++j) {
         const int s = sidx(i, j);
-        // -1/2 gt^lm d_l d_m gt_ij
-        double r = fma(-0.5, fma(gu[0], D2(1 + s, 0), fma(gu[3], D2(1 + s, 3), fmul(gu[5], D2(1 + s, 5), K))),
-                       -fma(gu[1], D2(1 + s, 1), fma(gu[2], D2(1 + s, 2), fmul(gu[4], D2(1 + s, 4), K))));
+        // -1/2 gt^lm d_l d_m gt_ij (pure and mixed second derivatives with their scales)
+        double r = fma(-ds.hs2p, fma(gu[0], D2(1 + s, 0), fma(gu[3], D2(1 + s, 3), fmul(gu[5], D2(1 + s, 5), K))),
+                       fmul(fma(gu[1], D2(1 + s, 1), fma(gu[2], D2(1 + s, 2), fmul(gu[4], D2(1 + s, 4), K))), -ds.s2m,
+                            K));
         // gt_k(i d_j) Gamt^k
         double a = 0.0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) a = fma(g[sidx(k, i)], dGam[k][j], fma(g[sidx(k, j)], dGam[k][i], a));
-        r = fma(0.5, a, r);
+        r = fma(ds.hs1, a, r);
         // (Gamma_d)^k Gamma_(ij)k
         double b = 0.0;
 #pragma unroll
@@ -434,7 +430,8 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
         // D_i D_j alpha with Gamma^k_ij - (delta^k_i d_j W + delta^k_j d_i W - gt_ij gt^kl d_l W) / W
         const double gd = fma(Gu[0][s], dal[0], fma(Gu[1][s], dal[1], fmul(Gu[2][s], dal[2], K)));
         const double wt = fma(dW[j], dal[i], fma(dW[i], dal[j], fmul(-g[s], dWdal, K)));
-        DDal[s] = fsub(D2(7, s), fma(-wt, iW, gd), K);
+        const double s2 = (s == 0 || s == 3 || s == 5) ? ds.s2p : ds.s2m;
+        DDal[s] = fma(D2(7, s), s2, -fma(-wt, iW, gd));
       }
   }
   double trR = 0.0, trDDal = 0.0;
@@ -468,14 +465,15 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) dbe[i][j] = D1(ZB + i, j);
+    for (int j = 0; j < 3; ++j) dbe[i][j] = fmul(D1(ZB + i, j), ds.s1, K);
   const double divb = fadd(fadd(dbe[0][0], dbe[1][1], K), dbe[2][2], K);
   const double Kt = fma(2.0, Th, Kh);
   const double third = 1.0 / 3.0, twothird = 2.0 / 3.0;
 
-#define ADV(f) fma(be[0], D1(f, 0), fma(be[1], D1(f, 1), fmul(be[2], D1(f, 2), K)))
+  // advection beta^i d_i f = s1 * BD(f), the scale applied where the term is added
+#define BD(f) fma(be[0], D1(f, 0), fma(be[1], D1(f, 1), fmul(be[2], D1(f, 2), K)))
   // W
-  rhs[ZW] = fma(fmul(third, W, K), fma(al, Kt, -divb), ADV(ZW));
+  rhs[ZW] = fma(fmul(third, W, K), fma(al, Kt, -divb), fmul(ds.s1, BD(ZW), K));
   // gt_ij and At_ij
   double X[6], trX = 0.0;
 #pragma unroll
@@ -499,24 +497,27 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
         la = fma(A[sidx(k, i)], dbe[k][j], fma(A[sidx(k, j)], dbe[k][i], la));
         aa = fma(Am[k][i], A[sidx(k, j)], aa);
       }
-      rhs[ZG + s] = fadd(ADV(ZG + s), fma(m2al, A[s], fma(m23divb, g[s], lg)), K);
+      rhs[ZG + s] = fma(ds.s1, BD(ZG + s), fma(m2al, A[s], fma(m23divb, g[s], lg)));
       const double tf = fma(m13trX, g[s], X[s]);
-      rhs[ZA + s] = fadd(ADV(ZA + s), fma(W2, tf, fma(alKt, A[s], fma(m2al, aa, fma(m23divb, A[s], la)))), K);
+      rhs[ZA + s] = fma(ds.s1, BD(ZA + s), fma(W2, tf, fma(alKt, A[s], fma(m2al, aa, fma(m23divb, A[s], la)))));
     }
   // Khat
   rhs[ZK] = fma(al, fma(fmul(third, Kt, K), Kt, AA),
-                fma(fmul(al, P.kappa1 * (1.0 - P.kappa2), K), Th, fsub(ADV(ZK), DiDial, K)));
+                fma(fmul(al, P.kappa1 * (1.0 - P.kappa2), K), Th, fma(ds.s1, BD(ZK), -DiDial)));
   // Gamt^i
   {
     const double dKh[3] = {D1(ZK, 0), D1(ZK, 1), D1(ZK, 2)};
     const double dTh[3] = {D1(ZTH, 0), D1(ZTH, 1), D1(ZTH, 2)};
-    double dd[3];  // d_j (2 Khat + Theta)
+    double dd[3];  // d_j (2 Khat + Theta), stencil sums (times s1 below)
 #pragma unroll
     for (int j = 0; j < 3; ++j) dd[j] = fma(2.0, dKh[j], dTh[j]);
-    // d_j d_k beta^k for each j
+    // d_j d_k beta^k for each j (the k = j term a pure second derivative)
     double ddivb[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) ddivb[j] = fadd(fadd(D2(8, sidx(j, 0)), D2(9, sidx(j, 1)), K), D2(10, sidx(j, 2)), K);
+    for (int j = 0; j < 3; ++j)
+      ddivb[j] = fma(D2(8, sidx(j, 0)), j == 0 ? ds.s2p : ds.s2m,
+                     fma(D2(9, sidx(j, 1)), j == 1 ? ds.s2p : ds.s2m,
+                         fmul(D2(10, sidx(j, 2)), j == 2 ? ds.s2p : ds.s2m, K)));
     const double m3iW = fmul(-3.0, iW, K);
     const double twoal = fmul(2.0, al, K);
     const double twothirddivb = fmul(twothird, divb, K);
@@ -538,30 +539,31 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
       }
       r = fma(-2.0, sA, r);
       br = fma(m3iW, sW, br);
-      br = fma(-third, sD, br);
+      br = fma(-ds.ts1, sD, br);
       // 1/3 gt^ij d_j d_k beta^k + gt^jk d_j d_k beta^i
       const double lap = fma(third, sL,
-                             fma(2.0, fma(gu[1], D2(8 + i, 1), fma(gu[2], D2(8 + i, 2), fmul(gu[4], D2(8 + i, 4), K))),
-                                 fma(gu[0], D2(8 + i, 0), fma(gu[3], D2(8 + i, 3), fmul(gu[5], D2(8 + i, 5), K)))));
+                             fma(ds.ts2m, fma(gu[1], D2(8 + i, 1), fma(gu[2], D2(8 + i, 2), fmul(gu[4], D2(8 + i, 4), K))),
+                                 fmul(fma(gu[0], D2(8 + i, 0), fma(gu[3], D2(8 + i, 3), fmul(gu[5], D2(8 + i, 5), K))),
+                                      ds.s2p, K)));
       r = fadd(fma(twoal, br, r), lap, K);
       r = fma(Gd[i], twothirddivb, r);
       r = fma(m2k1al, fsub(Gam[i], Gd[i], K), r);
-      rhs[ZGAM + i] = fadd(ADV(ZGAM + i), r, K);
+      rhs[ZGAM + i] = fma(ds.s1, BD(ZGAM + i), r);
     }
   }
   // Theta
   rhs[ZTH] = fma(fmul(0.5, al, K), fma(fmul(twothird, Kt, K), Kt, fsub(Rsc, AA, K)),
-                 fma(fmul(-al, P.kappa1 * (2.0 + P.kappa2), K), Th, ADV(ZTH)));
+                 fma(fmul(-al, P.kappa1 * (2.0 + P.kappa2), K), Th, fmul(ds.s1, BD(ZTH), K)));
   // lapse (1+log) and shift (Gamma-driver)
-  rhs[ZAL] = fma(m2al, Kh, ADV(ZAL));
+  rhs[ZAL] = fma(m2al, Kh, fmul(ds.s1, BD(ZAL), K));
 #pragma unroll
-  for (int i = 0; i < 3; ++i) rhs[ZB + i] = fadd(ADV(ZB + i), fma(0.75, Gam[i], fmul(-eta, be[i], K)), K);
+  for (int i = 0; i < 3; ++i) rhs[ZB + i] = fma(ds.s1, BD(ZB + i), fma(0.75, Gam[i], fmul(-eta, be[i], K)));
   if (kDiag) {
     diag[0] = Rsc;
     diag[1] = AA;
     diag[2] = Kt;
   }
-#undef ADV
+#undef BD
 #undef FLD
 #undef D1
 #undef D2
@@ -588,7 +590,7 @@ __global__ void __launch_bounds__(128, BPS) z4c_stage_kernel(StageArgs a, const 
       const int k = q / (T.nx * T.ny);
       const long o = (long)(T.z0 + k) * a.sz + (long)(T.y0 + j) * a.sy + (T.x0 + i);
       double rhs[kNZ4c];
-      z4c_rhs_point<false>(a.Y, S, a.fs, o, P, a.eta ? a.eta[o] : P.eta, rhs, nullptr, K);
+      z4c_rhs_point<false>(a.Y, S, a.fs, o, P, a.eta ? a.eta[o] : P.eta, a.ds, rhs, nullptr, K);
 #pragma unroll
       for (int f = 0; f < kNZ4c; ++f) {
         const long fo = (long)f * a.fs + o;
@@ -614,7 +616,7 @@ __global__ void __launch_bounds__(128, BPS) z4c_stage_kernel(StageArgs a, const 
 // out[c * out_stride + cell], cells numbered x-fastest within the box.
 __global__ void __launch_bounds__(128) z4c_constraints_kernel(const double* __restrict__ Y,
                                                              const double* __restrict__ S, double* __restrict__ out,
-                                                             long fs, int sy, int sz, Z4cParams P,
+                                                             long fs, int sy, int sz, Z4cParams P, DerivScales ds,
                                                              const Tile* __restrict__ tiles, int ntiles,
                                                              long out_stride, int bx, int by, int bz, int nbx,
                                                              int nby, FmaK K) {
@@ -626,9 +628,9 @@ __global__ void __launch_bounds__(128) z4c_constraints_kernel(const double* __re
       const long o = (long)az * sz + (long)ay * sy + ax;
       const long cell = ((long)(az - bz) * nby + (ay - by)) * nbx + (ax - bx);
 #define FLD(f) Y[(long)(f) * fs + o]
-#define D1(f, d) S[(long)(Q_D1 + 3 * (f) + (d)) * fs + o]
+#define D1(f, d) (ds.s1 * S[(long)(Q_D1 + 3 * (f) + (d)) * fs + o])
       double rhs[kNZ4c], diag[3];
-      z4c_rhs_point<true>(Y, S, fs, o, P, P.eta, rhs, diag, K);
+      z4c_rhs_point<true>(Y, S, fs, o, P, P.eta, ds, rhs, diag, K);
       out[cell] = diag[0] + (2.0 / 3.0) * diag[2] * diag[2] - diag[1];
       double g[6], A[6], gu[6];
       for (int s = 0; s < 6; ++s) {
@@ -738,24 +740,24 @@ cudaError_t z4c_init_launch_config() {
   return cudaSuccess;
 }
 
-cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy, int sz, double h, const Tile* tiles,
+cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy, int sz, const Tile* tiles,
                               int ntiles, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
   const int grid = ntiles < sm_count() * 16 ? ntiles : sm_count() * 16;
-  z4c_derivs_kernel<<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles);
+  z4c_derivs_kernel<<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, tiles, ntiles);
   return cudaGetLastError();
 }
 
-cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, double h, const RowSeg* segs, int nsegs,
+cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, const RowSeg* segs, int nsegs,
                            cudaStream_t s, int order) {
   if (nsegs == 0) return cudaSuccess;
   const int grid = nsegs < caps().dxy ? nsegs : caps().dxy;
-  if (order == 8) z4c_dxy_kernel<8><<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, h, FmaK{1.0, -1.0, -0.0});
-  else z4c_dxy_kernel<4><<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, h, FmaK{1.0, -1.0, -0.0});
+  if (order == 8) z4c_dxy_kernel<8><<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, FmaK{1.0, -1.0, -0.0});
+  else z4c_dxy_kernel<4><<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, FmaK{1.0, -1.0, -0.0});
   return cudaGetLastError();
 }
 
-cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz, double h,
+cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz,
                                     const Tile* tiles, int ntiles, cudaStream_t s, int order, int max_cols) {
   if (ntiles == 0) return cudaSuccess;
   if (max_cols < 1) return cudaErrorInvalidValue;
@@ -763,9 +765,9 @@ cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, i
   const int grid = units < caps().derivs ? (int)units : caps().derivs;
   const FmaK K{1.0, -1.0, -0.0};
   if (order == 8)
-    z4c_derivs_split_kernel<8><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles, max_cols, K);
+    z4c_derivs_split_kernel<8><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, tiles, ntiles, max_cols, K);
   else
-    z4c_derivs_split_kernel<4><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, h, tiles, ntiles, max_cols, K);
+    z4c_derivs_split_kernel<4><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, tiles, ntiles, max_cols, K);
   return cudaGetLastError();
 }
 
@@ -796,11 +798,11 @@ cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4
 }
 
 cudaError_t launch_z4c_constraints(const double* Y, const double* scratch, double* out, long fs, int sy, int sz,
-                                   const Z4cParams& p, const Tile* tiles, int ntiles, long out_stride,
-                                   const int* box_lo, const int* box_n, cudaStream_t s) {
+                                   const Z4cParams& p, const DerivScales& ds, const Tile* tiles, int ntiles,
+                                   long out_stride, const int* box_lo, const int* box_n, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
   const int grid = ntiles < sm_count() * 16 ? ntiles : sm_count() * 16;
-  z4c_constraints_kernel<<<grid, 128, 0, s>>>(Y, scratch, out, fs, sy, sz, p, tiles, ntiles, out_stride, box_lo[0],
+  z4c_constraints_kernel<<<grid, 128, 0, s>>>(Y, scratch, out, fs, sy, sz, p, ds, tiles, ntiles, out_stride, box_lo[0],
                                               box_lo[1], box_lo[2], box_n[0], box_n[1], FmaK{1.0, -1.0, -0.0});
   return cudaGetLastError();
 }
