@@ -114,11 +114,27 @@ __global__ void __launch_bounds__(kThreads) z4c_derivs_kernel(const double* __re
 // field of Hessian slot s (W, gt x6, alpha, beta x3): slots 0..6 -> fields 0..6, 7..10 -> 18..21
 __device__ __forceinline__ int d2_field(int s) { return s <= 6 ? s : s + 11; }
 
-// Centred first derivative from the differences dm = v_m - v_-m, m = 1..R
-// (R = ORD/2), as the integer-weight sum: 4th order 8 d1 - d2 (= 12 h u'),
-// 8th order 672 d1 - 168 d2 + 32 d3 - 3 d4 (= 840 h u').
+// The stencil sums are arranged for the FP64 issue rates of this GPU: a
+// fused multiply-add whose multiplier is not +-1 and whose addend is not zero
+// issues about 1.2x as fast as an addition (or a unit-multiplier FMA, or a
+// multiplication).  So every weighted value enters through a general FMA, and
+// only values of unit weight are added; pair sums v_m + v_-m are formed only
+// where two sums share them.  lo[m] = v_-(m+1), hi[m] = v_(m+1).
+
+// Centred first derivative as the integer-weight sum: 4th order
+// 8 (v_1 - v_-1) - (v_2 - v_-2) (= 12 h u'), one addition and two FMAs;
+// 8th order 672 d1 - 168 d2 + 32 d3 - 3 d4 (= 840 h u'), dm = v_m - v_-m.
 template <int ORD>
-__device__ __forceinline__ double dfirst(const double* d, const FmaK& K) {
+__device__ __forceinline__ double dfirst(const double* lo, const double* hi, const FmaK& K) {
+  if (ORD == 4) return fma(8.0, hi[0], fma(-8.0, lo[0], fsub(lo[1], hi[1], K)));
+  return fma(672.0, hi[0],
+             fma(-672.0, lo[0],
+                 fma(-168.0, hi[1],
+                     fma(168.0, lo[1], fma(32.0, hi[2], fma(-32.0, lo[2], fmul(3.0, fsub(lo[3], hi[3], K), K)))))));
+}
+// The same first derivative from the differences dm = v_m - v_-m, m = 1..R.
+template <int ORD>
+__device__ __forceinline__ double dfirst_d(const double* d, const FmaK& K) {
   if (ORD == 4) return fma(8.0, d[0], -d[1]);
   return fma(672.0, d[0], fma(-168.0, d[1], fma(32.0, d[2], fmul(-3.0, d[3], K))));
 }
@@ -127,7 +143,7 @@ __device__ __forceinline__ double dfirst(const double* d, const FmaK& K) {
 // 8064 p1 - 1008 p2 + 128 p3 - 9 p4 - 14350 u0 (= 5040 h^2 u'').
 template <int ORD>
 __device__ __forceinline__ double dsecond(const double* p, double u0, const FmaK& K) {
-  if (ORD == 4) return fma(-30.0, u0, fma(16.0, p[0], -p[1]));
+  if (ORD == 4) return fma(16.0, p[0], fma(-30.0, u0, -p[1]));
   return fma(-14350.0, u0, fma(8064.0, p[0], fma(-1008.0, p[1], fma(128.0, p[2], fmul(-9.0, p[3], K)))));
 }
 
@@ -143,16 +159,22 @@ __global__ void __launch_bounds__(128) z4c_dxy_kernel(const double* __restrict__
       const long o = sg.off + (q - slot * sg.n);
       const int f = d2_field(slot);
       const double* u = Y + (long)f * fs + o;
-      double d[R];
+      double lo[R], hi[R];
       if (sg.which & 1) {
 #pragma unroll
-        for (int m = 1; m <= R; ++m) d[m - 1] = fsub(u[m], u[-m], K);
-        S[(long)(Q_D1 + 3 * f + 0) * fs + o] = dfirst<ORD>(d, K);
+        for (int m = 1; m <= R; ++m) {
+          lo[m - 1] = u[-m];
+          hi[m - 1] = u[m];
+        }
+        S[(long)(Q_D1 + 3 * f + 0) * fs + o] = dfirst<ORD>(lo, hi, K);
       }
       if (sg.which & 2) {
 #pragma unroll
-        for (int m = 1; m <= R; ++m) d[m - 1] = fsub(u[m * sy], u[-m * sy], K);
-        S[(long)(Q_D1 + 3 * f + 1) * fs + o] = dfirst<ORD>(d, K);
+        for (int m = 1; m <= R; ++m) {
+          lo[m - 1] = u[-m * sy];
+          hi[m - 1] = u[m * sy];
+        }
+        S[(long)(Q_D1 + 3 * f + 1) * fs + o] = dfirst<ORD>(lo, hi, K);
       }
     }
   }
@@ -208,45 +230,118 @@ __global__ void __launch_bounds__(kThreads, 2) z4c_derivs_split_kernel(const dou
       for (int k = 0; k < T.nz; ++k) {
         const long o = o0 + k * sz;
         const double* v = u + k * sz;
-        const double u0 = w[WR];
-        double p[3][4], d[4];
-        // x and y from memory, z from the window
+        if (ORD == 4) {
+          // 4th order: every weighted value through a general FMA (see dfirst)
+          const double u0 = w[WR];
+          // u along x and y from memory, along z from the window
+          double lo[3][WR], hi[3][WR];
 #pragma unroll
-        for (int dim = 0; dim < 2; ++dim) {
-          const long s = dim == 0 ? 1 : sy;
-#pragma unroll
-          for (int m = 1; m <= WR; ++m) p[dim][m - 1] = fadd(v[-m * s], v[m * s], K);
+          for (int m = 1; m <= WR; ++m) {
+            lo[0][m - 1] = v[-m];
+            hi[0][m - 1] = v[m];
+            lo[1][m - 1] = v[-m * sy];
+            hi[1][m - 1] = v[m * sy];
+            lo[2][m - 1] = w[WR - m];
+            hi[2][m - 1] = w[WR + m];
+          }
+          // Kreiss-Oliger (r = 4): sum_d (u_-3 - 6 u_-2 + 15 u_-1 - 20 u_0 + 15 u_1 - 6 u_2 + u_3)
+          double ko;
           if (sl < 0) {
 #pragma unroll
-            for (int m = 1; m <= R; ++m) d[m - 1] = fsub(v[m * s], v[-m * s], K);
-            S[(long)(Q_D1 + 3 * f + dim) * fs + o] = dfirst<ORD>(d, K);
+            for (int dim = 0; dim < 3; ++dim) S[(long)(Q_D1 + 3 * f + dim) * fs + o] = dfirst<ORD>(lo[dim], hi[dim], K);
+            ko = fma(-60.0, u0, lo[0][2]);
+            ko = fadd(ko, hi[0][2], K);
+#pragma unroll
+            for (int dim = 1; dim < 3; ++dim) ko = fadd(fadd(ko, lo[dim][2], K), hi[dim][2], K);
+#pragma unroll
+            for (int dim = 0; dim < 3; ++dim)
+              ko = fma(15.0, hi[dim][0], fma(15.0, lo[dim][0], fma(-6.0, hi[dim][1], fma(-6.0, lo[dim][1], ko))));
+          } else {
+            // Hessian fields: the pair sums of the second derivatives, shared with the KO sum
+            double p[3][2];
+#pragma unroll
+            for (int dim = 0; dim < 3; ++dim)
+#pragma unroll
+              for (int m = 0; m < 2; ++m) p[dim][m] = fadd(lo[dim][m], hi[dim][m], K);
+            double* d2 = S + (long)(Q_D2 + 6 * sl) * fs + o;
+            d2[0 * fs] = dsecond<ORD>(p[0], u0, K);
+            d2[3 * fs] = dsecond<ORD>(p[1], u0, K);
+            d2[5 * fs] = dsecond<ORD>(p[2], u0, K);
+            ko = fma(-60.0, u0, lo[0][2]);
+            ko = fadd(ko, hi[0][2], K);
+#pragma unroll
+            for (int dim = 1; dim < 3; ++dim) ko = fadd(fadd(ko, lo[dim][2], K), hi[dim][2], K);
+            // D_z from the pair sums: 16 v_1 - 8 p1 - 2 v_2 + p2 = 8 (v_1 - v_-1) - (v_2 - v_-2)
+            S[(long)(Q_D1 + 3 * f + 2) * fs + o] =
+                fma(16.0, hi[2][0], fma(-8.0, p[2][0], fma(-2.0, hi[2][1], p[2][1])));
+#pragma unroll
+            for (int dim = 0; dim < 3; ++dim) ko = fma(15.0, p[dim][0], fma(-6.0, p[dim][1], ko));
+            // mixed: the first-derivative stencil applied to the stored D_x (along y and z) and D_y (along z)
+            double ml[R], mh[R];
+            const double* dxk = Dx + k * sz;
+#pragma unroll
+            for (int m = 1; m <= R; ++m) {
+              ml[m - 1] = dxk[-m * sy];
+              mh[m - 1] = dxk[m * sy];
+            }
+            d2[1 * fs] = dfirst<ORD>(ml, mh, K);  // D_y D_x
+#pragma unroll
+            for (int m = 1; m <= R; ++m) {
+              ml[m - 1] = wx[R - m];
+              mh[m - 1] = wx[R + m];
+            }
+            d2[2 * fs] = dfirst<ORD>(ml, mh, K);  // D_z D_x
+#pragma unroll
+            for (int m = 1; m <= R; ++m) {
+              ml[m - 1] = wy[R - m];
+              mh[m - 1] = wy[R + m];
+            }
+            d2[4 * fs] = dfirst<ORD>(ml, mh, K);  // D_z D_y
           }
-        }
+          S[(long)(Q_KO + f) * fs + o] = ko;
+        } else {
+          // 8th order: differences and pair sums formed first (fewer live values than the
+          // 4th-order arrangement, which spilled and ran slower here)
+          const double u0 = w[WR];
+          double p[3][4], d[4];
+          // x and y from memory, z from the window
 #pragma unroll
-        for (int m = 1; m <= WR; ++m) p[2][m - 1] = fadd(w[WR - m], w[WR + m], K);
+          for (int dim = 0; dim < 2; ++dim) {
+            const long s = dim == 0 ? 1 : sy;
 #pragma unroll
-        for (int m = 1; m <= R; ++m) d[m - 1] = fsub(w[WR + m], w[WR - m], K);
-        S[(long)(Q_D1 + 3 * f + 2) * fs + o] = dfirst<ORD>(d, K);
-        // Kreiss-Oliger (r = 4): sum_d (u_-3 - 6 u_-2 + 15 u_-1 - 20 u_0 + 15 u_1 - 6 u_2 + u_3)
-        const double P1 = fadd(fadd(p[0][0], p[1][0], K), p[2][0], K);
-        const double P2 = fadd(fadd(p[0][1], p[1][1], K), p[2][1], K);
-        const double P3 = fadd(fadd(p[0][2], p[1][2], K), p[2][2], K);
-        S[(long)(Q_KO + f) * fs + o] = fma(15.0, P1, fma(-6.0, P2, fma(-60.0, u0, P3)));
-        if (sl >= 0) {
-          double* d2 = S + (long)(Q_D2 + 6 * sl) * fs + o;
-          d2[0 * fs] = dsecond<ORD>(p[0], u0, K);
-          d2[3 * fs] = dsecond<ORD>(p[1], u0, K);
-          d2[5 * fs] = dsecond<ORD>(p[2], u0, K);
-          const double* dxk = Dx + k * sz;
+            for (int m = 1; m <= WR; ++m) p[dim][m - 1] = fadd(v[-m * s], v[m * s], K);
+            if (sl < 0) {
 #pragma unroll
-          for (int m = 1; m <= R; ++m) d[m - 1] = fsub(dxk[m * sy], dxk[-m * sy], K);
-          d2[1 * fs] = dfirst<ORD>(d, K);  // D_y D_x
+              for (int m = 1; m <= R; ++m) d[m - 1] = fsub(v[m * s], v[-m * s], K);
+              S[(long)(Q_D1 + 3 * f + dim) * fs + o] = dfirst_d<ORD>(d, K);
+            }
+          }
 #pragma unroll
-          for (int m = 1; m <= R; ++m) d[m - 1] = fsub(wx[R + m], wx[R - m], K);
-          d2[2 * fs] = dfirst<ORD>(d, K);  // D_z D_x
+          for (int m = 1; m <= WR; ++m) p[2][m - 1] = fadd(w[WR - m], w[WR + m], K);
 #pragma unroll
-          for (int m = 1; m <= R; ++m) d[m - 1] = fsub(wy[R + m], wy[R - m], K);
-          d2[4 * fs] = dfirst<ORD>(d, K);  // D_z D_y
+          for (int m = 1; m <= R; ++m) d[m - 1] = fsub(w[WR + m], w[WR - m], K);
+          S[(long)(Q_D1 + 3 * f + 2) * fs + o] = dfirst_d<ORD>(d, K);
+          // Kreiss-Oliger (r = 4): sum_d (u_-3 - 6 u_-2 + 15 u_-1 - 20 u_0 + 15 u_1 - 6 u_2 + u_3)
+          const double P1 = fadd(fadd(p[0][0], p[1][0], K), p[2][0], K);
+          const double P2 = fadd(fadd(p[0][1], p[1][1], K), p[2][1], K);
+          const double P3 = fadd(fadd(p[0][2], p[1][2], K), p[2][2], K);
+          S[(long)(Q_KO + f) * fs + o] = fma(15.0, P1, fma(-6.0, P2, fma(-60.0, u0, P3)));
+          if (sl >= 0) {
+            double* d2 = S + (long)(Q_D2 + 6 * sl) * fs + o;
+            d2[0 * fs] = dsecond<ORD>(p[0], u0, K);
+            d2[3 * fs] = dsecond<ORD>(p[1], u0, K);
+            d2[5 * fs] = dsecond<ORD>(p[2], u0, K);
+            const double* dxk = Dx + k * sz;
+#pragma unroll
+            for (int m = 1; m <= R; ++m) d[m - 1] = fsub(dxk[m * sy], dxk[-m * sy], K);
+            d2[1 * fs] = dfirst_d<ORD>(d, K);  // D_y D_x
+#pragma unroll
+            for (int m = 1; m <= R; ++m) d[m - 1] = fsub(wx[R + m], wx[R - m], K);
+            d2[2 * fs] = dfirst_d<ORD>(d, K);  // D_z D_x
+#pragma unroll
+            for (int m = 1; m <= R; ++m) d[m - 1] = fsub(wy[R + m], wy[R - m], K);
+            d2[4 * fs] = dfirst_d<ORD>(d, K);  // D_z D_y
+          }
         }
         if (k + 1 < T.nz) {  // slide the windows one cell up in z
 #pragma unroll
