@@ -109,7 +109,7 @@ struct Weights {
 // 1/(12h^2), 1/(144h^2); 8th order: 1/(840h), 1/(5040h^2), 1/(840h)^2).
 struct DerivScales {
   double s1, s2p, s2m;  // first, pure second and mixed second derivative
-  double hs1, ts1;      // s1 / 2 and s1 / 3
+  double hs1, ts1, qs1;  // s1 / 2, s1 / 3 and s1 / 4
   double hs2p, ts2m;    // s2p / 2 and 2 s2m
 };
 // The products are formed on the host so that the kernels take every factor
@@ -122,6 +122,7 @@ inline DerivScales deriv_scales(int order, double h) {
   d.s2m = 1.0 / (w1 * h * w1 * h);
   d.hs1 = 0.5 * d.s1;
   d.ts1 = d.s1 / 3.0;
+  d.qs1 = 0.25 * d.s1;
   d.hs2p = 0.5 * d.s2p;
   d.ts2m = 2.0 * d.s2m;
   return d;

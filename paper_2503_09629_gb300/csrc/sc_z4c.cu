@@ -423,20 +423,33 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
   for (int s = 0; s < 6; ++s)
 #pragma unroll
     for (int d = 0; d < 3; ++d) dg[s][d] = D1(ZG + s, d);
-  // Gl[k][s(ij)] = Gamma_{k,ij} = (d_i g_jk + d_j g_ik - d_k g_ij) / 2
-  double Gl[3][6], Gu[3][6];
+  // Gamma_{k,ij} = (d_i g_jk + d_j g_ik - d_k g_ij) / 2 = hs1 * Gs[k][s(ij)],
+  // Gs the combination of stored sums; where k is i or j two of the three
+  // terms cancel (k = i: d_j g_ii; k = j: d_i g_jj), where i = j != k two
+  // coincide (2 d_i g_ik - d_k g_ii).
+  double Gs[3][6], Gu[3][6];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = i; j < 3; ++j)
-        Gl[k][sidx(i, j)] = fma(ds.hs1, dg[sidx(j, k)][i], fma(ds.hs1, dg[sidx(i, k)][j], fmul(-ds.hs1, dg[sidx(i, j)][k], K)));
+      for (int j = i; j < 3; ++j) {
+        double v;
+        if (k == i) v = dg[sidx(i, i)][j];
+        else if (k == j) v = dg[sidx(j, j)][i];
+        else if (i == j) v = fma(2.0, dg[sidx(i, k)][i], -dg[sidx(i, i)][k]);
+        else v = fsub(fadd(dg[sidx(j, k)][i], dg[sidx(i, k)][j], K), dg[sidx(i, j)][k], K);
+        Gs[k][sidx(i, j)] = v;
+      }
+  // the factor hs1 of Gamma_{k,ij} carried by the metric that raises its index
+  double gus[6];
+#pragma unroll
+  for (int s = 0; s < 6; ++s) gus[s] = fmul(gu[s], ds.hs1, K);
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
     for (int s = 0; s < 6; ++s)
-      Gu[k][s] = fma(gu[sidx(k, 0)], Gl[0][s], fma(gu[sidx(k, 1)], Gl[1][s], fmul(gu[sidx(k, 2)], Gl[2][s], K)));
+      Gu[k][s] = fma(gus[sidx(k, 0)], Gs[0][s], fma(gus[sidx(k, 1)], Gs[1][s], fmul(gus[sidx(k, 2)], Gs[2][s], K)));
   // (Gamma_d)^k = gt^ij Gamma^k_ij
   double Gd[3];
 #pragma unroll
@@ -452,8 +465,8 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
     for (int k = 0; k < 3; ++k)
 #pragma unroll
       for (int l = 0; l < 3; ++l)
-        U[j][k][l] = fma(gu[sidx(l, 0)], Gl[j][sidx(k, 0)],
-                         fma(gu[sidx(l, 1)], Gl[j][sidx(k, 1)], fmul(gu[sidx(l, 2)], Gl[j][sidx(k, 2)], K)));
+        U[j][k][l] = fma(gus[sidx(l, 0)], Gs[j][sidx(k, 0)],
+                         fma(gus[sidx(l, 1)], Gs[j][sidx(k, 1)], fmul(gus[sidx(l, 2)], Gs[j][sidx(k, 2)], K)));
 
   const double dW[3] = {fmul(D1(ZW, 0), ds.s1, K), fmul(D1(ZW, 1), ds.s1, K), fmul(D1(ZW, 2), ds.s1, K)};
   const double dal[3] = {fmul(D1(ZAL, 0), ds.s1, K), fmul(D1(ZAL, 1), ds.s1, K), fmul(D1(ZAL, 2), ds.s1, K)};
@@ -476,52 +489,56 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
       DDW[s] = fma(D2(0, s), s2, -fma(Gu[0][s], dW[0], fma(Gu[1][s], dW[1], fmul(Gu[2][s], dW[2], K))));
       trDDW = fma(gw[s], DDW[s], trDDW);
     }
-    const double dGam[3][3] = {{D1(ZGAM, 0), D1(ZGAM, 1), D1(ZGAM, 2)},
-                               {D1(ZGAM + 1, 0), D1(ZGAM + 1, 1), D1(ZGAM + 1, 2)},
-                               {D1(ZGAM + 2, 0), D1(ZGAM + 2, 1), D1(ZGAM + 2, 2)}};
-    // T1[i][j] = Gamma^k_{li} U[j][k][l]
-    double T1[3][3];
+    // hs1 d_j Gamt^k, and the scales of the second-derivative terms carried by gt^lm
+    double dGh[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        double s = 0.0;
+      for (int j = 0; j < 3; ++j) dGh[k][j] = fmul(D1(ZGAM + k, j), ds.hs1, K);
+    double guS[6];  // -1/2 s2p gt^ll (pure), -s2m gt^lm (mixed: the pair lm, ml counted once)
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+    for (int s = 0; s < 6; ++s) guS[s] = fmul(gu[s], (s == 0 || s == 3 || s == 5) ? -ds.hs2p : -ds.s2m, K);
+    double Gdq[3];  // (Gamma_d)^k hs1 / 2
 #pragma unroll
-          for (int l = 0; l < 3; ++l) s = fma(Gu[k][sidx(l, i)], U[j][k][l], s);
-        T1[i][j] = s;
-      }
+    for (int k = 0; k < 3; ++k) Gdq[k] = fmul(Gd[k], ds.qs1, K);
     const double m2WiW = fmul(fmul(fmul(-2.0, dWdW, K), iW, K), iW, K);  // -2 |dW|^2 / W^2
+    // Every term of R_ij below is accumulated in one chain of FMAs.
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = i; j < 3; ++j) {
         const int s = sidx(i, j);
-        // -1/2 gt^lm d_l d_m gt_ij (pure and mixed second derivatives with their scales)
-        double r = fma(-ds.hs2p, fma(gu[0], D2(1 + s, 0), fma(gu[3], D2(1 + s, 3), fmul(gu[5], D2(1 + s, 5), K))),
-                       fmul(fma(gu[1], D2(1 + s, 1), fma(gu[2], D2(1 + s, 2), fmul(gu[4], D2(1 + s, 4), K))), -ds.s2m,
-                            K));
+        // gt^lm (2 Gamma^k_l(i Gamma_j)km + Gamma^k_im Gamma_klj) = T_ij + T_ji + t3,
+        // T_ij = Gamma^k_li U[j][k][l], t3 = Gamma^k_im U[k][j][m]
+        double r;
+        if (i == j) {
+          double t = fmul(Gu[0][sidx(0, i)], U[i][0][0], K);
+#pragma unroll
+          for (int q = 1; q < 9; ++q) t = fma(Gu[q / 3][sidx(q % 3, i)], U[i][q / 3][q % 3], t);
+          r = fmul(Gu[0][sidx(i, 0)], U[0][j][0], K);
+#pragma unroll
+          for (int q = 1; q < 9; ++q) r = fma(Gu[q / 3][sidx(i, q % 3)], U[q / 3][j][q % 3], r);
+          r = fma(2.0, t, r);
+        } else {
+          r = fmul(Gu[0][sidx(i, 0)], U[0][j][0], K);
+#pragma unroll
+          for (int q = 1; q < 9; ++q) r = fma(Gu[q / 3][sidx(i, q % 3)], U[q / 3][j][q % 3], r);
+#pragma unroll
+          for (int q = 0; q < 9; ++q)
+            r = fma(Gu[q / 3][sidx(q % 3, i)], U[j][q / 3][q % 3], fma(Gu[q / 3][sidx(q % 3, j)], U[i][q / 3][q % 3], r));
+        }
+        // -1/2 gt^lm d_l d_m gt_ij
+#pragma unroll
+        for (int q = 0; q < 6; ++q) r = fma(guS[q], D2(1 + s, q), r);
         // gt_k(i d_j) Gamt^k
-        double a = 0.0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) a = fma(g[sidx(k, i)], dGam[k][j], fma(g[sidx(k, j)], dGam[k][i], a));
-        r = fma(ds.hs1, a, r);
+        for (int k = 0; k < 3; ++k) r = fma(g[sidx(k, i)], dGh[k][j], fma(g[sidx(k, j)], dGh[k][i], r));
         // (Gamma_d)^k Gamma_(ij)k
-        double b = 0.0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) b = fma(Gd[k], fadd(Gl[i][sidx(j, k)], Gl[j][sidx(i, k)], K), b);
-        r = fma(0.5, b, r);
-        // gt^lm (2 Gamma^k_l(i Gamma_j)km + Gamma^k_im Gamma_klj)
-        double t3 = 0.0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-          for (int m = 0; m < 3; ++m) t3 = fma(Gu[k][sidx(i, m)], U[k][j][m], t3);
-        r = fadd(r, fadd(fadd(T1[i][j], T1[j][i], K), t3, K), K);
+        for (int k = 0; k < 3; ++k) r = fma(Gdq[k], Gs[i][sidx(j, k)], fma(Gdq[k], Gs[j][sidx(i, k)], r));
         // R^W_ij = (D_i D_j W + gt_ij D^l D_l W) / W - 2 gt_ij |dW|^2 / W^2
-        const double rw = fma(fma(g[s], trDDW, DDW[s]), iW, fmul(g[s], m2WiW, K));
-        R[s] = fadd(r, rw, K);
+        r = fma(g[s], m2WiW, r);
+        R[s] = fma(fma(g[s], trDDW, DDW[s]), iW, r);
         // D_i D_j alpha with Gamma^k_ij - (delta^k_i d_j W + delta^k_j d_i W - gt_ij gt^kl d_l W) / W
         const double gd = fma(Gu[0][s], dal[0], fma(Gu[1][s], dal[1], fmul(Gu[2][s], dal[2], K)));
         const double wt = fma(dW[j], dal[i], fma(dW[i], dal[j], fmul(-g[s], dWdal, K)));
@@ -565,10 +582,12 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
   const double Kt = fma(2.0, Th, Kh);
   const double third = 1.0 / 3.0, twothird = 2.0 / 3.0;
 
-  // advection beta^i d_i f = s1 * BD(f), the scale applied where the term is added
-#define BD(f) fma(be[0], D1(f, 0), fma(be[1], D1(f, 1), fmul(be[2], D1(f, 2), K)))
+  // advection beta^i d_i f added onto x, the scale s1 carried by beta
+  const double bes[3] = {fmul(be[0], ds.s1, K), fmul(be[1], ds.s1, K), fmul(be[2], ds.s1, K)};
+#define ADV_ON(f, x) fma(bes[0], D1(f, 0), fma(bes[1], D1(f, 1), fma(bes[2], D1(f, 2), (x))))
+#define ADV(f) fma(bes[0], D1(f, 0), fma(bes[1], D1(f, 1), fmul(bes[2], D1(f, 2), K)))
   // W
-  rhs[ZW] = fma(fmul(third, W, K), fma(al, Kt, -divb), fmul(ds.s1, BD(ZW), K));
+  rhs[ZW] = ADV_ON(ZW, fmul(fmul(third, W, K), fma(al, Kt, -divb), K));
   // gt_ij and At_ij
   double X[6], trX = 0.0;
 #pragma unroll
@@ -592,13 +611,13 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
         la = fma(A[sidx(k, i)], dbe[k][j], fma(A[sidx(k, j)], dbe[k][i], la));
         aa = fma(Am[k][i], A[sidx(k, j)], aa);
       }
-      rhs[ZG + s] = fma(ds.s1, BD(ZG + s), fma(m2al, A[s], fma(m23divb, g[s], lg)));
+      rhs[ZG + s] = ADV_ON(ZG + s, fma(m2al, A[s], fma(m23divb, g[s], lg)));
       const double tf = fma(m13trX, g[s], X[s]);
-      rhs[ZA + s] = fma(ds.s1, BD(ZA + s), fma(W2, tf, fma(alKt, A[s], fma(m2al, aa, fma(m23divb, A[s], la)))));
+      rhs[ZA + s] = ADV_ON(ZA + s, fma(W2, tf, fma(alKt, A[s], fma(m2al, aa, fma(m23divb, A[s], la)))));
     }
   // Khat
   rhs[ZK] = fma(al, fma(fmul(third, Kt, K), Kt, AA),
-                fma(fmul(al, P.kappa1 * (1.0 - P.kappa2), K), Th, fma(ds.s1, BD(ZK), -DiDial)));
+                fma(fmul(al, P.kappa1 * (1.0 - P.kappa2), K), Th, ADV_ON(ZK, -DiDial)));
   // Gamt^i
   {
     const double dKh[3] = {D1(ZK, 0), D1(ZK, 1), D1(ZK, 2)};
@@ -617,6 +636,7 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
     const double twoal = fmul(2.0, al, K);
     const double twothirddivb = fmul(twothird, divb, K);
     const double m2k1al = fmul(-2.0 * P.kappa1, al, K);
+    const double cGd = fsub(twothirddivb, m2k1al, K);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       // Gamt^i_jk At^jk
@@ -635,30 +655,30 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
       r = fma(-2.0, sA, r);
       br = fma(m3iW, sW, br);
       br = fma(-ds.ts1, sD, br);
+      r = fma(twoal, br, r);
       // 1/3 gt^ij d_j d_k beta^k + gt^jk d_j d_k beta^i
-      const double lap = fma(third, sL,
-                             fma(ds.ts2m, fma(gu[1], D2(8 + i, 1), fma(gu[2], D2(8 + i, 2), fmul(gu[4], D2(8 + i, 4), K))),
-                                 fmul(fma(gu[0], D2(8 + i, 0), fma(gu[3], D2(8 + i, 3), fmul(gu[5], D2(8 + i, 5), K))),
-                                      ds.s2p, K)));
-      r = fadd(fma(twoal, br, r), lap, K);
-      r = fma(Gd[i], twothirddivb, r);
-      r = fma(m2k1al, fsub(Gam[i], Gd[i], K), r);
-      rhs[ZGAM + i] = fma(ds.s1, BD(ZGAM + i), r);
+      r = fma(ds.ts2m, fma(gu[1], D2(8 + i, 1), fma(gu[2], D2(8 + i, 2), fmul(gu[4], D2(8 + i, 4), K))), r);
+      r = fma(ds.s2p, fma(gu[0], D2(8 + i, 0), fma(gu[3], D2(8 + i, 3), fmul(gu[5], D2(8 + i, 5), K))), r);
+      r = fma(third, sL, r);
+      // 2/3 (Gamma_d)^i div beta - 2 kappa1 alpha (Gamt^i - (Gamma_d)^i)
+      r = fma(Gd[i], cGd, fma(m2k1al, Gam[i], r));
+      rhs[ZGAM + i] = ADV_ON(ZGAM + i, r);
     }
   }
   // Theta
   rhs[ZTH] = fma(fmul(0.5, al, K), fma(fmul(twothird, Kt, K), Kt, fsub(Rsc, AA, K)),
-                 fma(fmul(-al, P.kappa1 * (2.0 + P.kappa2), K), Th, fmul(ds.s1, BD(ZTH), K)));
+                 fma(fmul(-al, P.kappa1 * (2.0 + P.kappa2), K), Th, ADV(ZTH)));
   // lapse (1+log) and shift (Gamma-driver)
-  rhs[ZAL] = fma(m2al, Kh, fmul(ds.s1, BD(ZAL), K));
+  rhs[ZAL] = fma(m2al, Kh, ADV(ZAL));
 #pragma unroll
-  for (int i = 0; i < 3; ++i) rhs[ZB + i] = fma(ds.s1, BD(ZB + i), fma(0.75, Gam[i], fmul(-eta, be[i], K)));
+  for (int i = 0; i < 3; ++i) rhs[ZB + i] = ADV_ON(ZB + i, fma(0.75, Gam[i], fmul(-eta, be[i], K)));
   if (kDiag) {
     diag[0] = Rsc;
     diag[1] = AA;
     diag[2] = Kt;
   }
-#undef BD
+#undef ADV_ON
+#undef ADV
 #undef FLD
 #undef D1
 #undef D2
