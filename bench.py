@@ -59,26 +59,28 @@ def _measured_hbm_gbs() -> float:
 
 
 HBM_GBS = _measured_hbm_gbs()
-# Algorithmic FP64 flops per interior cell of each Z4c pass in this
-# formulation: adds, multiplies and fused multiply-adds (2 flops) counted by
-# ncu on the kernels before their additions were re-expressed as FMAs with a
-# unit multiplier (that rewrite changes the instruction, not the arithmetic).
-# z4c_derivs = row-segment D_x/D_y pass (133) + per-cell pass (1047);
-# profiles/z4c_kernels_bl3level64_ncu.md.
+# Algorithmic FP64 flops per interior cell of each Z4c pass: adds,
+# multiplies and fused multiply-adds (2 flops) of the formulation as first
+# written, counted by ncu (z4c_derivs = row-segment D_x/D_y pass 133 +
+# per-cell pass 1047).  Later rewrites evaluate the same right-hand side with
+# fewer FP64 instructions (FP64_INSTR_PER_CELL); the flop counts stay fixed so
+# that achieved rates measure the method's work, and the issue fractions
+# measure the current instruction stream.
 FLOPS_PER_CELL = {"z4c_derivs": 1180.0, "z4c_stage": 1971.0}
-# DRAM bytes (read + write) per interior cell of each kernel from an ncu
-# capture of a 262,144-cell launch without cache flushes (--cache-control
-# none; profiles/z4c_kernels_bl3level64_ncu.md), scaled to a launch by its
-# cell count; None once the kernel has changed since the counters were taken.
-DRAM_BYTES_PER_CELL = {"z4c_derivs": None,
-                       "z4c_stage": (514.633984e6 + 278.21952e6) / 262144}
+# DRAM bytes (read + write) per interior cell of each kernel from a
+# cold-cache ncu capture of a 262,144-cell launch (ncu flushes the caches
+# before the launch; profiles/z4c_kernels_bl3level64_ncu.md), scaled to a
+# launch by its cell count; None once the kernel has changed since the
+# counters were taken.
+DRAM_BYTES_PER_CELL = {"z4c_derivs": (31.990528e6 + 5.853952e6 + 151.046656e6 + 247.058432e6) / 262144,
+                       "z4c_stage": (519.320064e6 + 258.5664e6) / 262144}
 # FP64 instructions (DFMA + DMUL + DADD, thread-level / cell) per interior
 # cell of each pass, counted by ncu on the 3-level 64^3 case
 # (profiles/z4c_kernels_bl3level64_ncu.md, profiles/z4c_derivs_fd8_bl3level64_ncu.md).
-# The derivative pass is stencil additions and unit-multiplier FMAs (issued
-# at the DADD rate); the stage kernel is mostly general FMAs.
-FP64_INSTR_PER_CELL = {4: {"z4c_derivs": 103.0 + 807.0, "z4c_stage": 1132.0},
-                       8: {"z4c_derivs": 242.0 + 1324.0, "z4c_stage": 1132.0}}
+# Both passes mix general FMAs with additions and unit-multiplier or
+# zero-addend FMAs, which issue at the slower DADD rate.
+FP64_INSTR_PER_CELL = {4: {"z4c_derivs": 72.1875 + 693.0, "z4c_stage": 1076.0},
+                       8: {"z4c_derivs": 209.0 + 1210.0, "z4c_stage": 1076.0}}
 # Kernel with the largest share of a coarse step in the ncu launch list
 # (profiles/z4c_bl_7level_launch_list.md).
 DOMINANT = "z4c_stage"
