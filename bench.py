@@ -76,11 +76,15 @@ DRAM_BYTES_PER_CELL = {"z4c_derivs": (31.990528e6 + 5.853952e6 + 151.046656e6 + 
                        "z4c_stage": (519.320064e6 + 258.5664e6) / 262144}
 # FP64 instructions (DFMA + DMUL + DADD, thread-level / cell) per interior
 # cell of each pass, counted by ncu on the 3-level 64^3 case
-# (profiles/z4c_kernels_bl3level64_ncu.md, profiles/z4c_derivs_fd8_bl3level64_ncu.md).
-# Both passes mix general FMAs with additions and unit-multiplier or
-# zero-addend FMAs, which issue at the slower DADD rate.
-FP64_INSTR_PER_CELL = {4: {"z4c_derivs": 72.1875 + 693.0, "z4c_stage": 1076.0},
-                       8: {"z4c_derivs": 209.0 + 1210.0, "z4c_stage": 1076.0}}
+# (profiles/z4c_kernels_bl3level64_ncu.md, profiles/z4c_fp64_op_classes_bl3level64_ncu.md).
+FP64_INSTR_PER_CELL = {4: {"z4c_derivs": 72.1875 + 693.0, "z4c_stage": 1072.0},
+                       8: {"z4c_derivs": 209.0 + 1210.0, "z4c_stage": 1072.0}}
+# The same passes split by issue rate (general FMAs, DADD-rate operations:
+# additions, multiplications, unit-multiplier FMAs), counted by ncu on their
+# op-class build (sc_run_op_class_pass, which issues every such operation as
+# a DADD or DMUL; profiles/z4c_fp64_op_classes_bl3level64_ncu.md).
+FP64_OP_CLASSES = {4: {"z4c_derivs": (48.125 + 451.0, 24.0625 + 242.0), "z4c_stage": (830.559, 13.0 + 235.445)},
+                   8: {"z4c_derivs": (156.75 + 429.0, 52.25 + 781.0), "z4c_stage": (830.559, 13.0 + 235.445)}}
 # Kernel with the largest share of a coarse step in the ncu launch list
 # (profiles/z4c_bl_7level_launch_list.md).
 DOMINANT = "z4c_stage"
@@ -400,7 +404,10 @@ def study_z4c3level(sc, W, steps: int, n: int = 64, fd_order: int = 4):
     """Brill-Lindquist head-on on 3 nested levels of n^3 (n = 64: about 1.3 GB
     of device state, more than L2): the small case the ncu captures of the
     Z4c and refinement-boundary kernels run on.  One untimed coarse step,
-    then `steps` timed ones."""
+    then `steps` timed ones, then the op-class pass of level 0 (the
+    derivative pass and stage kernel with additions and multiplications as
+    DADD/DMUL, for instruction counters that split the FP64 stream by issue
+    rate; kernel names carry PlainK)."""
     import torch
     h = W.bl_3level(n)
     h.fd_order = fd_order
@@ -415,6 +422,8 @@ def study_z4c3level(sc, W, steps: int, n: int = 64, fd_order: int = 4):
     ctx.sc_synchronize()
     out = {"workload": h.name, "coarse_steps": steps, "ms_per_coarse_step": e0.elapsed_time(e1) / max(steps, 1),
            "launches_per_coarse_step": ctx.sc_launches_per_step()}
+    ctx.sc_run_op_class_pass(0)
+    out["op_class_pass"] = {"level": 0, "interior_cells": h.interior_cells(0)}
     ctx.close()
     return out
 
@@ -515,11 +524,16 @@ def run_gpu(args, rank: int, world: int):
         fpc = FLOPS_PER_CELL[name] if (h.fd_order == 4 or name == "z4c_stage") else None
         ipc = FP64_INSTR_PER_CELL[h.fd_order][name]
         issue = cells * ipc / (t * 1e-3) / 1e9
+        gen, slow = FP64_OP_CLASSES[h.fd_order][name]
+        # shortest time of this instruction mix at the measured issue rates
+        t_mix = cells * (gen / pk["dfma_g_per_s"] + slow / pk["dadd_g_per_s"]) / 1e9 * 1e3
         r = {"ms_per_launch": t, "cells_per_launch": cells, "flops_per_cell": fpc,
              "fp64_issue": {"achieved_g_instr_per_s": issue, "instr_per_cell": ipc,
+                            "general_fma_per_cell": gen, "dadd_rate_ops_per_cell": slow,
                             "frac_of_nominal_dfma_issue": issue / (nominal_tflops * 1e3 / 2),
                             "frac_of_measured_dfma_issue": issue / pk["dfma_g_per_s"],
-                            "frac_of_measured_dadd_issue": issue / pk["dadd_g_per_s"]}}
+                            "frac_of_measured_dadd_issue": issue / pk["dadd_g_per_s"],
+                            "mix_ceiling_ms": t_mix, "frac_of_mix_ceiling": t_mix / t}}
         if fpc is not None:
             ach = cells * fpc / (t * 1e-3) / 1e12
             tb = DRAM_BYTES_PER_CELL.get(name) if h.fd_order == 4 else None

@@ -273,6 +273,18 @@ sc_status sc_footprint_estimate(const sc_desc* desc, size_t* bytes);
  * level's k2 and second stage buffer, which every coarse step recomputes
  * before reading; call between sc_advance calls.  Synchronises. */
 sc_status sc_time_stage_kernels(sc_ctx* ctx, int level, int nrep, double* ms);
+/* Measurement (no counterpart in the paper; Z4c only, SC_EINVAL for the
+ * scalar wave).  Run the kernels that sc_time_stage_kernels times (the
+ * derivative pass in its row-segment + per-cell form, then the right-hand
+ * side + update pass) once on one level in their op-class build: the same
+ * arithmetic, bitwise the same results, with every addition, subtraction and
+ * multiplication issued as a DADD or DMUL instead of a unit-constant FMA.  An
+ * instruction counter over these launches (their kernel names carry PlainK)
+ * then splits the FP64 stream into general FMAs and the operations that issue
+ * at the slower DADD rate.  Writes what sc_time_stage_kernels writes, plus the
+ * derivative scratch, which every stage recomputes; call between sc_advance
+ * calls.  Synchronises. */
+sc_status sc_run_op_class_pass(sc_ctx* ctx, int level);
 
 /* Z4c constraints of one box held by the caller, computed without allocating
  * any device memory.  The paper has no counterpart: this entry point serves

@@ -118,6 +118,7 @@ def lib():
     L.sc_footprint.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
     L.sc_footprint_estimate.argtypes = [ctypes.POINTER(sc_desc), ctypes.POINTER(ctypes.c_size_t)]
     L.sc_time_stage_kernels.argtypes = [P, I, I, DP]
+    L.sc_run_op_class_pass.argtypes = [P, I]
     L.sc_autotune.argtypes = [P, ctypes.POINTER(ctypes.c_int), DP]
     L.sc_get_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int)]
@@ -471,6 +472,9 @@ class Context:
         ms = np.zeros(2)
         _check(lib().sc_time_stage_kernels(self.ctx, level, nrep, _dp(ms)))
         return float(ms[0]), float(ms[1])
+
+    def sc_run_op_class_pass(self, level: int) -> None:
+        _check(lib().sc_run_op_class_pass(self.ctx, level))
 
     # convenience
     def set_initial_data_from(self, h=None):

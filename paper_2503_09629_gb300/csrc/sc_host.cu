@@ -2425,6 +2425,21 @@ sc_status sc_time_stage_kernels(sc_ctx* c, int level, int nrep, double* ms) {
   return SC_OK;
 }
 
+sc_status sc_run_op_class_pass(sc_ctx* c, int level) {
+  if (!c) return fail(SC_EINVAL, "null context");
+  if (c->system != SC_Z4C) return fail(SC_EINVAL, "the op-class pass exists for Z4c only");
+  if (level < 0 || level >= c->nlev) return fail(SC_EINVAL, "bad level %d", level);
+  Level& L = c->lev[level];
+  const Geom& g = L.g;
+  const StageArgs a = tuning_stage_args(L, c->order);
+  CU(launch_z4c_dxy(a.Y, c->scratch, g.fs, a.sy, L.dxy, L.ndxy, c->stream, c->order, true));
+  CU(launch_z4c_derivs_split(a.Y, c->scratch, g.fs, a.sy, a.sz, L.tiles, L.ntiles, c->stream, c->order, L.tile_cols,
+                             true));
+  CU(launch_z4c_stage(a, c->scratch, c->zp, L.ptiles, L.nptiles, c->stream, c->stage_bps, true));
+  CU(cudaStreamSynchronize(c->stream));
+  return SC_OK;
+}
+
 sc_status sc_check_finite(sc_ctx* c) {
   if (!c) return fail(SC_EINVAL, "null context");
   CU(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));

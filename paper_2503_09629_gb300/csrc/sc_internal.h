@@ -164,10 +164,19 @@ struct StageArgs {
 struct FmaK {
   double one, mone, mzero;
 };
+// The op-class form of the same arithmetic (sc_run_op_class_pass): each such
+// operation issued as a DADD or DMUL that the compiler never contracts into an
+// FMA, so an instruction counter separates the general FMAs (the faster issue
+// rate) from the operations that issue at the DADD rate.  Bitwise the same
+// results as FmaK.
+struct PlainK {};
 #ifdef __CUDACC__
 __device__ __forceinline__ double fadd(double a, double b, const FmaK& K) { return fma(a, K.one, b); }
 __device__ __forceinline__ double fsub(double a, double b, const FmaK& K) { return fma(b, K.mone, a); }
 __device__ __forceinline__ double fmul(double a, double b, const FmaK& K) { return fma(a, b, K.mzero); }
+__device__ __forceinline__ double fadd(double a, double b, const PlainK&) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double fsub(double a, double b, const PlainK&) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double fmul(double a, double b, const PlainK&) { return __dmul_rn(a, b); }
 #endif
 
 enum { kStageSingle = 0, kStageRk4 = 1, kStageTwo = 2, kStageNone = 3 };
@@ -217,17 +226,20 @@ cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy,
 // Occupancy-derived persistent grid sizes of the Z4c kernels (once per device,
 // before any graph capture).
 cudaError_t z4c_init_launch_config();
-// order: finite-difference order of the derivatives, 4 or 8 (Kreiss-Oliger stays r = 4)
+// order: finite-difference order of the derivatives, 4 or 8 (Kreiss-Oliger stays r = 4).
+// op_class: the PlainK build of the kernel (same results; see PlainK).
 cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, const RowSeg* segs, int nsegs,
-                           cudaStream_t s, int order = 4);
+                           cudaStream_t s, int order = 4, bool op_class = false);
 // max_cols: the largest nx * ny of the tiles (work is dealt out per tile in
 // chunks sized by it); cudaErrorInvalidValue if below 1.
 cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz,
-                                    const Tile* tiles, int ntiles, cudaStream_t s, int order, int max_cols);
+                                    const Tile* tiles, int ntiles, cudaStream_t s, int order, int max_cols,
+                                    bool op_class = false);
 // bps: 128-thread blocks per SM of the stage kernel's build, 2 or 3 (a tuning
-// choice); cudaErrorInvalidValue otherwise.
+// choice); cudaErrorInvalidValue otherwise.  op_class: the PlainK build
+// (stage form kStageSingle only, cudaErrorInvalidValue for the others).
 cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4cParams& p,
-                             const Tile* tiles, int ntiles, cudaStream_t s, int bps = 3);
+                             const Tile* tiles, int ntiles, cudaStream_t s, int bps = 3, bool op_class = false);
 cudaError_t launch_radiative_stage(const StageArgs& a, const int32_t* cells, int ncells, int F,
                                    const Geom& g, int system, cudaStream_t s);
 cudaError_t launch_z4c_constraints(const double* Y, const double* scratch, double* out, long fs, int sy,

@@ -124,8 +124,8 @@ __device__ __forceinline__ int d2_field(int s) { return s <= 6 ? s : s + 11; }
 // Centred first derivative as the integer-weight sum: 4th order
 // 8 (v_1 - v_-1) - (v_2 - v_-2) (= 12 h u'), one addition and two FMAs;
 // 8th order 672 d1 - 168 d2 + 32 d3 - 3 d4 (= 840 h u'), dm = v_m - v_-m.
-template <int ORD>
-__device__ __forceinline__ double dfirst(const double* lo, const double* hi, const FmaK& K) {
+template <int ORD, class KT>
+__device__ __forceinline__ double dfirst(const double* lo, const double* hi, const KT& K) {
   if (ORD == 4) return fma(8.0, hi[0], fma(-8.0, lo[0], fsub(lo[1], hi[1], K)));
   return fma(672.0, hi[0],
              fma(-672.0, lo[0],
@@ -133,23 +133,23 @@ __device__ __forceinline__ double dfirst(const double* lo, const double* hi, con
                      fma(168.0, lo[1], fma(32.0, hi[2], fma(-32.0, lo[2], fmul(3.0, fsub(lo[3], hi[3], K), K)))))));
 }
 // The same first derivative from the differences dm = v_m - v_-m, m = 1..R.
-template <int ORD>
-__device__ __forceinline__ double dfirst_d(const double* d, const FmaK& K) {
+template <int ORD, class KT>
+__device__ __forceinline__ double dfirst_d(const double* d, const KT& K) {
   if (ORD == 4) return fma(8.0, d[0], -d[1]);
   return fma(672.0, d[0], fma(-168.0, d[1], fma(32.0, d[2], fmul(-3.0, d[3], K))));
 }
 // Centred second derivative from the pair sums pm = v_m + v_-m, as the
 // integer-weight sum: 4th order 16 p1 - p2 - 30 u0 (= 12 h^2 u''), 8th order
 // 8064 p1 - 1008 p2 + 128 p3 - 9 p4 - 14350 u0 (= 5040 h^2 u'').
-template <int ORD>
-__device__ __forceinline__ double dsecond(const double* p, double u0, const FmaK& K) {
+template <int ORD, class KT>
+__device__ __forceinline__ double dsecond(const double* p, double u0, const KT& K) {
   if (ORD == 4) return fma(16.0, p[0], fma(-30.0, u0, -p[1]));
   return fma(-14350.0, u0, fma(8064.0, p[0], fma(-1008.0, p[1], fma(128.0, p[2], fmul(-9.0, p[3], K)))));
 }
 
-template <int ORD>
+template <int ORD, class KT = FmaK>
 __global__ void __launch_bounds__(128) z4c_dxy_kernel(const double* __restrict__ Y, double* __restrict__ S, long fs,
-                                                     int sy_, const RowSeg* __restrict__ segs, int nsegs, FmaK K) {
+                                                     int sy_, const RowSeg* __restrict__ segs, int nsegs, KT K) {
   constexpr int R = ORD / 2;
   const long sy = sy_;
   for (int sgi = blockIdx.x; sgi < nsegs; sgi += gridDim.x) {
@@ -180,11 +180,11 @@ __global__ void __launch_bounds__(128) z4c_dxy_kernel(const double* __restrict__
   }
 }
 
-template <int ORD>
+template <int ORD, class KT = FmaK>
 __global__ void __launch_bounds__(kThreads, 2) z4c_derivs_split_kernel(const double* __restrict__ Y,
                                                                       double* __restrict__ S, long fs, int sy_,
                                                                       int sz_, const Tile* __restrict__ tiles, int ntiles,
-                                                                      int max_cols, FmaK K) {
+                                                                      int max_cols, KT K) {
   // One thread per (x, y, field) column of a tile, walking z with sliding
   // windows: u at z-W..z+W (W = max(R, 3), R = ORD/2 the derivative radius,
   // 3 the Kreiss-Oliger radius) and, for the Hessian fields, the stored
@@ -380,10 +380,10 @@ struct Z4cPoint {
 // enter through constants that carry s1 (the Christoffel 1/2, the 1/3 of the
 // Gamt equation) or are scaled once where several terms use them (W, alpha,
 // beta), second derivatives through the scale of their pure or mixed kind.
-template <bool kDiag>
+template <bool kDiag, class KT>
 __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, const double* __restrict__ S, long fs,
                                               long o, const Z4cParams& P, double eta, const DerivScales& ds,
-                                              double* rhs, double* diag, const FmaK& K) {
+                                              double* rhs, double* diag, const KT& K) {
 #define FLD(f) Y[(long)(f) * fs + o]
 #define D1(f, d) S[(long)(Q_D1 + 3 * (f) + (d)) * fs + o]
 #define D2(sl, p) S[(long)(Q_D2 + 6 * (sl) + (p)) * fs + o]
@@ -482,12 +482,12 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
   double R[6], DDal[6];
   {
     double DDW[6];
-    double trDDW = 0.0;
+    double trDDW;
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
       const double s2 = (s == 0 || s == 3 || s == 5) ? ds.s2p : ds.s2m;
       DDW[s] = fma(D2(0, s), s2, -fma(Gu[0][s], dW[0], fma(Gu[1][s], dW[1], fmul(Gu[2][s], dW[2], K))));
-      trDDW = fma(gw[s], DDW[s], trDDW);
+      trDDW = s == 0 ? fmul(gw[0], DDW[0], K) : fma(gw[s], DDW[s], trDDW);
     }
     // hs1 d_j Gamt^k, and the scales of the second-derivative terms carried by gt^lm
     double dGh[3][3];
@@ -546,9 +546,9 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
         DDal[s] = fma(D2(7, s), s2, -fma(-wt, iW, gd));
       }
   }
-  double trR = 0.0, trDDal = 0.0;
+  double trR = fmul(gw[0], R[0], K), trDDal = fmul(gw[0], DDal[0], K);
 #pragma unroll
-  for (int s = 0; s < 6; ++s) {
+  for (int s = 1; s < 6; ++s) {
     trR = fma(gw[s], R[s], trR);
     trDDal = fma(gw[s], DDal[s], trDDal);
   }
@@ -589,31 +589,34 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
   // W
   rhs[ZW] = ADV_ON(ZW, fmul(fmul(third, W, K), fma(al, Kt, -divb), K));
   // gt_ij and At_ij
-  double X[6], trX = 0.0;
+  double X[6], trX;
 #pragma unroll
   for (int s = 0; s < 6; ++s) {
     X[s] = fma(al, R[s], -DDal[s]);
-    trX = fma(gw[s], X[s], trX);
+    trX = s == 0 ? fmul(gw[0], X[0], K) : fma(gw[s], X[s], trX);
   }
   const double alKt = fmul(al, Kt, K);
   const double m2al = fmul(-2.0, al, K);
   const double m23divb = fmul(-twothird, divb, K);
   const double m13trX = fmul(-third, trX, K);
+  const double cA = fadd(alKt, m23divb, K);  // (alpha Kt - 2/3 div beta), the coefficient of At_ij
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = i; j < 3; ++j) {
       const int s = sidx(i, j);
-      double lg = 0.0, la = 0.0, aa = 0.0;
+      // gt_k(i d_j) beta^k and At_k(i d_j) beta^k accumulated onto the terms
+      // in gt_ij and At_ij; At_ik At^k_j
+      double lg = fmul(m23divb, g[s], K), la = fmul(cA, A[s], K), aa = fmul(Am[0][i], A[sidx(0, j)], K);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         lg = fma(g[sidx(k, i)], dbe[k][j], fma(g[sidx(k, j)], dbe[k][i], lg));
         la = fma(A[sidx(k, i)], dbe[k][j], fma(A[sidx(k, j)], dbe[k][i], la));
-        aa = fma(Am[k][i], A[sidx(k, j)], aa);
+        if (k > 0) aa = fma(Am[k][i], A[sidx(k, j)], aa);
       }
-      rhs[ZG + s] = ADV_ON(ZG + s, fma(m2al, A[s], fma(m23divb, g[s], lg)));
+      rhs[ZG + s] = ADV_ON(ZG + s, fma(m2al, A[s], lg));
       const double tf = fma(m13trX, g[s], X[s]);
-      rhs[ZA + s] = ADV_ON(ZA + s, fma(W2, tf, fma(alKt, A[s], fma(m2al, aa, fma(m23divb, A[s], la)))));
+      rhs[ZA + s] = ADV_ON(ZA + s, fma(W2, tf, fma(m2al, aa, la)));
     }
   // Khat
   rhs[ZK] = fma(al, fma(fmul(third, Kt, K), Kt, AA),
@@ -642,14 +645,19 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
       // Gamt^i_jk At^jk
       double br = fma(2.0, fma(Gu[i][1], Auu[1], fma(Gu[i][2], Auu[2], fmul(Gu[i][4], Auu[4], K))),
                       fma(Gu[i][0], Auu[0], fma(Gu[i][3], Auu[3], fmul(Gu[i][5], Auu[5], K))));
-      double sA = 0.0, sW = 0.0, sD = 0.0, sL = 0.0, r = 0.0;
+      const double au0 = Auu[sidx(i, 0)], gu0 = gu[sidx(i, 0)];
+      double sA = fmul(au0, dal[0], K);     // At^ij d_j alpha
+      double sW = fmul(au0, dW[0], K);      // At^ij d_j W
+      double sD = fmul(gu0, dd[0], K);      // gt^ij d_j (2 Khat + Theta)
+      double sL = fmul(gu0, ddivb[0], K);   // gt^ij d_j d_k beta^k
+      double r = fmul(-Gd[0], dbe[i][0], K);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
+      for (int j = 1; j < 3; ++j) {
         const double auij = Auu[sidx(i, j)], guij = gu[sidx(i, j)];
-        sA = fma(auij, dal[j], sA);     // At^ij d_j alpha
-        sW = fma(auij, dW[j], sW);      // At^ij d_j W
-        sD = fma(guij, dd[j], sD);      // gt^ij d_j (2 Khat + Theta)
-        sL = fma(guij, ddivb[j], sL);   // gt^ij d_j d_k beta^k
+        sA = fma(auij, dal[j], sA);
+        sW = fma(auij, dW[j], sW);
+        sD = fma(guij, dd[j], sD);
+        sL = fma(guij, ddivb[j], sL);
         r = fma(-Gd[j], dbe[i][j], r);
       }
       r = fma(-2.0, sA, r);
@@ -692,9 +700,9 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
 // afford, while 3 warps per scheduler instead of 2 hide the FP64 dependency
 // latency better -- measured 5% faster on the 524,288-cell benchmark level)
 // or 2 (252 registers, no spills).
-template <int FORM, int BPS>
+template <int FORM, int BPS, class KT = FmaK>
 __global__ void __launch_bounds__(128, BPS) z4c_stage_kernel(StageArgs a, const double* __restrict__ S, Z4cParams P,
-                                                            const Tile* __restrict__ tiles, int ntiles, FmaK K) {
+                                                            const Tile* __restrict__ tiles, int ntiles, KT K) {
   const double ko = P.ko_sigma / (64.0 * a.h);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile T = tiles[t];
@@ -864,25 +872,41 @@ cudaError_t launch_z4c_derivs(const double* Y, double* scratch, long fs, int sy,
 }
 
 cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, const RowSeg* segs, int nsegs,
-                           cudaStream_t s, int order) {
+                           cudaStream_t s, int order, bool op_class) {
   if (nsegs == 0) return cudaSuccess;
   const int grid = nsegs < caps().dxy ? nsegs : caps().dxy;
-  if (order == 8) z4c_dxy_kernel<8><<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, FmaK{1.0, -1.0, -0.0});
-  else z4c_dxy_kernel<4><<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, FmaK{1.0, -1.0, -0.0});
+  const FmaK K{1.0, -1.0, -0.0};
+  if (op_class) {
+    if (order == 8) z4c_dxy_kernel<8, PlainK><<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, PlainK{});
+    else z4c_dxy_kernel<4, PlainK><<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, PlainK{});
+  } else if (order == 8) {
+    z4c_dxy_kernel<8><<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, K);
+  } else {
+    z4c_dxy_kernel<4><<<grid, 128, 0, s>>>(Y, scratch, fs, sy, segs, nsegs, K);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz,
-                                    const Tile* tiles, int ntiles, cudaStream_t s, int order, int max_cols) {
+                                    const Tile* tiles, int ntiles, cudaStream_t s, int order, int max_cols,
+                                    bool op_class) {
   if (ntiles == 0) return cudaSuccess;
   if (max_cols < 1) return cudaErrorInvalidValue;
   const long units = (long)ntiles * ((max_cols * kNZ4c + kThreads - 1) / kThreads);
   const int grid = units < caps().derivs ? (int)units : caps().derivs;
   const FmaK K{1.0, -1.0, -0.0};
-  if (order == 8)
+  if (op_class) {
+    if (order == 8)
+      z4c_derivs_split_kernel<8, PlainK><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, tiles, ntiles, max_cols,
+                                                                   PlainK{});
+    else
+      z4c_derivs_split_kernel<4, PlainK><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, tiles, ntiles, max_cols,
+                                                                   PlainK{});
+  } else if (order == 8) {
     z4c_derivs_split_kernel<8><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, tiles, ntiles, max_cols, K);
-  else
+  } else {
     z4c_derivs_split_kernel<4><<<grid, kThreads, 0, s>>>(Y, scratch, fs, sy, sz, tiles, ntiles, max_cols, K);
+  }
   return cudaGetLastError();
 }
 
@@ -890,8 +914,10 @@ namespace {
 
 template <int BPS>
 void launch_stage_bps(const StageArgs& a, const double* scratch, const Z4cParams& p, const Tile* tiles, int ntiles,
-                      int grid, cudaStream_t s, const FmaK& K) {
-  if (a.form == kStageRk4) z4c_stage_kernel<kStageRk4, BPS><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+                      int grid, cudaStream_t s, const FmaK& K, bool op_class) {
+  if (op_class)
+    z4c_stage_kernel<kStageSingle, BPS, PlainK><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, PlainK{});
+  else if (a.form == kStageRk4) z4c_stage_kernel<kStageRk4, BPS><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
   else if (a.form == kStageTwo) z4c_stage_kernel<kStageTwo, BPS><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
   else if (a.form == kStageNone)
     z4c_stage_kernel<kStageNone, BPS><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
@@ -901,14 +927,15 @@ void launch_stage_bps(const StageArgs& a, const double* scratch, const Z4cParams
 }  // namespace
 
 cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4cParams& p, const Tile* tiles,
-                             int ntiles, cudaStream_t s, int bps) {
+                             int ntiles, cudaStream_t s, int bps, bool op_class) {
   if (ntiles == 0) return cudaSuccess;
   if (bps != 2 && bps != 3) return cudaErrorInvalidValue;
+  if (op_class && a.form != kStageSingle) return cudaErrorInvalidValue;
   const int cap = caps().stage[bps];
   const int grid = ntiles < cap ? ntiles : cap;
   const FmaK K{1.0, -1.0, -0.0};
-  if (bps == 2) launch_stage_bps<2>(a, scratch, p, tiles, ntiles, grid, s, K);
-  else launch_stage_bps<3>(a, scratch, p, tiles, ntiles, grid, s, K);
+  if (bps == 2) launch_stage_bps<2>(a, scratch, p, tiles, ntiles, grid, s, K, op_class);
+  else launch_stage_bps<3>(a, scratch, p, tiles, ntiles, grid, s, K, op_class);
   return cudaGetLastError();
 }
 

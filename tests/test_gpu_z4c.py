@@ -221,3 +221,25 @@ def test_autotune_z4c_matches_oracle(sc, orc):
     o.advance(3)
     assert max_rel_diff(fetch(ctx, h), fetch(o, h)) <= TOL
     ctx.close()
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_op_class_pass_bitwise_equal(sc, order):
+    """sc_run_op_class_pass (additions and multiplications issued as DADD/DMUL
+    for instruction counting) computes bitwise what the production kernels
+    compute: the same k2 and stage output on every level."""
+    h = W.bl_3level(32 if order == 8 else 20)
+    if order == 8:
+        h.fd_order = 8
+    ctx = sc.Context(h)
+    ctx.sc_set_initial_data(h.id_kind, h.id_params)
+    ctx.sc_advance(1)
+    for lvl in range(h.nlevels):
+        outs = []
+        for run in (lambda: ctx.sc_time_stage_kernels(lvl, 1), lambda: ctx.sc_run_op_class_pass(lvl)):
+            run()
+            outs.append([np.stack([ctx.sc_debug_get_vector(lvl, b, v, f) for f in range(22)])
+                         for b in range(len(h.boxes[lvl])) for v in (5, 2, 3)])
+        for a, b in zip(*outs):
+            assert np.array_equal(a, b), lvl
+    ctx.close()
