@@ -300,8 +300,8 @@ __global__ void __launch_bounds__(kThreads, 2) z4c_derivs_split_kernel(const dou
           }
           S[(long)(Q_KO + f) * fs + o] = ko;
         } else {
-          // 8th order: differences and pair sums formed first (fewer live values than the
-          // 4th-order arrangement, which spilled and ran slower here)
+          // 8th order: differences and pair sums formed first (the 4th-order
+          // arrangement ran 6% slower at radius 4, with or without spills)
           const double u0 = w[WR];
           double p[3][4], d[4];
           // x and y from memory, z from the window
