@@ -158,9 +158,10 @@ struct StageArgs {
 // kernel arguments): fma(a, 1, b) = a + b, fma(b, -1, a) = a - b and
 // fma(x, y, -0) = x * y exactly, so the results are bitwise those of the
 // plain operations.  Measured on this GPU: the Z4c derivative and stage
-// kernels run 6% and 4% faster this way than with plain DADD/DSUB/DMUL
-// (bitwise-identical arithmetic), although an isolated chain of fma(x, 1, a) issues no
-// faster than DADD (504 G/s; a general DFMA 597 G/s).
+// kernels run about 5% faster this way than in their op-class build below,
+// the same arithmetic with DADD/DSUB/DMUL (ncu on a 262,144-cell level:
+// 339 against 358 us and 538 against 564 us), although an isolated chain of
+// fma(x, 1, a) issues no faster than DADD (504 G/s; a general DFMA 597 G/s).
 struct FmaK {
   double one, mone, mzero;
 };
