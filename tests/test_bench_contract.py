@@ -23,3 +23,22 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["dtype"] == "f64" and "workload" in d["config"]
+
+
+def test_roofline_instruction_tables_are_consistent():
+    """The op-class split (general FMAs + DADD-rate operations, counted on the
+    op-class build) accounts for the production kernels' FP64 instruction
+    counts to within 1% (the op-class build forms a few FMAs of its own), and
+    the mix ceiling it implies is never below the all-DFMA time."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for order in (4, 8):
+        for name in ("z4c_derivs", "z4c_stage"):
+            total = bench.FP64_INSTR_PER_CELL[order][name]
+            gen, slow = bench.FP64_OP_CLASSES[order][name]
+            assert gen > 0 and slow > 0
+            assert abs(gen + slow - total) <= 0.01 * total, (order, name, gen + slow, total)
+            dfma, dadd = 626.7, 527.9  # G/s, as measured in the bench run
+            assert gen / dfma + slow / dadd >= total / dfma
