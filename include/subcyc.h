@@ -342,7 +342,7 @@ sc_status sc_interpolate(sc_ctx* ctx, int npts, const double* xyz, int field, do
  * with CUDA events on its stream, time the candidate tile shapes of the
  * stencil kernel (the fused wave stage, or the Z4c derivative pass in its
  * two-kernel form), the one-kernel Z4c derivative pass (4th order) and the
- * Z4c stage kernel built for 2 and for 3 blocks per SM; keep the fastest
+ * Z4c stage kernel built for 2 and for 3 warps per scheduler; keep the fastest
  * derivative configuration and stage build, rebuild the tile lists and the
  * coarse-step graphs.  The choice is cached for the process per
  * (system, box shapes of every level); a cached context skips the timing
@@ -354,8 +354,9 @@ sc_status sc_autotune(sc_ctx* ctx, int* tile_out, double* ms_out);
  * kernels: D_x/D_y of the Hessian fields on rows, then the per-column pass
  * that differentiates them for the mixed derivatives) or 1 (one kernel per
  * cell and field with direct 16-point mixed stencils; Z4c at 4th order
- * only), stage_blocks_per_sm = 2 or 3 (the Z4c stage kernel's build: 128-
- * thread blocks per SM it is constrained to).  sc_set_tuning applies a
+ * only), stage_blocks_per_sm = 2 or 3 (the Z4c stage kernel's build: the
+ * register budget of that many 128-thread blocks per SM, i.e. 2 or 3 warps
+ * per scheduler; it runs as twice as many 64-thread blocks).  sc_set_tuning applies a
  * choice made elsewhere (rebuilds the tile lists and graphs; call between
  * sc_advance calls); SC_EINVAL for values outside those ranges. */
 sc_status sc_get_tuning(sc_ctx* ctx, int* tile, int* deriv_form, int* stage_blocks_per_sm);

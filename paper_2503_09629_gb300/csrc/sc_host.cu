@@ -255,7 +255,7 @@ struct Level {
   int ntiles = 0;
   int tile_cols = 0;                // largest nx * ny of the tiles
   std::vector<int> box_tile_begin;  // tiles of box b: [box_tile_begin[b], box_tile_begin[b + 1])
-  Tile* ptiles = nullptr;           // 32 x 4 x 1 tiles for the pointwise Z4c kernel (one cell per thread)
+  Tile* ptiles = nullptr;           // 32 x 2 x 1 tiles for the pointwise Z4c kernel (one cell per thread)
   int nptiles = 0;
   std::vector<int> box_ptile_begin;
   AmrCell* amr = nullptr;
@@ -768,14 +768,14 @@ sc_status classify_level(sc_ctx* c, int l, HostLists& hl) {
   for (const sc_box& B : L.boxes) {
     L.box_ptile_begin.push_back((int)hl.ptiles.size());
     for (int z = B.lo[2]; z <= B.hi[2]; ++z)
-      for (int y = B.lo[1]; y <= B.hi[1]; y += 4)
+      for (int y = B.lo[1]; y <= B.hi[1]; y += 2)
         for (int x = B.lo[0]; x <= B.hi[0]; x += 32) {
           Tile t;
           t.x0 = x - g.org[0];
           t.y0 = y - g.org[1];
           t.z0 = z - g.org[2];
           t.nx = std::min(32, B.hi[0] - x + 1);
-          t.ny = std::min(4, B.hi[1] - y + 1);
+          t.ny = std::min(2, B.hi[1] - y + 1);
           t.nz = 1;
           hl.ptiles.push_back(t);
         }

@@ -236,7 +236,8 @@ cudaError_t launch_z4c_dxy(const double* Y, double* scratch, long fs, int sy, co
 cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, int sy, int sz,
                                     const Tile* tiles, int ntiles, cudaStream_t s, int order, int max_cols,
                                     bool op_class = false);
-// bps: 128-thread blocks per SM of the stage kernel's build, 2 or 3 (a tuning
+// bps: warps per scheduler of the stage kernel's build (the register budget of
+// bps 128-thread blocks per SM; it runs as 2 bps 64-thread blocks), 2 or 3 (a tuning
 // choice); cudaErrorInvalidValue otherwise.  op_class: the PlainK build
 // (stage form kStageSingle only, cudaErrorInvalidValue for the others).
 cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4cParams& p,

@@ -25,6 +25,7 @@ namespace sc {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kStageThreads = 64;  // threads of a stage-kernel block (one per cell of a 64-cell tile)
 
 // scratch slots
 constexpr int Q_D1 = 0;    // 3 * f + d: first derivative of field f along d
@@ -694,14 +695,17 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
 
 // FORM: the stage update of StageArgs (kStageSingle, kStageRk4, kStageTwo,
 // kStageNone), fixed at compile time so the update adds no registers to the
-// RHS.  BPS: 128-thread blocks per SM the build is constrained to, a choice
-// of sc_autotune: 3 (at most 168 registers; the RHS then spills about 700
-// bytes per thread, written back to DRAM, which the FP64-bound kernel can
-// afford, while 3 warps per scheduler instead of 2 hide the FP64 dependency
-// latency better -- measured 5% faster on the 524,288-cell benchmark level)
-// or 2 (252 registers, no spills).
+// RHS.  BPS: warps per scheduler the build is constrained to (the register
+// budget of BPS 128-thread blocks per SM), a choice of sc_autotune: 3 (at
+// most 168 registers; the RHS then spills about 1 KB per thread, written back
+// to DRAM, which the FP64-bound kernel can afford, while 3 warps per
+// scheduler instead of 2 hide the FP64 dependency latency better) or 2 (255
+// registers, a few spills).  Blocks are kStageThreads = 64 threads over tiles
+// of 64 cells, 2 BPS blocks per SM: a 64^3 level's 4096 tiles then leave at
+// most 27 on an SM against an average of 26.95, where 128-cell tiles left 14
+// against 13.47.
 template <int FORM, int BPS, class KT = FmaK>
-__global__ void __launch_bounds__(128, BPS) z4c_stage_kernel(StageArgs a, const double* __restrict__ S, Z4cParams P,
+__global__ void __launch_bounds__(kStageThreads, 2 * BPS) z4c_stage_kernel(StageArgs a, const double* __restrict__ S, Z4cParams P,
                                                             const Tile* __restrict__ tiles, int ntiles, KT K) {
   const double ko = P.ko_sigma / (64.0 * a.h);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -826,7 +830,7 @@ __global__ void __launch_bounds__(128) z4c_constraints_kernel(const double* __re
 // evenly over the whole GPU instead of leaving a partial last wave.
 struct GridCaps {
   int ready = 0;
-  int stage[4] = {304, 304, 304, 456};  // by blocks per SM of the build (2 or 3)
+  int stage[4] = {608, 608, 608, 912};  // by warps per scheduler of the build (2 or 3)
   int derivs = 1216, dxy = 2432;
 };
 GridCaps g_caps[64];
@@ -846,11 +850,11 @@ cudaError_t z4c_init_launch_config() {
   GridCaps& c = g_caps[dev & 63];
   if (c.ready) return cudaSuccess;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel<kStageSingle, 2>, 128, 0)) !=
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel<kStageSingle, 2>, kStageThreads, 0)) !=
       cudaSuccess)
     return e;
   c.stage[2] = nsm * (occ > 0 ? occ : 1);
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel<kStageSingle, 3>, 128, 0)) !=
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel<kStageSingle, 3>, kStageThreads, 0)) !=
       cudaSuccess)
     return e;
   c.stage[3] = nsm * (occ > 0 ? occ : 1);
@@ -916,12 +920,12 @@ template <int BPS>
 void launch_stage_bps(const StageArgs& a, const double* scratch, const Z4cParams& p, const Tile* tiles, int ntiles,
                       int grid, cudaStream_t s, const FmaK& K, bool op_class) {
   if (op_class)
-    z4c_stage_kernel<kStageSingle, BPS, PlainK><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, PlainK{});
-  else if (a.form == kStageRk4) z4c_stage_kernel<kStageRk4, BPS><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
-  else if (a.form == kStageTwo) z4c_stage_kernel<kStageTwo, BPS><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+    z4c_stage_kernel<kStageSingle, BPS, PlainK><<<grid, kStageThreads, 0, s>>>(a, scratch, p, tiles, ntiles, PlainK{});
+  else if (a.form == kStageRk4) z4c_stage_kernel<kStageRk4, BPS><<<grid, kStageThreads, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+  else if (a.form == kStageTwo) z4c_stage_kernel<kStageTwo, BPS><<<grid, kStageThreads, 0, s>>>(a, scratch, p, tiles, ntiles, K);
   else if (a.form == kStageNone)
-    z4c_stage_kernel<kStageNone, BPS><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
-  else z4c_stage_kernel<kStageSingle, BPS><<<grid, 128, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+    z4c_stage_kernel<kStageNone, BPS><<<grid, kStageThreads, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+  else z4c_stage_kernel<kStageSingle, BPS><<<grid, kStageThreads, 0, s>>>(a, scratch, p, tiles, ntiles, K);
 }
 
 }  // namespace
