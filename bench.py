@@ -72,8 +72,8 @@ FLOPS_PER_CELL = {"z4c_derivs": 1180.0, "z4c_stage": 1971.0}
 # before the launch; profiles/z4c_kernels_bl3level64_ncu.md), scaled to a
 # launch by its cell count; None once the kernel has changed since the
 # counters were taken.
-DRAM_BYTES_PER_CELL = {"z4c_derivs": (31.990528e6 + 5.853952e6 + 151.046656e6 + 247.058432e6) / 262144,
-                       "z4c_stage": (519.320064e6 + 258.5664e6) / 262144}
+DRAM_BYTES_PER_CELL = {"z4c_derivs": (32.003584e6 + 5.960192e6 + 150.886144e6 + 247.183104e6) / 262144,
+                       "z4c_stage": (525.380608e6 + 289.159168e6) / 262144}
 # FP64 instructions (DFMA + DMUL + DADD, thread-level / cell) per interior
 # cell of each pass, counted by ncu on the 3-level 64^3 case
 # (profiles/z4c_kernels_bl3level64_ncu.md, profiles/z4c_fp64_op_classes_bl3level64_ncu.md).
