@@ -368,19 +368,18 @@ __device__ __forceinline__ int sidx(int i, int j) {
   return (i == j) ? (i == 0 ? 0 : (i == 1 ? 3 : 5)) : (i + j == 1 ? 1 : (i + j == 2 ? 2 : 4));
 }
 
-struct Z4cPoint {
-  double rhs[kNZ4c];
-};
-
 // Right-hand side of the Z4c system at one cell (Sec. III.A; vacuum, so the
 // matter terms vanish).  u: fields; S + o: derivatives in scratch.  Sums,
 // differences and products that do not fuse with a neighbour are written as
-// FMAs with the run-time unit constants of K (fadd, fsub, fmul; measured
-// faster than plain DADD/DMUL in this kernel, see FmaK).
-// The stored derivatives are stencil sums (DerivScales): first derivatives
-// enter through constants that carry s1 (the Christoffel 1/2, the 1/3 of the
-// Gamt equation) or are scaled once where several terms use them (W, alpha,
-// beta), second derivatives through the scale of their pure or mixed kind.
+// fadd, fsub, fmul: FMAs with the run-time unit constants of an FmaK
+// (measured faster than plain DADD/DMUL in this kernel), or the DADD/DMUL of
+// a PlainK in the op-class build.
+// The stored derivatives are stencil sums (DerivScales).  Their scales ride
+// on factors formed once per cell where several terms share them (the 1/2 of
+// the Christoffel symbols on the metric that raises their index, alpha, W,
+// beta, Gamt and second-derivative coefficients) or on kernel-parameter
+// constants of the FMAs that use them, so that each term stays one FMA and
+// every equation accumulates in one chain.
 template <bool kDiag, class KT>
 __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, const double* __restrict__ S, long fs,
                                               long o, const Z4cParams& P, double eta, const DerivScales& ds,
