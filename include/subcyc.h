@@ -356,7 +356,8 @@ sc_status sc_autotune(sc_ctx* ctx, int* tile_out, double* ms_out);
  * cell and field with direct 16-point mixed stencils; Z4c at 4th order
  * only), stage_blocks_per_sm = 2 or 3 (the Z4c stage kernel's build: the
  * register budget of that many 128-thread blocks per SM, i.e. 2 or 3 warps
- * per scheduler; it runs as twice as many 64-thread blocks).  sc_set_tuning applies a
+ * per scheduler; on levels of 2^17 cells or more it runs as twice as many
+ * 64-thread blocks over 64-cell tiles).  sc_set_tuning applies a
  * choice made elsewhere (rebuilds the tile lists and graphs; call between
  * sc_advance calls); SC_EINVAL for values outside those ranges. */
 sc_status sc_get_tuning(sc_ctx* ctx, int* tile, int* deriv_form, int* stage_blocks_per_sm);

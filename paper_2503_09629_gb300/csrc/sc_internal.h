@@ -237,11 +237,13 @@ cudaError_t launch_z4c_derivs_split(const double* Y, double* scratch, long fs, i
                                     const Tile* tiles, int ntiles, cudaStream_t s, int order, int max_cols,
                                     bool op_class = false);
 // bps: warps per scheduler of the stage kernel's build (the register budget of
-// bps 128-thread blocks per SM; it runs as 2 bps 64-thread blocks), 2 or 3 (a tuning
-// choice); cudaErrorInvalidValue otherwise.  op_class: the PlainK build
+// bps 128-thread blocks per SM), 2 or 3 (a tuning choice); threads: block
+// size, 128 (tiles of at most 128 cells) or 64 (tiles of at most 64 cells, 2 bps
+// blocks per SM); cudaErrorInvalidValue otherwise.  op_class: the PlainK build
 // (stage form kStageSingle only, cudaErrorInvalidValue for the others).
 cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4cParams& p,
-                             const Tile* tiles, int ntiles, cudaStream_t s, int bps = 3, bool op_class = false);
+                             const Tile* tiles, int ntiles, cudaStream_t s, int bps, int threads,
+                             bool op_class = false);
 cudaError_t launch_radiative_stage(const StageArgs& a, const int32_t* cells, int ncells, int F,
                                    const Geom& g, int system, cudaStream_t s);
 cudaError_t launch_z4c_constraints(const double* Y, const double* scratch, double* out, long fs, int sy,

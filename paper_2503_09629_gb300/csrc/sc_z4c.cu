@@ -25,7 +25,6 @@ namespace sc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kStageThreads = 64;  // threads of a stage-kernel block (one per cell of a 64-cell tile)
 
 // scratch slots
 constexpr int Q_D1 = 0;    // 3 * f + d: first derivative of field f along d
@@ -699,12 +698,11 @@ __device__ __forceinline__ void z4c_rhs_point(const double* __restrict__ Y, cons
 // most 168 registers; the RHS then spills about 1 KB per thread, written back
 // to DRAM, which the FP64-bound kernel can afford, while 3 warps per
 // scheduler instead of 2 hide the FP64 dependency latency better) or 2 (255
-// registers, a few spills).  Blocks are kStageThreads = 64 threads over tiles
-// of 64 cells, 2 BPS blocks per SM: a 64^3 level's 4096 tiles then leave at
-// most 27 on an SM against an average of 26.95, where 128-cell tiles left 14
-// against 13.47.
+// registers, a few spills).  Blocks of 128 threads over 128-cell tiles, or
+// of 64 threads over 64-cell tiles (twice as many per SM) on large levels,
+// where the finer split balances the SMs (the host picks per level).
 template <int FORM, int BPS, class KT = FmaK>
-__global__ void __launch_bounds__(kStageThreads, 2 * BPS) z4c_stage_kernel(StageArgs a, const double* __restrict__ S, Z4cParams P,
+__global__ void __launch_bounds__(128, BPS) z4c_stage_kernel(StageArgs a, const double* __restrict__ S, Z4cParams P,
                                                             const Tile* __restrict__ tiles, int ntiles, KT K) {
   const double ko = P.ko_sigma / (64.0 * a.h);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -829,7 +827,7 @@ __global__ void __launch_bounds__(128) z4c_constraints_kernel(const double* __re
 // evenly over the whole GPU instead of leaving a partial last wave.
 struct GridCaps {
   int ready = 0;
-  int stage[4] = {608, 608, 608, 912};  // by warps per scheduler of the build (2 or 3)
+  int stage[4] = {304, 304, 304, 456};  // 128-thread blocks, by warps per scheduler of the build (2 or 3)
   int derivs = 1216, dxy = 2432;
 };
 GridCaps g_caps[64];
@@ -849,11 +847,11 @@ cudaError_t z4c_init_launch_config() {
   GridCaps& c = g_caps[dev & 63];
   if (c.ready) return cudaSuccess;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel<kStageSingle, 2>, kStageThreads, 0)) !=
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel<kStageSingle, 2>, 128, 0)) !=
       cudaSuccess)
     return e;
   c.stage[2] = nsm * (occ > 0 ? occ : 1);
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel<kStageSingle, 3>, kStageThreads, 0)) !=
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, z4c_stage_kernel<kStageSingle, 3>, 128, 0)) !=
       cudaSuccess)
     return e;
   c.stage[3] = nsm * (occ > 0 ? occ : 1);
@@ -917,28 +915,31 @@ namespace {
 
 template <int BPS>
 void launch_stage_bps(const StageArgs& a, const double* scratch, const Z4cParams& p, const Tile* tiles, int ntiles,
-                      int grid, cudaStream_t s, const FmaK& K, bool op_class) {
+                      int grid, int threads, cudaStream_t s, const FmaK& K, bool op_class) {
   if (op_class)
-    z4c_stage_kernel<kStageSingle, BPS, PlainK><<<grid, kStageThreads, 0, s>>>(a, scratch, p, tiles, ntiles, PlainK{});
-  else if (a.form == kStageRk4) z4c_stage_kernel<kStageRk4, BPS><<<grid, kStageThreads, 0, s>>>(a, scratch, p, tiles, ntiles, K);
-  else if (a.form == kStageTwo) z4c_stage_kernel<kStageTwo, BPS><<<grid, kStageThreads, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+    z4c_stage_kernel<kStageSingle, BPS, PlainK><<<grid, threads, 0, s>>>(a, scratch, p, tiles, ntiles, PlainK{});
+  else if (a.form == kStageRk4) z4c_stage_kernel<kStageRk4, BPS><<<grid, threads, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+  else if (a.form == kStageTwo) z4c_stage_kernel<kStageTwo, BPS><<<grid, threads, 0, s>>>(a, scratch, p, tiles, ntiles, K);
   else if (a.form == kStageNone)
-    z4c_stage_kernel<kStageNone, BPS><<<grid, kStageThreads, 0, s>>>(a, scratch, p, tiles, ntiles, K);
-  else z4c_stage_kernel<kStageSingle, BPS><<<grid, kStageThreads, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+    z4c_stage_kernel<kStageNone, BPS><<<grid, threads, 0, s>>>(a, scratch, p, tiles, ntiles, K);
+  else z4c_stage_kernel<kStageSingle, BPS><<<grid, threads, 0, s>>>(a, scratch, p, tiles, ntiles, K);
 }
 
 }  // namespace
 
 cudaError_t launch_z4c_stage(const StageArgs& a, const double* scratch, const Z4cParams& p, const Tile* tiles,
-                             int ntiles, cudaStream_t s, int bps, bool op_class) {
+                             int ntiles, cudaStream_t s, int bps, int threads, bool op_class) {
   if (ntiles == 0) return cudaSuccess;
   if (bps != 2 && bps != 3) return cudaErrorInvalidValue;
+  if (threads != 64 && threads != 128) return cudaErrorInvalidValue;
   if (op_class && a.form != kStageSingle) return cudaErrorInvalidValue;
-  const int cap = caps().stage[bps];
+  // persistent grid: the resident blocks (twice as many at 64 threads, whose
+  // registers per block are half)
+  const int cap = caps().stage[bps] * (128 / threads);
   const int grid = ntiles < cap ? ntiles : cap;
   const FmaK K{1.0, -1.0, -0.0};
-  if (bps == 2) launch_stage_bps<2>(a, scratch, p, tiles, ntiles, grid, s, K, op_class);
-  else launch_stage_bps<3>(a, scratch, p, tiles, ntiles, grid, s, K, op_class);
+  if (bps == 2) launch_stage_bps<2>(a, scratch, p, tiles, ntiles, grid, threads, s, K, op_class);
+  else launch_stage_bps<3>(a, scratch, p, tiles, ntiles, grid, threads, s, K, op_class);
   return cudaGetLastError();
 }
 
